@@ -1,0 +1,32 @@
+"""Plain FP64 CPU oracle of the HEVI 1D-IMEX step (Abdi, Giraldo et al., arXiv:1702.04316).
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct reference that
+the CUDA library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  The
+product path (``paper_1702_04316_gb300``) never imports it and shares no code with it.
+
+Every function follows one passage of the paper, cited by section, equation label,
+algorithm or table:
+
+* ``lgl``        -- LGL nodes/weights and the nodal derivative matrix sD
+                    (Sec. "Volume kernels", Algorithms 1-2).
+* ``mesh``       -- box mesh, element-to-global map, direct stiffness summation
+                    (Sec. "Direct stiffness summation"; column numbering of
+                    Sec. "1D-IMEX kernels").
+* ``reference``  -- constants, equation of state and hydrostatic reference state
+                    (Sec. "Equation Set2NC"; sound speed of Sec. "Acoustic wave problem").
+* ``rhs``        -- explicit right-hand side R(q) of the Set2NC perturbation equations,
+                    element by element, then DSS (Sec. "Equation Set2NC",
+                    Sec. "Spatial discretization", Algorithm 2).
+* ``column``     -- the vertical operator L_V, the Schur-complement column operator,
+                    its Jacobian by probing (Algorithm 7), banded LU without pivoting
+                    (Algorithm 9), the solve and the extraction (Eqs. imex2nc, 2ncp,
+                    utteqn, helm2nc; Algorithms 4-5).
+* ``ark2``       -- the ARK2 double Butcher tableau (Table 1) and the SDIRK
+                    predictor-corrector stage form (Sec. "Linear multi-stage methods").
+* ``rk35``       -- the explicit five-stage third-order SSP comparator
+                    (Sec. "Performance of IMEX on manycore processors").
+
+Parity pins for every function live in ``tests/test_oracle_*.py``.  One function has no
+pin beyond its defining formula: see the ``PARITY UNPINNED`` note in ``rk35``.
+"""

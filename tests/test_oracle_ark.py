@@ -1,0 +1,165 @@
+"""Pins of the ARK2 tableau and stage algorithm, the RK35 comparator, and the HEVI step."""
+import math
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+from golden_io import read, values
+from oracle import ark2, rk35
+from oracle.column import Column
+from oracle.mesh import BoxMesh
+from oracle.reference import GAMMA, R_GAS
+import synthetic
+
+
+def _golden(key):
+    for row in read("paper_constants.txt"):
+        if row[0] == key:
+            return values(row[1:])
+    raise KeyError(key)
+
+
+def test_ark2_tableau_reading():
+    a, at, b, c = ark2.tableau()
+    np.testing.assert_allclose(c, _golden("ark2_c"), atol=1e-15)
+    assert abs(a[2, 1] - _golden("ark2_a32")[0]) < 1e-15
+    np.testing.assert_allclose(at.sum(1), c, atol=1e-15)       # c~ = c
+    assert abs(b.sum() - 1) < 1e-15                               # order 1
+    assert abs(b @ c - 0.5) < 1e-15                               # order 2
+    assert abs(b @ (a @ c) - 1 / 6) < 1e-15
+    assert np.all(np.diag(at)[1:] == at[1, 1]) and at[0, 0] == 0  # SDIRK, explicit first stage
+    assert abs((at[1, 0] - a[1, 0]) / at[1, 1] + 1.0) < 1e-15     # c21 = -1
+    pb = ark2.printed_b()                                         # the garbled printed row
+    assert abs(pb.sum() - 1) > 1.0                                # not even consistent
+
+
+def _split_system(n=6, seed=0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    Nmat = 0.3 * (A - A.T) + 0.05 * rng.standard_normal((n, n))   # non-stiff part
+    B = rng.standard_normal((n, n))
+    Lmat = -(B @ B.T) * 0.5 + 2.0 * (B - B.T)                      # stiff linear part
+    return Nmat, Lmat
+
+
+def _ark_direct(y, dt, Nmat, Lmat):
+    """ARK2 straight from the double tableau: Y_i = y + dt sum a_ij N Y_j + dt sum a~_ij L Y_j."""
+    a, at, b, _ = ark2.tableau()
+    n = len(y)
+    Y = []
+    for i in range(3):
+        rhs = y + dt * sum(a[i, j] * Nmat @ Y[j] + at[i, j] * Lmat @ Y[j] for j in range(i))
+        Y.append(np.linalg.solve(np.eye(n) - dt * at[i, i] * Lmat, rhs))
+    return y + dt * sum(b[i] * (Nmat + Lmat) @ Y[i] for i in range(3))
+
+
+def test_predictor_corrector_form_equals_double_tableau():
+    Nmat, Lmat = _split_system()
+    y = np.random.default_rng(1).standard_normal(6)
+    R = lambda q: (Nmat + Lmat) @ q
+    solve = lambda r, lam: np.linalg.solve(np.eye(6) - lam * Lmat, r)
+    for dt in (0.01, 0.3, 3.0):
+        np.testing.assert_allclose(ark2.ark_step(y, dt, R, solve), _ark_direct(y, dt, Nmat, Lmat),
+                                   rtol=1e-12, atol=1e-12)
+
+
+def test_ark2_second_order():
+    Nmat, Lmat = _split_system(seed=2)
+    y0 = np.random.default_rng(3).standard_normal(6)
+    R = lambda q: (Nmat + Lmat) @ q
+    solve = lambda r, lam: np.linalg.solve(np.eye(6) - lam * Lmat, r)
+    T = 1.0
+    errs = []
+    for n in (20, 40, 80):
+        y = y0
+        for _ in range(n):
+            y = ark2.ark_step(y, T / n, R, solve)
+        errs.append(np.linalg.norm(y - expm(T * (Nmat + Lmat)) @ y0))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8), rates
+
+
+def test_rk35_order_conditions_and_root():
+    A, b, c = rk35.butcher()
+    assert abs(b.sum() - 1) < 1e-15
+    assert abs(b @ c - 0.5) < 1e-15
+    assert abs(b @ (c * c) - 1 / 3) < 1e-15
+    assert abs(b @ (A @ c) - 1 / 6) < 1e-15
+    ratios = (1 - rk35.ALPHA) / rk35.BETA
+    assert abs(ratios.min() - 1 / 0.46) < 1e-12       # SSP coefficient 2.17
+    assert np.all(rk35.ALPHA >= 0) and np.all(rk35.BETA > 0)
+    # re-solve the four conditions in extended precision from a nearby start
+    import mpmath as mp
+    mp.mp.dps = 40
+
+    def conds(b2, b3, b4, a4):
+        beta = [mp.mpf("0.46"), b2, b3, b4, mp.mpf("0.46")]
+        alpha = [0, 0, 0, a4, 0]
+        prev = [mp.mpf(0)] * 5
+        out = []
+        for i in range(5):
+            cur = [(1 - alpha[i]) * p for p in prev]
+            cur[i] += beta[i]
+            out.append(cur)
+            prev = cur
+        Am = [[mp.mpf(0)] * 5] + out[:4]
+        bb = out[-1]
+        cc = [sum(r) for r in Am]
+        Ac = [sum(Am[i][j] * cc[j] for j in range(5)) for i in range(5)]
+        return [sum(bb) - 1, sum(bb[i] * cc[i] for i in range(5)) - mp.mpf(1) / 2,
+                sum(bb[i] * cc[i] ** 2 for i in range(5)) - mp.mpf(1) / 3,
+                sum(bb[i] * Ac[i] for i in range(5)) - mp.mpf(1) / 6]
+
+    root = mp.findroot(conds, (0.28, 0.22, 0.13, 0.58))
+    np.testing.assert_allclose([float(r) for r in root],
+                               [rk35.BETA[1], rk35.BETA[2], rk35.BETA[3], rk35.ALPHA[3]], rtol=1e-15)
+
+
+def test_rk35_third_order():
+    Nmat, Lmat = _split_system(seed=4)
+    Mmat = 0.2 * (Nmat + 0.1 * Lmat)
+    y0 = np.random.default_rng(5).standard_normal(6)
+    errs = []
+    for n in (10, 20, 40):
+        y = y0
+        for _ in range(n):
+            y = rk35.rk35_step(y, 1.0 / n, lambda q: Mmat @ q)
+        errs.append(np.linalg.norm(y - expm(Mmat) @ y0))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 2.8), rates
+
+
+def _box(nex=4, nez=4, L=10e3, Lz=10e3):
+    m = BoxMesh(nex, nex, nez, 4, L, L, Lz)
+    col = Column(m)
+    dzmin = (m.xi[1] - m.xi[0]) * m.dz / 2
+    return m, col, dzmin / np.sqrt(GAMMA * R_GAS * 300.0)
+
+
+def test_hevi_converges_to_rk35_at_small_courant():
+    """1D-IMEX at small C approaches explicit RK (the difference shrinks ~dt^2)."""
+    m, col, dt1 = _box(nex=3, nez=3)
+    xg, yg, zg = m.coords()
+    q0 = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Ly, m.Lz, col.rho0, col.theta0, 11)
+    T = 8 * dt1
+    E = rk35.Explicit(m, col)
+    ref = E.step(q0, T / 32, 32)
+    diffs = []
+    for n in (8, 16):
+        H = ark2.HEVI(m, col, T / n)
+        q = H.step(q0, n)
+        diffs.append(np.linalg.norm(q[3] - ref[3]) / np.linalg.norm(ref[3]))
+    assert diffs[1] < diffs[0] / 3.0 and diffs[1] < 1e-2, diffs
+
+
+@pytest.mark.parametrize("C,L", [(150, 3000e3)])
+def test_hevi_bounded_at_large_vertical_courant(C, L):
+    """Horizontally wide box (C_H = 0.5): ten steps at C_V = 150 stay bounded."""
+    m, col, dt1 = _box(L=L)
+    xg, yg, zg = m.coords()
+    q0 = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Ly, m.Lz, col.rho0, col.theta0, 12)
+    H = ark2.HEVI(m, col, C * dt1)
+    q = H.step(q0, 10)
+    assert np.isfinite(q).all()
+    assert np.abs(q[3]).max() < 1.0 and np.abs(q[4]).max() < 1.0
