@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 HEVI 1D-IMEX library.
+
+Workload (the GPU-scale configuration): 96 x 96 x 12 spectral elements of order N = 4 over a
+200 x 200 x 15 km box (385 x 385 columns of 49 levels, 7,263,025 nodes), FP64, isentropic
+reference state theta0 = 300 K plus a seeded 8-mode theta' perturbation (balanced rho').
+
+A timed "step" is one HEVI 1D-IMEX ARK2 step at vertical Courant number C = 15
+(dt = 9.32 s): three explicit right-hand sides, two fused implicit stages (predictor,
+Schur right-hand side, stored-LU column solve, extraction) and the final update.  Every
+timed step advances the same resident input state to a separate output buffer, so the
+(horizontally unstable, C_H = 9) configuration never overflows during timing; the state
+(290 MB) and the stored factors (0.99 GB) are larger than L2, so no L2 flush is needed.
+
+value = simulated seconds per wall-clock second of that step (dt / step time).  Measured
+alongside, outside the headline timed region: 1D-IMEX at C = 150 and the explicit RK35
+comparator at C = 1, and their sim-s/wall-s ratios.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 NumPy oracle on the host cores (one ARK2 step of the same
+workload restricted to a window of columns, scaled to the full mesh).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+if "reference" in sys.argv:
+    # the oracle arm runs single-threaded: fix the BLAS thread count before numpy loads
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NEX = NEY = 96
+NEZ = 12
+N = 4
+LX = LY = 200e3
+LZ = 15e3
+C_MAIN = 15.0
+SEED = 2024
+GAMMA = 1004.67 / (1004.67 - 287.17)
+C_S = (GAMMA * 287.17 * 300.0) ** 0.5          # sound speed at theta0 = 300 K
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+METRIC = "1D-IMEX sim-seconds/wall-second vs explicit C=1 on 1 GB300; % of HBM roofline"
+WORKLOAD = ("96x96x12 hex elements over 200x200x15 km, N=4 (385x385 columns x 49 levels), FP64, "
+            "HEVI 1D-IMEX ARK2 step at C=15")
+
+
+def lgl_min_fraction(n):
+    """Smallest LGL spacing on [-1, 1] / 2 (first interior node), for the Courant number."""
+    c = np.zeros(n + 1)
+    c[n] = 1.0
+    r = np.sort(np.polynomial.legendre.legroots(np.polynomial.legendre.legder(c)).real)
+    return (r[0] + 1.0) / 2.0
+
+
+def dt_for(C):
+    dz_min = lgl_min_fraction(N) * (LZ / NEZ)
+    return C * dz_min / C_S
+
+
+def dx_min():
+    return lgl_min_fraction(N) * (LX / NEX)
+
+
+def rhs_flops_per_node():
+    """Algorithmic FP64 flops of one right-hand side per global node: 18 derivative dot
+    products of length N+1 (2(N+1) flops each) and the pointwise Set2NC tendencies (46)."""
+    return 18 * 2 * (N + 1) + 46
+
+
+def stage_flops_per_node(stage):
+    """Algorithmic flops of one fused implicit stage per node (predictor, Schur RHS with a
+    length-(2N+1) vertical derivative, banded solve 2(4N+1), extraction)."""
+    pred = (3 * 4 + 2 * 2) if stage == 3 else (3 * 2 + 2 * 1)
+    schur = 4 + 2 * (N + 1) + 4
+    solve = 2 * (4 * N + 1)
+    extract = 2 * (N + 1) + 8
+    recomb = 2 * 3 if stage == 3 else 3
+    return 2 * pred + schur + solve + extract + recomb
+
+
+def source_sha(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1702_04316_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel, sha):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "%s_full_size.md" % kernel)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha:\s*([0-9a-f]+)", txt)
+    if not m or m.group(2) != sha:
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------------------------------
+def make_state(levels, xg, yg, zg, amp=0.5):
+    import synthetic
+    return synthetic.balanced_state(xg, yg, zg, LX, LY, LZ, levels["rho0"], levels["theta0"],
+                                    SEED, amp)
+
+
+def axis_coords(ne, h, xi):
+    c = np.empty(ne * N + 1)
+    for e in range(ne):
+        c[e * N:e * N + N + 1] = e * h + (1.0 + xi) * h / 2.0
+    return c
+
+
+def lgl_nodes():
+    c = np.zeros(N + 1)
+    c[N] = 1.0
+    r = np.sort(np.polynomial.legendre.legroots(np.polynomial.legendre.legder(c)).real)
+    return np.concatenate([[-1.0], r, [1.0]])
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import paper_1702_04316_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    dt15, dt150, dt1 = dt_for(C_MAIN), dt_for(150.0), dt_for(1.0)
+    g = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dt15)
+    lev = g.reference_levels()
+    xi = lgl_nodes()
+    xg = axis_coords(NEX, LX / NEX, xi)
+    yg = axis_coords(NEY, LY / NEY, xi)
+    q0h = make_state(lev, xg, yg, lev["z"])
+    q0 = torch.from_numpy(q0h).to(dev)
+    q1 = torch.empty_like(q0)
+    nbytes_state = q0.numel() * 8
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+
+    def time_steps(fn, k):
+        barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        ms = a.elapsed_time(b)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    imex = lambda: g.step_imex1d(q0, q1, 1)
+    for _ in range(args.warmup):
+        imex()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    g.profile(True)
+    ms = time_steps(imex, args.steps)
+    g.profile(False)
+    clk = clocks.stop()
+    kt = {k: g.profile_read(k) for k in (pkg.K_PRESSURE, pkg.K_RHS, pkg.K_STAGE)}
+    ms_step = ms / args.steps
+    value = dt15 / (ms_step / 1e3) * world
+    assert g.count_nonfinite(q1) == 0, "non-finite output"
+    assert g.status() == pkg.NUMA_OK
+
+    # C = 150: same kernels, different factors
+    g150 = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dt150)
+    for _ in range(args.warmup):
+        g150.step_imex1d(q0, q1, 1)
+    ms150 = time_steps(lambda: g150.step_imex1d(q0, q1, 1), args.steps) / args.steps
+    g150.close()
+    # explicit RK35 at C = 1
+    rk = lambda: g.step_explicit_rk(q0, dt1, q1, 1)
+    for _ in range(args.warmup):
+        rk()
+    ms_rk = time_steps(rk, args.steps) / args.steps
+    sps = lambda dt, m: dt / (m / 1e3)
+
+    # end to end through the host-buffer entry point: H2D of the state, the step, D2H
+    qin = torch.from_numpy(q0h).pin_memory()
+    qout = torch.empty_like(qin).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        g.run_host(0, qin, 1, 0.0, qout)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.run_host(0, qin, 1, 0.0, qout)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel (by measured share of the step)
+    nnode = g.nnode
+    shares = {k: v[0] for k, v in kt.items()}
+    names = {pkg.K_PRESSURE: "k_pressure", pkg.K_RHS: "k_rhs", pkg.K_STAGE: "k_stage"}
+    srcs = {pkg.K_PRESSURE: "rhs.cu", pkg.K_RHS: "rhs.cu", pkg.K_STAGE: "column.cu"}
+    top = max(shares, key=shares.get)
+    tot_ms, launches = kt[top]
+    per_launch_ms = tot_ms / max(launches, 1)
+    if top == pkg.K_RHS:
+        flops = rhs_flops_per_node() * nnode
+    elif top == pkg.K_STAGE:
+        flops = 0.5 * (stage_flops_per_node(2) + stage_flops_per_node(3)) * nnode
+    else:
+        flops = 40 * nnode
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    sha = source_sha(srcs[top], "numa_internal.cuh")
+    traffic = recorded_traffic(names[top], sha)
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "kernel": names[top], "per_launch_ms": round(per_launch_ms, 4),
+                "peak_note": "FP64 FMA peak: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (unit counts x max clock)"}
+    kernel_ms = {names[k]: {"total_ms": round(v[0], 3), "launches": v[1],
+                            "share": round(v[0] / max(ms, 1e-9), 4)} for k, v in kt.items()}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "sim-s/wall-s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "C_V": C_MAIN, "C_H": round(C_S * dt15 / dx_min(), 3),
+                   "dt_s": round(dt15, 5), "columns": g.ncol, "levels": g.M, "nodes": nnode,
+                   "l2": "inputs larger than L2 (state 290 MB, factors 0.99 GB); no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "imex_c15": {"sim_s_per_wall_s": round(sps(dt15, ms_step), 3), "ms_per_step": round(ms_step, 4),
+                     "dt_s": round(dt15, 5)},
+        "imex_c150": {"sim_s_per_wall_s": round(sps(dt150, ms150), 3), "ms_per_step": round(ms150, 4),
+                      "dt_s": round(dt150, 5), "C_H": round(C_S * dt150 / dx_min(), 2)},
+        "explicit_c1": {"sim_s_per_wall_s": round(sps(dt1, ms_rk), 3), "ms_per_step": round(ms_rk, 4),
+                        "dt_s": round(dt1, 5), "scheme": "RK35 (5-stage 3rd-order SSP)"},
+        "speedup_vs_explicit_c1": {"C15": round(sps(dt15, ms_step) / sps(dt1, ms_rk), 3),
+                                   "C150": round(sps(dt150, ms150) / sps(dt1, ms_rk), 3)},
+        "e2e": {"value": round(dt15 * args.steps / e2e_s * world, 3), "unit": "sim-s/wall-s",
+                "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state,
+                "api": "numa_run_host (pinned host buffers, one step per call)"},
+        "roofline": roofline,
+        "kernels": kernel_ms,
+        "gpu_launches": int(sum(v[1] for v in kt.values())),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    g.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+def oracle_sample_step(window_elems, nsteps_min, seconds):
+    """Time the oracle's ARK2 step on a window of W x W elements x all levels of the
+    workload (its own lateral walls) and scale to the full column count."""
+    from oracle import ark2
+    from oracle.column import Column
+    from oracle.mesh import BoxMesh
+    import synthetic
+    W = window_elems
+    m = BoxMesh(W, W, NEZ, N, W * LX / NEX, W * LY / NEY, LZ)
+    col = Column(m)
+    xg, yg, zg = m.coords()
+    q = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Ly, m.Lz, col.rho0, col.theta0, SEED)
+    dt = dt_for(C_MAIN)
+    H = ark2.HEVI(m, col, dt)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < nsteps_min or (time.perf_counter() - t_start) < seconds:
+        t0 = time.perf_counter()
+        H.step(q, 1)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= 200:
+            break
+    t_sample = float(np.median(times))
+    full_cols = (NEX * N + 1) * (NEY * N + 1)
+    scale = full_cols / m.ncol
+    return dt / (t_sample * scale), t_sample, m.ncol, len(times)
+
+
+def cpu_baseline(seconds):
+    """The oracle, as it stands, in a single-threaded subprocess (bounded sample)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "v, t, nc, n = bench.oracle_sample_step(8, 3, %f); "
+            "print(json.dumps([v, t, nc, n]))" % (ROOT, seconds))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=max(120, 10 * seconds))
+    if r.returncode != 0:
+        return {"value": None, "unit": "sim-s/wall-s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr.strip().splitlines()[-1][:200]}
+    v, t, nc, n = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": "sim-s/wall-s", "cores": 1, "kind": "oracle",
+            "sample": ("one ARK2 step at C=15 on an 8x8x12-element window (%d of 148225 columns), "
+                       "median of %d steps (%.2f s each), scaled by the column count" % (nc, n, t))}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    W = 8
+    dt = dt_for(C_MAIN)
+    from oracle import ark2
+    from oracle.column import Column
+    from oracle.mesh import BoxMesh
+    import synthetic
+    m = BoxMesh(W, W, NEZ, N, W * LX / NEX, W * LY / NEY, LZ)
+    col = Column(m)
+    xg, yg, zg = m.coords()
+    q = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Ly, m.Lz, col.rho0, col.theta0, SEED)
+    H = ark2.HEVI(m, col, dt)
+    for _ in range(args.warmup):
+        H.step(q, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H.step(q, 1)
+    el = time.perf_counter() - t0
+    scale = (NEX * N + 1) * (NEY * N + 1) / m.ncol
+    ms_step = el / args.steps * scale * 1e3
+    value = dt / (ms_step / 1e3)
+    sample = ("one ARK2 step at C=15 per timed step on an 8x8x12-element window (%d of 148225 columns) "
+              "of the workload, scaled by the column count" % m.ncol)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sim-s/wall-s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "C_V": C_MAIN},
+        "cpu_baseline": {"value": value, "unit": "sim-s/wall-s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "sim-s/wall-s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

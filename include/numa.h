@@ -1,0 +1,194 @@
+/*
+ * numa.h -- C ABI of the GB300 HEVI 1D-IMEX library.
+ *
+ * The library advances the compressible Euler equations in the Set2NC perturbation form
+ * (rho', u, v, w, theta') over a hydrostatic reference state, discretised with
+ * continuous-Galerkin spectral elements on Legendre-Gauss-Lobatto (LGL) nodes on a
+ * uniform box with walls on all six faces (Abdi, Giraldo et al., "Acceleration of the
+ * IMplicit-EXplicit non-hydrostatic unified model of the atmosphere on manycore
+ * processors", arXiv:1702.04316).  The time step is the horizontally-explicit,
+ * vertically-implicit (HEVI) "1D-IMEX" ARK2 step of Sec. "IMEX time integration"
+ * (Eq. sieqn1d, Table 1): explicit right-hand side plus per-column Schur-complement
+ * solves with banded LU factors formed once per time-step size (Sec. "1D-IMEX kernels",
+ * Algorithms 7 and 9).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh: nex x ney x nez elements of polynomial order N (1 <= N <= 8).  Global nodes:
+ *   nxg = nex*N+1, nyg = ney*N+1, M = nez*N+1 (nodes per column), ncol = nxg*nyg,
+ *   nnode = ncol*M.  Column id col = iy*nxg + ix; global node id g = col*M + iz
+ *   (the nodes of one column are consecutive: Sec. "1D-IMEX kernels").
+ * State layout ("SoA"): a contiguous float64 device array of 5*nnode values, field f at
+ *   offset f*nnode, fields in the order rho', u, v, w, theta' (SI units: kg/m^3, m/s,
+ *   m/s, m/s, K).  All device pointers must be 8-byte aligned; the library reads and
+ *   writes exactly the documented extents.
+ * Ownership: the caller owns every state/rhs/vector buffer it passes.  The context owns
+ *   its tables, the stored LU factors and its workspace, all allocated by numa_init and
+ *   released by numa_destroy.
+ * Streams: every device call is enqueued on the context's stream (numa_init /
+ *   numa_set_stream) and is asynchronous unless stated otherwise; a return of NUMA_OK
+ *   means "validated and enqueued".  Errors detected on the device (zero pivot,
+ *   non-finite values) are latched into a device status word that numa_status() reads.
+ * Errors: every int-returning call returns one of the NUMA_* codes below and never
+ *   aborts; numa_last_error() gives a one-line message for the last failing call.
+ */
+#ifndef NUMA_H
+#define NUMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  NUMA_OK = 0,
+  NUMA_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad mesh) */
+  NUMA_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  NUMA_ERR_OOM = 3,          /* device allocation failed */
+  NUMA_ERR_NOT_FACTORED = 4, /* a solve was requested before numa_factor_columns */
+  NUMA_ERR_PIVOT = 5,        /* zero or non-finite pivot in the column LU */
+  NUMA_ERR_NONFINITE = 6,    /* non-finite value detected in a state */
+  NUMA_ERR_TIMEOUT = 7       /* a bounded device wait gave up */
+};
+
+/* Uniform box mesh and reference state (Sec. "Equation Set2NC").
+ * theta_s: surface potential temperature of the reference state in K (<= 0 selects 300);
+ * n_bv: Brunt-Vaisala frequency in 1/s of the reference state (0: isentropic,
+ *       theta0 = theta_s; > 0: theta0 = theta_s exp(n_bv^2 z / g)). */
+typedef struct numa_mesh_desc {
+  int nex, ney, nez;
+  double Lx, Ly, Lz;
+  double theta_s;
+  double n_bv;
+} numa_mesh_desc;
+
+typedef struct numa_ctx numa_ctx;
+
+/* numa_query keys */
+enum {
+  NUMA_Q_NCOL = 0,          /* number of columns */
+  NUMA_Q_M = 1,             /* nodes per column */
+  NUMA_Q_NNODE = 2,         /* global nodes */
+  NUMA_Q_NELEM = 3,         /* elements */
+  NUMA_Q_HALF_BAND = 4,     /* half-bandwidth 2N of the column Schur matrix */
+  NUMA_Q_FACTOR_BYTES = 5,  /* bytes of stored LU factors */
+  NUMA_Q_WORKSPACE_BYTES = 6, /* bytes of step workspace */
+  NUMA_Q_FACTORED = 7,      /* 1 once numa_factor_columns succeeded */
+  NUMA_Q_N = 8              /* polynomial order */
+};
+
+/* Create a context: validates the mesh, builds the LGL nodes/weights/derivative matrix
+ * (Sec. "Volume kernels": sD), the reference state and its discrete vertical gradients
+ * (Sec. "Volume kernels": reference gradients computed once at startup), uploads the
+ * tables, allocates workspace and, if dt > 0, calls numa_factor_columns(ctx, dt).
+ * stream: a cudaStream_t (NULL = the legacy default stream) used by every later call.
+ * Synchronous.  On failure *out is NULL and the code says why (no message is kept). */
+int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_ctx** out);
+
+/* Release everything the context owns (synchronises its stream).  NULL is a no-op. */
+void numa_destroy(numa_ctx* ctx);
+
+/* Change the stream later calls are enqueued on. */
+int numa_set_stream(numa_ctx* ctx, void* stream);
+
+/* Explicit right-hand side R(q) of the Set2NC perturbation equations (Sec. "Equation
+ * Set2NC"), cG with LGL derivatives (Algorithm 2) and direct stiffness summation
+ * (Sec. "Direct stiffness summation"), wall-normal velocity tendencies zeroed on the
+ * six walls.  q, rhs: device SoA arrays of 5*nnode doubles; must not overlap. */
+int numa_rhs_explicit(numa_ctx* ctx, const double* q, double* rhs);
+
+/* Form, for every column, the Schur-complement matrix S(lam), lam = (1 - 1/sqrt2) dt
+ * (the SDIRK diagonal of Table 1 times dt), by probing the left-hand side with unit
+ * vectors (Algorithm 7), factor it by banded LU without pivoting (Algorithm 9) and store
+ * the factors (Sec. "1D-IMEX kernels").  Also sets the context's IMEX time step to dt.
+ * Per-column factor storage: M*(4N+1) doubles.  A zero or non-finite pivot latches
+ * NUMA_ERR_PIVOT in the device status. */
+int numa_factor_columns(numa_ctx* ctx, double dt);
+
+/* Solve S x = b for every column with the stored factors (forward then back
+ * substitution).  b, x: device arrays of ncol*M doubles in column order (g = col*M+iz);
+ * x == b (in place) is allowed.  NUMA_ERR_NOT_FACTORED before numa_factor_columns. */
+int numa_solve_columns(numa_ctx* ctx, const double* b, double* x);
+
+/* nsteps >= 0 HEVI 1D-IMEX ARK2 steps of size dt (the dt of the last
+ * numa_factor_columns) from q_in to q_out (Sec. "Linear multi-stage methods", Eq.
+ * sieqn1d, Table 1 with b = b~).  q_in == q_out (in place) is allowed; otherwise q_in is
+ * not modified.  nsteps == 0 copies q_in to q_out. */
+int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nsteps);
+
+/* One fused 1D-IMEX stage i in {2, 3} (rows 2 and 3 of Table 1): explicit predictor,
+ * Schur right-hand side (Algorithm 4), column solve, extraction of (rho', w, theta')
+ * and the q~ recombination, producing the stage value q(i).  qn = q^n, R1 = R(q(1)),
+ * R2 = R(q(2)) (stage 3 only), q2 = q(2) (stage 3 only; pass NULL for stage 2).
+ * Exposed so that each row of the step can be checked on its own. */
+int numa_imex_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1,
+                    const double* R2, const double* q2, double* q_out);
+
+/* nsteps explicit five-stage third-order SSP Runge-Kutta steps of size dt (the RK35
+ * comparator of Sec. "Performance of IMEX on manycore processors"; two-register
+ * Shu-Osher form, coefficients in numa_rk35_coefficients).  q_in == q_out allowed. */
+int numa_step_explicit_rk(numa_ctx* ctx, const double* q_in, double* q_out, double dt,
+                          int nsteps);
+
+/* Host-buffer driver: copies q_in_host (5*nnode doubles, pinned memory recommended) to
+ * the device, runs nsteps of method 0 (1D-IMEX, dt of the factors) or 1 (RK35 with the
+ * given dt), copies the result into q_out_host (may equal q_in_host) and synchronises.
+ * Uses a device state buffer owned by the context (allocated on first use). */
+int numa_run_host(numa_ctx* ctx, int method, const double* q_in_host, double* q_out_host,
+                  int nsteps, double dt);
+
+/* Per-kernel timing with CUDA events on the context's stream (off by default).
+ * numa_profile(ctx, 1) clears the records and starts recording a start/stop event pair
+ * around every kernel the context launches; numa_profile(ctx, 0) stops.
+ * numa_profile_read synchronises and returns, for one kernel kind, the summed device
+ * time in ms and the number of launches recorded. */
+enum {
+  NUMA_K_PRESSURE = 0,  /* equation-of-state pre-pass P'(q) of the right-hand side */
+  NUMA_K_RHS = 1,       /* explicit right-hand side (with its fused update epilogue) */
+  NUMA_K_STAGE = 2,     /* fused implicit stage: predictor, Schur RHS, solve, extraction */
+  NUMA_K_SOLVE = 3,     /* stand-alone column solve */
+  NUMA_K_FACTOR = 4,    /* probing + banded LU */
+  NUMA_K_NKINDS = 5
+};
+int numa_profile(numa_ctx* ctx, int enable);
+int numa_profile_read(numa_ctx* ctx, int kind, double* total_ms, long long* launches);
+
+/* Element-to-global map and its inverse, produced on the device by the same index
+ * functions the kernels use.  l2g: device int32 [nelem][(N+1)^3], element
+ * e = ex + nex*(ey + ney*ez), local node l = i + (N+1)*(j + (N+1)*k).  g2l: device int32
+ * [nnode][8]: the element-local ids e*(N+1)^3 + l that DSS sums into node g, ascending,
+ * padded with -1.  Either pointer may be NULL. */
+int numa_connectivity(numa_ctx* ctx, int32_t* l2g, int32_t* g2l);
+
+/* Copy the stored factors of one column to host memory: M*(4N+1) doubles, row-major
+ * [row][band], band index b = j - i + 2N for entry (i, j); the unit diagonal of L is not
+ * stored (entries b < 2N hold L, b >= 2N hold U).  Synchronous. */
+int numa_column_factors(numa_ctx* ctx, long long col, double* host_out);
+
+/* Host copy of the per-level reference tables, 8*M doubles in the order
+ * z, rho0, theta0, P0, G0, H0, d(rho0)/dz, d(theta0)/dz.  Synchronous. */
+int numa_reference_levels(const numa_ctx* ctx, double* host_out);
+
+/* Count the non-finite entries of a device array of n doubles; synchronous. */
+int numa_count_nonfinite(numa_ctx* ctx, const double* x, long long n, long long* count);
+
+/* Synchronise the stream and return the latched device status (NUMA_OK or the first
+ * NUMA_ERR_* a kernel recorded), then clear it. */
+int numa_status(numa_ctx* ctx, int* status);
+
+int numa_query(const numa_ctx* ctx, int what, long long* out);
+
+/* One-line message of the last failing call on this context ("" if none). */
+const char* numa_last_error(const numa_ctx* ctx);
+
+/* The RK35 two-register coefficients (alpha[5], beta[5]) and the ARK2 tableau
+ * (a[9], at[9], b[3], row-major 3x3) the library uses.  Host only; any pointer may be
+ * NULL. */
+void numa_rk35_coefficients(double* alpha, double* beta);
+void numa_ark2_tableau(double* a, double* at, double* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NUMA_H */

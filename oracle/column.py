@@ -81,8 +81,11 @@ class Column:
         ref = reference_profile(self.z, theta_s, n_bv)
         self.theta0, self.rho0, self.P0 = ref["theta0"], ref["rho0"], ref["P0"]
         self.G0, self.H0 = ref["G0"], ref["H0"]
-        self.drho0 = self.Dz @ self.rho0
-        self.dtheta0 = self.Dz @ self.theta0
+        # D_z annihilates constants (its rows sum to zero), so the surface value is taken
+        # out first: exact in real arithmetic, and an isentropic theta0 gets a gradient of
+        # exactly zero instead of rounding noise.
+        self.drho0 = self.Dz @ (self.rho0 - self.rho0[0])
+        self.dtheta0 = self.Dz @ (self.theta0 - self.theta0[0])
         self.F0z = self.G0 * self.drho0 + self.H0 * self.dtheta0
 
     # ---- Set2NC vertical linear operator -------------------------------------

@@ -58,6 +58,22 @@ def pressure(rho, theta):
     return P00 * (rho * R_GAS * theta / P00) ** GAMMA
 
 
+def pressure_perturbation(rho_p, theta_p, rho0, theta0, P0):
+    """P' = P(rho0 + rho', theta0 + theta') - P0 without cancellation.
+
+    With a = rho'/rho0 and b = theta'/theta0 the equation of state gives
+    P / P0 = ((1 + a)(1 + b))^gamma, so P' = P0 ((1 + x)^gamma - 1), x = a + b + a b,
+    evaluated as P0 expm1(gamma log1p(x)).  This is P - P0 exactly in real arithmetic;
+    the direct difference of two ~1e5 Pa pressures would carry ~1e-11 Pa of rounding
+    noise, which is the whole of P' in a balanced state (the perturbation split exists
+    for numerical accuracy: Sec. "Equation Set2NC").
+    """
+    a = rho_p / rho0
+    b = theta_p / theta0
+    x = a + b + a * b
+    return P0 * np.expm1(GAMMA * np.log1p(x))
+
+
 def sound_speed(P, rho):
     """a = sqrt(gamma P / rho) (Sec. "Acoustic wave problem")."""
     return np.sqrt(GAMMA * P / rho)

@@ -6,7 +6,8 @@ Test infrastructure (oracle).  Sec. "Equation Set2NC", perturbation form:
     d u/dt     = -( u.grad u + grad P' / (rho0 + rho') + (rho' / (rho0 + rho')) g z_hat )
     d theta'/dt= -( u.grad theta' + u.grad theta0 )
 
-with P' = P(rho0 + rho', theta0 + theta') - P0 from the equation of state.
+with P' = P(rho0 + rho', theta0 + theta') - P0 from the equation of state (evaluated without
+cancellation, see reference.pressure_perturbation).
 
 Discretisation (Sec. "Spatial discretization", Algorithm 2 GradDiv-3D, Sec. "Direct
 stiffness summation"): element by element, the five fields and P' are gathered to the
@@ -23,7 +24,7 @@ y-faces, w on z-faces).
 """
 import numpy as np
 
-from .reference import GRAV, pressure
+from .reference import GRAV, pressure_perturbation
 
 
 def rhs(mesh, col, q, l2g=None, mass=None):
@@ -37,7 +38,7 @@ def rhs(mesh, col, q, l2g=None, mass=None):
     rho0, theta0, P0 = col.rho0[iz], col.theta0[iz], col.P0[iz]
     drho0, dtheta0 = col.drho0[iz], col.dtheta0[iz]
     rho = rho0 + rho_p
-    Pp = pressure(rho, theta0 + th_p) - P0
+    Pp = pressure_perturbation(rho_p, th_p, rho0, theta0, P0)
 
     sx, sy, sz = 2.0 / mesh.dx, 2.0 / mesh.dy, 2.0 / mesh.dz
 

@@ -1,0 +1,682 @@
+// C ABI of libnuma (declared in include/numa.h): the context, the host-side set-up
+// (LGL tables, reference state, column derivative and stage tables) and the entry points
+// that enqueue the kernels of rhs.cu, column.cu and misc.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "numa.h"
+#include "numa_internal.cuh"
+
+namespace {
+
+// ---- ARK2 tableau (Table 1; b = b~ = last implicit row) --------------------------------
+struct Ark2 {
+  double a[3][3], at[3][3], b[3];
+  Ark2() {
+    const double s2 = std::sqrt(2.0);
+    std::memset(this, 0, sizeof(*this));
+    a[1][0] = 2.0 - s2;
+    a[2][1] = (3.0 + 2.0 * s2) / 6.0;
+    a[2][0] = 1.0 - a[2][1];
+    at[1][0] = at[1][1] = 1.0 - 1.0 / s2;
+    at[2][0] = at[2][1] = 1.0 / (2.0 * s2);
+    at[2][2] = 1.0 - 1.0 / s2;
+    for (int i = 0; i < 3; ++i) b[i] = at[2][i];
+  }
+};
+
+// ---- RK35: five-stage third-order SSP, two-register Shu-Osher form -------------------
+//   u_i = alpha_i u_0 + (1 - alpha_i) u_{i-1} + beta_i dt F(u_{i-1});  beta_1 = beta_5 =
+//   0.46, alpha_2 = alpha_3 = alpha_5 = 0, the rest the real root of the third-order
+//   conditions with beta_2 > beta_3 (SSP coefficient 1/0.46).
+const double kRkAlpha[5] = {0.0, 0.0, 0.0, 0.5764252463942515726402586, 0.0};
+const double kRkBeta[5] = {0.46, 0.2805744403033042654640453, 0.22110850739434604175949,
+                           0.1326553823821179192508848, 0.46};
+
+// ---- LGL nodes, weights and derivative matrix --------------------------------------------
+// P_N and P_{N-1} by the three-term recurrence.
+void legendre(int N, double x, double& PN, double& PNm1) {
+  double p0 = 1.0, p1 = x;
+  if (N == 0) { PN = 1.0; PNm1 = 0.0; return; }
+  for (int n = 1; n < N; ++n) {
+    const double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  PN = p1;
+  PNm1 = p0;
+}
+
+// Interior LGL nodes are the roots of f(x) = x P_N - P_{N-1} = (x^2-1) P_N'/N inside
+// (-1, 1); with x P_N' - P_{N-1}' = N P_N one gets f' = (N+1) P_N, so Newton reads
+// x <- x - (x P_N - P_{N-1}) / ((N+1) P_N), started from the Chebyshev-Lobatto points.
+void lgl_host(int N, double* x, double* w, double* D) {
+  const int Nq = N + 1;
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int j = 1; j < N; ++j) {
+    double xj = -std::cos(M_PI * j / N);
+    for (int it = 0; it < 100; ++it) {
+      double PN, PNm1;
+      legendre(N, xj, PN, PNm1);
+      const double dx = (xj * PN - PNm1) / ((N + 1.0) * PN);
+      xj -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    x[j] = xj;
+  }
+  for (int j = 0; j < Nq / 2; ++j) {    // exact mirror symmetry
+    const double s = 0.5 * (x[N - j] - x[j]);
+    x[j] = -s;
+    x[N - j] = s;
+  }
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  std::vector<double> PNv(Nq);
+  for (int j = 0; j < Nq; ++j) {
+    double PN, PNm1;
+    legendre(N, x[j], PN, PNm1);
+    PNv[j] = PN;
+    w[j] = 2.0 / (N * (N + 1.0) * PN * PN);
+  }
+  for (int i = 0; i < Nq; ++i)
+    for (int j = 0; j < Nq; ++j)
+      D[i * Nq + j] = (i == j) ? 0.0 : PNv[i] / (PNv[j] * (x[i] - x[j]));
+  D[0] = -N * (N + 1) / 4.0;
+  D[N * Nq + N] = N * (N + 1) / 4.0;
+}
+
+void set_axis(AxisCoef& c, int N, const double* w, const double* D, double h) {
+  const int Nq = N + 1;
+  std::memset(&c, 0, sizeof(c));
+  const double s = 2.0 / h;
+  for (int i = 0; i < Nq; ++i)
+    for (int n = 0; n < Nq; ++n) c.D[i * Nq + n] = D[i * Nq + n] * s;
+  const double wl = w[N], wr = w[0];
+  for (int n = 0; n < Nq; ++n) {
+    c.Dl[n] = wl / (wl + wr) * D[N * Nq + n] * s;
+    c.Dr[n] = wr / (wl + wr) * D[0 * Nq + n] * s;
+  }
+}
+
+}  // namespace
+
+// ---- the context ---------------------------------------------------------------------------
+struct numa_ctx {
+  Geom G;
+  Coef3 C;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double dt = 0.0, lam = 0.0;
+  bool factored = false;
+  double theta_s = 300.0, n_bv = 0.0;
+  // host copies of the per-level tables
+  std::vector<double> z, rho0, theta0, P0, G0, H0, drho0, dtheta0, F0z, dzband;
+  // device memory
+  double* d_lev = nullptr;      // reference tables + dz band + stage tables
+  RefLev R{};
+  StageTab T{};
+  double* d_stage_tab = nullptr;
+  Factors F{};
+  double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (each 5*nnode except Pp)
+  double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
+  unsigned* d_status = nullptr;
+  unsigned long long* d_count = nullptr;
+  double* d_hoststate = nullptr;
+  size_t factor_bytes = 0, work_bytes = 0;
+  // per-kernel event timing
+  struct ProfRec { int kind; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof;
+  size_t prof_n = 0;
+  bool prof_on = false;
+};
+
+namespace {
+
+int fail(numa_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(numa_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, NUMA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define NUMA_CK(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+// Event pair around one launch when profiling is on (index into ctx->prof, or -1).
+long prof_begin(numa_ctx* c, int kind) {
+  if (!c->prof_on) return -1;
+  if (c->prof_n == c->prof.size()) {
+    numa_ctx::ProfRec r{kind, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+    c->prof.push_back(r);
+  }
+  numa_ctx::ProfRec& r = c->prof[c->prof_n];
+  r.kind = kind;
+  cudaEventRecord(r.a, c->stream);
+  return (long)c->prof_n++;
+}
+
+void prof_end(numa_ctx* c, long idx) {
+  if (idx >= 0) cudaEventRecord(c->prof[idx].b, c->stream);
+}
+
+void free_all(numa_ctx* c) {
+  for (auto& r : c->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  cudaFree(c->d_lev);
+  cudaFree(c->d_stage_tab);
+  cudaFree(c->F.L);
+  cudaFree(c->F.U);
+  cudaFree(c->d_work);
+  cudaFree(c->d_status);
+  cudaFree(c->d_count);
+  cudaFree(c->d_hoststate);
+}
+
+// Host reference state and the column derivative (Sec. "Equation Set2NC",
+// Sec. "Direct stiffness summation").
+void build_levels(numa_ctx* c, const double* xi, const double* w, const double* D, double dz) {
+  const int N = c->G.N, M = c->G.M, nez = c->G.nez, Nq = N + 1, W = 2 * N + 1;
+  c->z.assign(M, 0.0);
+  for (int ez = 0; ez < nez; ++ez)
+    for (int k = 0; k < Nq; ++k) c->z[ez * N + k] = ez * dz + (1.0 + xi[k]) * dz / 2.0;
+  const double g = NUMA_GRAV, cp = NUMA_CP, R = NUMA_RGAS, gam = NUMA_GAMMA;
+  c->theta0.resize(M); c->rho0.resize(M); c->P0.resize(M); c->G0.resize(M); c->H0.resize(M);
+  for (int m = 0; m < M; ++m) {
+    const double zz = c->z[m];
+    double th, pi;
+    if (c->n_bv == 0.0) {
+      th = c->theta_s;
+      pi = 1.0 - g * zz / (cp * c->theta_s);
+    } else {
+      const double s = c->n_bv * c->n_bv / g;
+      th = c->theta_s * std::exp(s * zz);
+      pi = 1.0 + g * g / (cp * c->theta_s * c->n_bv * c->n_bv) * (std::exp(-s * zz) - 1.0);
+    }
+    const double P0 = NUMA_P00 * std::pow(pi, cp / R);
+    c->theta0[m] = th;
+    c->P0[m] = P0;
+    c->rho0[m] = P0 / (R * pi * th);
+    c->G0[m] = gam * P0 / c->rho0[m];
+    c->H0[m] = gam * P0 / th;
+  }
+  // DSS'd vertical derivative: element ez gives node m = ez*N + k the row (2/dz) D[k,:]
+  // weighted by w_k; rows are divided by the summed weights.
+  std::vector<double> num((size_t)M * W, 0.0), den(M, 0.0);
+  for (int ez = 0; ez < nez; ++ez)
+    for (int k = 0; k < Nq; ++k) {
+      const int m = ez * N + k;
+      for (int n = 0; n < Nq; ++n) {
+        const int j = ez * N + n;
+        num[(size_t)m * W + (j - m + N)] += w[k] * D[k * Nq + n] * (2.0 / dz);
+      }
+      den[m] += w[k];
+    }
+  c->dzband.assign((size_t)M * W, 0.0);
+  for (int m = 0; m < M; ++m)
+    for (int b = 0; b < W; ++b) c->dzband[(size_t)m * W + b] = num[(size_t)m * W + b] / den[m];
+  c->drho0.assign(M, 0.0);
+  c->dtheta0.assign(M, 0.0);
+  c->F0z.resize(M);
+  for (int m = 0; m < M; ++m) {
+    for (int b = 0; b < W; ++b) {
+      const int j = m - N + b;
+      if (j < 0 || j >= M) continue;
+      // D_z annihilates constants: taking the surface value out first is exact and gives
+      // an isentropic theta0 a gradient of exactly zero.
+      c->drho0[m] += c->dzband[(size_t)m * W + b] * (c->rho0[j] - c->rho0[0]);
+      c->dtheta0[m] += c->dzband[(size_t)m * W + b] * (c->theta0[j] - c->theta0[0]);
+    }
+    c->F0z[m] = c->G0[m] * c->drho0[m] + c->H0[m] * c->dtheta0[m];
+  }
+}
+
+int upload_levels(numa_ctx* c) {
+  const int M = c->G.M, W = 2 * c->G.N + 1;
+  const int nt = 10;
+  std::vector<double> h((size_t)nt * M + (size_t)M * W);
+  auto put = [&](int slot, const std::vector<double>& v) {
+    std::memcpy(&h[(size_t)slot * M], v.data(), sizeof(double) * M);
+  };
+  std::vector<double> inv_rho0(M), inv_theta0(M);
+  for (int m = 0; m < M; ++m) {
+    inv_rho0[m] = 1.0 / c->rho0[m];
+    inv_theta0[m] = 1.0 / c->theta0[m];
+  }
+  put(0, c->rho0); put(1, inv_rho0); put(2, c->theta0); put(3, inv_theta0); put(4, c->P0);
+  put(5, c->G0); put(6, c->H0); put(7, c->drho0); put(8, c->dtheta0); put(9, c->F0z);
+  std::memcpy(&h[(size_t)nt * M], c->dzband.data(), sizeof(double) * M * W);
+  NUMA_CK(c, cudaMalloc(&c->d_lev, h.size() * sizeof(double)));
+  NUMA_CK(c, cudaMemcpy(c->d_lev, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const double* d = c->d_lev;
+  c->R = RefLev{d, d + M, d + 2 * M, d + 3 * M, d + 4 * M, d + 5 * M, d + 6 * M,
+                d + 7 * M, d + 8 * M, d + 9 * M, d + (size_t)nt * M};
+  return NUMA_OK;
+}
+
+// Stage tables for one lam (the coefficient tables listed with StageTab).
+int upload_stage_tables(numa_ctx* c, double lam) {
+  const int M = c->G.M;
+  const double g = NUMA_GRAV;
+  std::vector<double> h((size_t)11 * M);
+  for (int m = 0; m < M; ++m) {
+    const bool wall = (m == 0 || m == M - 1);
+    const double A = 1.0 + lam * lam * g * c->dtheta0[m] / c->theta0[m];
+    h[0 * M + m] = lam * g / c->theta0[m];
+    h[1 * M + m] = wall ? 0.0 : 1.0 / A;
+    h[2 * M + m] = lam * c->F0z[m];
+    h[3 * M + m] = lam * c->rho0[m] * c->G0[m];
+    h[4 * M + m] = wall ? 0.0 : lam / (A * c->rho0[m]);
+    h[5 * M + m] = wall ? 0.0 : lam * g / (A * c->G0[m] * c->rho0[m]);
+    h[6 * M + m] = lam * c->dtheta0[m];
+    h[7 * M + m] = 1.0 / c->G0[m];
+    h[8 * M + m] = c->H0[m] / c->G0[m];
+    h[9 * M + m] = c->G0[m];
+    h[10 * M + m] = c->H0[m];
+  }
+  if (!c->d_stage_tab) NUMA_CK(c, cudaMalloc(&c->d_stage_tab, h.size() * sizeof(double)));
+  NUMA_CK(c, cudaMemcpyAsync(c->d_stage_tab, h.data(), h.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream));
+  NUMA_CK(c, cudaStreamSynchronize(c->stream));
+  const double* d = c->d_stage_tab;
+  c->T = StageTab{d, d + M, d + 2 * M, d + 3 * M, d + 4 * M, d + 5 * M,
+                  d + 6 * M, d + 7 * M, d + 8 * M, d + 9 * M, d + 10 * M};
+  return NUMA_OK;
+}
+
+int check_ptr(numa_ctx* c, const void* p, const char* name) {
+  if (!p) return fail(c, NUMA_ERR_ARG, std::string(name) + " is NULL");
+  if (((uintptr_t)p) % 8) return fail(c, NUMA_ERR_ARG, std::string(name) + " not 8-byte aligned");
+  return NUMA_OK;
+}
+
+int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep) {
+  long p = prof_begin(c, NUMA_K_PRESSURE);
+  NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
+  prof_end(c, p);
+  p = prof_begin(c, NUMA_K_RHS);
+  NUMA_CK(c, launch_rhs(q, c->Pp, out, c->G, c->C, c->R, ep, c->stream));
+  prof_end(c, p);
+  return NUMA_OK;
+}
+
+int enqueue_stage(numa_ctx* c, int stage, const double* qn, const double* R1, const double* R2,
+                  const double* q2, double* out, const StageCoef& sc) {
+  long p = prof_begin(c, NUMA_K_STAGE);
+  NUMA_CK(c, launch_stage(stage, qn, R1, R2, q2, out, c->G, c->R, c->F, sc, c->T, c->stream));
+  prof_end(c, p);
+  return NUMA_OK;
+}
+
+StageCoef stage_coef(const numa_ctx* c, int stage) {
+  static const Ark2 t;
+  StageCoef sc{};
+  const int i = stage - 1;
+  sc.dt = c->dt;
+  sc.lam = t.at[i][i] * c->dt;
+  for (int j = 0; j < 2; ++j) {
+    sc.a[j] = (j < i) ? t.a[i][j] : 0.0;
+    sc.c[j] = (j < i) ? (t.at[i][j] - t.a[i][j]) / t.at[i][i] : 0.0;
+  }
+  return sc;
+}
+
+}  // namespace
+
+// ---- entry points ---------------------------------------------------------------------------
+extern "C" {
+
+int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_ctx** out) {
+  if (!out) return NUMA_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || N < 1 || N > NUMA_MAXN || mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 ||
+      !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0) || !(dt >= 0) ||
+      !(mesh->n_bv >= 0) || !std::isfinite(mesh->Lx + mesh->Ly + mesh->Lz + dt))
+    return NUMA_ERR_ARG;
+  Geom G{};
+  G.N = N; G.Nq = N + 1;
+  G.nex = mesh->nex; G.ney = mesh->ney; G.nez = mesh->nez;
+  G.nxg = mesh->nex * N + 1; G.nyg = mesh->ney * N + 1; G.M = mesh->nez * N + 1;
+  G.ncol = (long long)G.nxg * G.nyg;
+  G.nnode = G.ncol * G.M;
+  const long long nelem = (long long)mesh->nex * mesh->ney * mesh->nez;
+  // int32 connectivity ids and 32-bit grid dimensions bound the mesh size
+  if (nelem * G.Nq * G.Nq * G.Nq >= (1LL << 31) || 5 * G.nnode >= (1LL << 40) ||
+      (G.ncol + 63) / 64 >= (1LL << 31))
+    return NUMA_ERR_ARG;
+  numa_ctx* c = new numa_ctx();
+  c->G = G;
+  c->stream = (cudaStream_t)stream;
+  c->theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
+  c->n_bv = mesh->n_bv;
+  double xi[NUMA_MAXNQ], w[NUMA_MAXNQ], D[NUMA_MAXNQ * NUMA_MAXNQ];
+  lgl_host(N, xi, w, D);
+  set_axis(c->C.x, N, w, D, mesh->Lx / mesh->nex);
+  set_axis(c->C.y, N, w, D, mesh->Ly / mesh->ney);
+  set_axis(c->C.z, N, w, D, mesh->Lz / mesh->nez);
+  build_levels(c, xi, w, D, mesh->Lz / mesh->nez);
+  int rc = upload_levels(c);
+  const int hb = 2 * N;
+  c->F.hb = hb;
+  c->factor_bytes = (size_t)G.M * (2 * hb + 1) * G.ncol * sizeof(double);
+  c->work_bytes = (size_t)(1 + 4 * 5) * G.nnode * sizeof(double);
+  if (rc == NUMA_OK) {
+    if (cudaMalloc(&c->F.L, (size_t)G.M * hb * G.ncol * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->F.U, (size_t)G.M * (hb + 1) * G.ncol * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_work, c->work_bytes) != cudaSuccess ||
+        cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = NUMA_ERR_OOM;
+    }
+  }
+  if (rc == NUMA_OK) {
+    const long long n5 = 5 * G.nnode;
+    c->Pp = c->d_work;
+    c->R1 = c->Pp + G.nnode;
+    c->R2 = c->R1 + n5;
+    c->q2 = c->R2 + n5;
+    c->q3 = c->q2 + n5;
+    if (cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = NUMA_ERR_CUDA;
+  }
+  if (rc == NUMA_OK && dt > 0) rc = numa_factor_columns(c, dt);
+  if (rc == NUMA_OK) rc = (cudaDeviceSynchronize() == cudaSuccess) ? NUMA_OK : NUMA_ERR_CUDA;
+  if (rc != NUMA_OK) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return NUMA_OK;
+}
+
+void numa_destroy(numa_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  delete ctx;
+}
+
+int numa_set_stream(numa_ctx* ctx, void* stream) {
+  if (!ctx) return NUMA_ERR_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return NUMA_OK;
+}
+
+int numa_rhs_explicit(numa_ctx* ctx, const double* q, double* rhs) {
+  if (!ctx) return NUMA_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(ctx, q, "q")) || (rc = check_ptr(ctx, rhs, "rhs"))) return rc;
+  if (q == rhs) return fail(ctx, NUMA_ERR_ARG, "q and rhs must not overlap");
+  RhsEpilogue ep{};
+  ep.mode = 0;
+  return enqueue_rhs(ctx, q, rhs, ep);
+}
+
+int numa_factor_columns(numa_ctx* ctx, double dt) {
+  if (!ctx) return NUMA_ERR_ARG;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, NUMA_ERR_ARG, "dt must be > 0");
+  const double lam = (1.0 - 1.0 / std::sqrt(2.0)) * dt;
+  int rc = upload_stage_tables(ctx, lam);
+  if (rc) return rc;
+  long p = prof_begin(ctx, NUMA_K_FACTOR);
+  NUMA_CK(ctx, launch_factor(ctx->G, ctx->R, lam, ctx->F, ctx->d_status, ctx->stream));
+  prof_end(ctx, p);
+  ctx->dt = dt;
+  ctx->lam = lam;
+  ctx->factored = true;
+  return NUMA_OK;
+}
+
+int numa_solve_columns(numa_ctx* ctx, const double* b, double* x) {
+  if (!ctx) return NUMA_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(ctx, b, "b")) || (rc = check_ptr(ctx, x, "x"))) return rc;
+  if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  long p = prof_begin(ctx, NUMA_K_SOLVE);
+  NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->stream));
+  prof_end(ctx, p);
+  return NUMA_OK;
+}
+
+int numa_imex_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1,
+                    const double* R2, const double* q2, double* q_out) {
+  if (!ctx) return NUMA_ERR_ARG;
+  if (stage != 2 && stage != 3) return fail(ctx, NUMA_ERR_ARG, "stage must be 2 or 3");
+  int rc;
+  if ((rc = check_ptr(ctx, qn, "qn")) || (rc = check_ptr(ctx, R1, "R1")) ||
+      (rc = check_ptr(ctx, q_out, "q_out")))
+    return rc;
+  if (stage == 3 && ((rc = check_ptr(ctx, R2, "R2")) || (rc = check_ptr(ctx, q2, "q2")))) return rc;
+  if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  return enqueue_stage(ctx, stage, qn, R1, R2, q2, q_out, stage_coef(ctx, stage));
+}
+
+int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nsteps) {
+  if (!ctx) return NUMA_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(ctx, q_in, "q_in")) || (rc = check_ptr(ctx, q_out, "q_out"))) return rc;
+  if (nsteps < 0) return fail(ctx, NUMA_ERR_ARG, "nsteps < 0");
+  if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  const long long n5 = 5 * ctx->G.nnode;
+  if (nsteps == 0) {
+    if (q_in != q_out)
+      NUMA_CK(ctx, cudaMemcpyAsync(q_out, q_in, n5 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+    return NUMA_OK;
+  }
+  static const Ark2 t;
+  const StageCoef s2 = stage_coef(ctx, 2), s3 = stage_coef(ctx, 3);
+  const double* cur = q_in;
+  for (int s = 0; s < nsteps; ++s) {
+    RhsEpilogue e0{};
+    if ((rc = enqueue_rhs(ctx, cur, ctx->R1, e0))) return rc;
+    if ((rc = enqueue_stage(ctx, 2, cur, ctx->R1, nullptr, nullptr, ctx->q2, s2))) return rc;
+    if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0))) return rc;
+    if ((rc = enqueue_stage(ctx, 3, cur, ctx->R1, ctx->R2, ctx->q2, ctx->q3, s3))) return rc;
+    RhsEpilogue ef{};
+    ef.mode = 2;
+    ef.b1dt = t.b[0] * ctx->dt;
+    ef.b2dt = t.b[1] * ctx->dt;
+    ef.b3dt = t.b[2] * ctx->dt;
+    ef.u0 = cur;
+    ef.R1 = ctx->R1;
+    ef.R2 = ctx->R2;
+    if ((rc = enqueue_rhs(ctx, ctx->q3, q_out, ef))) return rc;
+    cur = q_out;
+  }
+  return NUMA_OK;
+}
+
+int numa_step_explicit_rk(numa_ctx* ctx, const double* q_in, double* q_out, double dt,
+                          int nsteps) {
+  if (!ctx) return NUMA_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(ctx, q_in, "q_in")) || (rc = check_ptr(ctx, q_out, "q_out"))) return rc;
+  if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt))
+    return fail(ctx, NUMA_ERR_ARG, "need nsteps >= 0 and dt > 0");
+  const long long n5 = 5 * ctx->G.nnode;
+  if (nsteps == 0) {
+    if (q_in != q_out)
+      NUMA_CK(ctx, cudaMemcpyAsync(q_out, q_in, n5 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+    return NUMA_OK;
+  }
+  // ping-pong between two workspace states; the last stage (alpha_5 = 0) writes q_out, so
+  // q_in may equal q_out.
+  double* buf[2] = {ctx->q2, ctx->q3};
+  const double* u0 = q_in;
+  for (int s = 0; s < nsteps; ++s) {
+    const double* prev = u0;
+    for (int i = 0; i < 5; ++i) {
+      double* dst = (i == 4) ? q_out : buf[i & 1];
+      RhsEpilogue ep{};
+      ep.mode = 1;
+      ep.alpha = kRkAlpha[i];
+      ep.beta_dt = kRkBeta[i] * dt;
+      ep.u0 = u0;
+      if ((rc = enqueue_rhs(ctx, prev, dst, ep))) return rc;
+      prev = dst;
+    }
+    u0 = q_out;
+  }
+  return NUMA_OK;
+}
+
+int numa_run_host(numa_ctx* ctx, int method, const double* q_in_host, double* q_out_host,
+                  int nsteps, double dt) {
+  if (!ctx) return NUMA_ERR_ARG;
+  if (!q_in_host || !q_out_host || (method != 0 && method != 1))
+    return fail(ctx, NUMA_ERR_ARG, "bad method or host buffer");
+  const size_t bytes = 5 * (size_t)ctx->G.nnode * sizeof(double);
+  if (!ctx->d_hoststate) {
+    if (cudaMalloc(&ctx->d_hoststate, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, NUMA_ERR_OOM, "host-run state buffer");
+    }
+  }
+  NUMA_CK(ctx, cudaMemcpyAsync(ctx->d_hoststate, q_in_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  int rc = (method == 0) ? numa_step_imex1d(ctx, ctx->d_hoststate, ctx->d_hoststate, nsteps)
+                         : numa_step_explicit_rk(ctx, ctx->d_hoststate, ctx->d_hoststate, dt, nsteps);
+  if (rc) return rc;
+  NUMA_CK(ctx, cudaMemcpyAsync(q_out_host, ctx->d_hoststate, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return NUMA_OK;
+}
+
+int numa_profile(numa_ctx* ctx, int enable) {
+  if (!ctx) return NUMA_ERR_ARG;
+  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (enable) ctx->prof_n = 0;
+  ctx->prof_on = enable != 0;
+  return NUMA_OK;
+}
+
+int numa_profile_read(numa_ctx* ctx, int kind, double* total_ms, long long* launches) {
+  if (!ctx || !total_ms || !launches || kind < 0 || kind >= NUMA_K_NKINDS) return NUMA_ERR_ARG;
+  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  double t = 0.0;
+  long long n = 0;
+  for (size_t i = 0; i < ctx->prof_n; ++i) {
+    if (ctx->prof[i].kind != kind) continue;
+    float ms = 0.0f;
+    NUMA_CK(ctx, cudaEventElapsedTime(&ms, ctx->prof[i].a, ctx->prof[i].b));
+    t += ms;
+    ++n;
+  }
+  *total_ms = t;
+  *launches = n;
+  return NUMA_OK;
+}
+
+int numa_connectivity(numa_ctx* ctx, int32_t* l2g, int32_t* g2l) {
+  if (!ctx) return NUMA_ERR_ARG;
+  NUMA_CK(ctx, launch_connectivity(ctx->G, l2g, g2l, ctx->stream));
+  return NUMA_OK;
+}
+
+int numa_column_factors(numa_ctx* ctx, long long col, double* host_out) {
+  if (!ctx) return NUMA_ERR_ARG;
+  if (!host_out || col < 0 || col >= ctx->G.ncol) return fail(ctx, NUMA_ERR_ARG, "bad column");
+  if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  const int M = ctx->G.M, hb = ctx->F.hb, W = 2 * hb + 1;
+  const size_t pitch = (size_t)ctx->G.ncol * sizeof(double);
+  std::vector<double> L((size_t)M * hb), U((size_t)M * (hb + 1));
+  NUMA_CK(ctx, cudaMemcpy2DAsync(L.data(), sizeof(double), ctx->F.L + col, pitch, sizeof(double),
+                                 (size_t)M * hb, cudaMemcpyDeviceToHost, ctx->stream));
+  NUMA_CK(ctx, cudaMemcpy2DAsync(U.data(), sizeof(double), ctx->F.U + col, pitch, sizeof(double),
+                                 (size_t)M * (hb + 1), cudaMemcpyDeviceToHost, ctx->stream));
+  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < M; ++i) {
+    for (int b = 0; b < W; ++b) host_out[(size_t)i * W + b] = 0.0;
+    for (int k = 1; k <= hb; ++k)
+      if (i - k >= 0) host_out[(size_t)i * W + (hb - k)] = L[(size_t)i * hb + k - 1];
+    host_out[(size_t)i * W + hb] = 1.0 / U[(size_t)i * (hb + 1)];
+    for (int k = 1; k <= hb; ++k)
+      if (i + k < M) host_out[(size_t)i * W + hb + k] = U[(size_t)i * (hb + 1) + k];
+  }
+  return NUMA_OK;
+}
+
+int numa_reference_levels(const numa_ctx* ctx, double* host_out) {
+  if (!ctx || !host_out) return NUMA_ERR_ARG;
+  const int M = ctx->G.M;
+  const std::vector<double>* v[8] = {&ctx->z, &ctx->rho0, &ctx->theta0, &ctx->P0,
+                                     &ctx->G0, &ctx->H0, &ctx->drho0, &ctx->dtheta0};
+  for (int k = 0; k < 8; ++k) std::memcpy(host_out + (size_t)k * M, v[k]->data(), M * sizeof(double));
+  return NUMA_OK;
+}
+
+int numa_count_nonfinite(numa_ctx* ctx, const double* x, long long n, long long* count) {
+  if (!ctx) return NUMA_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(ctx, x, "x"))) return rc;
+  if (!count || n < 0) return fail(ctx, NUMA_ERR_ARG, "bad count or n");
+  NUMA_CK(ctx, cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned long long), ctx->stream));
+  NUMA_CK(ctx, launch_count_nonfinite(x, n, ctx->d_count, ctx->stream));
+  unsigned long long h = 0;
+  NUMA_CK(ctx, cudaMemcpyAsync(&h, ctx->d_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  *count = (long long)h;
+  return NUMA_OK;
+}
+
+int numa_status(numa_ctx* ctx, int* status) {
+  if (!ctx || !status) return NUMA_ERR_ARG;
+  unsigned h = 0;
+  NUMA_CK(ctx, cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  NUMA_CK(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  *status = (h & NUMA_ST_PIVOT) ? NUMA_ERR_PIVOT : (h & NUMA_ST_NONFINITE) ? NUMA_ERR_NONFINITE : NUMA_OK;
+  return NUMA_OK;
+}
+
+int numa_query(const numa_ctx* ctx, int what, long long* out) {
+  if (!ctx || !out) return NUMA_ERR_ARG;
+  const Geom& G = ctx->G;
+  switch (what) {
+    case NUMA_Q_NCOL: *out = G.ncol; break;
+    case NUMA_Q_M: *out = G.M; break;
+    case NUMA_Q_NNODE: *out = G.nnode; break;
+    case NUMA_Q_NELEM: *out = (long long)G.nex * G.ney * G.nez; break;
+    case NUMA_Q_HALF_BAND: *out = 2 * G.N; break;
+    case NUMA_Q_FACTOR_BYTES: *out = (long long)ctx->factor_bytes; break;
+    case NUMA_Q_WORKSPACE_BYTES: *out = (long long)ctx->work_bytes; break;
+    case NUMA_Q_FACTORED: *out = ctx->factored ? 1 : 0; break;
+    case NUMA_Q_N: *out = G.N; break;
+    default: return NUMA_ERR_ARG;
+  }
+  return NUMA_OK;
+}
+
+const char* numa_last_error(const numa_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void numa_rk35_coefficients(double* alpha, double* beta) {
+  for (int i = 0; i < 5; ++i) {
+    if (alpha) alpha[i] = kRkAlpha[i];
+    if (beta) beta[i] = kRkBeta[i];
+  }
+}
+
+void numa_ark2_tableau(double* a, double* at, double* b) {
+  static const Ark2 t;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      if (a) a[i * 3 + j] = t.a[i][j];
+      if (at) at[i * 3 + j] = t.at[i][j];
+    }
+    if (b) b[i] = t.b[i];
+  }
+}
+
+}  // extern "C"

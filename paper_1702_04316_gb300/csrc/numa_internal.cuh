@@ -1,0 +1,143 @@
+// Internal declarations shared by the CUDA translation units of libnuma.
+// Nothing here is part of the C ABI (include/numa.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define NUMA_MAXN 8
+#define NUMA_MAXNQ (NUMA_MAXN + 1)
+
+// Physical constants of the model.  R and c_p reproduce the sound speed of 347.32 m/s at
+// theta0 = 300 K (Sec. "Acoustic wave problem"); the paper does not give g.
+#define NUMA_GRAV 9.80616
+#define NUMA_P00 1.0e5
+#define NUMA_RGAS 287.17
+#define NUMA_CP 1004.67
+#define NUMA_CV (NUMA_CP - NUMA_RGAS)
+#define NUMA_GAMMA (NUMA_CP / NUMA_CV)
+
+// Device status bits latched by kernels (read back by numa_status).
+#define NUMA_ST_PIVOT 1u
+#define NUMA_ST_NONFINITE 2u
+
+// Mesh sizes (see the conventions in include/numa.h).
+struct Geom {
+  int N, Nq;
+  int nex, ney, nez;
+  int nxg, nyg, M;
+  long long ncol, nnode;
+};
+
+// LGL derivative rows of one axis, already scaled by the metric 2/h of that axis.
+//   D[i*Nq + n]  : derivative at local node i from local node n (interior / wall rows);
+//   Dl[n], Dr[n] : the two halves of the DSS-weighted derivative at an element interface
+//                  node, from the element on the left (its row N) and on the right (its
+//                  row 0), each multiplied by its local-weight share w/(w_N + w_0).
+struct AxisCoef {
+  double D[NUMA_MAXNQ * NUMA_MAXNQ];
+  double Dl[NUMA_MAXNQ];
+  double Dr[NUMA_MAXNQ];
+};
+
+struct Coef3 {
+  AxisCoef x, y, z;
+};
+
+// Per-level reference tables on the device (length M each).  The box reference state
+// depends on z only.
+struct RefLev {
+  const double* rho0;
+  const double* inv_rho0;
+  const double* theta0;
+  const double* inv_theta0;
+  const double* P0;
+  const double* G0;
+  const double* H0;
+  const double* drho0;    // D_z rho0 (DSS'd discrete vertical derivative)
+  const double* dtheta0;  // D_z theta0
+  const double* F0z;      // G0 drho0 + H0 dtheta0
+  const double* dz_band;  // DSS'd vertical derivative on a column, [M][2N+1], column j = m-N+b
+};
+
+// Stored column factors, transposed so that consecutive columns are contiguous:
+//   facL[(i*hb + k-1)*ncol + col] = L(i, i-k),  k = 1..hb   (unit diagonal not stored)
+//   facU[(i*(hb+1) + 0)*ncol + col] = 1 / U(i, i)
+//   facU[(i*(hb+1) + k)*ncol + col] = U(i, i+k), k = 1..hb
+// hb = 2N.  Entries outside the matrix are stored as zero.
+struct Factors {
+  double* L;
+  double* U;
+  int hb;
+};
+
+// Coefficients of one IMEX stage (Table 1 with b = b~).
+struct StageCoef {
+  double dt;
+  double lam;       // a~_ii dt
+  double a[2];      // a_i1, a_i2 (explicit)
+  double c[2];      // c_ij = (a~_ij - a_ij) / a~_ii
+};
+
+// Per-level coefficient tables of one lam for the fused stage (length M each):
+//   wa_th = lam g / theta0;  wa_s = 1/A (0 at the two walls: w_a = 0 there)
+//   kF = lam F0z;  kD = lam rho0 G0
+//   kp1 = lam / (A rho0), kp2 = lam g / (A G0 rho0)  (0 at the two walls: w_p = 0 there)
+//   kth = lam d(theta0)/dz;  invG0 = 1/G0;  H0G0 = H0/G0;  G0, H0
+// with A = 1 + lam^2 (g/theta0) d(theta0)/dz.
+struct StageTab {
+  const double *wa_th, *wa_s, *kF, *kD, *kp1, *kp2, *kth, *invG0, *H0G0, *G0, *H0;
+};
+
+// ---- launchers (return the launch error) ----------------------------------------------
+// rhs.cu
+cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const RefLev& R,
+                            cudaStream_t s);
+// MODE 0: out = R(q);  MODE 1 (RK stage): out = alpha*u0 + (1-alpha)*q + beta*dt*R(q);
+// MODE 2 (ARK final): out = qn + dt*(b1*R1 + b2*R2 + b3*R(q)).
+struct RhsEpilogue {
+  int mode;
+  double alpha, beta_dt;          // mode 1
+  double b1dt, b2dt, b3dt;        // mode 2
+  const double* u0;               // mode 1: u0; mode 2: qn
+  const double* R1;
+  const double* R2;
+};
+cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const Geom& G,
+                       const Coef3& C, const RefLev& R, const RhsEpilogue& ep,
+                       cudaStream_t s);
+
+// column.cu
+cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
+                          unsigned* status, cudaStream_t s);
+cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F,
+                         cudaStream_t s);
+cudaError_t launch_stage(int stage, const double* qn, const double* R1, const double* R2,
+                         const double* q2, double* out, const Geom& G, const RefLev& R,
+                         Factors F, const StageCoef& sc, const StageTab& tb, cudaStream_t s);
+
+// misc.cu
+cudaError_t launch_connectivity(const Geom& G, int32_t* l2g, int32_t* g2l, cudaStream_t s);
+cudaError_t launch_count_nonfinite(const double* x, long long n, unsigned long long* count,
+                                   cudaStream_t s);
+cudaError_t launch_ark_final(const double* qn, const double* R1, const double* R2,
+                             const double* R3, double* out, long long n, double b1dt,
+                             double b2dt, double b3dt, cudaStream_t s);
+
+// ---- index helpers shared by every kernel (the DSS indexing) ---------------------------
+// Along one axis with nel elements of order N, global node index idx in [0, nel*N]:
+// element e and local index i with idx = e*N + i, i in [0, N) except the last node
+// (e = nel-1, i = N).  An interface node (i == 0 and e > 0) is also local node N of
+// element e-1.
+__host__ __device__ __forceinline__ void axis_owner(int idx, int N, int nel, int& e, int& i) {
+  e = idx / N;
+  i = idx - e * N;
+  if (e == nel) {
+    e = nel - 1;
+    i = N;
+  }
+}
+
+__host__ __device__ __forceinline__ long long global_id(const Geom& G, int ix, int iy, int iz) {
+  return ((long long)iy * G.nxg + ix) * G.M + iz;
+}

@@ -1,0 +1,63 @@
+"""The C ABI library loads and exports every symbol include/numa.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1702_04316_gb300 as p
+    if not os.path.exists(p.LIB_PATH):
+        from paper_1702_04316_gb300 import build
+        build.build()
+    return p
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "numa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(numa_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    L = pkg.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(pkg.EXPORTS) == names
+
+
+def test_invalid_arguments_are_rejected_before_any_device_call(pkg):
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    bad = [pkg.MeshDesc(0, 4, 4, 1e4, 1e4, 1e4, 300.0, 0.0),
+           pkg.MeshDesc(4, 4, 4, -1.0, 1e4, 1e4, 300.0, 0.0),
+           pkg.MeshDesc(4, 4, 4, 1e4, 1e4, 1e4, 300.0, -1.0)]
+    for d in bad:
+        assert L.numa_init(ctypes.byref(d), 4, 1.0, None, ctypes.byref(h)) == 1
+        assert not h.value
+    ok = pkg.MeshDesc(4, 4, 4, 1e4, 1e4, 1e4, 300.0, 0.0)
+    assert L.numa_init(ctypes.byref(ok), 0, 1.0, None, ctypes.byref(h)) == 1    # N < 1
+    assert L.numa_init(ctypes.byref(ok), 9, 1.0, None, ctypes.byref(h)) == 1    # N > 8
+    assert L.numa_init(ctypes.byref(ok), 4, -1.0, None, ctypes.byref(h)) == 1   # dt < 0
+    assert L.numa_init(ctypes.byref(ok), 4, 1.0, None, None) == 1               # out NULL
+    big = pkg.MeshDesc(1 << 12, 1 << 12, 1 << 8, 1e4, 1e4, 1e4, 300.0, 0.0)
+    assert L.numa_init(ctypes.byref(big), 8, 1.0, None, ctypes.byref(h)) == 1   # int32 ids overflow
+
+
+def test_host_tableaux_match_the_oracle(pkg):
+    from oracle import ark2, rk35
+    a, at, b = pkg.ark2_tableau()
+    oa, oat, ob, _ = ark2.tableau()
+    np.testing.assert_allclose(a, oa, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(at, oat, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(b, ob, rtol=0, atol=1e-15)
+    al, be = pkg.rk35_coefficients()
+    np.testing.assert_array_equal(al, rk35.ALPHA)
+    np.testing.assert_array_equal(be, rk35.BETA)

@@ -1,0 +1,91 @@
+"""Parity at the full GPU-scale configuration (96 x 96 x 12 elements over 200 x 200 x 15 km,
+N = 4: 385 x 385 columns of 49 nodes), in the launch configuration the benchmark times.
+
+The oracle cannot run the whole mesh in seconds, so it runs on sub-boxes ("windows") of
+7 x 7 elements (all levels) cut from the same state.  A window's artificial lateral walls
+only corrupt the outer element ring of its RHS, and each further RHS evaluation moves
+the corruption one element inward; nodes at least k elements from the window edge are
+exact after k RHS evaluations.  The comparison uses only those nodes.
+"""
+import numpy as np
+import pytest
+
+from helpers import Case, rel_l2, window, window_nodes
+
+pytestmark = pytest.mark.gpu
+
+NEX, NEZ, N, L, LZ = 96, 12, 4, 200e3, 15e3
+WINDOWS = [(0, 0), (44, 61), (89, 89), (20, 87)]     # element origins of 7x7 windows
+W = 7
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    case = Case(NEX, NEX, NEZ, N, L, L, LZ)
+    dt = case.dt_for(15.0)
+    q0 = case.state(2001, kind="balanced")
+    rng = np.random.default_rng(2002)
+    # add small smooth velocities so that every term of the RHS is exercised
+    q0 = q0 + case.state(2003, kind="random", amp=0.1) * np.array([0, 1, 1, 1, 0])[:, None]
+    g = pkg.Numa(NEX, NEX, NEZ, L, L, LZ, N, dt)
+    return dict(torch=torch, pkg=pkg, case=case, dt=dt, q0=q0, g=g, qg=torch.from_numpy(q0).cuda(), rng=rng)
+
+
+def test_rhs_sampled(setup):
+    from oracle.column import Column
+    from oracle.rhs import rhs
+    s = setup
+    r = s["g"].rhs_explicit(s["qg"]).cpu().numpy()
+    for ex0, ey0 in WINDOWS:
+        sub, qs = window(s["case"].mesh, s["q0"], ex0, ey0, W)
+        margin = 1
+        gi, wi = window_nodes(s["case"].mesh, ex0, ey0, W, margin)
+        rr = rhs(sub, Column(sub), qs)
+        e = rel_l2(r[:, gi], rr[:, wi])
+        assert np.all(e <= 1e-11), (ex0, ey0, e)
+    assert s["g"].count_nonfinite(s["qg"]) == 0
+
+
+def test_solve_sampled(setup):
+    from oracle.column import lu_nopivot_banded, lu_solve_banded
+    s = setup
+    torch = s["torch"]
+    m, col = s["case"].mesh, s["case"].col
+    lam = (1 - 1 / np.sqrt(2)) * s["dt"]
+    LU = lu_nopivot_banded(col.jacobian_by_probing(lam), col.half_band)
+    b = s["rng"].standard_normal(m.ncol * m.M)
+    x = s["g"].solve_columns(torch.from_numpy(b).cuda()).cpu().numpy().reshape(m.ncol, m.M)
+    cols = np.r_[0, 1, 383, 384, m.ncol // 2, m.ncol - 1, s["rng"].integers(0, m.ncol, 64)]
+    xr = lu_solve_banded(LU, col.half_band, b.reshape(m.ncol, m.M)[cols])
+    assert np.linalg.norm(x[cols] - xr) <= 1e-12 * np.linalg.norm(xr)
+
+
+def test_full_step_sampled(setup):
+    from oracle import ark2
+    from oracle.column import Column
+    s = setup
+    out = s["g"].step_imex1d(s["qg"], s["g"].empty_state(), 1).cpu().numpy()
+    for ex0, ey0 in WINDOWS:
+        sub, qs = window(s["case"].mesh, s["q0"], ex0, ey0, W)
+        ref = ark2.HEVI(sub, Column(sub), s["dt"]).step(qs, 1)
+        margin = 3
+        # windows touching the real walls are exact up to the wall itself
+        gi, wi = window_nodes(s["case"].mesh, ex0, ey0, W, margin)
+        e = rel_l2(out[:, gi], ref[:, wi])
+        assert np.all(e <= 1e-9), (ex0, ey0, e)
+
+
+def test_rk35_step_sampled(setup):
+    """One RK35 step has five RHS evaluations: an 11 x 11 window, margin 5."""
+    from oracle import rk35
+    from oracle.column import Column
+    s = setup
+    dt1 = s["case"].dt_for(1.0)
+    out = s["g"].step_explicit_rk(s["qg"], dt1, s["g"].empty_state(), 1).cpu().numpy()
+    sub, qs = window(s["case"].mesh, s["q0"], 40, 40, 11)
+    ref = rk35.Explicit(sub, Column(sub)).step(qs, dt1, 1)
+    gi, wi = window_nodes(s["case"].mesh, 40, 40, 11, 5)
+    e = rel_l2(out[:, gi], ref[:, wi])
+    assert np.all(e <= 1e-9), e

@@ -25,8 +25,18 @@ def _lattice(m):
 def test_rest_state_gives_zero():
     m, col = _setup()
     R = rhs(m, col, np.zeros((5, m.nnode)))
-    assert np.abs(R[0]).max() == 0.0 and np.abs(R[4]).max() == 0.0
-    assert np.abs(R[1:4]).max() < 1e-11        # only round-off of P(rho0,theta0) - P0
+    assert np.abs(R).max() == 0.0               # P' = 0 exactly at rest
+
+
+def test_pressure_perturbation_is_the_eos_difference():
+    from oracle.reference import pressure, pressure_perturbation
+    m, col = _setup()
+    rng = np.random.default_rng(4)
+    rp = 1e-2 * rng.standard_normal(m.M) * col.rho0
+    tp = 2.0 * rng.standard_normal(m.M)
+    direct = pressure(col.rho0 + rp, col.theta0 + tp) - col.P0
+    stable = pressure_perturbation(rp, tp, col.rho0, col.theta0, col.P0)
+    np.testing.assert_allclose(stable, direct, rtol=1e-9, atol=1e-9)
 
 
 def test_balanced_state_gives_pure_buoyancy():
@@ -71,6 +81,11 @@ def test_polynomial_velocity_field_is_exact():
     np.testing.assert_allclose(R[3][~mz], Rw[~mz], rtol=1e-8, atol=1e-12)
     np.testing.assert_allclose(R[4], -w * dth0, rtol=1e-9, atol=1e-16)
     assert np.all(R[1][mx] == 0) and np.all(R[2][my] == 0) and np.all(R[3][mz] == 0)
+
+
+def test_isentropic_reference_gradient_is_zero():
+    m, col = _setup()
+    assert np.all(col.dtheta0 == 0.0)
 
 
 def test_pressure_gradient_against_finite_differences():
