@@ -1,0 +1,57 @@
+"""Small-case driver for Nsight Compute captures of the library's kernels.
+
+Runs ``--steps`` HEVI 1D-IMEX ARK2 steps (and optionally RK35 steps) of the benchmark's
+workload shape on a smaller box: ``--nex`` x ``--nex`` x 12 elements of order 4 over
+(2.083 km * nex)^2 x 15 km, the same element size as the benchmark.  The default nex = 72
+gives a 164 MB state (larger than the 129 MB L2) and about 1.7 GB of device memory.
+Every step reads the same input and writes a separate output.
+
+  python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0]
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nex", type=int, default=72)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--rk", type=int, default=0)
+    ap.add_argument("--C", type=float, default=15.0)
+    a = ap.parse_args()
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    import synthetic
+
+    nex, nez, N = a.nex, 12, 4
+    L, Lz = 200e3 / 96 * nex, 15e3
+    xi = np.array([-1.0, -np.sqrt(3.0 / 7.0), 0.0, np.sqrt(3.0 / 7.0), 1.0])
+    c_s = (1004.67 / (1004.67 - 287.17) * 287.17 * 300.0) ** 0.5
+    dt = a.C * (xi[1] + 1.0) / 2.0 * (Lz / nez) / c_s
+    g = pkg.Numa(nex, nex, nez, L, L, Lz, N, dt)
+    lev = g.reference_levels()
+    h = L / nex
+    ax = np.concatenate([e * h + (1.0 + xi[:-1]) * h / 2.0 for e in range(nex)] + [[L]])
+    q0 = torch.from_numpy(synthetic.balanced_state(ax, ax, lev["z"], L, L, Lz, lev["rho0"],
+                                                   lev["theta0"], 7)).cuda()
+    q1 = torch.empty_like(q0)
+    for _ in range(a.steps):
+        g.step_imex1d(q0, q1, 1)
+    for _ in range(a.rk):
+        g.step_explicit_rk(q0, dt / a.C, q1, 1)
+    torch.cuda.synchronize()
+    assert g.count_nonfinite(q1) == 0
+    assert g.status() == pkg.NUMA_OK
+    g.close()
+    print("profile_case ok: nex=%d steps=%d rk=%d" % (nex, a.steps, a.rk))
+
+
+if __name__ == "__main__":
+    main()
