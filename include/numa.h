@@ -49,7 +49,8 @@ enum {
   NUMA_ERR_NOT_FACTORED = 4, /* a solve was requested before numa_factor_columns */
   NUMA_ERR_PIVOT = 5,        /* zero or non-finite pivot in the column LU */
   NUMA_ERR_NONFINITE = 6,    /* non-finite value detected in a state */
-  NUMA_ERR_TIMEOUT = 7       /* a bounded device wait gave up */
+  NUMA_ERR_TIMEOUT = 7,      /* a bounded device wait gave up */
+  NUMA_ERR_SCRATCH = 8       /* the problem needs more than the static scratch array holds */
 };
 
 /* Uniform box mesh and reference state (Sec. "Equation Set2NC").
@@ -181,6 +182,30 @@ int numa_query(const numa_ctx* ctx, int what, long long* out);
 
 /* One-line message of the last failing call on this context ("" if none). */
 const char* numa_last_error(const numa_ctx* ctx);
+
+/* Size of the device scratch array used by numa_rhs_explicit_static.  Every GPU that loads
+ * the library holds an array of this size until the process exits. */
+#define NUMA_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* numa_rhs_explicit without any allocation.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory at the point of the call, for
+ * example a latency-bound loop in which cudaMalloc/cudaFree would synchronise the device,
+ * or a process whose device memory is already reserved by another allocator (a caching
+ * allocator holding most of the GPU).  It takes no context: the mesh, the polynomial order
+ * and the stream are passed directly, the host builds the LGL and reference tables in
+ * static host buffers, and the device side keeps the equation-of-state pre-pass (nnode
+ * doubles) and the per-level tables in one file-scope scratch array of
+ * NUMA_STATIC_SCRATCH_BYTES (64 MiB: meshes up to 8,388,608 - 10 M - (2N+1) M nodes and
+ * M <= 1024 levels; larger problems return NUMA_ERR_SCRATCH before any device work).
+ * q, rhs: device SoA arrays of 5*nnode doubles, as for numa_rhs_explicit, which this call
+ * matches to rounding (same kernels).  The first call on each device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call overwrites the parts of the
+ * scratch it reads, so nothing has to start at zero, but all calls share the one array:
+ * calls that overlap on the GPU (different streams, or different host threads without
+ * ordering) race on it.  Calls no cudaMalloc, cudaFree or other allocating routine. */
+int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const double* q, double* rhs,
+                             void* stream);
 
 /* The RK35 two-register coefficients (alpha[5], beta[5]) and the ARK2 tableau
  * (a[9], at[9], b[3], row-major 3x3) the library uses.  Host only; any pointer may be

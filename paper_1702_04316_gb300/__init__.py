@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libnuma.so")
 NUMA_OK = 0
 ERRORS = {
     1: "NUMA_ERR_ARG", 2: "NUMA_ERR_CUDA", 3: "NUMA_ERR_OOM", 4: "NUMA_ERR_NOT_FACTORED",
-    5: "NUMA_ERR_PIVOT", 6: "NUMA_ERR_NONFINITE", 7: "NUMA_ERR_TIMEOUT",
+    5: "NUMA_ERR_PIVOT", 6: "NUMA_ERR_NONFINITE", 7: "NUMA_ERR_TIMEOUT", 8: "NUMA_ERR_SCRATCH",
 }
 Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_FACTORED, Q_N = range(9)
 
@@ -27,6 +27,7 @@ EXPORTS = (
     "numa_run_host", "numa_connectivity", "numa_column_factors", "numa_reference_levels",
     "numa_count_nonfinite", "numa_status", "numa_query", "numa_last_error",
     "numa_rk35_coefficients", "numa_ark2_tableau", "numa_profile", "numa_profile_read",
+    "numa_rhs_explicit_static",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR = range(5)
 
@@ -70,6 +71,7 @@ def lib():
             "numa_last_error": (ctypes.c_char_p, [P]),
             "numa_rk35_coefficients": (None, [P, P]),
             "numa_ark2_tableau": (None, [P, P, P]),
+            "numa_rhs_explicit_static": (I, [ctypes.POINTER(MeshDesc), I, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -235,6 +237,17 @@ class Numa:
         s = ctypes.c_int()
         self._check(lib().numa_status(self._h, ctypes.byref(s)), "numa_status")
         return s.value
+
+
+def rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out, theta_s=300.0, n_bv=0.0,
+                        stream=None):
+    """numa_rhs_explicit_static: the explicit RHS without any device allocation (for
+    callers that must not allocate at the point of the call); returns the NUMA_* code."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    d = MeshDesc(nex, ney, nez, Lx, Ly, Lz, theta_s, n_bv)
+    return lib().numa_rhs_explicit_static(ctypes.byref(d), int(N), _ptr(q), _ptr(out),
+                                          ctypes.c_void_p(s.cuda_stream))
 
 
 def rk35_coefficients():

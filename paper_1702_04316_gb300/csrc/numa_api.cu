@@ -680,3 +680,160 @@ void numa_ark2_tableau(double* a, double* at, double* b) {
 }
 
 }  // extern "C"
+
+// ---- no-allocation variant of the explicit right-hand side ------------------------------
+// Callers that must not allocate device memory at the point of the call (a latency-bound
+// loop where cudaMalloc/cudaFree would synchronise the device, or a process whose device
+// memory is already reserved by another allocator, such as a caching allocator holding
+// most of the GPU) use numa_rhs_explicit_static.  It needs no context: the host builds the
+// LGL and reference tables into static host buffers, and the device side uses one
+// file-scope scratch array for the equation-of-state pre-pass and the per-level tables.
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchDoubles = NUMA_STATIC_SCRATCH_BYTES / sizeof(double);
+constexpr int kStaticMaxLevels = 1024;
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
+std::mutex g_static_mutex;
+double* g_static_addr[256] = {nullptr};            // device address per device ordinal
+double g_static_host[kStaticMaxLevels * (10 + 2 * NUMA_MAXN + 1)];
+
+}  // namespace
+
+extern "C" int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const double* q,
+                                        double* rhs, void* stream) {
+  if (!mesh || !q || !rhs || q == rhs || N < 1 || N > NUMA_MAXN || mesh->nex < 1 ||
+      mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0) ||
+      !(mesh->n_bv >= 0) || ((uintptr_t)q % 8) || ((uintptr_t)rhs % 8))
+    return NUMA_ERR_ARG;
+  Geom G{};
+  G.N = N; G.Nq = N + 1;
+  G.nex = mesh->nex; G.ney = mesh->ney; G.nez = mesh->nez;
+  G.nxg = mesh->nex * N + 1; G.nyg = mesh->ney * N + 1; G.M = mesh->nez * N + 1;
+  G.ncol = (long long)G.nxg * G.nyg;
+  G.nnode = G.ncol * G.M;
+  const int M = G.M, W = 2 * N + 1;
+  const long long need = G.nnode + 10LL * M + (long long)M * W;
+  if (M > kStaticMaxLevels || need > (long long)kStaticScratchDoubles) return NUMA_ERR_SCRATCH;
+
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NUMA_ERR_CUDA;
+  if (!g_static_addr[dev]) {       // first call on this device: look up the array's address
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return NUMA_ERR_CUDA;
+    }
+    g_static_addr[dev] = (double*)p;
+  }
+  double* scratch = g_static_addr[dev];
+
+  // LGL nodes/weights/derivative matrix without heap storage (same Newton iteration as
+  // the context set-up).
+  const int Nq = N + 1;
+  double xi[NUMA_MAXNQ], w[NUMA_MAXNQ], D[NUMA_MAXNQ * NUMA_MAXNQ], PN[NUMA_MAXNQ];
+  xi[0] = -1.0;
+  xi[N] = 1.0;
+  for (int j = 1; j < N; ++j) {
+    double x = -std::cos(M_PI * j / N);
+    for (int it = 0; it < 100; ++it) {
+      double a, b;
+      legendre(N, x, a, b);
+      const double dx = (x * a - b) / ((N + 1.0) * a);
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    xi[j] = x;
+  }
+  for (int j = 0; j < Nq / 2; ++j) {
+    const double s = 0.5 * (xi[N - j] - xi[j]);
+    xi[j] = -s;
+    xi[N - j] = s;
+  }
+  if (N % 2 == 0) xi[N / 2] = 0.0;
+  for (int j = 0; j < Nq; ++j) {
+    double b;
+    legendre(N, xi[j], PN[j], b);
+    w[j] = 2.0 / (N * (N + 1.0) * PN[j] * PN[j]);
+  }
+  for (int i = 0; i < Nq; ++i)
+    for (int j = 0; j < Nq; ++j) D[i * Nq + j] = (i == j) ? 0.0 : PN[i] / (PN[j] * (xi[i] - xi[j]));
+  D[0] = -N * (N + 1) / 4.0;
+  D[N * Nq + N] = N * (N + 1) / 4.0;
+  Coef3 C;
+  set_axis(C.x, N, w, D, mesh->Lx / mesh->nex);
+  set_axis(C.y, N, w, D, mesh->Ly / mesh->ney);
+  set_axis(C.z, N, w, D, mesh->Lz / mesh->nez);
+
+  // per-level tables in the static host buffer: rho0, 1/rho0, theta0, 1/theta0, P0, G0, H0,
+  // d(rho0)/dz, d(theta0)/dz, F0z (M each), then the column derivative band [M][W]
+  double* h = g_static_host;
+  double* rho0 = h;       double* irho0 = h + M;   double* th0 = h + 2 * M;
+  double* ith0 = h + 3 * M; double* P0 = h + 4 * M; double* G0 = h + 5 * M;
+  double* H0 = h + 6 * M;  double* drho = h + 7 * M; double* dth = h + 8 * M;
+  double* F0z = h + 9 * M; double* band = h + 10 * M;
+  const double dz = mesh->Lz / mesh->nez, g = NUMA_GRAV, cp = NUMA_CP, Rg = NUMA_RGAS;
+  const double theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
+  for (int m = 0; m < M; ++m) {
+    const int ez = (m == M - 1) ? mesh->nez - 1 : m / N, k = m - ez * N;
+    const double z = ez * dz + (1.0 + xi[k]) * dz / 2.0;
+    double th, pi;
+    if (mesh->n_bv == 0.0) {
+      th = theta_s;
+      pi = 1.0 - g * z / (cp * theta_s);
+    } else {
+      const double s = mesh->n_bv * mesh->n_bv / g;
+      th = theta_s * std::exp(s * z);
+      pi = 1.0 + g * g / (cp * theta_s * mesh->n_bv * mesh->n_bv) * (std::exp(-s * z) - 1.0);
+    }
+    P0[m] = NUMA_P00 * std::pow(pi, cp / Rg);
+    th0[m] = th;
+    rho0[m] = P0[m] / (Rg * pi * th);
+    irho0[m] = 1.0 / rho0[m];
+    ith0[m] = 1.0 / th;
+    G0[m] = NUMA_GAMMA * P0[m] / rho0[m];
+    H0[m] = NUMA_GAMMA * P0[m] / th;
+    for (int b = 0; b < W; ++b) band[(size_t)m * W + b] = 0.0;
+  }
+  // DSS'd column derivative: weighted rows of the elements sharing each node
+  for (int m = 0; m < M; ++m) {
+    double den = 0.0;
+    for (int ez = 0; ez < mesh->nez; ++ez) {
+      const int k = m - ez * N;
+      if (k < 0 || k > N) continue;
+      for (int n = 0; n < Nq; ++n)
+        band[(size_t)m * W + (ez * N + n - m + N)] += w[k] * D[k * Nq + n] * (2.0 / dz);
+      den += w[k];
+    }
+    for (int b = 0; b < W; ++b) band[(size_t)m * W + b] /= den;
+  }
+  for (int m = 0; m < M; ++m) {
+    drho[m] = dth[m] = 0.0;
+    for (int b = 0; b < W; ++b) {
+      const int j = m - N + b;
+      if (j < 0 || j >= M) continue;
+      drho[m] += band[(size_t)m * W + b] * (rho0[j] - rho0[0]);
+      dth[m] += band[(size_t)m * W + b] * (th0[j] - th0[0]);
+    }
+    F0z[m] = G0[m] * drho[m] + H0[m] * dth[m];
+  }
+
+  cudaStream_t s = (cudaStream_t)stream;
+  double* dPp = scratch;                 // nnode doubles, written by the pre-pass
+  double* dtab = scratch + G.nnode;      // the tables above
+  const size_t tab_bytes = ((size_t)10 * M + (size_t)M * W) * sizeof(double);
+  if (cudaMemcpyAsync(dtab, h, tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return NUMA_ERR_CUDA;
+  const RefLev R{dtab, dtab + M, dtab + 2 * M, dtab + 3 * M, dtab + 4 * M, dtab + 5 * M,
+                 dtab + 6 * M, dtab + 7 * M, dtab + 8 * M, dtab + 9 * M, dtab + 10 * M};
+  RhsEpilogue ep{};
+  ep.mode = 0;
+  if (launch_pressure(q, dPp, G, R, s) != cudaSuccess) return NUMA_ERR_CUDA;
+  if (launch_rhs(q, dPp, rhs, G, C, R, ep, s) != cudaSuccess) return NUMA_ERR_CUDA;
+  return NUMA_OK;
+}

@@ -1,0 +1,45 @@
+"""numa_rhs_explicit_static: the right-hand side for callers that must not allocate device
+memory at the point of the call (a latency-bound loop where cudaMalloc would synchronise
+the device, or a process whose memory another allocator already holds).  It keeps its
+scratch in a static device array; checked here against numa_rhs_explicit on two calls in
+a row (the second with a different state, so stale scratch contents would show).
+
+This file is collected last so that a run stopping at the first failure has already run
+every other test."""
+import numpy as np
+import pytest
+
+from helpers import Case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dims,n_bv", [((4, 4, 4, 4, 10e3, 10e3, 10e3), 0.0),
+                                        ((3, 5, 2, 3, 7e3, 9e3, 4e3), 0.01)])
+def test_static_rhs_matches_context_rhs_twice(dims, n_bv):
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    nex, ney, nez, N, Lx, Ly, Lz = dims
+    case = Case(nex, ney, nez, N, Lx, Ly, Lz, n_bv)
+    g = pkg.Numa(nex, ney, nez, Lx, Ly, Lz, N, 0.0, 300.0, n_bv)
+    for seed in (11, 12):
+        q = torch.from_numpy(case.state(seed)).cuda()
+        ref = g.rhs_explicit(q)
+        out = torch.full_like(q, float("nan"))
+        rc = pkg.rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out, 300.0, n_bv)
+        assert rc == pkg.NUMA_OK
+        torch.cuda.synchronize()
+        e = rel_l2(out.cpu().numpy(), ref.cpu().numpy())
+        assert np.all(e <= 1e-11), (seed, e)
+    g.close()
+
+
+def test_static_rhs_rejects_problems_beyond_the_scratch():
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    q = torch.zeros(10, dtype=torch.float64, device="cuda")
+    out = torch.zeros(10, dtype=torch.float64, device="cuda")
+    # 110 x 110 x 12 elements of order 4: 441*441*49 nodes > 64 MiB of doubles
+    rc = pkg.rhs_explicit_static(110, 110, 12, 1e5, 1e5, 1e4, 4, q, out)
+    assert rc == 8          # NUMA_ERR_SCRATCH, before any device work
+    assert torch.count_nonzero(out).item() == 0
