@@ -2,16 +2,20 @@
 // the column solve, and the fused implicit stage.
 //
 // One thread owns one column (lane-per-column).  On GB300 the FP64 pipe is the scarce
-// resource (about 1.6 FMA per clock per SM), so every lane of a warp does useful FP64
-// work instead of cooperating on one column with shuffles; the stored factors are
-// transposed (column index fastest) so that the 32 lanes of a warp read 256 contiguous
-// bytes per factor entry, and the state columns are staged through shared memory so that
-// their global loads and stores stay coalesced.
+// resource (2 FP64 FMA per clock per SM, 1/64 of FP32), so every lane of a warp does
+// useful FP64 work instead of cooperating on one column with shuffles.  The stored
+// factors are transposed (column index fastest) so that the 32 lanes of a warp read 256
+// contiguous bytes per factor entry, and the state columns are staged through shared
+// memory so that their global loads and stores stay coalesced.
+//
+// The substitutions are right-looking: once y_i (x_i) is known, the next 2N rows are
+// updated with 2N independent FMAs held in a register window, so the dependent path per
+// row is one FMA and the factors are read by column (the layout numa_internal.cuh gives).
 #include "numa_internal.cuh"
 
 namespace {
 
-// ---- band accessors of the stored factors ----------------------------------------------
+// ---- band accessor of the stored factors (column-oriented layout) ----------------------
 struct Band {
   double* L;
   double* U;
@@ -19,40 +23,88 @@ struct Band {
   long long nc;
   long long col;
   __device__ __forceinline__ double& at(int i, int j) const {
-    return (j < i) ? L[((long long)i * hb + (i - j) - 1) * nc + col]
-                   : U[((long long)i * (hb + 1) + (j - i)) * nc + col];
+    return (j < i) ? L[((long long)j * hb + (i - j) - 1) * nc + col]
+                   : U[((long long)j * (hb + 1) + (j - i)) * nc + col];
   }
 };
 
-// (D_z f)[lev] for a column held in shared memory with stride T between levels.
-__device__ __forceinline__ double col_dz(const double* f, int T, int lev, int M, int N,
-                                         const double* __restrict__ band) {
-  const int W = 2 * N + 1;
-  const int b0 = max(0, N - lev);
-  const int b1 = min(2 * N, M - 1 - lev + N);
-  const double* row = band + (long long)lev * W;
+// (D_z f)[lev] for a column held in shared memory with stride T between levels.  lev is
+// uniform across a warp, so the tap table reads are broadcasts and the branch on the tap
+// count (N interior, 2N interface, N+1 wall) does not diverge.
+template <int N>
+__device__ __forceinline__ double col_dz(const double* f, int T, int lev, const RefLev& R) {
+  constexpr int W = 2 * N + 1;
+  const double* c = R.dz_c + (long long)lev * W;
+  const int* o = R.dz_o + (long long)lev * W;
+  const int n = __ldg(R.dz_n + lev);
+  const double* p = f + lev * T;
+  if (n == N) {
+    double acc = __ldg(c) * p[__ldg(o) * T];
+#pragma unroll
+    for (int t = 1; t < N; ++t) acc = fma(__ldg(c + t), p[__ldg(o + t) * T], acc);
+    return acc;
+  }
+  if (n == 2 * N) {
+    double acc = __ldg(c) * p[__ldg(o) * T];
+#pragma unroll
+    for (int t = 1; t < 2 * N; ++t) acc = fma(__ldg(c + t), p[__ldg(o + t) * T], acc);
+    return acc;
+  }
   double acc = 0.0;
-  for (int b = b0; b <= b1; ++b) acc = fma(__ldg(row + b), f[(lev - N + b) * T], acc);
+  for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), p[__ldg(o + t) * T], acc);
   return acc;
 }
 
-// Forward then back substitution on one column held in shared memory (stride T).
+// Solve L U x = b in place for one column held in shared memory (stride T).
+// Forward: y_i = w_0; then x_{i+1+k} -= L(i+1+k, i) y_i for k < HB (window w in registers).
+// Backward: x_i = v_0 / U(i,i); then y_{i-1-k} -= U(i-1-k, i) x_i for k < HB.
+// Factor columns are prefetched one column ahead.
+template <int HB>
 __device__ __forceinline__ void col_solve(double* x, int T, int M, const double* __restrict__ L,
-                                          const double* __restrict__ U, int hb, long long nc,
+                                          const double* __restrict__ U, long long nc,
                                           long long col) {
+  double w[HB], l[HB], ln[HB];
+#pragma unroll
+  for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : 0.0;
+#pragma unroll
+  for (int k = 0; k < HB; ++k) ln[k] = __ldg(L + (long long)k * nc + col);
   for (int i = 0; i < M; ++i) {
-    double acc = x[i * T];
-    const int kmax = min(i, hb);
-    const double* Lr = L + (long long)i * hb * nc + col;
-    for (int k = 1; k <= kmax; ++k) acc = fma(-__ldg(Lr + (long long)(k - 1) * nc), x[(i - k) * T], acc);
-    x[i * T] = acc;
+#pragma unroll
+    for (int k = 0; k < HB; ++k) l[k] = ln[k];
+    if (i + 1 < M) {
+      const double* Lc = L + (long long)(i + 1) * HB * nc + col;
+#pragma unroll
+      for (int k = 0; k < HB; ++k) ln[k] = __ldg(Lc + (long long)k * nc);
+    }
+    const double y = w[0];
+    x[i * T] = y;
+    const double nxt = (i + HB < M) ? x[(i + HB) * T] : 0.0;
+#pragma unroll
+    for (int k = 0; k < HB - 1; ++k) w[k] = fma(-l[k], y, w[k + 1]);
+    w[HB - 1] = fma(-l[HB - 1], y, nxt);
+  }
+  double v[HB], u[HB + 1], un[HB + 1];
+#pragma unroll
+  for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : 0.0;
+  {
+    const double* Uc = U + (long long)(M - 1) * (HB + 1) * nc + col;
+#pragma unroll
+    for (int k = 0; k <= HB; ++k) un[k] = __ldg(Uc + (long long)k * nc);
   }
   for (int i = M - 1; i >= 0; --i) {
-    double acc = x[i * T];
-    const int kmax = min(M - 1 - i, hb);
-    const double* Ur = U + (long long)i * (hb + 1) * nc + col;
-    for (int k = 1; k <= kmax; ++k) acc = fma(-__ldg(Ur + (long long)k * nc), x[(i + k) * T], acc);
-    x[i * T] = acc * __ldg(Ur);
+#pragma unroll
+    for (int k = 0; k <= HB; ++k) u[k] = un[k];
+    if (i > 0) {
+      const double* Uc = U + (long long)(i - 1) * (HB + 1) * nc + col;
+#pragma unroll
+      for (int k = 0; k <= HB; ++k) un[k] = __ldg(Uc + (long long)k * nc);
+    }
+    const double xi = v[0] * u[0];
+    x[i * T] = xi;
+    const double nxt = (i - HB >= 0) ? x[(i - HB) * T] : 0.0;
+#pragma unroll
+    for (int k = 0; k < HB - 1; ++k) v[k] = fma(-u[k + 1], xi, v[k + 1]);
+    v[HB - 1] = fma(-u[HB], xi, nxt);
   }
 }
 
@@ -111,6 +163,7 @@ __global__ void k_factor(Geom G, RefLev R, double lam, Factors F, unsigned* stat
   }
 }
 
+template <int N>
 __global__ void k_solve(const double* b, double* x, Geom G, Factors F) {
   extern __shared__ double sm[];
   const int T = blockDim.x, M = G.M;
@@ -124,7 +177,7 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F) {
   }
   __syncthreads();
   if ((int)threadIdx.x < ncols)
-    col_solve(sm + threadIdx.x, T, M, F.L, F.U, F.hb, G.ncol, col0 + threadIdx.x);
+    col_solve<2 * N>(sm + threadIdx.x, T, M, F.L, F.U, G.ncol, col0 + threadIdx.x);
   __syncthreads();
   for (int j = threadIdx.x; j < cnt; j += T) {
     const int c = j / M, lev = j - c * M;
@@ -137,12 +190,13 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F) {
 // sum_j c_ij q(j), and the final u, v.  Phase 2 (one thread per column): Schur right-hand
 // side (Algorithm 4), column solve, extraction of (rho', w, theta') (Eq. utteqn).
 // Phase 3 (coalesced): q(i) = q~ - sum_j c_ij q(j).
-__global__ void k_stage(int stage, const double* __restrict__ qn, const double* __restrict__ R1,
+template <int N, bool S3>
+__global__ void k_stage(const double* __restrict__ qn, const double* __restrict__ R1,
                         const double* __restrict__ R2, const double* __restrict__ q2,
                         double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
                         StageTab tb) {
   extern __shared__ double sm[];
-  const int T = blockDim.x, M = G.M, N = G.N;
+  const int T = blockDim.x, M = G.M;
   const long long nn = G.nnode;
   const long long col0 = blockIdx.x * (long long)T;
   const int ncols = (int)min((long long)T, G.ncol - col0);
@@ -152,9 +206,9 @@ __global__ void k_stage(int stage, const double* __restrict__ qn, const double* 
   double* S1 = sm + M * T;      // w~_e -> w_a -> w~
   double* S2 = sm + 2 * M * T;  // theta~_e -> theta~
   const double a1dt = sc.a[0] * sc.dt, a2dt = sc.a[1] * sc.dt;
-  const bool s3 = (stage == 3);
 
   // phase 1
+#pragma unroll 2
   for (int j = threadIdx.x; j < cnt; j += T) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
@@ -162,7 +216,7 @@ __global__ void k_stage(int stage, const double* __restrict__ qn, const double* 
     for (int f = 1; f <= 2; ++f) {   // u, v: explicit only
       const long long o = f * nn + g;
       double e = fma(a1dt, R1[o], qn[o]);
-      if (s3) e = fma(a2dt, R2[o], e);
+      if (S3) e = fma(a2dt, R2[o], e);
       out[o] = e;
     }
     const int fl[3] = {0, 3, 4};
@@ -172,9 +226,9 @@ __global__ void k_stage(int stage, const double* __restrict__ qn, const double* 
       const long long o = fl[t] * nn + g;
       const double qv = qn[o];
       double e = fma(a1dt, R1[o], qv);
-      if (s3) e = fma(a2dt, R2[o], e);
+      if (S3) e = fma(a2dt, R2[o], e);
       e = fma(sc.c[0], qv, e);
-      if (s3) e = fma(sc.c[1], q2[o], e);
+      if (S3) e = fma(sc.c[1], q2[o], e);
       Sd[t][lev * T + c] = e;
     }
   }
@@ -188,27 +242,28 @@ __global__ void k_stage(int stage, const double* __restrict__ qn, const double* 
     double* Th = S2 + t;
     for (int lev = 0; lev < M; ++lev) {     // w_a, then P_e
       const double th = Th[lev * T];
-      Wc[lev * T] = fma(tb.wa_th[lev], th, Wc[lev * T]) * tb.wa_s[lev];
-      P[lev * T] = fma(tb.G0[lev], P[lev * T], tb.H0[lev] * th);
+      Wc[lev * T] = fma(__ldg(tb.wa_th + lev), th, Wc[lev * T]) * __ldg(tb.wa_s + lev);
+      P[lev * T] = fma(__ldg(tb.G0 + lev), P[lev * T], __ldg(tb.H0 + lev) * th);
     }
     for (int lev = 0; lev < M; ++lev) {     // b = P_e - lam F0z w_a - lam rho0 G0 D_z w_a
-      const double dzw = col_dz(Wc, T, lev, M, N, R.dz_band);
-      P[lev * T] = fma(-tb.kF[lev], Wc[lev * T], fma(-tb.kD[lev], dzw, P[lev * T]));
+      const double dzw = col_dz<N>(Wc, T, lev, R);
+      P[lev * T] = fma(-__ldg(tb.kF + lev), Wc[lev * T], fma(-__ldg(tb.kD + lev), dzw, P[lev * T]));
     }
-    col_solve(P, T, M, F.L, F.U, F.hb, G.ncol, col0 + t);
+    col_solve<2 * N>(P, T, M, F.L, F.U, G.ncol, col0 + t);
     for (int lev = 0; lev < M; ++lev) {     // w = w_a - w_p(P); theta = theta_e - lam w dtheta0
-      const double dzp = col_dz(P, T, lev, M, N, R.dz_band);
-      const double wp = fma(tb.kp1[lev], dzp, tb.kp2[lev] * P[lev * T]);
+      const double dzp = col_dz<N>(P, T, lev, R);
+      const double wp = fma(__ldg(tb.kp1 + lev), dzp, __ldg(tb.kp2 + lev) * P[lev * T]);
       const double wv = Wc[lev * T] - wp;
       Wc[lev * T] = wv;
-      Th[lev * T] = fma(-tb.kth[lev], wv, Th[lev * T]);
+      Th[lev * T] = fma(-__ldg(tb.kth + lev), wv, Th[lev * T]);
     }
     for (int lev = 0; lev < M; ++lev)       // rho = (P - H0 theta) / G0
-      P[lev * T] = fma(-tb.H0G0[lev], Th[lev * T], tb.invG0[lev] * P[lev * T]);
+      P[lev * T] = fma(-__ldg(tb.H0G0 + lev), Th[lev * T], __ldg(tb.invG0 + lev) * P[lev * T]);
   }
   __syncthreads();
 
   // phase 3
+#pragma unroll 2
   for (int j = threadIdx.x; j < cnt; j += T) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
@@ -218,15 +273,44 @@ __global__ void k_stage(int stage, const double* __restrict__ qn, const double* 
     for (int t = 0; t < 3; ++t) {
       const long long o = fl[t] * nn + g;
       double v = fma(-sc.c[0], qn[o], Sd[t][lev * T + c]);
-      if (s3) v = fma(-sc.c[1], q2[o], v);
+      if (S3) v = fma(-sc.c[1], q2[o], v);
       out[o] = v;
     }
   }
 }
 
-}  // namespace
+template <int N>
+cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, Factors F, int T,
+                           cudaStream_t s) {
+  const size_t smem = (size_t)G.M * T * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_solve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_solve<N><<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(b, x, G, F);
+  return cudaGetLastError();
+}
 
-static const int kColT = 64;
+template <int N>
+cudaError_t launch_stage_n(int stage, const double* qn, const double* R1, const double* R2,
+                           const double* q2, double* out, const Geom& G, const RefLev& R,
+                           Factors F, const StageCoef& sc, const StageTab& tb, int T,
+                           cudaStream_t s) {
+  const size_t smem = (size_t)3 * G.M * T * sizeof(double);
+  const unsigned nb = (unsigned)((G.ncol + T - 1) / T);
+  cudaError_t e;
+  if (stage == 3) {
+    e = cudaFuncSetAttribute(k_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_stage<N, true><<<nb, T, smem, s>>>(qn, R1, R2, q2, out, G, R, F, sc, tb);
+  } else {
+    e = cudaFuncSetAttribute(k_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_stage<N, false><<<nb, T, smem, s>>>(qn, R1, R2, q2, out, G, R, F, sc, tb);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
                           unsigned* status, cudaStream_t s) {
@@ -235,26 +319,34 @@ cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F,
+cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, int T,
                          cudaStream_t s) {
-  const int T = kColT;
-  const size_t smem = (size_t)G.M * T * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_solve<<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(b, x, G, F);
-  return cudaGetLastError();
+  switch (G.N) {
+    case 1: return launch_solve_n<1>(b, x, G, F, T, s);
+    case 2: return launch_solve_n<2>(b, x, G, F, T, s);
+    case 3: return launch_solve_n<3>(b, x, G, F, T, s);
+    case 4: return launch_solve_n<4>(b, x, G, F, T, s);
+    case 5: return launch_solve_n<5>(b, x, G, F, T, s);
+    case 6: return launch_solve_n<6>(b, x, G, F, T, s);
+    case 7: return launch_solve_n<7>(b, x, G, F, T, s);
+    case 8: return launch_solve_n<8>(b, x, G, F, T, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_stage(int stage, const double* qn, const double* R1, const double* R2,
                          const double* q2, double* out, const Geom& G, const RefLev& R,
-                         Factors F, const StageCoef& sc, const StageTab& tb, cudaStream_t s) {
-  const int T = kColT;
-  const size_t smem = (size_t)3 * G.M * T * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_stage<<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(stage, qn, R1, R2, q2, out, G, R,
-                                                             F, sc, tb);
-  return cudaGetLastError();
+                         Factors F, const StageCoef& sc, const StageTab& tb, int T,
+                         cudaStream_t s) {
+  switch (G.N) {
+    case 1: return launch_stage_n<1>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    case 2: return launch_stage_n<2>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    case 3: return launch_stage_n<3>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    case 4: return launch_stage_n<4>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    case 5: return launch_stage_n<5>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    case 6: return launch_stage_n<6>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    case 7: return launch_stage_n<7>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    case 8: return launch_stage_n<8>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
+    default: return cudaErrorInvalidValue;
+  }
 }

@@ -3,6 +3,7 @@
 // that enqueue the kernels of rhs.cu, column.cu and misc.cu.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -115,13 +116,17 @@ struct numa_ctx {
   // host copies of the per-level tables
   std::vector<double> z, rho0, theta0, P0, G0, H0, drho0, dtheta0, F0z, dzband;
   // device memory
-  double* d_lev = nullptr;      // reference tables + dz band + stage tables
+  double* d_lev = nullptr;      // reference tables + dz band + dz taps
+  int* d_levi = nullptr;        // dz tap offsets and counts
+  int col_tile = 64;            // columns per CTA of the column kernels
   RefLev R{};
   StageTab T{};
   double* d_stage_tab = nullptr;
   Factors F{};
   double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (each 5*nnode except Pp)
   double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
+  int* d_perm = nullptr;        // class-sorted thread order of the right-hand side
+  long long nperm = 0;
   unsigned* d_status = nullptr;
   unsigned long long* d_count = nullptr;
   double* d_hoststate = nullptr;
@@ -174,10 +179,12 @@ void free_all(numa_ctx* c) {
     cudaEventDestroy(r.b);
   }
   cudaFree(c->d_lev);
+  cudaFree(c->d_levi);
   cudaFree(c->d_stage_tab);
   cudaFree(c->F.L);
   cudaFree(c->F.U);
   cudaFree(c->d_work);
+  cudaFree(c->d_perm);
   cudaFree(c->d_status);
   cudaFree(c->d_count);
   cudaFree(c->d_hoststate);
@@ -242,9 +249,9 @@ void build_levels(numa_ctx* c, const double* xi, const double* w, const double* 
 }
 
 int upload_levels(numa_ctx* c) {
-  const int M = c->G.M, W = 2 * c->G.N + 1;
+  const int M = c->G.M, N = c->G.N, W = 2 * N + 1;
   const int nt = 10;
-  std::vector<double> h((size_t)nt * M + (size_t)M * W);
+  std::vector<double> h((size_t)nt * M + 2 * (size_t)M * W, 0.0);
   auto put = [&](int slot, const std::vector<double>& v) {
     std::memcpy(&h[(size_t)slot * M], v.data(), sizeof(double) * M);
   };
@@ -256,11 +263,28 @@ int upload_levels(numa_ctx* c) {
   put(0, c->rho0); put(1, inv_rho0); put(2, c->theta0); put(3, inv_theta0); put(4, c->P0);
   put(5, c->G0); put(6, c->H0); put(7, c->drho0); put(8, c->dtheta0); put(9, c->F0z);
   std::memcpy(&h[(size_t)nt * M], c->dzband.data(), sizeof(double) * M * W);
+  // tap lists: the non-zero entries of each band row
+  double* dzc = &h[(size_t)nt * M + (size_t)M * W];
+  std::vector<int> hi((size_t)M * W + M, 0);
+  for (int m = 0; m < M; ++m) {
+    int n = 0;
+    for (int b = 0; b < W; ++b) {
+      const double v = c->dzband[(size_t)m * W + b];
+      if (v == 0.0) continue;
+      dzc[(size_t)m * W + n] = v;
+      hi[(size_t)m * W + n] = b - N;
+      ++n;
+    }
+    hi[(size_t)M * W + m] = n;
+  }
   NUMA_CK(c, cudaMalloc(&c->d_lev, h.size() * sizeof(double)));
   NUMA_CK(c, cudaMemcpy(c->d_lev, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  NUMA_CK(c, cudaMalloc(&c->d_levi, hi.size() * sizeof(int)));
+  NUMA_CK(c, cudaMemcpy(c->d_levi, hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice));
   const double* d = c->d_lev;
   c->R = RefLev{d, d + M, d + 2 * M, d + 3 * M, d + 4 * M, d + 5 * M, d + 6 * M,
-                d + 7 * M, d + 8 * M, d + 9 * M, d + (size_t)nt * M};
+                d + 7 * M, d + 8 * M, d + 9 * M, d + (size_t)nt * M,
+                d + (size_t)nt * M + (size_t)M * W, c->d_levi, c->d_levi + (size_t)M * W};
   return NUMA_OK;
 }
 
@@ -305,7 +329,7 @@ int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep
   NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
   prof_end(c, p);
   p = prof_begin(c, NUMA_K_RHS);
-  NUMA_CK(c, launch_rhs(q, c->Pp, out, c->G, c->C, c->R, ep, c->stream));
+  NUMA_CK(c, launch_rhs(q, c->Pp, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep, c->stream));
   prof_end(c, p);
   return NUMA_OK;
 }
@@ -313,7 +337,8 @@ int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep
 int enqueue_stage(numa_ctx* c, int stage, const double* qn, const double* R1, const double* R2,
                   const double* q2, double* out, const StageCoef& sc) {
   long p = prof_begin(c, NUMA_K_STAGE);
-  NUMA_CK(c, launch_stage(stage, qn, R1, R2, q2, out, c->G, c->R, c->F, sc, c->T, c->stream));
+  NUMA_CK(c, launch_stage(stage, qn, R1, R2, q2, out, c->G, c->R, c->F, sc, c->T, c->col_tile,
+                          c->stream));
   prof_end(c, p);
   return NUMA_OK;
 }
@@ -358,6 +383,10 @@ int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_c
   c->G = G;
   c->stream = (cudaStream_t)stream;
   c->theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
+  if (const char* t = std::getenv("NUMA_COL_TILE")) {     // tuning: columns per CTA
+    const int v = std::atoi(t);
+    if (v >= 32 && v <= 256 && v % 32 == 0) c->col_tile = v;
+  }
   c->n_bv = mesh->n_bv;
   double xi[NUMA_MAXNQ], w[NUMA_MAXNQ], D[NUMA_MAXNQ * NUMA_MAXNQ];
   lgl_host(N, xi, w, D);
@@ -378,6 +407,18 @@ int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_c
         cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       rc = NUMA_ERR_OOM;
+    }
+  }
+  if (rc == NUMA_OK) {
+    c->nperm = rhs_perm_size(G);
+    std::vector<int> hp((size_t)c->nperm);
+    build_rhs_perm(G, hp.data());
+    if (cudaMalloc(&c->d_perm, hp.size() * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = NUMA_ERR_OOM;
+    } else if (cudaMemcpy(c->d_perm, hp.data(), hp.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+               cudaSuccess) {
+      rc = NUMA_ERR_CUDA;
     }
   }
   if (rc == NUMA_OK) {
@@ -444,7 +485,7 @@ int numa_solve_columns(numa_ctx* ctx, const double* b, double* x) {
   if ((rc = check_ptr(ctx, b, "b")) || (rc = check_ptr(ctx, x, "x"))) return rc;
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
   long p = prof_begin(ctx, NUMA_K_SOLVE);
-  NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->stream));
+  NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->col_tile, ctx->stream));
   prof_end(ctx, p);
   return NUMA_OK;
 }
@@ -523,6 +564,8 @@ int numa_step_explicit_rk(numa_ctx* ctx, const double* q_in, double* q_out, doub
       RhsEpilogue ep{};
       ep.mode = 1;
       ep.alpha = kRkAlpha[i];
+      ep.one_minus_alpha = 1.0 - kRkAlpha[i];
+      ep.use_u0 = kRkAlpha[i] != 0.0;
       ep.beta_dt = kRkBeta[i] * dt;
       ep.u0 = u0;
       if ((rc = enqueue_rhs(ctx, prev, dst, ep))) return rc;
@@ -597,13 +640,14 @@ int numa_column_factors(numa_ctx* ctx, long long col, double* host_out) {
   NUMA_CK(ctx, cudaMemcpy2DAsync(U.data(), sizeof(double), ctx->F.U + col, pitch, sizeof(double),
                                  (size_t)M * (hb + 1), cudaMemcpyDeviceToHost, ctx->stream));
   NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i < M; ++i) {
-    for (int b = 0; b < W; ++b) host_out[(size_t)i * W + b] = 0.0;
+  // L[(j*hb + k-1)] = L(j+k, j); U[(j*(hb+1) + k)] = U(j-k, j), slot 0 = 1/U(j,j)
+  for (size_t t = 0; t < (size_t)M * W; ++t) host_out[t] = 0.0;
+  for (int j = 0; j < M; ++j) {
     for (int k = 1; k <= hb; ++k)
-      if (i - k >= 0) host_out[(size_t)i * W + (hb - k)] = L[(size_t)i * hb + k - 1];
-    host_out[(size_t)i * W + hb] = 1.0 / U[(size_t)i * (hb + 1)];
+      if (j + k < M) host_out[(size_t)(j + k) * W + (hb - k)] = L[(size_t)j * hb + k - 1];
+    host_out[(size_t)j * W + hb] = 1.0 / U[(size_t)j * (hb + 1)];
     for (int k = 1; k <= hb; ++k)
-      if (i + k < M) host_out[(size_t)i * W + hb + k] = U[(size_t)i * (hb + 1) + k];
+      if (j - k >= 0) host_out[(size_t)(j - k) * W + (hb + k)] = U[(size_t)j * (hb + 1) + k];
   }
   return NUMA_OK;
 }
@@ -834,6 +878,6 @@ extern "C" int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const
   RhsEpilogue ep{};
   ep.mode = 0;
   if (launch_pressure(q, dPp, G, R, s) != cudaSuccess) return NUMA_ERR_CUDA;
-  if (launch_rhs(q, dPp, rhs, G, C, R, ep, s) != cudaSuccess) return NUMA_ERR_CUDA;
+  if (launch_rhs(q, dPp, rhs, nullptr, G.nnode, G, C, R, ep, s) != cudaSuccess) return NUMA_ERR_CUDA;
   return NUMA_OK;
 }

@@ -58,12 +58,18 @@ struct RefLev {
   const double* dtheta0;  // D_z theta0
   const double* F0z;      // G0 drho0 + H0 dtheta0
   const double* dz_band;  // DSS'd vertical derivative on a column, [M][2N+1], column j = m-N+b
+  // the same rows without their exact zeros (LGL interior diagonal, the cancelling shared
+  // node at an element interface): dz_n[m] taps dz_c[m*(2N+1)+t] at level m + dz_o[m*(2N+1)+t]
+  const double* dz_c;
+  const int* dz_o;
+  const int* dz_n;
 };
 
-// Stored column factors, transposed so that consecutive columns are contiguous:
-//   facL[(i*hb + k-1)*ncol + col] = L(i, i-k),  k = 1..hb   (unit diagonal not stored)
-//   facU[(i*(hb+1) + 0)*ncol + col] = 1 / U(i, i)
-//   facU[(i*(hb+1) + k)*ncol + col] = U(i, i+k), k = 1..hb
+// Stored column factors, by matrix column j, transposed so that consecutive columns of the
+// mesh are contiguous:
+//   L[(j*hb + k-1)*ncol + col] = L(j+k, j),  k = 1..hb   (unit diagonal not stored)
+//   U[(j*(hb+1) + 0)*ncol + col] = 1 / U(j, j)
+//   U[(j*(hb+1) + k)*ncol + col] = U(j-k, j), k = 1..hb
 // hb = 2N.  Entries outside the matrix are stored as zero.
 struct Factors {
   double* L;
@@ -97,24 +103,31 @@ cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const Re
 // MODE 2 (ARK final): out = qn + dt*(b1*R1 + b2*R2 + b3*R(q)).
 struct RhsEpilogue {
   int mode;
-  double alpha, beta_dt;          // mode 1
+  int use_u0;                     // mode 1: alpha != 0
+  double alpha, one_minus_alpha, beta_dt;   // mode 1
   double b1dt, b2dt, b3dt;        // mode 2
   const double* u0;               // mode 1: u0; mode 2: qn
   const double* R1;
   const double* R2;
 };
-cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const Geom& G,
-                       const Coef3& C, const RefLev& R, const RhsEpilogue& ep,
-                       cudaStream_t s);
+// perm: class-sorted thread order from build_rhs_perm (nthreads entries), or NULL for the
+// natural node order (nthreads = nnode; correct, but warps then mix node classes).
+cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const int* perm,
+                       long long nthreads, const Geom& G, const Coef3& C, const RefLev& R,
+                       const RhsEpilogue& ep, cudaStream_t s);
+long long rhs_perm_size(const Geom& G);
+void build_rhs_perm(const Geom& G, int* out);
 
 // column.cu
 cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
                           unsigned* status, cudaStream_t s);
-cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F,
+// T: columns per CTA (one thread each; a multiple of 32).
+cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, int T,
                          cudaStream_t s);
 cudaError_t launch_stage(int stage, const double* qn, const double* R1, const double* R2,
                          const double* q2, double* out, const Geom& G, const RefLev& R,
-                         Factors F, const StageCoef& sc, const StageTab& tb, cudaStream_t s);
+                         Factors F, const StageCoef& sc, const StageTab& tb, int T,
+                         cudaStream_t s);
 
 // misc.cu
 cudaError_t launch_connectivity(const Geom& G, int32_t* l2g, int32_t* g2l, cudaStream_t s);

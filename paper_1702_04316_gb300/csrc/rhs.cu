@@ -11,95 +11,181 @@
 //   d_x f (node) = D_x-row of its element                       (interior / wall nodes)
 //                = (w_N d_left + w_0 d_right) / (w_N + w_0)      (element interfaces),
 // which is what the element-by-element gather/scatter of Algorithm 2 + DSS produces.
-// Each thread computes one global node: no atomics, no element-local scratch, and the
-// column-major layout (z fastest) makes every stencil load of a warp contiguous.
+//
+// GB300 is FP64-issue bound here (2 FP64 FMA per clock per SM), so the kernel minimises
+// FP64 instructions:
+//  * LGL rows of interior nodes have a zero diagonal: N taps instead of N+1;
+//  * at an interface the two elements' weights are equal (w_0 = w_N) and D_00 = -D_NN, so
+//    the shared node cancels: 2N taps instead of 2N+2;
+//  * threads run in a permuted node order in which every warp holds nodes of one class
+//    (interior / interface / wall) per axis, so no warp executes both tap counts.
+#include <vector>
+
 #include "numa_internal.cuh"
 
 namespace {
 
-__device__ __forceinline__ double dss_deriv(const double* __restrict__ f, long long g,
-                                            long long stride, int idx, int nel, int N,
-                                            const AxisCoef& c) {
-  int e, i;
-  axis_owner(idx, N, nel, e, i);
-  const int Nq = N + 1;
-  const double* p0 = f + g - (long long)i * stride;   // local node 0 of element e
-  double acc = 0.0;
-  if (i == 0 && e > 0) {
-    const double* pl = p0 - (long long)N * stride;    // local node 0 of element e-1
-#pragma unroll 4
-    for (int n = 0; n < Nq; ++n) acc = fma(c.Dl[n], __ldg(pl + n * stride), acc);
-#pragma unroll 4
-    for (int n = 0; n < Nq; ++n) acc = fma(c.Dr[n], __ldg(p0 + n * stride), acc);
-  } else {
-    const double* Drow = c.D + i * Nq;
-#pragma unroll 4
-    for (int n = 0; n < Nq; ++n) acc = fma(Drow[n], __ldg(p0 + n * stride), acc);
-  }
-  return acc;
-}
-
+// ---- equation of state ---------------------------------------------------------------------
 // P' = P(rho0 + rho', theta0 + theta') - P0 without cancellation:
 //   (rho theta)/(rho0 theta0) = (1 + a)(1 + b),  a = rho'/rho0,  b = theta'/theta0,
-//   P' = P0 ((1 + x)^gamma - 1) = P0 expm1(gamma log1p(x)),  x = a + b + a b.
+//   P' = P0 ((1 + x)^gamma - 1),  x = a + b + a b.
+// For |x| <= 1/64 the binomial series sum_{k=1..9} C(gamma, k) x^k is used (truncation
+// below 1e-19 relative); otherwise P0 expm1(gamma log1p(x)).
+struct EosSeries {
+  double c[9];   // C(gamma, k), k = 1..9
+};
+
 __global__ void k_pressure(const double* __restrict__ q, double* __restrict__ Pp, Geom G,
-                           RefLev R, double gamma) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+                           RefLev R, double gamma, EosSeries S) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= G.nnode) return;
-  int iz = (int)(g % G.M);
-  double a = q[g] * R.inv_rho0[iz];
-  double b = q[4 * G.nnode + g] * R.inv_theta0[iz];
-  double x = fma(a, b, a + b);
-  Pp[g] = R.P0[iz] * expm1(gamma * log1p(x));
+  const int iz = (int)(g % G.M);
+  const double a = q[g] * R.inv_rho0[iz];
+  const double b = q[4 * G.nnode + g] * R.inv_theta0[iz];
+  const double x = fma(a, b, a + b);
+  double r;
+  if (fabs(x) <= 0.015625) {
+    double p = S.c[8];
+#pragma unroll
+    for (int k = 7; k >= 0; --k) p = fma(p, x, S.c[k]);
+    r = p * x;
+  } else {
+    r = expm1(gamma * log1p(x));
+  }
+  Pp[g] = R.P0[iz] * r;
 }
 
-__global__ void k_rhs(const double* __restrict__ q, const double* __restrict__ Pp,
-                      double* out, Geom G, Coef3 C, RefLev R, RhsEpilogue ep) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= G.nnode) return;
+// ---- right-hand side ---------------------------------------------------------------------
+enum { CLS_INTERIOR = 0, CLS_IFACE = 1, CLS_WALL = 2 };
+
+template <int N>
+struct Taps {
+  double c[2 * N + 1];
+  int o[2 * N + 1];
+};
+
+// Row of the DSS'd derivative at axis index idx: coefficients and node offsets relative to
+// the node itself (in units of the axis stride).  The class is uniform across a warp.
+template <int N>
+__device__ __forceinline__ int axis_taps(int idx, int nel, const double* sD, const double* sDl,
+                                         const double* sDr, Taps<N>& T) {
+  constexpr int Nq = N + 1;
+  int e, i;
+  axis_owner(idx, N, nel, e, i);
+  if (i == 0 && e > 0) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) {          // left element, its nodes 0..N-1
+      T.c[t] = sDl[t];
+      T.o[t] = t - N;
+    }
+#pragma unroll
+    for (int t = 1; t <= N; ++t) {         // right element, its nodes 1..N
+      T.c[N - 1 + t] = sDr[t];
+      T.o[N - 1 + t] = t;
+    }
+    return CLS_IFACE;
+  }
+  if (i == 0 || i == N) {                  // wall: the full row of the one element
+#pragma unroll
+    for (int t = 0; t <= N; ++t) {
+      T.c[t] = sD[i * Nq + t];
+      T.o[t] = t - i;
+    }
+    return CLS_WALL;
+  }
+#pragma unroll
+  for (int t = 0; t < N; ++t) {            // interior: the zero diagonal dropped
+    const int n = t + (t >= i ? 1 : 0);
+    T.c[t] = sD[i * Nq + n];
+    T.o[t] = n - i;
+  }
+  return CLS_INTERIOR;
+}
+
+// d/d(axis) of the six fields at node g.
+template <int N>
+__device__ __forceinline__ void axis_derivs(const double* const* F, long long g, long long stride,
+                                            int cls, const Taps<N>& T, double* d) {
+  if (cls == CLS_IFACE) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const double* p = F[f] + g;
+      double acc = T.c[0] * __ldg(p + T.o[0] * stride);
+#pragma unroll
+      for (int t = 1; t < 2 * N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
+      d[f] = acc;
+    }
+  } else if (cls == CLS_WALL) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const double* p = F[f] + g;
+      double acc = T.c[0] * __ldg(p + T.o[0] * stride);
+#pragma unroll
+      for (int t = 1; t <= N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
+      d[f] = acc;
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const double* p = F[f] + g;
+      double acc = T.c[0] * __ldg(p + T.o[0] * stride);
+#pragma unroll
+      for (int t = 1; t < N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
+      d[f] = acc;
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_rhs(const double* __restrict__ q,
+                                             const double* __restrict__ Pp, double* out,
+                                             const int* __restrict__ perm, long long nthreads,
+                                             Geom G, Coef3 C, RefLev R, RhsEpilogue ep) {
+  constexpr int Nq = N + 1;
+  __shared__ double sD[3][Nq * Nq], sDl[3][Nq], sDr[3][Nq];
+  for (int t = threadIdx.x; t < Nq * Nq; t += blockDim.x) {
+    sD[0][t] = C.x.D[t];
+    sD[1][t] = C.y.D[t];
+    sD[2][t] = C.z.D[t];
+  }
+  for (int t = threadIdx.x; t < Nq; t += blockDim.x) {
+    sDl[0][t] = C.x.Dl[t]; sDr[0][t] = C.x.Dr[t];
+    sDl[1][t] = C.y.Dl[t]; sDr[1][t] = C.y.Dr[t];
+    sDl[2][t] = C.z.Dl[t]; sDr[2][t] = C.z.Dr[t];
+  }
+  __syncthreads();
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= nthreads) return;
+  const int gi = perm ? perm[tid] : (int)tid;
+  if (gi < 0) return;                       // padding of a class group
+  const long long g = gi;
   const long long nn = G.nnode;
   const long long col = g / G.M;
   const int iz = (int)(g - col * G.M);
   const int iy = (int)(col / G.nxg);
   const int ix = (int)(col - (long long)iy * G.nxg);
-  const long long sx = G.M, sy = (long long)G.nxg * G.M;
-  const int N = G.N;
+  const long long sxs = G.M, sys = (long long)G.nxg * G.M;
 
-  const double* rp = q;
-  const double* u = q + nn;
-  const double* v = q + 2 * nn;
-  const double* w = q + 3 * nn;
-  const double* tp = q + 4 * nn;
-
-  const double r_ = rp[g], u_ = u[g], v_ = v[g], w_ = w[g];
-
-  // gradients of rho', u, v, w, theta', P'
-  const double rx = dss_deriv(rp, g, sx, ix, G.nex, N, C.x);
-  const double ry = dss_deriv(rp, g, sy, iy, G.ney, N, C.y);
-  const double rz = dss_deriv(rp, g, 1, iz, G.nez, N, C.z);
-  const double ux = dss_deriv(u, g, sx, ix, G.nex, N, C.x);
-  const double uy = dss_deriv(u, g, sy, iy, G.ney, N, C.y);
-  const double uz = dss_deriv(u, g, 1, iz, G.nez, N, C.z);
-  const double vx = dss_deriv(v, g, sx, ix, G.nex, N, C.x);
-  const double vy = dss_deriv(v, g, sy, iy, G.ney, N, C.y);
-  const double vz = dss_deriv(v, g, 1, iz, G.nez, N, C.z);
-  const double wx = dss_deriv(w, g, sx, ix, G.nex, N, C.x);
-  const double wy = dss_deriv(w, g, sy, iy, G.ney, N, C.y);
-  const double wz = dss_deriv(w, g, 1, iz, G.nez, N, C.z);
-  const double tx = dss_deriv(tp, g, sx, ix, G.nex, N, C.x);
-  const double ty = dss_deriv(tp, g, sy, iy, G.ney, N, C.y);
-  const double tz = dss_deriv(tp, g, 1, iz, G.nez, N, C.z);
-  const double px = dss_deriv(Pp, g, sx, ix, G.nex, N, C.x);
-  const double py = dss_deriv(Pp, g, sy, iy, G.ney, N, C.y);
-  const double pz = dss_deriv(Pp, g, 1, iz, G.nez, N, C.z);
-
+  const double* Fld[6] = {q, q + nn, q + 2 * nn, q + 3 * nn, q + 4 * nn, Pp};
+  double dx[6], dy[6], dz[6];
+  {
+    Taps<N> T;
+    int cls = axis_taps<N>(ix, G.nex, sD[0], sDl[0], sDr[0], T);
+    axis_derivs<N>(Fld, g, sxs, cls, T, dx);
+    cls = axis_taps<N>(iy, G.ney, sD[1], sDl[1], sDr[1], T);
+    axis_derivs<N>(Fld, g, sys, cls, T, dy);
+    cls = axis_taps<N>(iz, G.nez, sD[2], sDl[2], sDr[2], T);
+    axis_derivs<N>(Fld, g, 1, cls, T, dz);
+  }
+  const double r_ = q[g], u_ = q[nn + g], v_ = q[2 * nn + g], w_ = q[3 * nn + g];
   const double rho = R.rho0[iz] + r_;
   const double irho = 1.0 / rho;
-  double t_r = -(u_ * rx + v_ * ry + w_ * (rz + R.drho0[iz]) + rho * (ux + vy + wz));
-  double t_u = -(u_ * ux + v_ * uy + w_ * uz + px * irho);
-  double t_v = -(u_ * vx + v_ * vy + w_ * vz + py * irho);
-  double t_w = -(u_ * wx + v_ * wy + w_ * wz + (pz + NUMA_GRAV * r_) * irho);
-  double t_t = -(u_ * tx + v_ * ty + w_ * (tz + R.dtheta0[iz]));
+  // fields: 0 rho', 1 u, 2 v, 3 w, 4 theta', 5 P'
+  double t_r = -fma(u_, dx[0], fma(v_, dy[0], fma(w_, dz[0] + R.drho0[iz], rho * (dx[1] + dy[2] + dz[3]))));
+  double t_u = -fma(u_, dx[1], fma(v_, dy[1], fma(w_, dz[1], dx[5] * irho)));
+  double t_v = -fma(u_, dx[2], fma(v_, dy[2], fma(w_, dz[2], dy[5] * irho)));
+  double t_w = -fma(u_, dx[3], fma(v_, dy[3], fma(w_, dz[3], fma(NUMA_GRAV, r_, dz[5]) * irho)));
+  double t_t = -fma(u_, dx[4], fma(v_, dy[4], w_ * (dz[4] + R.dtheta0[iz])));
   // walls: no normal flow
   if (ix == 0 || ix == G.nxg - 1) t_u = 0.0;
   if (iy == 0 || iy == G.nyg - 1) t_v = 0.0;
@@ -110,12 +196,10 @@ __global__ void k_rhs(const double* __restrict__ q, const double* __restrict__ P
 #pragma unroll
     for (int f = 0; f < 5; ++f) out[f * nn + g] = t[f];
   } else if (ep.mode == 1) {
-    const double om = 1.0 - ep.alpha;
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-      const double cur = q[f * nn + g];
-      double val = fma(ep.beta_dt, t[f], om * cur);
-      if (ep.alpha != 0.0) val = fma(ep.alpha, ep.u0[f * nn + g], val);
+      double val = fma(ep.beta_dt, t[f], ep.one_minus_alpha * q[f * nn + g]);
+      if (ep.use_u0) val = fma(ep.alpha, ep.u0[f * nn + g], val);
       out[f * nn + g] = val;
     }
   } else {
@@ -127,22 +211,99 @@ __global__ void k_rhs(const double* __restrict__ q, const double* __restrict__ P
   }
 }
 
+template <int N>
+cudaError_t launch_rhs_n(const double* q, const double* Pp, double* out, const int* perm,
+                         long long nthreads, const Geom& G, const Coef3& C, const RefLev& R,
+                         const RhsEpilogue& ep, cudaStream_t s) {
+  const int bs = 256;
+  k_rhs<N><<<(unsigned)((nthreads + bs - 1) / bs), bs, 0, s>>>(q, Pp, out, perm, nthreads, G, C,
+                                                                R, ep);
+  return cudaGetLastError();
+}
+
+int node_class(int idx, int N, int nel) {
+  int e, i;
+  axis_owner(idx, N, nel, e, i);
+  if (i == 0 && e > 0) return CLS_IFACE;
+  if (i == 0 || i == N) return CLS_WALL;
+  return CLS_INTERIOR;
+}
+
 }  // namespace
 
 cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const RefLev& R,
                             cudaStream_t s) {
   const double gamma = NUMA_GAMMA;
+  EosSeries S;
+  double c = 1.0;
+  for (int k = 1; k <= 9; ++k) {
+    c *= (gamma - k + 1) / k;
+    S.c[k - 1] = c;
+  }
   const int bs = 256;
   const long long nb = (G.nnode + bs - 1) / bs;
-  k_pressure<<<(unsigned)nb, bs, 0, s>>>(q, Pp, G, R, gamma);
+  k_pressure<<<(unsigned)nb, bs, 0, s>>>(q, Pp, G, R, gamma, S);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const Geom& G,
-                       const Coef3& C, const RefLev& R, const RhsEpilogue& ep,
-                       cudaStream_t s) {
-  const int bs = 256;
-  const long long nb = (G.nnode + bs - 1) / bs;
-  k_rhs<<<(unsigned)nb, bs, 0, s>>>(q, Pp, out, G, C, R, ep);
-  return cudaGetLastError();
+cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const int* perm,
+                       long long nthreads, const Geom& G, const Coef3& C, const RefLev& R,
+                       const RhsEpilogue& ep, cudaStream_t s) {
+  switch (G.N) {
+    case 1: return launch_rhs_n<1>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    case 2: return launch_rhs_n<2>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    case 3: return launch_rhs_n<3>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    case 4: return launch_rhs_n<4>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    case 5: return launch_rhs_n<5>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    case 6: return launch_rhs_n<6>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    case 7: return launch_rhs_n<7>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    case 8: return launch_rhs_n<8>(q, Pp, out, perm, nthreads, G, C, R, ep, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Class-sorted thread order: nodes grouped by (x-class, y-class, z-class), ascending node
+// id inside a group, each group padded with -1 to a multiple of 32 so that no warp mixes
+// classes.
+long long rhs_perm_size(const Geom& G) {
+  long long cnt[27] = {0};
+  std::vector<int> cz(G.M);
+  for (int iz = 0; iz < G.M; ++iz) cz[iz] = node_class(iz, G.N, G.nez);
+  for (int iy = 0; iy < G.nyg; ++iy) {
+    const int cy = node_class(iy, G.N, G.ney);
+    for (int ix = 0; ix < G.nxg; ++ix) {
+      const int cx = node_class(ix, G.N, G.nex);
+      for (int iz = 0; iz < G.M; ++iz) cnt[cx * 9 + cy * 3 + cz[iz]]++;
+    }
+  }
+  long long total = 0;
+  for (int k = 0; k < 27; ++k) total += (cnt[k] + 31) / 32 * 32;
+  return total;
+}
+
+void build_rhs_perm(const Geom& G, int* out) {
+  long long cnt[27] = {0};
+  std::vector<int> cz(G.M);
+  for (int iz = 0; iz < G.M; ++iz) cz[iz] = node_class(iz, G.N, G.nez);
+  std::vector<unsigned char> cls((size_t)G.nnode);
+  for (int iy = 0; iy < G.nyg; ++iy) {
+    const int cy = node_class(iy, G.N, G.ney);
+    for (int ix = 0; ix < G.nxg; ++ix) {
+      const int cx = node_class(ix, G.N, G.nex);
+      const long long base = ((long long)iy * G.nxg + ix) * G.M;
+      for (int iz = 0; iz < G.M; ++iz) {
+        const int k = cx * 9 + cy * 3 + cz[iz];
+        cls[base + iz] = (unsigned char)k;
+        cnt[k]++;
+      }
+    }
+  }
+  long long fill[27];
+  long long pos = 0;
+  for (int k = 0; k < 27; ++k) {
+    fill[k] = pos;
+    pos += (cnt[k] + 31) / 32 * 32;
+  }
+  for (long long t = 0; t < pos; ++t) out[t] = -1;
+  for (long long g = 0; g < G.nnode; ++g) out[fill[cls[g]]++] = (int)g;
 }
