@@ -39,16 +39,22 @@ __device__ __forceinline__ double col_dz(const double* f, int T, int lev, const 
   const int n = __ldg(R.dz_n + lev);
   const double* p = f + lev * T;
   if (n == N) {
-    double acc = __ldg(c) * p[__ldg(o) * T];
+    double a0 = __ldg(c) * p[__ldg(o) * T], a1 = 0.0;
 #pragma unroll
-    for (int t = 1; t < N; ++t) acc = fma(__ldg(c + t), p[__ldg(o + t) * T], acc);
-    return acc;
+    for (int t = 1; t < N; ++t) {
+      if (t & 1) a1 = fma(__ldg(c + t), p[__ldg(o + t) * T], a1);
+      else a0 = fma(__ldg(c + t), p[__ldg(o + t) * T], a0);
+    }
+    return a0 + a1;
   }
   if (n == 2 * N) {
-    double acc = __ldg(c) * p[__ldg(o) * T];
+    double a0 = __ldg(c) * p[__ldg(o) * T], a1 = __ldg(c + 1) * p[__ldg(o + 1) * T];
 #pragma unroll
-    for (int t = 1; t < 2 * N; ++t) acc = fma(__ldg(c + t), p[__ldg(o + t) * T], acc);
-    return acc;
+    for (int t = 2; t < 2 * N; ++t) {
+      if (t & 1) a1 = fma(__ldg(c + t), p[__ldg(o + t) * T], a1);
+      else a0 = fma(__ldg(c + t), p[__ldg(o + t) * T], a0);
+    }
+    return a0 + a1;
   }
   double acc = 0.0;
   for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), p[__ldg(o + t) * T], acc);

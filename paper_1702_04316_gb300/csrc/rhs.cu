@@ -262,48 +262,50 @@ cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const int
   }
 }
 
-// Class-sorted thread order: nodes grouped by (x-class, y-class, z-class), ascending node
-// id inside a group, each group padded with -1 to a multiple of 32 so that no warp mixes
-// classes.
-long long rhs_perm_size(const Geom& G) {
-  long long cnt[27] = {0};
+// Class-sorted thread order: the (x, y) node plane is cut into tiles of kTile x kTile
+// elements (all levels); inside a tile, nodes are grouped by (x-class, y-class, z-class),
+// ascending node id inside a group, and each group is padded with -1 to a multiple of 32,
+// so that no warp mixes classes while consecutive blocks stay within one tile (its
+// stencil neighbours are still in L2).
+static const int kTile = 4;
+
+template <typename Emit>
+static void walk_rhs_perm(const Geom& G, Emit emit) {
+  const int tn = kTile * G.N;
   std::vector<int> cz(G.M);
   for (int iz = 0; iz < G.M; ++iz) cz[iz] = node_class(iz, G.N, G.nez);
-  for (int iy = 0; iy < G.nyg; ++iy) {
-    const int cy = node_class(iy, G.N, G.ney);
-    for (int ix = 0; ix < G.nxg; ++ix) {
-      const int cx = node_class(ix, G.N, G.nex);
-      for (int iz = 0; iz < G.M; ++iz) cnt[cx * 9 + cy * 3 + cz[iz]]++;
+  std::vector<long long> bucket[27];
+  for (int y0 = 0; y0 < G.nyg; y0 += tn) {
+    const int y1 = (G.nyg - y0 <= tn + 1) ? G.nyg : y0 + tn;   // the last tile takes the end node
+    for (int x0 = 0; x0 < G.nxg; x0 += tn) {
+      const int x1 = (G.nxg - x0 <= tn + 1) ? G.nxg : x0 + tn;
+      for (auto& b : bucket) b.clear();
+      for (int iy = y0; iy < y1; ++iy) {
+        const int cy = node_class(iy, G.N, G.ney);
+        for (int ix = x0; ix < x1; ++ix) {
+          const int cx = node_class(ix, G.N, G.nex);
+          const long long base = ((long long)iy * G.nxg + ix) * G.M;
+          for (int iz = 0; iz < G.M; ++iz) bucket[cx * 9 + cy * 3 + cz[iz]].push_back(base + iz);
+        }
+      }
+      for (auto& b : bucket) {
+        if (b.empty()) continue;
+        for (long long g : b) emit(g);
+        for (size_t p = b.size(); p % 32; ++p) emit(-1);
+      }
+      if (x1 == G.nxg) break;
     }
+    if (y1 == G.nyg) break;
   }
-  long long total = 0;
-  for (int k = 0; k < 27; ++k) total += (cnt[k] + 31) / 32 * 32;
-  return total;
+}
+
+long long rhs_perm_size(const Geom& G) {
+  long long n = 0;
+  walk_rhs_perm(G, [&](long long) { ++n; });
+  return n;
 }
 
 void build_rhs_perm(const Geom& G, int* out) {
-  long long cnt[27] = {0};
-  std::vector<int> cz(G.M);
-  for (int iz = 0; iz < G.M; ++iz) cz[iz] = node_class(iz, G.N, G.nez);
-  std::vector<unsigned char> cls((size_t)G.nnode);
-  for (int iy = 0; iy < G.nyg; ++iy) {
-    const int cy = node_class(iy, G.N, G.ney);
-    for (int ix = 0; ix < G.nxg; ++ix) {
-      const int cx = node_class(ix, G.N, G.nex);
-      const long long base = ((long long)iy * G.nxg + ix) * G.M;
-      for (int iz = 0; iz < G.M; ++iz) {
-        const int k = cx * 9 + cy * 3 + cz[iz];
-        cls[base + iz] = (unsigned char)k;
-        cnt[k]++;
-      }
-    }
-  }
-  long long fill[27];
-  long long pos = 0;
-  for (int k = 0; k < 27; ++k) {
-    fill[k] = pos;
-    pos += (cnt[k] + 31) / 32 * 32;
-  }
-  for (long long t = 0; t < pos; ++t) out[t] = -1;
-  for (long long g = 0; g < G.nnode; ++g) out[fill[cls[g]]++] = (int)g;
+  long long n = 0;
+  walk_rhs_perm(G, [&](long long g) { out[n++] = (int)g; });
 }
