@@ -76,8 +76,23 @@ enum {
   NUMA_Q_FACTOR_BYTES = 5,  /* bytes of stored LU factors */
   NUMA_Q_WORKSPACE_BYTES = 6, /* bytes of step workspace */
   NUMA_Q_FACTORED = 7,      /* 1 once numa_factor_columns succeeded */
-  NUMA_Q_N = 8              /* polynomial order */
+  NUMA_Q_N = 8,             /* polynomial order */
+  NUMA_Q_PRECISION = 9      /* NUMA_PREC_FP64 or NUMA_PREC_MIXED */
 };
+
+/* Options of numa_init_ex.
+ * precision: NUMA_PREC_FP64 (default) -- the method in FP64 throughout;
+ *            NUMA_PREC_MIXED -- the mixed-precision form: the explicit right-hand side in
+ *            FP32 on FP32 copies of the perturbation fields (P' from the equation of state
+ *            and the reference state stay FP64), the column Schur matrices factored and
+ *            solved in FP32 with refine_iters sweeps of FP64 iterative refinement (FP64
+ *            residual with the matrix-free Schur operator), FP64 state accumulation.
+ * refine_iters: FP64 refinement sweeps per solve in the mixed form (0..8; default 2). */
+enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1 };
+typedef struct numa_options {
+  int precision;
+  int refine_iters;
+} numa_options;
 
 /* Create a context: validates the mesh, builds the LGL nodes/weights/derivative matrix
  * (Sec. "Volume kernels": sD), the reference state and its discrete vertical gradients
@@ -86,6 +101,11 @@ enum {
  * stream: a cudaStream_t (NULL = the legacy default stream) used by every later call.
  * Synchronous.  On failure *out is NULL and the code says why (no message is kept). */
 int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_ctx** out);
+
+/* numa_init with options (NULL = the defaults of numa_init).  Every entry point below
+ * follows the context's precision; buffers passed by the caller are FP64 in both. */
+int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_options* opt,
+                 void* stream, numa_ctx** out);
 
 /* Release everything the context owns (synchronises its stream).  NULL is a no-op. */
 void numa_destroy(numa_ctx* ctx);
@@ -164,7 +184,8 @@ int numa_connectivity(numa_ctx* ctx, int32_t* l2g, int32_t* g2l);
 
 /* Copy the stored factors of one column to host memory: M*(4N+1) doubles, row-major
  * [row][band], band index b = j - i + 2N for entry (i, j); the unit diagonal of L is not
- * stored (entries b < 2N hold L, b >= 2N hold U).  Synchronous. */
+ * stored (entries b < 2N hold L, b >= 2N hold U).  The mixed form's FP32 factors are
+ * widened to double.  Synchronous. */
 int numa_column_factors(numa_ctx* ctx, long long col, double* host_out);
 
 /* Host copy of the per-level reference tables, 8*M doubles in the order

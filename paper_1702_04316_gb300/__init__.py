@@ -18,11 +18,13 @@ ERRORS = {
     1: "NUMA_ERR_ARG", 2: "NUMA_ERR_CUDA", 3: "NUMA_ERR_OOM", 4: "NUMA_ERR_NOT_FACTORED",
     5: "NUMA_ERR_PIVOT", 6: "NUMA_ERR_NONFINITE", 7: "NUMA_ERR_TIMEOUT", 8: "NUMA_ERR_SCRATCH",
 }
-Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_FACTORED, Q_N = range(9)
+Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_FACTORED, Q_N, \
+    Q_PRECISION = range(10)
+PRECISIONS = {"fp64": 0, "mixed": 1}
 
 # Every symbol include/numa.h declares (checked by tests/test_abi.py).
 EXPORTS = (
-    "numa_init", "numa_destroy", "numa_set_stream", "numa_rhs_explicit", "numa_factor_columns",
+    "numa_init", "numa_init_ex", "numa_destroy", "numa_set_stream", "numa_rhs_explicit", "numa_factor_columns",
     "numa_solve_columns", "numa_step_imex1d", "numa_imex_stage", "numa_step_explicit_rk",
     "numa_run_host", "numa_connectivity", "numa_column_factors", "numa_reference_levels",
     "numa_count_nonfinite", "numa_status", "numa_query", "numa_last_error",
@@ -30,6 +32,10 @@ EXPORTS = (
     "numa_rhs_explicit_static",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR = range(5)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("refine_iters", ctypes.c_int)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -51,6 +57,8 @@ def lib():
         P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
         sig = {
             "numa_init": (I, [ctypes.POINTER(MeshDesc), I, D, P, ctypes.POINTER(P)]),
+            "numa_init_ex": (I, [ctypes.POINTER(MeshDesc), I, D, ctypes.POINTER(Options), P,
+                                 ctypes.POINTER(P)]),
             "numa_destroy": (None, [P]),
             "numa_set_stream": (I, [P, P]),
             "numa_rhs_explicit": (I, [P, P, P]),
@@ -93,7 +101,7 @@ class Numa:
     """One mesh, one reference state, one IMEX time step size (a numa_ctx)."""
 
     def __init__(self, nex, ney, nez, Lx, Ly, Lz, N, dt=0.0, theta_s=300.0, n_bv=0.0,
-                 stream=None):
+                 stream=None, precision="fp64", refine_iters=2):
         import torch
         self._torch = torch
         L = lib()
@@ -101,13 +109,15 @@ class Numa:
         s = torch.cuda.current_stream() if stream is None else stream
         self._stream = s
         h = ctypes.c_void_p()
-        rc = L.numa_init(ctypes.byref(self._desc), N, float(dt), ctypes.c_void_p(s.cuda_stream),
-                         ctypes.byref(h))
+        self._opt = Options(PRECISIONS[precision], int(refine_iters))
+        rc = L.numa_init_ex(ctypes.byref(self._desc), N, float(dt), ctypes.byref(self._opt),
+                            ctypes.c_void_p(s.cuda_stream), ctypes.byref(h))
         if rc != NUMA_OK:
             raise NumaError("numa_init failed: %s" % ERRORS.get(rc, rc))
         self._h = h
         self.N = N
         self.dt = float(dt)
+        self.precision = precision
         self.ncol = self.query(Q_NCOL)
         self.M = self.query(Q_M)
         self.nnode = self.query(Q_NNODE)

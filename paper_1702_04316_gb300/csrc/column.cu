@@ -1,12 +1,13 @@
 // Column kernels of the 1D-IMEX method: factorisation of the Schur-complement matrix,
-// the column solve, and the fused implicit stage.
+// the column solve, and the fused implicit stage, for the FP64 method and for the
+// mixed-precision form (FP32 factors with FP64 iterative refinement).
 //
 // One thread owns one column (lane-per-column).  On GB300 the FP64 pipe is the scarce
 // resource (2 FP64 FMA per clock per SM, 1/64 of FP32), so every lane of a warp does
 // useful FP64 work instead of cooperating on one column with shuffles.  The stored
-// factors are transposed (column index fastest) so that the 32 lanes of a warp read 256
-// contiguous bytes per factor entry, and the state columns are staged through shared
-// memory so that their global loads and stores stay coalesced.
+// factors are transposed (column index fastest) so that the 32 lanes of a warp read
+// contiguous factor entries, and the state columns are staged through shared memory so
+// that their global loads and stores stay coalesced.
 //
 // The substitutions are right-looking: once y_i (x_i) is known, the next 2N rows are
 // updated with 2N independent FMAs held in a register window, so the dependent path per
@@ -16,13 +17,14 @@
 namespace {
 
 // ---- band accessor of the stored factors (column-oriented layout) ----------------------
+template <typename FT>
 struct Band {
-  double* L;
-  double* U;
+  FT* L;
+  FT* U;
   int hb;
   long long nc;
   long long col;
-  __device__ __forceinline__ double& at(int i, int j) const {
+  __device__ __forceinline__ FT& at(int i, int j) const {
     return (j < i) ? L[((long long)j * hb + (i - j) - 1) * nc + col]
                    : U[((long long)j * (hb + 1) + (j - i)) * nc + col];
   }
@@ -61,56 +63,92 @@ __device__ __forceinline__ double col_dz(const double* f, int T, int lev, const 
   return acc;
 }
 
-// Solve L U x = b in place for one column held in shared memory (stride T).
-// Forward: y_i = w_0; then x_{i+1+k} -= L(i+1+k, i) y_i for k < HB (window w in registers).
-// Backward: x_i = v_0 / U(i,i); then y_{i-1-k} -= U(i-1-k, i) x_i for k < HB.
+// w_p(x)[lev] = lam A^-1 (D_z x / rho0 + g x / (G0 rho0)), zero at the two walls (the
+// tables kp1, kp2 carry the zeros).
+template <int N>
+__device__ __forceinline__ double col_wp(const double* x, int T, int lev, const RefLev& R,
+                                         const StageTab& tb) {
+  return fma(__ldg(tb.kp1 + lev), col_dz<N>(x, T, lev, R), __ldg(tb.kp2 + lev) * x[lev * T]);
+}
+
+// Solve L U x = b in place for one column held in shared memory (stride T), VT the value
+// type, FT the factor type.  Forward: y_i = w_0; x_{i+1+k} -= L(i+1+k, i) y_i for k < HB
+// (window w in registers).  Backward: x_i = v_0 / U(i,i); y_{i-1-k} -= U(i-1-k, i) x_i.
 // Factor columns are prefetched one column ahead.
-template <int HB>
-__device__ __forceinline__ void col_solve(double* x, int T, int M, const double* __restrict__ L,
-                                          const double* __restrict__ U, long long nc,
-                                          long long col) {
-  double w[HB], l[HB], ln[HB];
+template <int HB, typename VT, typename FT>
+__device__ __forceinline__ void col_solve(VT* x, int T, int M, const FT* __restrict__ L,
+                                          const FT* __restrict__ U, long long nc, long long col) {
+  VT w[HB], l[HB], ln[HB];
 #pragma unroll
-  for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : 0.0;
+  for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : (VT)0;
 #pragma unroll
-  for (int k = 0; k < HB; ++k) ln[k] = __ldg(L + (long long)k * nc + col);
+  for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(L + (long long)k * nc + col);
   for (int i = 0; i < M; ++i) {
 #pragma unroll
     for (int k = 0; k < HB; ++k) l[k] = ln[k];
     if (i + 1 < M) {
-      const double* Lc = L + (long long)(i + 1) * HB * nc + col;
+      const FT* Lc = L + (long long)(i + 1) * HB * nc + col;
 #pragma unroll
-      for (int k = 0; k < HB; ++k) ln[k] = __ldg(Lc + (long long)k * nc);
+      for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(Lc + (long long)k * nc);
     }
-    const double y = w[0];
+    const VT y = w[0];
     x[i * T] = y;
-    const double nxt = (i + HB < M) ? x[(i + HB) * T] : 0.0;
+    const VT nxt = (i + HB < M) ? x[(i + HB) * T] : (VT)0;
 #pragma unroll
     for (int k = 0; k < HB - 1; ++k) w[k] = fma(-l[k], y, w[k + 1]);
     w[HB - 1] = fma(-l[HB - 1], y, nxt);
   }
-  double v[HB], u[HB + 1], un[HB + 1];
+  VT v[HB], u[HB + 1], un[HB + 1];
 #pragma unroll
-  for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : 0.0;
+  for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : (VT)0;
   {
-    const double* Uc = U + (long long)(M - 1) * (HB + 1) * nc + col;
+    const FT* Uc = U + (long long)(M - 1) * (HB + 1) * nc + col;
 #pragma unroll
-    for (int k = 0; k <= HB; ++k) un[k] = __ldg(Uc + (long long)k * nc);
+    for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * nc);
   }
   for (int i = M - 1; i >= 0; --i) {
 #pragma unroll
     for (int k = 0; k <= HB; ++k) u[k] = un[k];
     if (i > 0) {
-      const double* Uc = U + (long long)(i - 1) * (HB + 1) * nc + col;
+      const FT* Uc = U + (long long)(i - 1) * (HB + 1) * nc + col;
 #pragma unroll
-      for (int k = 0; k <= HB; ++k) un[k] = __ldg(Uc + (long long)k * nc);
+      for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * nc);
     }
-    const double xi = v[0] * u[0];
+    const VT xi = v[0] * u[0];
     x[i * T] = xi;
-    const double nxt = (i - HB >= 0) ? x[(i - HB) * T] : 0.0;
+    const VT nxt = (i - HB >= 0) ? x[(i - HB) * T] : (VT)0;
 #pragma unroll
     for (int k = 0; k < HB - 1; ++k) v[k] = fma(-u[k + 1], xi, v[k + 1]);
     v[HB - 1] = fma(-u[HB], xi, nxt);
+  }
+}
+
+// S x = b for one column: FP64 factors, or FP32 factors with FP64 iterative refinement
+// (r = b - S x with the FP64 matrix-free operator, correction solved in FP32).
+//   b: FP64 right-hand side (kept), tmp: FP64 scratch column, X: FP64 solution,
+//   Tf: FP32 scratch column (mixed form only).
+template <int N, bool MIXED>
+__device__ __forceinline__ void col_solve_refined(const double* b, double* tmp, double* X, float* Tf,
+                                                  int T, int M, const Factors& F, long long nc,
+                                                  long long col, const RefLev& R,
+                                                  const StageTab& tb, int iters) {
+  if (!MIXED) {
+    for (int lev = 0; lev < M; ++lev) X[lev * T] = b[lev * T];
+    col_solve<2 * N, double, double>(X, T, M, F.L, F.U, nc, col);
+    return;
+  }
+  for (int lev = 0; lev < M; ++lev) Tf[lev * T] = (float)b[lev * T];
+  col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, nc, col);
+  for (int lev = 0; lev < M; ++lev) X[lev * T] = (double)Tf[lev * T];
+  for (int it = 0; it < iters; ++it) {
+    for (int lev = 0; lev < M; ++lev) tmp[lev * T] = col_wp<N>(X, T, lev, R, tb);
+    for (int lev = 0; lev < M; ++lev) {
+      const double Sx = X[lev * T] - fma(__ldg(tb.kF + lev), tmp[lev * T],
+                                         __ldg(tb.kD + lev) * col_dz<N>(tmp, T, lev, R));
+      Tf[lev * T] = (float)(b[lev * T] - Sx);
+    }
+    col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, nc, col);
+    for (int lev = 0; lev < M; ++lev) X[lev * T] += (double)Tf[lev * T];
   }
 }
 
@@ -118,16 +156,18 @@ __device__ __forceinline__ void col_solve(double* x, int T, int M, const double*
 // S(lam) is the left-hand side applied to the unit vector e_m,
 //   w_p = A^-1 lam (D_z e_m / rho0 + g e_m / (G0 rho0))   (zero at the two walls)
 //   S e_m = e_m - lam F0z w_p - lam rho0 G0 D_z w_p,
-// then Algorithm 9 (LUdecompose): banded LU without pivoting, in place.
-__global__ void k_factor(Geom G, RefLev R, double lam, Factors F, unsigned* status) {
+// assembled in FP64 and stored as FT, then Algorithm 9 (LUdecompose): banded LU without
+// pivoting, in place, in FT arithmetic.
+template <typename FT>
+__global__ void k_factor(Geom G, RefLev R, double lam, FT* Lf, FT* Uf, int hb, unsigned* status) {
   const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (col >= G.ncol) return;
-  const int M = G.M, N = G.N, hb = F.hb, W = 2 * N + 1;
+  const int M = G.M, N = G.N, W = 2 * N + 1;
   const long long nc = G.ncol;
-  Band A{F.L, F.U, hb, nc, col};
+  Band<FT> A{Lf, Uf, hb, nc, col};
   for (int i = 0; i < M; ++i) {
-    for (int k = 0; k < hb; ++k) F.L[((long long)i * hb + k) * nc + col] = 0.0;
-    for (int k = 0; k <= hb; ++k) F.U[((long long)i * (hb + 1) + k) * nc + col] = 0.0;
+    for (int k = 0; k < hb; ++k) Lf[((long long)i * hb + k) * nc + col] = (FT)0;
+    for (int k = 0; k <= hb; ++k) Uf[((long long)i * (hb + 1) + k) * nc + col] = (FT)0;
   }
   auto dz = [&](int l, int j) -> double {   // D_z(l, j), |l - j| <= N
     return __ldg(R.dz_band + (long long)l * W + (j - l + N));
@@ -149,19 +189,19 @@ __global__ void k_factor(Geom G, RefLev R, double lam, Factors F, unsigned* stat
       const int la = max(max(0, i - N), l0), lb = min(min(M - 1, i + N), l1);
       for (int l = la; l <= lb; ++l) acc = fma(dz(i, l), wp[l - m + N], acc);
       s -= lam * R.rho0[i] * R.G0[i] * acc;
-      A.at(i, m) = s;
+      A.at(i, m) = (FT)s;
     }
   }
   for (int k = 0; k < M; ++k) {
-    double piv = A.at(k, k);
-    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+    FT piv = A.at(k, k);
+    if (!(fabs((double)piv) > 0.0) || !isfinite((double)piv)) {
       atomicOr(status, NUMA_ST_PIVOT);
-      piv = 1.0;
+      piv = (FT)1;
     }
-    const double ip = 1.0 / piv;
+    const FT ip = (FT)1 / piv;
     const int E = min(k + hb, M - 1);
     for (int i = k + 1; i <= E; ++i) {
-      const double l = A.at(i, k) * ip;
+      const FT l = A.at(i, k) * ip;
       A.at(i, k) = l;
       for (int j = k + 1; j <= E; ++j) A.at(i, j) = fma(-l, A.at(k, j), A.at(i, j));
     }
@@ -169,38 +209,52 @@ __global__ void k_factor(Geom G, RefLev R, double lam, Factors F, unsigned* stat
   }
 }
 
-template <int N>
-__global__ void k_solve(const double* b, double* x, Geom G, Factors F) {
+template <int N, bool MIXED>
+__global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R, StageTab tb,
+                        int iters) {
   extern __shared__ double sm[];
   const int T = blockDim.x, M = G.M;
   const long long col0 = blockIdx.x * (long long)T;
   const int ncols = (int)min((long long)T, G.ncol - col0);
   const long long base = col0 * M;
   const int cnt = ncols * M;
+  double* Sb = sm;
+  double* Sx = sm + M * T;
+  double* St = sm + 2 * M * T;
+  float* Tf = (float*)(sm + 3 * M * T);
   for (int j = threadIdx.x; j < cnt; j += T) {
     const int c = j / M, lev = j - c * M;
-    sm[lev * T + c] = b[base + j];
+    Sb[lev * T + c] = b[base + j];
   }
   __syncthreads();
-  if ((int)threadIdx.x < ncols)
-    col_solve<2 * N>(sm + threadIdx.x, T, M, F.L, F.U, G.ncol, col0 + threadIdx.x);
+  if ((int)threadIdx.x < ncols) {
+    const int t = threadIdx.x;
+    col_solve_refined<N, MIXED>(Sb + t, St + t, Sx + t, Tf + t, T, M, F, G.ncol, col0 + t, R, tb,
+                                iters);
+  }
   __syncthreads();
   for (int j = threadIdx.x; j < cnt; j += T) {
     const int c = j / M, lev = j - c * M;
-    x[base + j] = sm[lev * T + c];
+    x[base + j] = Sx[lev * T + c];
   }
 }
 
-// Fused 1D-IMEX stage (rows 2 or 3 of Table 1).  Phase 1 (all threads, coalesced): the
-// explicit predictor q(i)_e = q^n + dt sum_j a_ij R_j, the q~ shift q~_e = q(i)_e +
-// sum_j c_ij q(j), and the final u, v.  Phase 2 (one thread per column): Schur right-hand
-// side (Algorithm 4), column solve, extraction of (rho', w, theta') (Eq. utteqn).
-// Phase 3 (coalesced): q(i) = q~ - sum_j c_ij q(j).
-template <int N, bool S3>
-__global__ void k_stage(const double* __restrict__ qn, const double* __restrict__ R1,
-                        const double* __restrict__ R2, const double* __restrict__ q2,
+// Fused 1D-IMEX stage (rows 2 or 3 of Table 1).
+// Phase 1 (all threads, coalesced): the explicit predictor q(i)_e = q^n + dt sum_j a_ij R_j
+//   and the shift q~_e = q(i)_e + sum_j c_ij q(j); u, v are final here.  Shared memory keeps
+//   P_e = G0 rho~_e + H0 theta~_e and w_a = A^-1 (w~_e + lam g theta~_e / theta0).
+// Phase 2 (one thread per column): Schur right-hand side b (Algorithm 4), the column solve,
+//   and w_p(P) (Eq. utteqn).
+// Phase 3 (coalesced): w~ = w_a - w_p(P), theta~ = theta~_e - lam w~ d(theta0)/dz,
+//   rho~ = (P - H0 theta~) / G0 (w_a and theta~_e recomputed from their sources rather than
+//   kept in shared memory, which doubles the resident columns), then
+//   q(i) = q~ - sum_j c_ij q(j).
+// RT: type of R1, R2 (double, or float in the mixed form).
+template <int N, bool S3, bool MIXED, typename RT>
+__global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
+                        const RT* __restrict__ R2, const double* __restrict__ q2,
                         double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
-                        StageTab tb) {
+                        StageTab tb, int iters) {
   extern __shared__ double sm[];
   const int T = blockDim.x, M = G.M;
   const long long nn = G.nnode;
@@ -208,63 +262,53 @@ __global__ void k_stage(const double* __restrict__ qn, const double* __restrict_
   const int ncols = (int)min((long long)T, G.ncol - col0);
   const long long base = col0 * M;
   const int cnt = ncols * M;
-  double* S0 = sm;              // rho~_e -> b -> P -> rho~
-  double* S1 = sm + M * T;      // w~_e -> w_a -> w~
-  double* S2 = sm + 2 * M * T;  // theta~_e -> theta~
+  double* S0 = sm;              // P_e -> b
+  double* S1 = sm + M * T;      // w_a -> (scratch) -> w_p(P)
+  double* SX = MIXED ? sm + 2 * M * T : S0;   // P (the mixed form keeps b)
+  float* Tf = (float*)(sm + 3 * M * T);
   const double a1dt = sc.a[0] * sc.dt, a2dt = sc.a[1] * sc.dt;
+  const double c1 = sc.c[0], c2 = sc.c[1];
+
+  // predictor of field f at global offset o (q(i)_e, shifted to q~_e unless u, v)
+  auto pred = [&](int f, long long o) -> double {
+    const double qv = qn[o];
+    double v = fma(a1dt, (double)R1[o], qv);
+    if (S3) v = fma(a2dt, (double)R2[o], v);
+    if (f == 1 || f == 2) return v;
+    v = fma(c1, qv, v);
+    if (S3) v = fma(c2, q2[o], v);
+    return v;
+  };
 
   // phase 1
 #pragma unroll 2
   for (int j = threadIdx.x; j < cnt; j += T) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
-#pragma unroll
-    for (int f = 1; f <= 2; ++f) {   // u, v: explicit only
-      const long long o = f * nn + g;
-      double e = fma(a1dt, R1[o], qn[o]);
-      if (S3) e = fma(a2dt, R2[o], e);
-      out[o] = e;
-    }
-    const int fl[3] = {0, 3, 4};
-    double* Sd[3] = {S0, S1, S2};
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const long long o = fl[t] * nn + g;
-      const double qv = qn[o];
-      double e = fma(a1dt, R1[o], qv);
-      if (S3) e = fma(a2dt, R2[o], e);
-      e = fma(sc.c[0], qv, e);
-      if (S3) e = fma(sc.c[1], q2[o], e);
-      Sd[t][lev * T + c] = e;
-    }
+    out[nn + g] = pred(1, nn + g);
+    out[2 * nn + g] = pred(2, 2 * nn + g);
+    const double re = pred(0, g), we = pred(3, 3 * nn + g), te = pred(4, 4 * nn + g);
+    S1[lev * T + c] = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
+    S0[lev * T + c] = fma(__ldg(tb.G0 + lev), re, __ldg(tb.H0 + lev) * te);
   }
   __syncthreads();
 
   // phase 2
   if ((int)threadIdx.x < ncols) {
     const int t = threadIdx.x;
-    double* P = S0 + t;
-    double* Wc = S1 + t;
-    double* Th = S2 + t;
-    for (int lev = 0; lev < M; ++lev) {     // w_a, then P_e
-      const double th = Th[lev * T];
-      Wc[lev * T] = fma(__ldg(tb.wa_th + lev), th, Wc[lev * T]) * __ldg(tb.wa_s + lev);
-      P[lev * T] = fma(__ldg(tb.G0 + lev), P[lev * T], __ldg(tb.H0 + lev) * th);
-    }
+    double* B = S0 + t;
+    double* Wt = S1 + t;
     for (int lev = 0; lev < M; ++lev) {     // b = P_e - lam F0z w_a - lam rho0 G0 D_z w_a
-      const double dzw = col_dz<N>(Wc, T, lev, R);
-      P[lev * T] = fma(-__ldg(tb.kF + lev), Wc[lev * T], fma(-__ldg(tb.kD + lev), dzw, P[lev * T]));
+      const double dzw = col_dz<N>(Wt, T, lev, R);
+      B[lev * T] = fma(-__ldg(tb.kF + lev), Wt[lev * T], fma(-__ldg(tb.kD + lev), dzw, B[lev * T]));
     }
-    col_solve<2 * N>(P, T, M, F.L, F.U, G.ncol, col0 + t);
-    for (int lev = 0; lev < M; ++lev) {     // w = w_a - w_p(P); theta = theta_e - lam w dtheta0
-      const double dzp = col_dz<N>(P, T, lev, R);
-      const double wp = fma(__ldg(tb.kp1 + lev), dzp, __ldg(tb.kp2 + lev) * P[lev * T]);
-      const double wv = Wc[lev * T] - wp;
-      Wc[lev * T] = wv;
-      Th[lev * T] = fma(-__ldg(tb.kth + lev), wv, Th[lev * T]);
+    double* X = SX + t;
+    if (MIXED) {
+      col_solve_refined<N, true>(B, Wt, X, Tf + t, T, M, F, G.ncol, col0 + t, R, tb, iters);
+    } else {
+      col_solve<2 * N, double, double>(B, T, M, F.L, F.U, G.ncol, col0 + t);
     }
-    for (int lev = 0; lev < M; ++lev)       // rho = (P - H0 theta) / G0
-      P[lev * T] = fma(-__ldg(tb.H0G0 + lev), Th[lev * T], __ldg(tb.invG0 + lev) * P[lev * T]);
+    for (int lev = 0; lev < M; ++lev) Wt[lev * T] = col_wp<N>(X, T, lev, R, tb);
   }
   __syncthreads();
 
@@ -273,47 +317,75 @@ __global__ void k_stage(const double* __restrict__ qn, const double* __restrict_
   for (int j = threadIdx.x; j < cnt; j += T) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
-    const int fl[3] = {0, 3, 4};
-    const double* Sd[3] = {S0, S1, S2};
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const long long o = fl[t] * nn + g;
-      double v = fma(-sc.c[0], qn[o], Sd[t][lev * T + c]);
-      if (S3) v = fma(-sc.c[1], q2[o], v);
-      out[o] = v;
+    const long long orr = g, ow = 3 * nn + g, oth = 4 * nn + g;
+    const double te = pred(4, oth), we = pred(3, ow);
+    const double wa = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
+    const double wv = wa - S1[lev * T + c];
+    const double thv = fma(-__ldg(tb.kth + lev), wv, te);
+    const double rv = fma(-__ldg(tb.H0G0 + lev), thv, __ldg(tb.invG0 + lev) * SX[lev * T + c]);
+    double o_r = fma(-c1, qn[orr], rv), o_w = fma(-c1, qn[ow], wv), o_t = fma(-c1, qn[oth], thv);
+    if (S3) {
+      o_r = fma(-c2, q2[orr], o_r);
+      o_w = fma(-c2, q2[ow], o_w);
+      o_t = fma(-c2, q2[oth], o_t);
     }
+    out[orr] = o_r;
+    out[ow] = o_w;
+    out[oth] = o_t;
   }
 }
 
-template <int N>
-cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, Factors F, int T,
-                           cudaStream_t s) {
-  const size_t smem = (size_t)G.M * T * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_solve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+size_t stage_smem(int M, int T, bool mixed) {
+  return mixed ? ((size_t)3 * 8 + 4) * M * T : (size_t)2 * 8 * M * T;
+}
+
+template <int N, bool MIXED>
+cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, const Factors& F,
+                           const RefLev& R, const StageTab& tb, int T, int iters, cudaStream_t s) {
+  const size_t smem = ((size_t)3 * 8 + (MIXED ? 4 : 0)) * G.M * T;
+  cudaError_t e = cudaFuncSetAttribute(k_solve<N, MIXED>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_solve<N><<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(b, x, G, F);
+  k_solve<N, MIXED><<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(b, x, G, F, R, tb, iters);
+  return cudaGetLastError();
+}
+
+template <int N, bool S3, bool MIXED, typename RT>
+cudaError_t launch_stage_k(const double* qn, const RT* R1, const RT* R2, const double* q2,
+                           double* out, const Geom& G, const RefLev& R, const Factors& F,
+                           const StageCoef& sc, const StageTab& tb, int T, int iters,
+                           cudaStream_t s) {
+  const size_t smem = stage_smem(G.M, T, MIXED);
+  cudaError_t e = cudaFuncSetAttribute(k_stage<N, S3, MIXED, RT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_stage<N, S3, MIXED, RT><<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(
+      qn, R1, R2, q2, out, G, R, F, sc, tb, iters);
   return cudaGetLastError();
 }
 
 template <int N>
-cudaError_t launch_stage_n(int stage, const double* qn, const double* R1, const double* R2,
+cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const void* R2,
                            const double* q2, double* out, const Geom& G, const RefLev& R,
-                           Factors F, const StageCoef& sc, const StageTab& tb, int T,
-                           cudaStream_t s) {
-  const size_t smem = (size_t)3 * G.M * T * sizeof(double);
-  const unsigned nb = (unsigned)((G.ncol + T - 1) / T);
-  cudaError_t e;
-  if (stage == 3) {
-    e = cudaFuncSetAttribute(k_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_stage<N, true><<<nb, T, smem, s>>>(qn, R1, R2, q2, out, G, R, F, sc, tb);
-  } else {
-    e = cudaFuncSetAttribute(k_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_stage<N, false><<<nb, T, smem, s>>>(qn, R1, R2, q2, out, G, R, F, sc, tb);
+                           const Factors& F, const StageCoef& sc, const StageTab& tb, int T,
+                           bool r_float, cudaStream_t s) {
+  const int it = F.refine_iters;
+  if (F.mixed && !r_float) {
+    const double* a = (const double*)R1;
+    const double* b = (const double*)R2;
+    return stage == 3 ? launch_stage_k<N, true, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
+                      : launch_stage_k<N, false, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
   }
-  return cudaGetLastError();
+  if (F.mixed) {
+    const float* a = (const float*)R1;
+    const float* b = (const float*)R2;
+    return stage == 3 ? launch_stage_k<N, true, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
+                      : launch_stage_k<N, false, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
+  }
+  const double* a = (const double*)R1;
+  const double* b = (const double*)R2;
+  return stage == 3 ? launch_stage_k<N, true, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
+                    : launch_stage_k<N, false, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
 }
 
 }  // namespace
@@ -321,38 +393,42 @@ cudaError_t launch_stage_n(int stage, const double* qn, const double* R1, const 
 cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
                           unsigned* status, cudaStream_t s) {
   const int bs = 128;
-  k_factor<<<(unsigned)((G.ncol + bs - 1) / bs), bs, 0, s>>>(G, R, lam, F, status);
+  const unsigned nb = (unsigned)((G.ncol + bs - 1) / bs);
+  if (F.mixed) k_factor<float><<<nb, bs, 0, s>>>(G, R, lam, F.L32, F.U32, F.hb, status);
+  else k_factor<double><<<nb, bs, 0, s>>>(G, R, lam, F.L, F.U, F.hb, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, int T,
-                         cudaStream_t s) {
+cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, const RefLev& R,
+                         const StageTab& tb, int T, cudaStream_t s) {
+  const int it = F.refine_iters;
+#define NUMA_SOLVE_CASE(n)                                                             \
+  case n:                                                                              \
+    return F.mixed ? launch_solve_n<n, true>(b, x, G, F, R, tb, T, it, s)              \
+                   : launch_solve_n<n, false>(b, x, G, F, R, tb, T, it, s);
   switch (G.N) {
-    case 1: return launch_solve_n<1>(b, x, G, F, T, s);
-    case 2: return launch_solve_n<2>(b, x, G, F, T, s);
-    case 3: return launch_solve_n<3>(b, x, G, F, T, s);
-    case 4: return launch_solve_n<4>(b, x, G, F, T, s);
-    case 5: return launch_solve_n<5>(b, x, G, F, T, s);
-    case 6: return launch_solve_n<6>(b, x, G, F, T, s);
-    case 7: return launch_solve_n<7>(b, x, G, F, T, s);
-    case 8: return launch_solve_n<8>(b, x, G, F, T, s);
+    NUMA_SOLVE_CASE(1) NUMA_SOLVE_CASE(2) NUMA_SOLVE_CASE(3) NUMA_SOLVE_CASE(4)
+    NUMA_SOLVE_CASE(5) NUMA_SOLVE_CASE(6) NUMA_SOLVE_CASE(7) NUMA_SOLVE_CASE(8)
+    default: return cudaErrorInvalidValue;
+  }
+#undef NUMA_SOLVE_CASE
+}
+
+cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void* R2,
+                         const double* q2, double* out, const Geom& G, const RefLev& R,
+                         Factors F, const StageCoef& sc, const StageTab& tb, int T,
+                         bool r_float, cudaStream_t s) {
+  switch (G.N) {
+    case 1: return launch_stage_n<1>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    case 2: return launch_stage_n<2>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    case 3: return launch_stage_n<3>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    case 4: return launch_stage_n<4>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    case 5: return launch_stage_n<5>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    case 6: return launch_stage_n<6>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    case 7: return launch_stage_n<7>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    case 8: return launch_stage_n<8>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_stage(int stage, const double* qn, const double* R1, const double* R2,
-                         const double* q2, double* out, const Geom& G, const RefLev& R,
-                         Factors F, const StageCoef& sc, const StageTab& tb, int T,
-                         cudaStream_t s) {
-  switch (G.N) {
-    case 1: return launch_stage_n<1>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    case 2: return launch_stage_n<2>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    case 3: return launch_stage_n<3>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    case 4: return launch_stage_n<4>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    case 5: return launch_stage_n<5>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    case 6: return launch_stage_n<6>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    case 7: return launch_stage_n<7>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    case 8: return launch_stage_n<8>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
+size_t stage_smem_bytes(int M, int T, bool mixed) { return stage_smem(M, T, mixed); }

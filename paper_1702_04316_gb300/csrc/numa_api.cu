@@ -125,6 +125,9 @@ struct numa_ctx {
   Factors F{};
   double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (each 5*nnode except Pp)
   double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
+  // mixed-precision form: FP32 stencil fields (6 x nnode) and FP32 R1, R2 (5 x nnode each)
+  float *F32 = nullptr, *R1f = nullptr, *R2f = nullptr;
+  int precision = NUMA_PREC_FP64;
   int* d_perm = nullptr;        // class-sorted thread order of the right-hand side
   long long nperm = 0;
   unsigned* d_status = nullptr;
@@ -183,6 +186,8 @@ void free_all(numa_ctx* c) {
   cudaFree(c->d_stage_tab);
   cudaFree(c->F.L);
   cudaFree(c->F.U);
+  cudaFree(c->F.L32);
+  cudaFree(c->F.U32);
   cudaFree(c->d_work);
   cudaFree(c->d_perm);
   cudaFree(c->d_status);
@@ -324,21 +329,30 @@ int check_ptr(numa_ctx* c, const void* p, const char* name) {
   return NUMA_OK;
 }
 
-int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep) {
+// One right-hand side.  FP64 method: P' pre-pass, FP64 kernel.  Mixed form: FP64 P' and
+// FP32 field copies, FP32 kernel; in mode 0, out32 receives the FP32 tendencies.
+int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep,
+                float* out32 = nullptr) {
   long p = prof_begin(c, NUMA_K_PRESSURE);
-  NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
+  if (c->precision == NUMA_PREC_MIXED) NUMA_CK(c, launch_prep32(q, c->F32, c->G, c->R, c->stream));
+  else NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
   prof_end(c, p);
   p = prof_begin(c, NUMA_K_RHS);
-  NUMA_CK(c, launch_rhs(q, c->Pp, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep, c->stream));
+  if (c->precision == NUMA_PREC_MIXED)
+    NUMA_CK(c, launch_rhs32(q, c->F32, out32, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep,
+                            c->stream));
+  else
+    NUMA_CK(c, launch_rhs(q, c->Pp, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep, c->stream));
   prof_end(c, p);
   return NUMA_OK;
 }
 
-int enqueue_stage(numa_ctx* c, int stage, const double* qn, const double* R1, const double* R2,
-                  const double* q2, double* out, const StageCoef& sc) {
+// r_float: R1, R2 are the mixed form's internal FP32 tendencies (else FP64 arrays).
+int enqueue_stage(numa_ctx* c, int stage, const double* qn, const void* R1, const void* R2,
+                  const double* q2, double* out, const StageCoef& sc, bool r_float = false) {
   long p = prof_begin(c, NUMA_K_STAGE);
   NUMA_CK(c, launch_stage(stage, qn, R1, R2, q2, out, c->G, c->R, c->F, sc, c->T, c->col_tile,
-                          c->stream));
+                          r_float, c->stream));
   prof_end(c, p);
   return NUMA_OK;
 }
@@ -362,7 +376,18 @@ StageCoef stage_coef(const numa_ctx* c, int stage) {
 extern "C" {
 
 int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_ctx** out) {
+  return numa_init_ex(mesh, N, dt, nullptr, stream, out);
+}
+
+int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_options* opt,
+                 void* stream, numa_ctx** out) {
   if (!out) return NUMA_ERR_ARG;
+  const int precision = opt ? opt->precision : NUMA_PREC_FP64;
+  const int refine = opt ? opt->refine_iters : 2;
+  if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED) || refine < 0 || refine > 8) {
+    *out = nullptr;
+    return NUMA_ERR_ARG;
+  }
   *out = nullptr;
   if (!mesh || N < 1 || N > NUMA_MAXN || mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 ||
       !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0) || !(dt >= 0) ||
@@ -382,6 +407,9 @@ int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_c
   numa_ctx* c = new numa_ctx();
   c->G = G;
   c->stream = (cudaStream_t)stream;
+  c->precision = precision;
+  c->F.mixed = precision == NUMA_PREC_MIXED;
+  c->F.refine_iters = refine;
   c->theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
   if (const char* t = std::getenv("NUMA_COL_TILE")) {     // tuning: columns per CTA
     const int v = std::atoi(t);
@@ -397,14 +425,23 @@ int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_c
   int rc = upload_levels(c);
   const int hb = 2 * N;
   c->F.hb = hb;
-  c->factor_bytes = (size_t)G.M * (2 * hb + 1) * G.ncol * sizeof(double);
-  c->work_bytes = (size_t)(1 + 4 * 5) * G.nnode * sizeof(double);
+  const bool mixed = c->F.mixed;
+  const size_t fsz = mixed ? sizeof(float) : sizeof(double);
+  c->factor_bytes = (size_t)G.M * (2 * hb + 1) * G.ncol * fsz;
+  c->work_bytes = mixed ? (size_t)(2 * 5) * G.nnode * sizeof(double) +
+                              (size_t)(6 + 2 * 5) * G.nnode * sizeof(float)
+                        : (size_t)(1 + 4 * 5) * G.nnode * sizeof(double);
   if (rc == NUMA_OK) {
-    if (cudaMalloc(&c->F.L, (size_t)G.M * hb * G.ncol * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->F.U, (size_t)G.M * (hb + 1) * G.ncol * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->d_work, c->work_bytes) != cudaSuccess ||
-        cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess) {
+    bool ok = cudaMalloc(&c->d_work, c->work_bytes) == cudaSuccess &&
+              cudaMalloc(&c->d_status, sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&c->d_count, sizeof(unsigned long long)) == cudaSuccess;
+    if (ok && mixed)
+      ok = cudaMalloc(&c->F.L32, (size_t)G.M * hb * G.ncol * sizeof(float)) == cudaSuccess &&
+           cudaMalloc(&c->F.U32, (size_t)G.M * (hb + 1) * G.ncol * sizeof(float)) == cudaSuccess;
+    else if (ok)
+      ok = cudaMalloc(&c->F.L, (size_t)G.M * hb * G.ncol * sizeof(double)) == cudaSuccess &&
+           cudaMalloc(&c->F.U, (size_t)G.M * (hb + 1) * G.ncol * sizeof(double)) == cudaSuccess;
+    if (!ok) {
       cudaGetLastError();
       rc = NUMA_ERR_OOM;
     }
@@ -423,11 +460,21 @@ int numa_init(const numa_mesh_desc* mesh, int N, double dt, void* stream, numa_c
   }
   if (rc == NUMA_OK) {
     const long long n5 = 5 * G.nnode;
-    c->Pp = c->d_work;
-    c->R1 = c->Pp + G.nnode;
-    c->R2 = c->R1 + n5;
-    c->q2 = c->R2 + n5;
-    c->q3 = c->q2 + n5;
+    if (mixed) {
+      c->R1 = c->R2 = nullptr;
+      c->Pp = nullptr;
+      c->q2 = c->d_work;
+      c->q3 = c->q2 + n5;
+      c->F32 = (float*)(c->q3 + n5);
+      c->R1f = c->F32 + 6 * G.nnode;
+      c->R2f = c->R1f + n5;
+    } else {
+      c->Pp = c->d_work;
+      c->R1 = c->Pp + G.nnode;
+      c->R2 = c->R1 + n5;
+      c->q2 = c->R2 + n5;
+      c->q3 = c->q2 + n5;
+    }
     if (cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = NUMA_ERR_CUDA;
   }
   if (rc == NUMA_OK && dt > 0) rc = numa_factor_columns(c, dt);
@@ -461,6 +508,15 @@ int numa_rhs_explicit(numa_ctx* ctx, const double* q, double* rhs) {
   if (q == rhs) return fail(ctx, NUMA_ERR_ARG, "q and rhs must not overlap");
   RhsEpilogue ep{};
   ep.mode = 0;
+  if (ctx->precision == NUMA_PREC_MIXED) {
+    long p = prof_begin(ctx, NUMA_K_PRESSURE);
+    NUMA_CK(ctx, launch_prep32(q, ctx->F32, ctx->G, ctx->R, ctx->stream));
+    prof_end(ctx, p);
+    p = prof_begin(ctx, NUMA_K_RHS);
+    NUMA_CK(ctx, launch_rhs32d(q, ctx->F32, rhs, ctx->G, ctx->C, ctx->R, ctx->stream));
+    prof_end(ctx, p);
+    return NUMA_OK;
+  }
   return enqueue_rhs(ctx, q, rhs, ep);
 }
 
@@ -485,7 +541,7 @@ int numa_solve_columns(numa_ctx* ctx, const double* b, double* x) {
   if ((rc = check_ptr(ctx, b, "b")) || (rc = check_ptr(ctx, x, "x"))) return rc;
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
   long p = prof_begin(ctx, NUMA_K_SOLVE);
-  NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->col_tile, ctx->stream));
+  NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->R, ctx->T, ctx->col_tile, ctx->stream));
   prof_end(ctx, p);
   return NUMA_OK;
 }
@@ -518,21 +574,24 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
   }
   static const Ark2 t;
   const StageCoef s2 = stage_coef(ctx, 2), s3 = stage_coef(ctx, 3);
+  const bool mixed = ctx->precision == NUMA_PREC_MIXED;
+  void* R1 = mixed ? (void*)ctx->R1f : (void*)ctx->R1;
+  void* R2 = mixed ? (void*)ctx->R2f : (void*)ctx->R2;
   const double* cur = q_in;
   for (int s = 0; s < nsteps; ++s) {
     RhsEpilogue e0{};
-    if ((rc = enqueue_rhs(ctx, cur, ctx->R1, e0))) return rc;
-    if ((rc = enqueue_stage(ctx, 2, cur, ctx->R1, nullptr, nullptr, ctx->q2, s2))) return rc;
-    if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0))) return rc;
-    if ((rc = enqueue_stage(ctx, 3, cur, ctx->R1, ctx->R2, ctx->q2, ctx->q3, s3))) return rc;
+    if ((rc = enqueue_rhs(ctx, cur, ctx->R1, e0, ctx->R1f))) return rc;
+    if ((rc = enqueue_stage(ctx, 2, cur, R1, nullptr, nullptr, ctx->q2, s2, mixed))) return rc;
+    if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0, ctx->R2f))) return rc;
+    if ((rc = enqueue_stage(ctx, 3, cur, R1, R2, ctx->q2, ctx->q3, s3, mixed))) return rc;
     RhsEpilogue ef{};
     ef.mode = 2;
     ef.b1dt = t.b[0] * ctx->dt;
     ef.b2dt = t.b[1] * ctx->dt;
     ef.b3dt = t.b[2] * ctx->dt;
     ef.u0 = cur;
-    ef.R1 = ctx->R1;
-    ef.R2 = ctx->R2;
+    ef.R1 = R1;
+    ef.R2 = R2;
     if ((rc = enqueue_rhs(ctx, ctx->q3, q_out, ef))) return rc;
     cur = q_out;
   }
@@ -633,13 +692,25 @@ int numa_column_factors(numa_ctx* ctx, long long col, double* host_out) {
   if (!host_out || col < 0 || col >= ctx->G.ncol) return fail(ctx, NUMA_ERR_ARG, "bad column");
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
   const int M = ctx->G.M, hb = ctx->F.hb, W = 2 * hb + 1;
-  const size_t pitch = (size_t)ctx->G.ncol * sizeof(double);
   std::vector<double> L((size_t)M * hb), U((size_t)M * (hb + 1));
-  NUMA_CK(ctx, cudaMemcpy2DAsync(L.data(), sizeof(double), ctx->F.L + col, pitch, sizeof(double),
-                                 (size_t)M * hb, cudaMemcpyDeviceToHost, ctx->stream));
-  NUMA_CK(ctx, cudaMemcpy2DAsync(U.data(), sizeof(double), ctx->F.U + col, pitch, sizeof(double),
-                                 (size_t)M * (hb + 1), cudaMemcpyDeviceToHost, ctx->stream));
-  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->F.mixed) {
+    const size_t pitch = (size_t)ctx->G.ncol * sizeof(float);
+    std::vector<float> Lf(L.size()), Uf(U.size());
+    NUMA_CK(ctx, cudaMemcpy2DAsync(Lf.data(), sizeof(float), ctx->F.L32 + col, pitch, sizeof(float),
+                                   (size_t)M * hb, cudaMemcpyDeviceToHost, ctx->stream));
+    NUMA_CK(ctx, cudaMemcpy2DAsync(Uf.data(), sizeof(float), ctx->F.U32 + col, pitch, sizeof(float),
+                                   (size_t)M * (hb + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t t = 0; t < L.size(); ++t) L[t] = Lf[t];
+    for (size_t t = 0; t < U.size(); ++t) U[t] = Uf[t];
+  } else {
+    const size_t pitch = (size_t)ctx->G.ncol * sizeof(double);
+    NUMA_CK(ctx, cudaMemcpy2DAsync(L.data(), sizeof(double), ctx->F.L + col, pitch, sizeof(double),
+                                   (size_t)M * hb, cudaMemcpyDeviceToHost, ctx->stream));
+    NUMA_CK(ctx, cudaMemcpy2DAsync(U.data(), sizeof(double), ctx->F.U + col, pitch, sizeof(double),
+                                   (size_t)M * (hb + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   // L[(j*hb + k-1)] = L(j+k, j); U[(j*(hb+1) + k)] = U(j-k, j), slot 0 = 1/U(j,j)
   for (size_t t = 0; t < (size_t)M * W; ++t) host_out[t] = 0.0;
   for (int j = 0; j < M; ++j) {
@@ -698,6 +769,7 @@ int numa_query(const numa_ctx* ctx, int what, long long* out) {
     case NUMA_Q_WORKSPACE_BYTES: *out = (long long)ctx->work_bytes; break;
     case NUMA_Q_FACTORED: *out = ctx->factored ? 1 : 0; break;
     case NUMA_Q_N: *out = G.N; break;
+    case NUMA_Q_PRECISION: *out = ctx->precision; break;
     default: return NUMA_ERR_ARG;
   }
   return NUMA_OK;

@@ -71,10 +71,16 @@ struct RefLev {
 //   U[(j*(hb+1) + 0)*ncol + col] = 1 / U(j, j)
 //   U[(j*(hb+1) + k)*ncol + col] = U(j-k, j), k = 1..hb
 // hb = 2N.  Entries outside the matrix are stored as zero.
+// The mixed-precision form stores the same layout in float (L32, U32) and refines each
+// solve refine_iters times with the FP64 operator.
 struct Factors {
   double* L;
   double* U;
+  float* L32;
+  float* U32;
   int hb;
+  int mixed;
+  int refine_iters;
 };
 
 // Coefficients of one IMEX stage (Table 1 with b = b~).
@@ -107,27 +113,40 @@ struct RhsEpilogue {
   double alpha, one_minus_alpha, beta_dt;   // mode 1
   double b1dt, b2dt, b3dt;        // mode 2
   const double* u0;               // mode 1: u0; mode 2: qn
-  const double* R1;
-  const double* R2;
+  const void* R1;                 // mode 2: double (FP64 method) or float (mixed form)
+  const void* R2;
 };
 // perm: class-sorted thread order from build_rhs_perm (nthreads entries), or NULL for the
 // natural node order (nthreads = nnode; correct, but warps then mix node classes).
 cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const int* perm,
                        long long nthreads, const Geom& G, const Coef3& C, const RefLev& R,
                        const RhsEpilogue& ep, cudaStream_t s);
+// Mixed-precision form: FP64 P', FP32 copies of the six stencil fields (6 x nnode floats),
+// and the FP32 right-hand side (mode 0 writes out32; modes 1 and 2 as launch_rhs, with R1
+// and R2 given as float arrays).
+cudaError_t launch_prep32(const double* q, float* F32, const Geom& G, const RefLev& R,
+                          cudaStream_t s);
+cudaError_t launch_rhs32(const double* q, const float* F32, float* out32, double* out,
+                         const int* perm, long long nthreads, const Geom& G, const Coef3& C,
+                         const RefLev& R, const RhsEpilogue& ep, cudaStream_t s);
+// FP32 right-hand side written as FP64 (mode 0, natural order) for numa_rhs_explicit.
+cudaError_t launch_rhs32d(const double* q, const float* F32, double* out0, const Geom& G,
+                          const Coef3& C, const RefLev& R, cudaStream_t s);
 long long rhs_perm_size(const Geom& G);
 void build_rhs_perm(const Geom& G, int* out);
 
 // column.cu
 cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
                           unsigned* status, cudaStream_t s);
-// T: columns per CTA (one thread each; a multiple of 32).
-cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, int T,
-                         cudaStream_t s);
-cudaError_t launch_stage(int stage, const double* qn, const double* R1, const double* R2,
+// T: columns per CTA (one thread each; a multiple of 32).  R1, R2: float arrays when
+// r_float (the mixed form's internal tendencies), else double arrays.
+cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, const RefLev& R,
+                         const StageTab& tb, int T, cudaStream_t s);
+cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void* R2,
                          const double* q2, double* out, const Geom& G, const RefLev& R,
                          Factors F, const StageCoef& sc, const StageTab& tb, int T,
-                         cudaStream_t s);
+                         bool r_float, cudaStream_t s);
+size_t stage_smem_bytes(int M, int T, bool mixed);
 
 // misc.cu
 cudaError_t launch_connectivity(const Geom& G, int32_t* l2g, int32_t* g2l, cudaStream_t s);
