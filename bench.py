@@ -321,6 +321,16 @@ def run_gpu(args):
         "gpu_launches": int(sum(v[1] for v in kt.values())),
         "clocks": clk,
     }
+    # the mixed-precision form on the same workload
+    gm = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dt15, precision="mixed", refine_iters=1)
+    for _ in range(args.warmup):
+        gm.step_imex1d(q0, q1, 1)
+    ms_mx = time_steps(lambda: gm.step_imex1d(q0, q1, 1), args.steps) / args.steps
+    gm.close()
+    out["imex_c15_mixed"] = {"sim_s_per_wall_s": round(sps(dt15, ms_mx), 3), "ms_per_step": round(ms_mx, 4),
+                             "form": "FP32 RHS over FP64 reference, FP32 LU + 1 FP64 refinement sweep"}
+    if not args.no_forms:
+        out["precision_form"] = precision_form(pkg, torch, min(args.steps, 20), args.warmup)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     g.close()
@@ -332,6 +342,64 @@ def run_gpu(args):
 
 
 # ---------------------------------------------------------------------------------------
+def precision_form(pkg, torch, steps, warmup, nsteps_err=200):
+    """The mixed-precision form on its own workload: 64 x 64 x 10 elements of order 7 over
+    2000 x 2000 x 10 km (the box size is not given; this one keeps C_H = 0.48 at C_V = 15),
+    seeded perturbation amplitude in [0.1, 2] K.  Times one HEVI step of each precision
+    (out of place from the same input) and states the mixed form's relative L2 error of
+    theta' and w after nsteps_err steps against the FP64 path."""
+    import synthetic
+    nex, nez, n, L, Lz, C = 64, 10, 7, 2000e3, 10e3, 15.0
+    c = np.zeros(n + 1)
+    c[n] = 1.0
+    r = np.sort(np.polynomial.legendre.legroots(np.polynomial.legendre.legder(c)).real)
+    xi = np.concatenate([[-1.0], r, [1.0]])
+    fmin = (r[0] + 1.0) / 2.0
+    dt = C * fmin * (Lz / nez) / C_S
+    amp = float(np.random.Generator(np.random.PCG64(3000)).uniform(0.1, 2.0))
+    out = {"workload": "64x64x10 hex elements over 2000x2000x10 km, N=7 (449x449 columns x 71 levels), "
+                       "HEVI 1D-IMEX ARK2 at C=15",
+           "dt_s": round(dt, 4), "C_H": round(C_S * dt / (fmin * L / nex), 3), "amp_K": round(amp, 4)}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        g = pkg.Numa(nex, nex, nez, L, L, Lz, n, dt, precision=prec, refine_iters=1)
+        lev = g.reference_levels()
+        h = L / nex
+        ax = np.concatenate([e * h + (1.0 + xi[:-1]) * h / 2.0 for e in range(nex)] + [[L]])
+        q0 = torch.from_numpy(synthetic.balanced_state(ax, ax, lev["z"], L, L, Lz, lev["rho0"],
+                                                       lev["theta0"], 3001, amp)).cuda()
+        q1 = torch.empty_like(q0)
+        for _ in range(warmup):
+            g.step_imex1d(q0, q1, 1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            g.step_imex1d(q0, q1, 1)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        qr = q0.clone()
+        g.step_imex1d(qr, None, nsteps_err)
+        torch.cuda.synchronize()
+        res[prec] = (ms, qr, g.query(pkg.Q_FACTOR_BYTES))
+        g.close()
+    ms64, q64, fb64 = res["fp64"]
+    msmx, qmx, fbmx = res["mixed"]
+    def rel(f):
+        return float(torch.linalg.norm(qmx[f] - q64[f]) / torch.linalg.norm(q64[f]))
+    out.update({
+        "fp64": {"ms_per_step": round(ms64, 4), "sim_s_per_wall_s": round(dt / (ms64 / 1e3), 2),
+                 "factor_bytes": fb64},
+        "mixed": {"ms_per_step": round(msmx, 4), "sim_s_per_wall_s": round(dt / (msmx / 1e3), 2),
+                  "factor_bytes": fbmx, "refine_iters": 1},
+        "speedup_mixed_vs_fp64": round(ms64 / msmx, 3),
+        "rel_l2_vs_fp64_after_%d_steps" % nsteps_err: {"theta": rel(4), "w": rel(3), "rho": rel(0)},
+        "finite": bool(torch.isfinite(qmx).all().item() and torch.isfinite(q64).all().item()),
+    })
+    return out
+
+
 def oracle_sample_step(window_elems, nsteps_min, seconds):
     """Time the oracle's ARK2 step on a window of W x W elements x all levels of the
     workload (its own lateral walls) and scale to the full column count."""
@@ -423,6 +491,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision-form workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -101,7 +101,7 @@ class Numa:
     """One mesh, one reference state, one IMEX time step size (a numa_ctx)."""
 
     def __init__(self, nex, ney, nez, Lx, Ly, Lz, N, dt=0.0, theta_s=300.0, n_bv=0.0,
-                 stream=None, precision="fp64", refine_iters=2):
+                 stream=None, precision="fp64", refine_iters=1):
         import torch
         self._torch = torch
         L = lib()

@@ -33,42 +33,43 @@ struct Band {
 // (D_z f)[lev] for a column held in shared memory with stride T between levels.  lev is
 // uniform across a warp, so the tap table reads are broadcasts and the branch on the tap
 // count (N interior, 2N interface, N+1 wall) does not diverge.
-template <int N>
-__device__ __forceinline__ double col_dz(const double* f, int T, int lev, const RefLev& R) {
+template <int N, typename XT>
+__device__ __forceinline__ double col_dz(const XT* f, int T, int lev, const RefLev& R) {
   constexpr int W = 2 * N + 1;
   const double* c = R.dz_c + (long long)lev * W;
   const int* o = R.dz_o + (long long)lev * W;
   const int n = __ldg(R.dz_n + lev);
-  const double* p = f + lev * T;
+  const XT* p = f + lev * T;
   if (n == N) {
-    double a0 = __ldg(c) * p[__ldg(o) * T], a1 = 0.0;
+    double a0 = __ldg(c) * (double)p[__ldg(o) * T], a1 = 0.0;
 #pragma unroll
     for (int t = 1; t < N; ++t) {
-      if (t & 1) a1 = fma(__ldg(c + t), p[__ldg(o + t) * T], a1);
-      else a0 = fma(__ldg(c + t), p[__ldg(o + t) * T], a0);
+      if (t & 1) a1 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a1);
+      else a0 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a0);
     }
     return a0 + a1;
   }
   if (n == 2 * N) {
-    double a0 = __ldg(c) * p[__ldg(o) * T], a1 = __ldg(c + 1) * p[__ldg(o + 1) * T];
+    double a0 = __ldg(c) * (double)p[__ldg(o) * T], a1 = __ldg(c + 1) * (double)p[__ldg(o + 1) * T];
 #pragma unroll
     for (int t = 2; t < 2 * N; ++t) {
-      if (t & 1) a1 = fma(__ldg(c + t), p[__ldg(o + t) * T], a1);
-      else a0 = fma(__ldg(c + t), p[__ldg(o + t) * T], a0);
+      if (t & 1) a1 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a1);
+      else a0 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a0);
     }
     return a0 + a1;
   }
   double acc = 0.0;
-  for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), p[__ldg(o + t) * T], acc);
+  for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);
   return acc;
 }
 
 // w_p(x)[lev] = lam A^-1 (D_z x / rho0 + g x / (G0 rho0)), zero at the two walls (the
 // tables kp1, kp2 carry the zeros).
-template <int N>
-__device__ __forceinline__ double col_wp(const double* x, int T, int lev, const RefLev& R,
+template <int N, typename XT>
+__device__ __forceinline__ double col_wp(const XT* x, int T, int lev, const RefLev& R,
                                          const StageTab& tb) {
-  return fma(__ldg(tb.kp1 + lev), col_dz<N>(x, T, lev, R), __ldg(tb.kp2 + lev) * x[lev * T]);
+  return fma(__ldg(tb.kp1 + lev), col_dz<N, XT>(x, T, lev, R),
+             __ldg(tb.kp2 + lev) * (double)x[lev * T]);
 }
 
 // Solve L U x = b in place for one column held in shared memory (stride T), VT the value
@@ -124,32 +125,49 @@ __device__ __forceinline__ void col_solve(VT* x, int T, int M, const FT* __restr
 }
 
 // S x = b for one column: FP64 factors, or FP32 factors with FP64 iterative refinement
-// (r = b - S x with the FP64 matrix-free operator, correction solved in FP32).
-//   b: FP64 right-hand side (kept), tmp: FP64 scratch column, X: FP64 solution,
-//   Tf: FP32 scratch column (mixed form only).
+// (r = b - S X with the FP64 matrix-free operator, correction solved in FP32).
+//   B: FP64 right-hand side; on return it holds x.
+//   tmp: FP64 scratch column (w_p of the current iterate);
+//   Tf, Td: FP32 scratch columns; Xd: FP64 iterate, needed only when iters >= 2.
+// The first FP32 solution x0 (Tf) is exact as a double, so the first residual reads it
+// from float; later iterates are FP64 (Xd).
+// r = b - S X at one level, with tmp = w_p(X) and xl = X[lev].
+template <int N>
+__device__ __forceinline__ double col_residual(const double* B, const double* tmp, int T, int lev,
+                                               const RefLev& R, const StageTab& tb, double xl) {
+  const double Sx = xl - fma(__ldg(tb.kF + lev), tmp[lev * T],
+                             __ldg(tb.kD + lev) * col_dz<N, double>(tmp, T, lev, R));
+  return B[lev * T] - Sx;
+}
+
 template <int N, bool MIXED>
-__device__ __forceinline__ void col_solve_refined(const double* b, double* tmp, double* X, float* Tf,
-                                                  int T, int M, const Factors& F, long long nc,
-                                                  long long col, const RefLev& R,
+__device__ __forceinline__ void col_solve_refined(double* B, double* tmp, float* Tf, float* Td,
+                                                  double* Xd, int T, int M, const Factors& F,
+                                                  long long nc, long long col, const RefLev& R,
                                                   const StageTab& tb, int iters) {
   if (!MIXED) {
-    for (int lev = 0; lev < M; ++lev) X[lev * T] = b[lev * T];
-    col_solve<2 * N, double, double>(X, T, M, F.L, F.U, nc, col);
+    col_solve<2 * N, double, double>(B, T, M, F.L, F.U, nc, col);
     return;
   }
-  for (int lev = 0; lev < M; ++lev) Tf[lev * T] = (float)b[lev * T];
+  for (int lev = 0; lev < M; ++lev) Tf[lev * T] = (float)B[lev * T];
   col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, nc, col);
-  for (int lev = 0; lev < M; ++lev) X[lev * T] = (double)Tf[lev * T];
   for (int it = 0; it < iters; ++it) {
-    for (int lev = 0; lev < M; ++lev) tmp[lev * T] = col_wp<N>(X, T, lev, R, tb);
+    const bool first = (it == 0), last = (it == iters - 1);
+    for (int lev = 0; lev < M; ++lev)
+      tmp[lev * T] = first ? col_wp<N, float>(Tf, T, lev, R, tb) : col_wp<N, double>(Xd, T, lev, R, tb);
     for (int lev = 0; lev < M; ++lev) {
-      const double Sx = X[lev * T] - fma(__ldg(tb.kF + lev), tmp[lev * T],
-                                         __ldg(tb.kD + lev) * col_dz<N>(tmp, T, lev, R));
-      Tf[lev * T] = (float)(b[lev * T] - Sx);
+      const double xl = first ? (double)Tf[lev * T] : Xd[lev * T];
+      Td[lev * T] = (float)col_residual<N>(B, tmp, T, lev, R, tb, xl);
     }
-    col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, nc, col);
-    for (int lev = 0; lev < M; ++lev) X[lev * T] += (double)Tf[lev * T];
+    col_solve<2 * N, float, float>(Td, T, M, F.L32, F.U32, nc, col);
+    for (int lev = 0; lev < M; ++lev) {
+      const double x = (first ? (double)Tf[lev * T] : Xd[lev * T]) + (double)Td[lev * T];
+      if (last) B[lev * T] = x;
+      else Xd[lev * T] = x;
+    }
   }
+  if (iters == 0)
+    for (int lev = 0; lev < M; ++lev) B[lev * T] = (double)Tf[lev * T];
 }
 
 // Algorithm 7 (BuildJacobian) for the Schur form, one column per thread: column m of
@@ -209,6 +227,13 @@ __global__ void k_factor(Geom G, RefLev R, double lam, FT* Lf, FT* Uf, int hb, u
   }
 }
 
+// Shared memory of the column kernels, per column and level: the FP64 method keeps two
+// FP64 columns; the mixed form adds two FP32 columns and, for two or more refinement
+// sweeps, a third FP64 column.
+__host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
+  return mixed ? 2 * 8 + 2 * 4 + (iters >= 2 ? 8 : 0) : 2 * 8;
+}
+
 template <int N, bool MIXED>
 __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R, StageTab tb,
                         int iters) {
@@ -219,9 +244,10 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
   const long long base = col0 * M;
   const int cnt = ncols * M;
   double* Sb = sm;
-  double* Sx = sm + M * T;
-  double* St = sm + 2 * M * T;
-  float* Tf = (float*)(sm + 3 * M * T);
+  double* St = sm + M * T;
+  double* Sx = sm + 2 * M * T;                                  // only when iters >= 2
+  float* Tf = (float*)(sm + (iters >= 2 ? 3 : 2) * M * T);
+  float* Td = Tf + M * T;
   for (int j = threadIdx.x; j < cnt; j += T) {
     const int c = j / M, lev = j - c * M;
     Sb[lev * T + c] = b[base + j];
@@ -229,13 +255,13 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
   __syncthreads();
   if ((int)threadIdx.x < ncols) {
     const int t = threadIdx.x;
-    col_solve_refined<N, MIXED>(Sb + t, St + t, Sx + t, Tf + t, T, M, F, G.ncol, col0 + t, R, tb,
-                                iters);
+    col_solve_refined<N, MIXED>(Sb + t, St + t, Tf + t, Td + t, Sx + t, T, M, F, G.ncol, col0 + t,
+                                R, tb, iters);
   }
   __syncthreads();
   for (int j = threadIdx.x; j < cnt; j += T) {
     const int c = j / M, lev = j - c * M;
-    x[base + j] = Sx[lev * T + c];
+    x[base + j] = Sb[lev * T + c];
   }
 }
 
@@ -262,10 +288,11 @@ __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1
   const int ncols = (int)min((long long)T, G.ncol - col0);
   const long long base = col0 * M;
   const int cnt = ncols * M;
-  double* S0 = sm;              // P_e -> b
+  double* S0 = sm;              // P_e -> b -> P
   double* S1 = sm + M * T;      // w_a -> (scratch) -> w_p(P)
-  double* SX = MIXED ? sm + 2 * M * T : S0;   // P (the mixed form keeps b)
-  float* Tf = (float*)(sm + 3 * M * T);
+  double* SXd = sm + 2 * M * T; // mixed form with >= 2 sweeps: FP64 iterate
+  float* Tf = (float*)(sm + (iters >= 2 ? 3 : 2) * M * T);
+  float* Td = Tf + M * T;
   const double a1dt = sc.a[0] * sc.dt, a2dt = sc.a[1] * sc.dt;
   const double c1 = sc.c[0], c2 = sc.c[1];
 
@@ -299,16 +326,12 @@ __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1
     double* B = S0 + t;
     double* Wt = S1 + t;
     for (int lev = 0; lev < M; ++lev) {     // b = P_e - lam F0z w_a - lam rho0 G0 D_z w_a
-      const double dzw = col_dz<N>(Wt, T, lev, R);
+      const double dzw = col_dz<N, double>(Wt, T, lev, R);
       B[lev * T] = fma(-__ldg(tb.kF + lev), Wt[lev * T], fma(-__ldg(tb.kD + lev), dzw, B[lev * T]));
     }
-    double* X = SX + t;
-    if (MIXED) {
-      col_solve_refined<N, true>(B, Wt, X, Tf + t, T, M, F, G.ncol, col0 + t, R, tb, iters);
-    } else {
-      col_solve<2 * N, double, double>(B, T, M, F.L, F.U, G.ncol, col0 + t);
-    }
-    for (int lev = 0; lev < M; ++lev) Wt[lev * T] = col_wp<N>(X, T, lev, R, tb);
+    col_solve_refined<N, MIXED>(B, Wt, Tf + t, Td + t, SXd + t, T, M, F, G.ncol, col0 + t, R, tb,
+                                iters);
+    for (int lev = 0; lev < M; ++lev) Wt[lev * T] = col_wp<N, double>(B, T, lev, R, tb);
   }
   __syncthreads();
 
@@ -322,7 +345,7 @@ __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1
     const double wa = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
     const double wv = wa - S1[lev * T + c];
     const double thv = fma(-__ldg(tb.kth + lev), wv, te);
-    const double rv = fma(-__ldg(tb.H0G0 + lev), thv, __ldg(tb.invG0 + lev) * SX[lev * T + c]);
+    const double rv = fma(-__ldg(tb.H0G0 + lev), thv, __ldg(tb.invG0 + lev) * S0[lev * T + c]);
     double o_r = fma(-c1, qn[orr], rv), o_w = fma(-c1, qn[ow], wv), o_t = fma(-c1, qn[oth], thv);
     if (S3) {
       o_r = fma(-c2, q2[orr], o_r);
@@ -335,14 +358,14 @@ __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1
   }
 }
 
-size_t stage_smem(int M, int T, bool mixed) {
-  return mixed ? ((size_t)3 * 8 + 4) * M * T : (size_t)2 * 8 * M * T;
+size_t stage_smem(int M, int T, bool mixed, int iters) {
+  return col_smem_per_level(mixed, iters) * M * T;
 }
 
 template <int N, bool MIXED>
 cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, const Factors& F,
                            const RefLev& R, const StageTab& tb, int T, int iters, cudaStream_t s) {
-  const size_t smem = ((size_t)3 * 8 + (MIXED ? 4 : 0)) * G.M * T;
+  const size_t smem = col_smem_per_level(MIXED, iters) * G.M * T;
   cudaError_t e = cudaFuncSetAttribute(k_solve<N, MIXED>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -355,7 +378,7 @@ cudaError_t launch_stage_k(const double* qn, const RT* R1, const RT* R2, const d
                            double* out, const Geom& G, const RefLev& R, const Factors& F,
                            const StageCoef& sc, const StageTab& tb, int T, int iters,
                            cudaStream_t s) {
-  const size_t smem = stage_smem(G.M, T, MIXED);
+  const size_t smem = stage_smem(G.M, T, MIXED, iters);
   cudaError_t e = cudaFuncSetAttribute(k_stage<N, S3, MIXED, RT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -431,4 +454,6 @@ cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void
   }
 }
 
-size_t stage_smem_bytes(int M, int T, bool mixed) { return stage_smem(M, T, mixed); }
+size_t stage_smem_bytes(int M, int T, bool mixed, int iters) {
+  return stage_smem(M, T, mixed, iters);
+}

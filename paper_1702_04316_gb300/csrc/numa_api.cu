@@ -383,7 +383,7 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
                  void* stream, numa_ctx** out) {
   if (!out) return NUMA_ERR_ARG;
   const int precision = opt ? opt->precision : NUMA_PREC_FP64;
-  const int refine = opt ? opt->refine_iters : 2;
+  const int refine = opt ? opt->refine_iters : 1;
   if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED) || refine < 0 || refine > 8) {
     *out = nullptr;
     return NUMA_ERR_ARG;

@@ -146,7 +146,7 @@ cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void
                          const double* q2, double* out, const Geom& G, const RefLev& R,
                          Factors F, const StageCoef& sc, const StageTab& tb, int T,
                          bool r_float, cudaStream_t s);
-size_t stage_smem_bytes(int M, int T, bool mixed);
+size_t stage_smem_bytes(int M, int T, bool mixed, int iters);
 
 // misc.cu
 cudaError_t launch_connectivity(const Geom& G, int32_t* l2g, int32_t* g2l, cudaStream_t s);

@@ -6,7 +6,7 @@ workload shape on a smaller box: ``--nex`` x ``--nex`` x 12 elements of order 4 
 gives a 164 MB state (larger than the 129 MB L2) and about 1.7 GB of device memory.
 Every step reads the same input and writes a separate output.
 
-  python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0]
+  python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0] [--precision mixed]
 """
 import argparse
 import os
@@ -25,6 +25,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--rk", type=int, default=0)
     ap.add_argument("--C", type=float, default=15.0)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     a = ap.parse_args()
     import torch
     import paper_1702_04316_gb300 as pkg
@@ -35,7 +36,7 @@ def main():
     xi = np.array([-1.0, -np.sqrt(3.0 / 7.0), 0.0, np.sqrt(3.0 / 7.0), 1.0])
     c_s = (1004.67 / (1004.67 - 287.17) * 287.17 * 300.0) ** 0.5
     dt = a.C * (xi[1] + 1.0) / 2.0 * (Lz / nez) / c_s
-    g = pkg.Numa(nex, nex, nez, L, L, Lz, N, dt)
+    g = pkg.Numa(nex, nex, nez, L, L, Lz, N, dt, precision=a.precision)
     lev = g.reference_levels()
     h = L / nex
     ax = np.concatenate([e * h + (1.0 + xi[:-1]) * h / 2.0 for e in range(nex)] + [[L]])

@@ -11,7 +11,7 @@ from helpers import Case, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def ctx(case, dt=0.0, iters=2):
+def ctx(case, dt=0.0, iters=1):
     import paper_1702_04316_gb300 as pkg
     nex, ney, nez, Lx, Ly, Lz, N = case.args
     return pkg.Numa(nex, ney, nez, Lx, Ly, Lz, N, dt, 300.0, case.n_bv, precision="mixed",
@@ -31,7 +31,7 @@ def test_mixed_rhs_error(dims, n_bv):
     assert np.all(e < 2e-6), e
 
 
-@pytest.mark.parametrize("C,iters,tol", [(15, 2, 1e-12), (150, 3, 1e-11)])
+@pytest.mark.parametrize("C,iters,tol", [(15, 1, 1e-10), (15, 2, 1e-12), (150, 3, 1e-11)])
 def test_mixed_solve_refined_to_fp64(C, iters, tol):
     import torch
     from oracle.column import lu_nopivot_banded, lu_solve_banded
