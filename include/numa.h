@@ -87,7 +87,8 @@ enum {
  *            and the reference state stay FP64), the column Schur matrices factored and
  *            solved in FP32 with refine_iters sweeps of FP64 iterative refinement (FP64
  *            residual with the matrix-free Schur operator), FP64 state accumulation.
- * refine_iters: FP64 refinement sweeps per solve in the mixed form (0..8; default 2). */
+ * refine_iters: FP64 refinement sweeps per solve in the mixed form (0..8; numa_init_ex with
+ *               opt = NULL uses 1). */
 enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1 };
 typedef struct numa_options {
   int precision;
@@ -203,6 +204,41 @@ int numa_query(const numa_ctx* ctx, int what, long long* out);
 
 /* One-line message of the last failing call on this context ("" if none). */
 const char* numa_last_error(const numa_ctx* ctx);
+
+/* ---- ensembles ("batching form") -------------------------------------------------------
+ * An ensemble of independent members, each with its own uniform box mesh, polynomial order
+ * (4 <= N <= 6), reference state and HEVI time step dt (its column factors are formed at
+ * its own dt).  Every phase of a step is one persistent launch for the whole ensemble (a
+ * work list of (member, block) items); each step is captured as a CUDA graph on first use
+ * for a given (q_in, q_out) pair and replayed.  numa_batch_init autotunes the right-hand
+ * side's threads per CTA and the stage's columns per CTA on the ensemble.
+ * States are packed: member m occupies doubles [off[m], off[m+1]) of one device array
+ * (numa_batch_layout), in the single-mesh SoA layout of that member.  All calls use the
+ * stream given to numa_batch_init and follow the error conventions above. */
+typedef struct numa_batch numa_batch;
+
+/* Synchronous set-up of nmembers members: meshes[m], N[m], dt[m].  On failure *out is NULL. */
+int numa_batch_init(const numa_mesh_desc* meshes, const int* N, const double* dt, int nmembers,
+                    void* stream, numa_batch** out);
+void numa_batch_destroy(numa_batch* b);
+
+/* Packed-state offsets: nmembers+1 values (the last is the total length in doubles). */
+int numa_batch_layout(const numa_batch* b, long long* offsets);
+
+/* nsteps HEVI 1D-IMEX steps of every member (each at its own dt) from q_in to q_out
+ * (packed device arrays; in place allowed). */
+int numa_batch_step_imex1d(numa_batch* b, const double* q_in, double* q_out, int nsteps);
+
+/* 1 (default): replay each step as a CUDA graph; 0: launch the kernels directly. */
+int numa_batch_set_graph(numa_batch* b, int enable);
+
+/* The autotuned threads per CTA of the right-hand side and columns per CTA of the stage. */
+int numa_batch_tuning(const numa_batch* b, int* rhs_threads, int* col_tile);
+
+/* numa_query / numa_reference_levels of one member. */
+int numa_batch_member_query(const numa_batch* b, int member, int what, long long* out);
+int numa_batch_reference_levels(const numa_batch* b, int member, double* host_out);
+const char* numa_batch_last_error(const numa_batch* b);
 
 /* Size of the device scratch array used by numa_rhs_explicit_static.  Every GPU that loads
  * the library holds an array of this size until the process exits. */

@@ -29,7 +29,9 @@ EXPORTS = (
     "numa_run_host", "numa_connectivity", "numa_column_factors", "numa_reference_levels",
     "numa_count_nonfinite", "numa_status", "numa_query", "numa_last_error",
     "numa_rk35_coefficients", "numa_ark2_tableau", "numa_profile", "numa_profile_read",
-    "numa_rhs_explicit_static",
+    "numa_rhs_explicit_static", "numa_batch_init", "numa_batch_destroy", "numa_batch_layout",
+    "numa_batch_step_imex1d", "numa_batch_set_graph", "numa_batch_tuning",
+    "numa_batch_member_query", "numa_batch_reference_levels", "numa_batch_last_error",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR = range(5)
 
@@ -80,6 +82,15 @@ def lib():
             "numa_rk35_coefficients": (None, [P, P]),
             "numa_ark2_tableau": (None, [P, P, P]),
             "numa_rhs_explicit_static": (I, [ctypes.POINTER(MeshDesc), I, P, P, P]),
+            "numa_batch_init": (I, [ctypes.POINTER(MeshDesc), P, P, I, P, ctypes.POINTER(P)]),
+            "numa_batch_destroy": (None, [P]),
+            "numa_batch_layout": (I, [P, P]),
+            "numa_batch_step_imex1d": (I, [P, P, P, I]),
+            "numa_batch_set_graph": (I, [P, I]),
+            "numa_batch_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "numa_batch_member_query": (I, [P, I, I, ctypes.POINTER(LL)]),
+            "numa_batch_reference_levels": (I, [P, I, P]),
+            "numa_batch_last_error": (ctypes.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -247,6 +258,79 @@ class Numa:
         s = ctypes.c_int()
         self._check(lib().numa_status(self._h, ctypes.byref(s)), "numa_status")
         return s.value
+
+
+class Batch:
+    """An ensemble of independent members (numa_batch): meshes is a list of
+    (nex, ney, nez, Lx, Ly, Lz) tuples, N and dt lists of the same length."""
+
+    def __init__(self, meshes, N, dt, theta_s=300.0, n_bv=0.0, stream=None):
+        import torch
+        self._torch = torch
+        n = len(meshes)
+        descs = (MeshDesc * n)(*[MeshDesc(*m, theta_s, n_bv) for m in meshes])
+        Ns = (ctypes.c_int * n)(*[int(v) for v in N])
+        dts = (ctypes.c_double * n)(*[float(v) for v in dt])
+        s = torch.cuda.current_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        rc = lib().numa_batch_init(descs, ctypes.cast(Ns, ctypes.c_void_p), ctypes.cast(dts, ctypes.c_void_p),
+                                   n, ctypes.c_void_p(s.cuda_stream), ctypes.byref(h))
+        if rc != NUMA_OK:
+            raise NumaError("numa_batch_init failed: %s" % ERRORS.get(rc, rc))
+        self._h = h
+        self.n = n
+        off = (ctypes.c_longlong * (n + 1))()
+        self._check(lib().numa_batch_layout(self._h, ctypes.cast(off, ctypes.c_void_p)), "layout")
+        self.offsets = list(off)
+        self.total = self.offsets[-1]
+
+    def _check(self, rc, what):
+        if rc != NUMA_OK:
+            raise NumaError("%s: %s (%s)" % (what, ERRORS.get(rc, rc),
+                                             lib().numa_batch_last_error(self._h).decode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().numa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_state(self):
+        return self._torch.empty(self.total, dtype=self._torch.float64, device="cuda")
+
+    def member(self, state, m):
+        """View of member m in a packed state: (5, nnode)."""
+        return state[self.offsets[m]:self.offsets[m + 1]].view(5, -1)
+
+    def step_imex1d(self, q_in, q_out=None, nsteps=1):
+        q_out = q_in if q_out is None else q_out
+        self._check(lib().numa_batch_step_imex1d(self._h, _ptr(q_in), _ptr(q_out), int(nsteps)), "step")
+        return q_out
+
+    def set_graph(self, enable):
+        self._check(lib().numa_batch_set_graph(self._h, 1 if enable else 0), "set_graph")
+
+    def tuning(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().numa_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(b)), "tuning")
+        return {"rhs_threads_per_cta": a.value, "stage_columns_per_cta": b.value}
+
+    def member_query(self, m, what):
+        v = ctypes.c_longlong()
+        self._check(lib().numa_batch_member_query(self._h, int(m), int(what), ctypes.byref(v)), "query")
+        return v.value
+
+    def reference_levels(self, m):
+        M = self.member_query(m, Q_M)
+        out = np.empty((8, M), dtype=np.float64)
+        self._check(lib().numa_batch_reference_levels(self._h, int(m), out.ctypes.data_as(ctypes.c_void_p)),
+                    "reference_levels")
+        return dict(zip(("z", "rho0", "theta0", "P0", "G0", "H0", "drho0", "dtheta0"), out))
 
 
 def rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out, theta_s=300.0, n_bv=0.0,

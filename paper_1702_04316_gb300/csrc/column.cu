@@ -14,161 +14,10 @@
 // row is one FMA and the factors are read by column (the layout numa_internal.cuh gives).
 #include "numa_internal.cuh"
 
+#include "column_device.cuh"
+
 namespace {
-
-// ---- band accessor of the stored factors (column-oriented layout) ----------------------
-template <typename FT>
-struct Band {
-  FT* L;
-  FT* U;
-  int hb;
-  long long nc;
-  long long col;
-  __device__ __forceinline__ FT& at(int i, int j) const {
-    return (j < i) ? L[((long long)j * hb + (i - j) - 1) * nc + col]
-                   : U[((long long)j * (hb + 1) + (j - i)) * nc + col];
-  }
-};
-
-// (D_z f)[lev] for a column held in shared memory with stride T between levels.  lev is
-// uniform across a warp, so the tap table reads are broadcasts and the branch on the tap
-// count (N interior, 2N interface, N+1 wall) does not diverge.
-template <int N, typename XT>
-__device__ __forceinline__ double col_dz(const XT* f, int T, int lev, const RefLev& R) {
-  constexpr int W = 2 * N + 1;
-  const double* c = R.dz_c + (long long)lev * W;
-  const int* o = R.dz_o + (long long)lev * W;
-  const int n = __ldg(R.dz_n + lev);
-  const XT* p = f + lev * T;
-  if (n == N) {
-    double a0 = __ldg(c) * (double)p[__ldg(o) * T], a1 = 0.0;
-#pragma unroll
-    for (int t = 1; t < N; ++t) {
-      if (t & 1) a1 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a1);
-      else a0 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a0);
-    }
-    return a0 + a1;
-  }
-  if (n == 2 * N) {
-    double a0 = __ldg(c) * (double)p[__ldg(o) * T], a1 = __ldg(c + 1) * (double)p[__ldg(o + 1) * T];
-#pragma unroll
-    for (int t = 2; t < 2 * N; ++t) {
-      if (t & 1) a1 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a1);
-      else a0 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a0);
-    }
-    return a0 + a1;
-  }
-  double acc = 0.0;
-  for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);
-  return acc;
-}
-
-// w_p(x)[lev] = lam A^-1 (D_z x / rho0 + g x / (G0 rho0)), zero at the two walls (the
-// tables kp1, kp2 carry the zeros).
-template <int N, typename XT>
-__device__ __forceinline__ double col_wp(const XT* x, int T, int lev, const RefLev& R,
-                                         const StageTab& tb) {
-  return fma(__ldg(tb.kp1 + lev), col_dz<N, XT>(x, T, lev, R),
-             __ldg(tb.kp2 + lev) * (double)x[lev * T]);
-}
-
-// Solve L U x = b in place for one column held in shared memory (stride T), VT the value
-// type, FT the factor type.  Forward: y_i = w_0; x_{i+1+k} -= L(i+1+k, i) y_i for k < HB
-// (window w in registers).  Backward: x_i = v_0 / U(i,i); y_{i-1-k} -= U(i-1-k, i) x_i.
-// Factor columns are prefetched one column ahead.
-template <int HB, typename VT, typename FT>
-__device__ __forceinline__ void col_solve(VT* x, int T, int M, const FT* __restrict__ L,
-                                          const FT* __restrict__ U, long long nc, long long col) {
-  VT w[HB], l[HB], ln[HB];
-#pragma unroll
-  for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : (VT)0;
-#pragma unroll
-  for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(L + (long long)k * nc + col);
-  for (int i = 0; i < M; ++i) {
-#pragma unroll
-    for (int k = 0; k < HB; ++k) l[k] = ln[k];
-    if (i + 1 < M) {
-      const FT* Lc = L + (long long)(i + 1) * HB * nc + col;
-#pragma unroll
-      for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(Lc + (long long)k * nc);
-    }
-    const VT y = w[0];
-    x[i * T] = y;
-    const VT nxt = (i + HB < M) ? x[(i + HB) * T] : (VT)0;
-#pragma unroll
-    for (int k = 0; k < HB - 1; ++k) w[k] = fma(-l[k], y, w[k + 1]);
-    w[HB - 1] = fma(-l[HB - 1], y, nxt);
-  }
-  VT v[HB], u[HB + 1], un[HB + 1];
-#pragma unroll
-  for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : (VT)0;
-  {
-    const FT* Uc = U + (long long)(M - 1) * (HB + 1) * nc + col;
-#pragma unroll
-    for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * nc);
-  }
-  for (int i = M - 1; i >= 0; --i) {
-#pragma unroll
-    for (int k = 0; k <= HB; ++k) u[k] = un[k];
-    if (i > 0) {
-      const FT* Uc = U + (long long)(i - 1) * (HB + 1) * nc + col;
-#pragma unroll
-      for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * nc);
-    }
-    const VT xi = v[0] * u[0];
-    x[i * T] = xi;
-    const VT nxt = (i - HB >= 0) ? x[(i - HB) * T] : (VT)0;
-#pragma unroll
-    for (int k = 0; k < HB - 1; ++k) v[k] = fma(-u[k + 1], xi, v[k + 1]);
-    v[HB - 1] = fma(-u[HB], xi, nxt);
-  }
-}
-
-// S x = b for one column: FP64 factors, or FP32 factors with FP64 iterative refinement
-// (r = b - S X with the FP64 matrix-free operator, correction solved in FP32).
-//   B: FP64 right-hand side; on return it holds x.
-//   tmp: FP64 scratch column (w_p of the current iterate);
-//   Tf, Td: FP32 scratch columns; Xd: FP64 iterate, needed only when iters >= 2.
-// The first FP32 solution x0 (Tf) is exact as a double, so the first residual reads it
-// from float; later iterates are FP64 (Xd).
-// r = b - S X at one level, with tmp = w_p(X) and xl = X[lev].
-template <int N>
-__device__ __forceinline__ double col_residual(const double* B, const double* tmp, int T, int lev,
-                                               const RefLev& R, const StageTab& tb, double xl) {
-  const double Sx = xl - fma(__ldg(tb.kF + lev), tmp[lev * T],
-                             __ldg(tb.kD + lev) * col_dz<N, double>(tmp, T, lev, R));
-  return B[lev * T] - Sx;
-}
-
-template <int N, bool MIXED>
-__device__ __forceinline__ void col_solve_refined(double* B, double* tmp, float* Tf, float* Td,
-                                                  double* Xd, int T, int M, const Factors& F,
-                                                  long long nc, long long col, const RefLev& R,
-                                                  const StageTab& tb, int iters) {
-  if (!MIXED) {
-    col_solve<2 * N, double, double>(B, T, M, F.L, F.U, nc, col);
-    return;
-  }
-  for (int lev = 0; lev < M; ++lev) Tf[lev * T] = (float)B[lev * T];
-  col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, nc, col);
-  for (int it = 0; it < iters; ++it) {
-    const bool first = (it == 0), last = (it == iters - 1);
-    for (int lev = 0; lev < M; ++lev)
-      tmp[lev * T] = first ? col_wp<N, float>(Tf, T, lev, R, tb) : col_wp<N, double>(Xd, T, lev, R, tb);
-    for (int lev = 0; lev < M; ++lev) {
-      const double xl = first ? (double)Tf[lev * T] : Xd[lev * T];
-      Td[lev * T] = (float)col_residual<N>(B, tmp, T, lev, R, tb, xl);
-    }
-    col_solve<2 * N, float, float>(Td, T, M, F.L32, F.U32, nc, col);
-    for (int lev = 0; lev < M; ++lev) {
-      const double x = (first ? (double)Tf[lev * T] : Xd[lev * T]) + (double)Td[lev * T];
-      if (last) B[lev * T] = x;
-      else Xd[lev * T] = x;
-    }
-  }
-  if (iters == 0)
-    for (int lev = 0; lev < M; ++lev) B[lev * T] = (double)Tf[lev * T];
-}
+using namespace numa_dev;
 
 // Algorithm 7 (BuildJacobian) for the Schur form, one column per thread: column m of
 // S(lam) is the left-hand side applied to the unit vector e_m,
@@ -227,13 +76,6 @@ __global__ void k_factor(Geom G, RefLev R, double lam, FT* Lf, FT* Uf, int hb, u
   }
 }
 
-// Shared memory of the column kernels, per column and level: the FP64 method keeps two
-// FP64 columns; the mixed form adds two FP32 columns and, for two or more refinement
-// sweeps, a third FP64 column.
-__host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
-  return mixed ? 2 * 8 + 2 * 4 + (iters >= 2 ? 8 : 0) : 2 * 8;
-}
-
 template <int N, bool MIXED>
 __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R, StageTab tb,
                         int iters) {
@@ -265,97 +107,14 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
   }
 }
 
-// Fused 1D-IMEX stage (rows 2 or 3 of Table 1).
-// Phase 1 (all threads, coalesced): the explicit predictor q(i)_e = q^n + dt sum_j a_ij R_j
-//   and the shift q~_e = q(i)_e + sum_j c_ij q(j); u, v are final here.  Shared memory keeps
-//   P_e = G0 rho~_e + H0 theta~_e and w_a = A^-1 (w~_e + lam g theta~_e / theta0).
-// Phase 2 (one thread per column): Schur right-hand side b (Algorithm 4), the column solve,
-//   and w_p(P) (Eq. utteqn).
-// Phase 3 (coalesced): w~ = w_a - w_p(P), theta~ = theta~_e - lam w~ d(theta0)/dz,
-//   rho~ = (P - H0 theta~) / G0 (w_a and theta~_e recomputed from their sources rather than
-//   kept in shared memory, which doubles the resident columns), then
-//   q(i) = q~ - sum_j c_ij q(j).
-// RT: type of R1, R2 (double, or float in the mixed form).
 template <int N, bool S3, bool MIXED, typename RT>
 __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
                         const RT* __restrict__ R2, const double* __restrict__ q2,
                         double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
                         StageTab tb, int iters) {
   extern __shared__ double sm[];
-  const int T = blockDim.x, M = G.M;
-  const long long nn = G.nnode;
-  const long long col0 = blockIdx.x * (long long)T;
-  const int ncols = (int)min((long long)T, G.ncol - col0);
-  const long long base = col0 * M;
-  const int cnt = ncols * M;
-  double* S0 = sm;              // P_e -> b -> P
-  double* S1 = sm + M * T;      // w_a -> (scratch) -> w_p(P)
-  double* SXd = sm + 2 * M * T; // mixed form with >= 2 sweeps: FP64 iterate
-  float* Tf = (float*)(sm + (iters >= 2 ? 3 : 2) * M * T);
-  float* Td = Tf + M * T;
-  const double a1dt = sc.a[0] * sc.dt, a2dt = sc.a[1] * sc.dt;
-  const double c1 = sc.c[0], c2 = sc.c[1];
-
-  // predictor of field f at global offset o (q(i)_e, shifted to q~_e unless u, v)
-  auto pred = [&](int f, long long o) -> double {
-    const double qv = qn[o];
-    double v = fma(a1dt, (double)R1[o], qv);
-    if (S3) v = fma(a2dt, (double)R2[o], v);
-    if (f == 1 || f == 2) return v;
-    v = fma(c1, qv, v);
-    if (S3) v = fma(c2, q2[o], v);
-    return v;
-  };
-
-  // phase 1
-#pragma unroll 2
-  for (int j = threadIdx.x; j < cnt; j += T) {
-    const long long g = base + j;
-    const int c = j / M, lev = j - c * M;
-    out[nn + g] = pred(1, nn + g);
-    out[2 * nn + g] = pred(2, 2 * nn + g);
-    const double re = pred(0, g), we = pred(3, 3 * nn + g), te = pred(4, 4 * nn + g);
-    S1[lev * T + c] = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
-    S0[lev * T + c] = fma(__ldg(tb.G0 + lev), re, __ldg(tb.H0 + lev) * te);
-  }
-  __syncthreads();
-
-  // phase 2
-  if ((int)threadIdx.x < ncols) {
-    const int t = threadIdx.x;
-    double* B = S0 + t;
-    double* Wt = S1 + t;
-    for (int lev = 0; lev < M; ++lev) {     // b = P_e - lam F0z w_a - lam rho0 G0 D_z w_a
-      const double dzw = col_dz<N, double>(Wt, T, lev, R);
-      B[lev * T] = fma(-__ldg(tb.kF + lev), Wt[lev * T], fma(-__ldg(tb.kD + lev), dzw, B[lev * T]));
-    }
-    col_solve_refined<N, MIXED>(B, Wt, Tf + t, Td + t, SXd + t, T, M, F, G.ncol, col0 + t, R, tb,
-                                iters);
-    for (int lev = 0; lev < M; ++lev) Wt[lev * T] = col_wp<N, double>(B, T, lev, R, tb);
-  }
-  __syncthreads();
-
-  // phase 3
-#pragma unroll 2
-  for (int j = threadIdx.x; j < cnt; j += T) {
-    const long long g = base + j;
-    const int c = j / M, lev = j - c * M;
-    const long long orr = g, ow = 3 * nn + g, oth = 4 * nn + g;
-    const double te = pred(4, oth), we = pred(3, ow);
-    const double wa = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
-    const double wv = wa - S1[lev * T + c];
-    const double thv = fma(-__ldg(tb.kth + lev), wv, te);
-    const double rv = fma(-__ldg(tb.H0G0 + lev), thv, __ldg(tb.invG0 + lev) * S0[lev * T + c]);
-    double o_r = fma(-c1, qn[orr], rv), o_w = fma(-c1, qn[ow], wv), o_t = fma(-c1, qn[oth], thv);
-    if (S3) {
-      o_r = fma(-c2, q2[orr], o_r);
-      o_w = fma(-c2, q2[ow], o_w);
-      o_t = fma(-c2, q2[oth], o_t);
-    }
-    out[orr] = o_r;
-    out[ow] = o_w;
-    out[oth] = o_t;
-  }
+  stage_body<N, S3, MIXED, RT>(blockIdx.x * (long long)blockDim.x, sm, qn, R1, R2, q2, out, G, R,
+                               F, sc, tb, iters);
 }
 
 size_t stage_smem(int M, int T, bool mixed, int iters) {

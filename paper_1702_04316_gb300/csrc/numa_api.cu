@@ -10,6 +10,7 @@
 
 #include "numa.h"
 #include "numa_internal.cuh"
+#include "numa_ctx.h"
 
 namespace {
 
@@ -103,43 +104,6 @@ void set_axis(AxisCoef& c, int N, const double* w, const double* D, double h) {
 }
 
 }  // namespace
-
-// ---- the context ---------------------------------------------------------------------------
-struct numa_ctx {
-  Geom G;
-  Coef3 C;
-  cudaStream_t stream = nullptr;
-  std::string err;
-  double dt = 0.0, lam = 0.0;
-  bool factored = false;
-  double theta_s = 300.0, n_bv = 0.0;
-  // host copies of the per-level tables
-  std::vector<double> z, rho0, theta0, P0, G0, H0, drho0, dtheta0, F0z, dzband;
-  // device memory
-  double* d_lev = nullptr;      // reference tables + dz band + dz taps
-  int* d_levi = nullptr;        // dz tap offsets and counts
-  int col_tile = 64;            // columns per CTA of the column kernels
-  RefLev R{};
-  StageTab T{};
-  double* d_stage_tab = nullptr;
-  Factors F{};
-  double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (each 5*nnode except Pp)
-  double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
-  // mixed-precision form: FP32 stencil fields (6 x nnode) and FP32 R1, R2 (5 x nnode each)
-  float *F32 = nullptr, *R1f = nullptr, *R2f = nullptr;
-  int precision = NUMA_PREC_FP64;
-  int* d_perm = nullptr;        // class-sorted thread order of the right-hand side
-  long long nperm = 0;
-  unsigned* d_status = nullptr;
-  unsigned long long* d_count = nullptr;
-  double* d_hoststate = nullptr;
-  size_t factor_bytes = 0, work_bytes = 0;
-  // per-kernel event timing
-  struct ProfRec { int kind; cudaEvent_t a, b; };
-  std::vector<ProfRec> prof;
-  size_t prof_n = 0;
-  bool prof_on = false;
-};
 
 namespace {
 
@@ -357,7 +321,9 @@ int enqueue_stage(numa_ctx* c, int stage, const double* qn, const void* R1, cons
   return NUMA_OK;
 }
 
-StageCoef stage_coef(const numa_ctx* c, int stage) {
+}  // namespace
+
+StageCoef numa_stage_coef(const numa_ctx* c, int stage) {
   static const Ark2 t;
   StageCoef sc{};
   const int i = stage - 1;
@@ -369,6 +335,8 @@ StageCoef stage_coef(const numa_ctx* c, int stage) {
   }
   return sc;
 }
+
+namespace {
 
 }  // namespace
 
@@ -556,7 +524,7 @@ int numa_imex_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1
     return rc;
   if (stage == 3 && ((rc = check_ptr(ctx, R2, "R2")) || (rc = check_ptr(ctx, q2, "q2")))) return rc;
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
-  return enqueue_stage(ctx, stage, qn, R1, R2, q2, q_out, stage_coef(ctx, stage));
+  return enqueue_stage(ctx, stage, qn, R1, R2, q2, q_out, numa_stage_coef(ctx, stage));
 }
 
 int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nsteps) {
@@ -573,7 +541,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
     return NUMA_OK;
   }
   static const Ark2 t;
-  const StageCoef s2 = stage_coef(ctx, 2), s3 = stage_coef(ctx, 3);
+  const StageCoef s2 = numa_stage_coef(ctx, 2), s3 = numa_stage_coef(ctx, 3);
   const bool mixed = ctx->precision == NUMA_PREC_MIXED;
   void* R1 = mixed ? (void*)ctx->R1f : (void*)ctx->R1;
   void* R2 = mixed ? (void*)ctx->R2f : (void*)ctx->R2;

@@ -1,0 +1,48 @@
+// Host-side definition of the context (include/numa.h declares it opaque).  Shared by
+// numa_api.cu and batch.cu.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "numa.h"
+#include "numa_internal.cuh"
+
+struct numa_ctx {
+  Geom G;
+  Coef3 C;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double dt = 0.0, lam = 0.0;
+  bool factored = false;
+  double theta_s = 300.0, n_bv = 0.0;
+  // host copies of the per-level tables
+  std::vector<double> z, rho0, theta0, P0, G0, H0, drho0, dtheta0, F0z, dzband;
+  // device memory
+  double* d_lev = nullptr;      // reference tables + dz band + dz taps
+  int* d_levi = nullptr;        // dz tap offsets and counts
+  int col_tile = 64;            // columns per CTA of the column kernels
+  RefLev R{};
+  StageTab T{};
+  double* d_stage_tab = nullptr;
+  Factors F{};
+  double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (each 5*nnode except Pp)
+  double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
+  // mixed-precision form: FP32 stencil fields (6 x nnode) and FP32 R1, R2 (5 x nnode each)
+  float *F32 = nullptr, *R1f = nullptr, *R2f = nullptr;
+  int precision = NUMA_PREC_FP64;
+  int* d_perm = nullptr;        // class-sorted thread order of the right-hand side
+  long long nperm = 0;
+  unsigned* d_status = nullptr;
+  unsigned long long* d_count = nullptr;
+  double* d_hoststate = nullptr;
+  size_t factor_bytes = 0, work_bytes = 0;
+  // per-kernel event timing
+  struct ProfRec { int kind; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof;
+  size_t prof_n = 0;
+  bool prof_on = false;
+};
+
+
+// Coefficients of IMEX stage 2 or 3 for the context's dt (Table 1 with b = b~).
+StageCoef numa_stage_coef(const numa_ctx* c, int stage);

@@ -1,0 +1,224 @@
+// Device code of the explicit right-hand side, shared by the single-mesh kernels (rhs.cu)
+// and the persistent ensemble kernels (batch.cu).  See rhs.cu for the method.
+#pragma once
+#include "numa_internal.cuh"
+
+namespace numa_dev {
+
+
+// ---- equation of state ---------------------------------------------------------------------
+// P' = P(rho0 + rho', theta0 + theta') - P0 without cancellation:
+//   (rho theta)/(rho0 theta0) = (1 + a)(1 + b),  a = rho'/rho0,  b = theta'/theta0,
+//   P' = P0 ((1 + x)^gamma - 1),  x = a + b + a b.
+// For |x| <= 1/64 the binomial series sum_{k=1..9} C(gamma, k) x^k is used (truncation
+// below 1e-19 relative); otherwise P0 expm1(gamma log1p(x)).
+struct EosSeries {
+  double c[9];   // C(gamma, k), k = 1..9
+};
+
+// (1 + x)^gamma - 1 for x = a + b + a b at one node.
+__device__ __forceinline__ double eos_rel(double rp, double tp, double inv_rho0, double inv_theta0,
+                                          double gamma, const EosSeries& S) {
+  const double a = rp * inv_rho0;
+  const double b = tp * inv_theta0;
+  const double x = fma(a, b, a + b);
+  if (fabs(x) <= 0.015625) {
+    double p = S.c[8];
+#pragma unroll
+    for (int k = 7; k >= 0; --k) p = fma(p, x, S.c[k]);
+    return p * x;
+  }
+  return expm1(gamma * log1p(x));
+}
+
+// P' of node g of state q (FP64).
+__device__ __forceinline__ double eos_node(const double* __restrict__ q, long long g, const Geom& G,
+                                           const RefLev& R, const EosSeries& S) {
+  const int iz = (int)(g % G.M);
+  return R.P0[iz] * eos_rel(q[g], q[4 * G.nnode + g], R.inv_rho0[iz], R.inv_theta0[iz],
+                            NUMA_GAMMA, S);
+}
+
+// The series coefficients C(gamma, k), k = 1..9.
+inline EosSeries eos_series() {
+  EosSeries S;
+  double c = 1.0;
+  for (int k = 1; k <= 9; ++k) {
+    c *= (NUMA_GAMMA - k + 1) / k;
+    S.c[k - 1] = c;
+  }
+  return S;
+}
+
+// ---- right-hand side ---------------------------------------------------------------------
+enum { CLS_INTERIOR = 0, CLS_IFACE = 1, CLS_WALL = 2 };
+
+template <int N, typename RT>
+struct Taps {
+  RT c[2 * N + 1];
+  int o[2 * N + 1];
+};
+
+// Row of the DSS'd derivative at axis index idx: coefficients and node offsets relative to
+// the node itself (in units of the axis stride).  The class is uniform across a warp.
+template <int N, typename RT>
+__device__ __forceinline__ int axis_taps(int idx, int nel, const RT* sD, const RT* sDl,
+                                         const RT* sDr, Taps<N, RT>& T) {
+  constexpr int Nq = N + 1;
+  int e, i;
+  axis_owner(idx, N, nel, e, i);
+  if (i == 0 && e > 0) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) {          // left element, its nodes 0..N-1
+      T.c[t] = sDl[t];
+      T.o[t] = t - N;
+    }
+#pragma unroll
+    for (int t = 1; t <= N; ++t) {         // right element, its nodes 1..N
+      T.c[N - 1 + t] = sDr[t];
+      T.o[N - 1 + t] = t;
+    }
+    return CLS_IFACE;
+  }
+  if (i == 0 || i == N) {                  // wall: the full row of the one element
+#pragma unroll
+    for (int t = 0; t <= N; ++t) {
+      T.c[t] = sD[i * Nq + t];
+      T.o[t] = t - i;
+    }
+    return CLS_WALL;
+  }
+#pragma unroll
+  for (int t = 0; t < N; ++t) {            // interior: the zero diagonal dropped
+    const int n = t + (t >= i ? 1 : 0);
+    T.c[t] = sD[i * Nq + n];
+    T.o[t] = n - i;
+  }
+  return CLS_INTERIOR;
+}
+
+// d/d(axis) of the six fields at node g.
+template <int N, typename RT>
+__device__ __forceinline__ void axis_derivs(const RT* const* F, long long g, long long stride,
+                                            int cls, const Taps<N, RT>& T, RT* d) {
+  if (cls == CLS_IFACE) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const RT* p = F[f] + g;
+      RT acc = T.c[0] * __ldg(p + T.o[0] * stride);
+#pragma unroll
+      for (int t = 1; t < 2 * N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
+      d[f] = acc;
+    }
+  } else if (cls == CLS_WALL) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const RT* p = F[f] + g;
+      RT acc = T.c[0] * __ldg(p + T.o[0] * stride);
+#pragma unroll
+      for (int t = 1; t <= N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
+      d[f] = acc;
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const RT* p = F[f] + g;
+      RT acc = T.c[0] * __ldg(p + T.o[0] * stride);
+#pragma unroll
+      for (int t = 1; t < N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
+      d[f] = acc;
+    }
+  }
+}
+
+// One node of the right-hand side (thread index tid of the class-sorted order, or of the
+// natural order when perm is NULL).  sD, sDl, sDr: the three axes' derivative rows
+// (axis a at sD + a*(N+1)^2, sDl + a*(N+1), sDr + a*(N+1)), normally in shared memory.
+// RT: type of the stencil fields and of the arithmetic (double: the FP64 method, fields =
+// the state and P'; float: the mixed-precision form, fields = the FP32 copies from
+// k_prep32).  fld holds rho', u, v, w, theta' (stride nnode), fp holds P'.  OT: type
+// written in mode 0.  Modes 1 and 2 read and write the FP64 state; R1, R2 are OT arrays.
+template <int N, typename RT, typename OT>
+__device__ __forceinline__ void rhs_node(long long tid, const double* __restrict__ q,
+                                         const RT* __restrict__ fld, const RT* __restrict__ fp,
+                                         OT* out0, double* out, const int* __restrict__ perm,
+                                         long long nthreads, const Geom& G, const RefLev& R,
+                                         const RhsEpilogue& ep, const RT* sD, const RT* sDl,
+                                         const RT* sDr) {
+  constexpr int Nq = N + 1;
+  if (tid >= nthreads) return;
+  const int gi = perm ? perm[tid] : (int)tid;
+  if (gi < 0) return;                       // padding of a class group
+  const long long g = gi;
+  const long long nn = G.nnode;
+  const long long col = g / G.M;
+  const int iz = (int)(g - col * G.M);
+  const int iy = (int)(col / G.nxg);
+  const int ix = (int)(col - (long long)iy * G.nxg);
+  const long long sxs = G.M, sys = (long long)G.nxg * G.M;
+
+  // fields: 0 rho', 1 u, 2 v, 3 w, 4 theta', 5 P'
+  const RT* Fld[6] = {fld, fld + nn, fld + 2 * nn, fld + 3 * nn, fld + 4 * nn, fp};
+  RT dx[6], dy[6], dz[6];
+  {
+    Taps<N, RT> T;
+    int cls = axis_taps<N, RT>(ix, G.nex, sD, sDl, sDr, T);
+    axis_derivs<N, RT>(Fld, g, sxs, cls, T, dx);
+    cls = axis_taps<N, RT>(iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
+    axis_derivs<N, RT>(Fld, g, sys, cls, T, dy);
+    cls = axis_taps<N, RT>(iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
+    axis_derivs<N, RT>(Fld, g, 1, cls, T, dz);
+  }
+  const RT r_ = fld[g], u_ = fld[nn + g], v_ = fld[2 * nn + g], w_ = fld[3 * nn + g];
+  const RT rho = (RT)R.rho0[iz] + r_;
+  const RT irho = (RT)1 / rho;
+  const RT grav = (RT)NUMA_GRAV;
+  RT t_r = -fma(u_, dx[0], fma(v_, dy[0], fma(w_, dz[0] + (RT)R.drho0[iz], rho * (dx[1] + dy[2] + dz[3]))));
+  RT t_u = -fma(u_, dx[1], fma(v_, dy[1], fma(w_, dz[1], dx[5] * irho)));
+  RT t_v = -fma(u_, dx[2], fma(v_, dy[2], fma(w_, dz[2], dy[5] * irho)));
+  RT t_w = -fma(u_, dx[3], fma(v_, dy[3], fma(w_, dz[3], fma(grav, r_, dz[5]) * irho)));
+  RT t_t = -fma(u_, dx[4], fma(v_, dy[4], w_ * (dz[4] + (RT)R.dtheta0[iz])));
+  // walls: no normal flow
+  if (ix == 0 || ix == G.nxg - 1) t_u = (RT)0;
+  if (iy == 0 || iy == G.nyg - 1) t_v = (RT)0;
+  if (iz == 0 || iz == G.M - 1) t_w = (RT)0;
+
+  const RT t[5] = {t_r, t_u, t_v, t_w, t_t};
+  if (ep.mode == 0) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) out0[f * nn + g] = (OT)t[f];
+  } else if (ep.mode == 1) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      double val = fma(ep.beta_dt, (double)t[f], ep.one_minus_alpha * q[f * nn + g]);
+      if (ep.use_u0) val = fma(ep.alpha, ep.u0[f * nn + g], val);
+      out[f * nn + g] = val;
+    }
+  } else {
+    const OT* R1 = (const OT*)ep.R1;
+    const OT* R2 = (const OT*)ep.R2;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const long long o = f * nn + g;
+      out[o] = fma(ep.b3dt, (double)t[f], fma(ep.b2dt, (double)R2[o], fma(ep.b1dt, (double)R1[o], ep.u0[o])));
+    }
+  }
+}
+
+// The three axes' derivative rows of C into shared memory (cast to RT).
+template <int N, typename RT>
+__device__ __forceinline__ void load_rows(const Coef3& C, RT* sD, RT* sDl, RT* sDr) {
+  constexpr int Nq = N + 1;
+  for (int t = threadIdx.x; t < Nq * Nq; t += blockDim.x) {
+    sD[t] = (RT)C.x.D[t];
+    sD[Nq * Nq + t] = (RT)C.y.D[t];
+    sD[2 * Nq * Nq + t] = (RT)C.z.D[t];
+  }
+  for (int t = threadIdx.x; t < Nq; t += blockDim.x) {
+    sDl[t] = (RT)C.x.Dl[t]; sDr[t] = (RT)C.x.Dr[t];
+    sDl[Nq + t] = (RT)C.y.Dl[t]; sDr[Nq + t] = (RT)C.y.Dr[t];
+    sDl[2 * Nq + t] = (RT)C.z.Dl[t]; sDr[2 * Nq + t] = (RT)C.z.Dr[t];
+  }
+}
+
+}  // namespace numa_dev
