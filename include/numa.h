@@ -208,10 +208,11 @@ const char* numa_last_error(const numa_ctx* ctx);
 /* ---- ensembles ("batching form") -------------------------------------------------------
  * An ensemble of independent members, each with its own uniform box mesh, polynomial order
  * (4 <= N <= 6), reference state and HEVI time step dt (its column factors are formed at
- * its own dt).  Every phase of a step is one persistent launch for the whole ensemble (a
- * work list of (member, block) items); each step is captured as a CUDA graph on first use
- * for a given (q_in, q_out) pair and replayed.  numa_batch_init autotunes the right-hand
- * side's threads per CTA and the stage's columns per CTA on the ensemble.
+ * its own dt).  Every phase of a step is one persistent launch per polynomial order present
+ * for the whole ensemble (a work list of (member, block) items), so the launches per step
+ * do not grow with the number of members; each step is captured as a CUDA graph on first
+ * use for a given (q_in, q_out) pair and replayed.  numa_batch_init autotunes, per order,
+ * the right-hand side's threads per CTA and the stage's columns per CTA on the ensemble.
  * States are packed: member m occupies doubles [off[m], off[m+1]) of one device array
  * (numa_batch_layout), in the single-mesh SoA layout of that member.  All calls use the
  * stream given to numa_batch_init and follow the error conventions above. */
@@ -232,8 +233,9 @@ int numa_batch_step_imex1d(numa_batch* b, const double* q_in, double* q_out, int
 /* 1 (default): replay each step as a CUDA graph; 0: launch the kernels directly. */
 int numa_batch_set_graph(numa_batch* b, int enable);
 
-/* The autotuned threads per CTA of the right-hand side and columns per CTA of the stage. */
-int numa_batch_tuning(const numa_batch* b, int* rhs_threads, int* col_tile);
+/* The autotuned threads per CTA of the right-hand side and columns per CTA of the stage for
+ * the members of order N (0 and 0 if the ensemble has none). */
+int numa_batch_tuning(const numa_batch* b, int N, int* rhs_threads, int* col_tile);
 
 /* numa_query / numa_reference_levels of one member. */
 int numa_batch_member_query(const numa_batch* b, int member, int what, long long* out);

@@ -87,7 +87,7 @@ def lib():
             "numa_batch_layout": (I, [P, P]),
             "numa_batch_step_imex1d": (I, [P, P, P, I]),
             "numa_batch_set_graph": (I, [P, I]),
-            "numa_batch_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "numa_batch_tuning": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
             "numa_batch_member_query": (I, [P, I, I, ctypes.POINTER(LL)]),
             "numa_batch_reference_levels": (I, [P, I, P]),
             "numa_batch_last_error": (ctypes.c_char_p, [P]),
@@ -316,9 +316,14 @@ class Batch:
         self._check(lib().numa_batch_set_graph(self._h, 1 if enable else 0), "set_graph")
 
     def tuning(self):
-        a, b = ctypes.c_int(), ctypes.c_int()
-        self._check(lib().numa_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(b)), "tuning")
-        return {"rhs_threads_per_cta": a.value, "stage_columns_per_cta": b.value}
+        """{N: {"rhs_threads_per_cta", "stage_columns_per_cta"}} for the orders present."""
+        out = {}
+        for n in (4, 5, 6):
+            a, b = ctypes.c_int(), ctypes.c_int()
+            self._check(lib().numa_batch_tuning(self._h, n, ctypes.byref(a), ctypes.byref(b)), "tuning")
+            if a.value:
+                out[n] = {"rhs_threads_per_cta": a.value, "stage_columns_per_cta": b.value}
+        return out
 
     def member_query(self, m, what):
         v = ctypes.c_longlong()

@@ -3,11 +3,13 @@
 //
 // Each member is set up exactly like a single-mesh context (tables, per-column factors at
 // its own dt, workspace).  Every phase of a HEVI step (EOS pre-pass, right-hand side,
-// implicit stage) is then ONE persistent launch for the whole ensemble: a grid sized to
-// the GPU walks a work list of (member, block) items, so a step is eight launches for any
-// number of members; each step is captured once as a CUDA graph and replayed.  The
-// members' work lists are built for the right-hand side's threads per CTA and the stage's
-// columns per CTA that an autotuner picks by timing the candidates on the ensemble itself.
+// implicit stage) is then one persistent launch per polynomial order present (at most
+// three, N = 4..6) for the whole ensemble: a grid sized to the GPU walks a work list of
+// (member, block) items, so the number of launches per step does not grow with the number
+// of members; each step is captured once as a CUDA graph and replayed.  Each order group
+// has its own kernels (registers and shared memory sized for that order and its tallest
+// column) and its own work lists, built for the right-hand side's threads per CTA and the
+// stage's columns per CTA that an autotuner picks by timing candidates on the ensemble.
 // Blocks never wait on one another: items are assigned by a static stride.
 #include <algorithm>
 #include <cmath>
@@ -95,39 +97,29 @@ __device__ __forceinline__ void batch_rhs_item(const MemberDev& d, long long tid
                               sDr);
 }
 
+template <int N>
 __global__ void k_batch_rhs(const MemberDev* __restrict__ md, WorkList W, int src, int mode,
                             const double* qin, double* qout) {
-  __shared__ double sD[3 * NUMA_MAXNQ * NUMA_MAXNQ], sDl[3 * NUMA_MAXNQ], sDr[3 * NUMA_MAXNQ];
+  constexpr int Nq = N + 1;
+  __shared__ double sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
   for (long long item = blockIdx.x; item < W.nitems; item += gridDim.x) {
     const int k = find_slot(W, item);
     const MemberDev& d = md[W.order[k]];
     const long long tid = (item - W.start[k]) * blockDim.x + threadIdx.x;
-    switch (d.G.N) {
-      case 4: batch_rhs_item<4>(d, tid, src, mode, qin, qout, sD, sDl, sDr); break;
-      case 5: batch_rhs_item<5>(d, tid, src, mode, qin, qout, sD, sDl, sDr); break;
-      case 6: batch_rhs_item<6>(d, tid, src, mode, qin, qout, sD, sDl, sDr); break;
-      default: break;
-    }
+    batch_rhs_item<N>(d, tid, src, mode, qin, qout, sD, sDl, sDr);
     __syncthreads();
   }
 }
 
-template <bool S3>
+template <int N, bool S3>
 __global__ void k_batch_stage(const MemberDev* __restrict__ md, WorkList W, const double* qin) {
   extern __shared__ double sm[];
   for (long long item = blockIdx.x; item < W.nitems; item += gridDim.x) {
     const int k = find_slot(W, item);
     const MemberDev& d = md[W.order[k]];
     const long long col0 = (item - W.start[k]) * blockDim.x;
-    const double* qn = qin + d.soff;
-    double* out = S3 ? d.q3 : d.q2;
-    const StageCoef& sc = S3 ? d.s3 : d.s2;
-    switch (d.G.N) {
-      case 4: stage_body<4, S3, false, double>(col0, sm, qn, d.R1, d.R2, d.q2, out, d.G, d.R, d.F, sc, d.tb, 0); break;
-      case 5: stage_body<5, S3, false, double>(col0, sm, qn, d.R1, d.R2, d.q2, out, d.G, d.R, d.F, sc, d.tb, 0); break;
-      case 6: stage_body<6, S3, false, double>(col0, sm, qn, d.R1, d.R2, d.q2, out, d.G, d.R, d.F, sc, d.tb, 0); break;
-      default: break;
-    }
+    stage_body<N, S3, false, double>(col0, sm, qin + d.soff, d.R1, d.R2, d.q2, S3 ? d.q3 : d.q2,
+                                     d.G, d.R, d.F, S3 ? d.s3 : d.s2, d.tb, 0);
     __syncthreads();
   }
 }
@@ -143,6 +135,16 @@ struct HostList {
 
 }  // namespace
 
+// The members of one polynomial order: their work lists, tiles and launch shapes.
+struct OrderGroup {
+  int N = 0;
+  std::vector<int> members;
+  HostList rhs_list, col_list;
+  int rhs_threads = 256, col_tile = 64;
+  int grid_rhs = 0, grid_col = 0;
+  size_t stage_smem = 0;
+};
+
 struct numa_batch {
   std::vector<numa_ctx*> mem;
   cudaStream_t stream = nullptr;
@@ -150,10 +152,9 @@ struct numa_batch {
   MemberDev* d_md = nullptr;
   std::vector<long long> soff;
   long long total = 0;                 // doubles of one packed state
-  HostList node_list, rhs_list, col_list;
-  int rhs_threads = 256, col_tile = 64;
-  int grid_node = 0, grid_rhs = 0, grid_col = 0;
-  size_t stage_smem = 0;
+  HostList node_list;
+  int grid_node = 0;
+  OrderGroup groups[3];                // N = 4, 5, 6
   double* d_state = nullptr;           // packed scratch state for tuning
   bool use_graph = true;
   // graphs are captured and launched on a private stream (capture is not allowed on the
@@ -202,59 +203,111 @@ void make_list(HostList& L, const std::vector<int>& order, const std::vector<lon
   for (int m : order) L.start.push_back(L.start.back() + items[m]);
 }
 
+template <int N>
+int group_shapes(numa_batch* b, OrderGroup& g, int nsm) {
+  int per = 0;
+  NUMA_BCK(b, cudaFuncSetAttribute(k_batch_stage<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.stage_smem));
+  NUMA_BCK(b, cudaFuncSetAttribute(k_batch_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.stage_smem));
+  NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_rhs<N>, g.rhs_threads, 0));
+  g.grid_rhs = nsm * std::max(per, 1);
+  NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_stage<N, true>, g.col_tile, g.stage_smem));
+  if (per < 1) return bfail(b, NUMA_ERR_ARG, "stage tile does not fit in shared memory");
+  g.grid_col = nsm * per;
+  return NUMA_OK;
+}
+
+// Work lists and launch shapes of one order group (its members' RHS blocks, and their
+// stage blocks with the tallest columns dealt first so that static striding balances).
+int build_group(numa_batch* b, OrderGroup& g) {
+  const int n = (int)b->mem.size();
+  std::vector<long long> it_rhs(n, 0), it_col(n, 0);
+  int maxM = 0;
+  for (int m : g.members) {
+    const numa_ctx* c = b->mem[m];
+    it_rhs[m] = (c->nperm + g.rhs_threads - 1) / g.rhs_threads;
+    it_col[m] = (c->G.ncol + g.col_tile - 1) / g.col_tile;
+    maxM = std::max(maxM, c->G.M);
+  }
+  std::vector<int> by_m = g.members;
+  std::stable_sort(by_m.begin(), by_m.end(),
+                   [&](int a, int c) { return b->mem[a]->G.M > b->mem[c]->G.M; });
+  make_list(g.rhs_list, g.members, it_rhs);
+  make_list(g.col_list, by_m, it_col);
+  int rc;
+  if ((rc = upload_list(b, g.rhs_list)) || (rc = upload_list(b, g.col_list))) return rc;
+  g.stage_smem = col_smem_per_level(false, 0) * (size_t)maxM * g.col_tile;
+  int dev = 0, nsm = 0;
+  NUMA_BCK(b, cudaGetDevice(&dev));
+  NUMA_BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  switch (g.N) {
+    case 4: return group_shapes<4>(b, g, nsm);
+    case 5: return group_shapes<5>(b, g, nsm);
+    case 6: return group_shapes<6>(b, g, nsm);
+    default: return NUMA_ERR_ARG;
+  }
+}
+
 int build_lists(numa_batch* b) {
   const int n = (int)b->mem.size();
   std::vector<int> natural(n);
   for (int m = 0; m < n; ++m) natural[m] = m;
-  std::vector<long long> it_node(n), it_rhs(n), it_col(n);
-  for (int m = 0; m < n; ++m) {
-    const numa_ctx* c = b->mem[m];
-    it_node[m] = (c->G.nnode + 255) / 256;
-    it_rhs[m] = (c->nperm + b->rhs_threads - 1) / b->rhs_threads;
-    it_col[m] = (c->G.ncol + b->col_tile - 1) / b->col_tile;
-  }
-  // stage items cost ~ M: deal the tallest columns first so static striding balances
-  std::vector<int> by_m = natural;
-  std::stable_sort(by_m.begin(), by_m.end(),
-                   [&](int a, int c) { return b->mem[a]->G.M > b->mem[c]->G.M; });
+  std::vector<long long> it_node(n);
+  for (int m = 0; m < n; ++m) it_node[m] = (b->mem[m]->G.nnode + 255) / 256;
   make_list(b->node_list, natural, it_node);
-  make_list(b->rhs_list, natural, it_rhs);
-  make_list(b->col_list, by_m, it_col);
-  int rc;
-  if ((rc = upload_list(b, b->node_list)) || (rc = upload_list(b, b->rhs_list)) ||
-      (rc = upload_list(b, b->col_list)))
-    return rc;
-  int maxM = 0;
-  for (auto* c : b->mem) maxM = std::max(maxM, c->G.M);
-  b->stage_smem = col_smem_per_level(false, 0) * (size_t)maxM * b->col_tile;
+  int rc = upload_list(b, b->node_list);
+  if (rc) return rc;
   int dev = 0, nsm = 0, per = 0;
   NUMA_BCK(b, cudaGetDevice(&dev));
   NUMA_BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  NUMA_BCK(b, cudaFuncSetAttribute(k_batch_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->stage_smem));
-  NUMA_BCK(b, cudaFuncSetAttribute(k_batch_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->stage_smem));
   NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_pressure, 256, 0));
   b->grid_node = nsm * std::max(per, 1);
-  NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_rhs, b->rhs_threads, 0));
-  b->grid_rhs = nsm * std::max(per, 1);
-  NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_stage<true>, b->col_tile, b->stage_smem));
-  if (per < 1) return bfail(b, NUMA_ERR_ARG, "stage tile does not fit in shared memory");
-  b->grid_col = nsm * per;
+  for (auto& g : b->groups)
+    if (!g.members.empty() && (rc = build_group(b, g))) return rc;
   return NUMA_OK;
+}
+
+template <int N>
+void launch_group_rhs(numa_batch* b, const OrderGroup& g, int src, int mode, const double* qin,
+                      double* qout, cudaStream_t s) {
+  k_batch_rhs<N><<<g.grid_rhs, g.rhs_threads, 0, s>>>(b->d_md, g.rhs_list.dev(), src, mode, qin, qout);
+}
+
+template <int N>
+void launch_group_stage(numa_batch* b, const OrderGroup& g, bool s3, const double* qin,
+                        cudaStream_t s) {
+  if (s3) k_batch_stage<N, true><<<g.grid_col, g.col_tile, g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin);
+  else k_batch_stage<N, false><<<g.grid_col, g.col_tile, g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin);
+}
+
+void enqueue_rhs_all(numa_batch* b, int src, int mode, const double* qin, double* qout, cudaStream_t s) {
+  for (auto& g : b->groups) {
+    if (g.members.empty()) continue;
+    if (g.N == 4) launch_group_rhs<4>(b, g, src, mode, qin, qout, s);
+    else if (g.N == 5) launch_group_rhs<5>(b, g, src, mode, qin, qout, s);
+    else launch_group_rhs<6>(b, g, src, mode, qin, qout, s);
+  }
+}
+
+void enqueue_stage_all(numa_batch* b, bool s3, const double* qin, cudaStream_t s) {
+  for (auto& g : b->groups) {
+    if (g.members.empty()) continue;
+    if (g.N == 4) launch_group_stage<4>(b, g, s3, qin, s);
+    else if (g.N == 5) launch_group_stage<5>(b, g, s3, qin, s);
+    else launch_group_stage<6>(b, g, s3, qin, s);
+  }
 }
 
 int enqueue_step(numa_batch* b, const double* qin, double* qout, cudaStream_t s) {
   const EosSeries S = eos_series();
-  const WorkList Wn = b->node_list.dev(), Wr = b->rhs_list.dev(), Wc = b->col_list.dev();
-  const int rt = b->rhs_threads, ct = b->col_tile;
-  const size_t sm = b->stage_smem;
+  const WorkList Wn = b->node_list.dev();
   k_batch_pressure<<<b->grid_node, 256, 0, s>>>(b->d_md, Wn, 0, qin, S);
-  k_batch_rhs<<<b->grid_rhs, rt, 0, s>>>(b->d_md, Wr, 0, 0, qin, qout);
-  k_batch_stage<false><<<b->grid_col, ct, sm, s>>>(b->d_md, Wc, qin);
+  enqueue_rhs_all(b, 0, 0, qin, qout, s);
+  enqueue_stage_all(b, false, qin, s);
   k_batch_pressure<<<b->grid_node, 256, 0, s>>>(b->d_md, Wn, 1, qin, S);
-  k_batch_rhs<<<b->grid_rhs, rt, 0, s>>>(b->d_md, Wr, 1, 0, qin, qout);
-  k_batch_stage<true><<<b->grid_col, ct, sm, s>>>(b->d_md, Wc, qin);
+  enqueue_rhs_all(b, 1, 0, qin, qout, s);
+  enqueue_stage_all(b, true, qin, s);
   k_batch_pressure<<<b->grid_node, 256, 0, s>>>(b->d_md, Wn, 2, qin, S);
-  k_batch_rhs<<<b->grid_rhs, rt, 0, s>>>(b->d_md, Wr, 2, 2, qin, qout);
+  enqueue_rhs_all(b, 2, 2, qin, qout, s);
   NUMA_BCK(b, cudaGetLastError());
   return NUMA_OK;
 }
@@ -295,14 +348,16 @@ int step_graph(numa_batch* b, const double* qin, double* qout, cudaGraphExec_t* 
   return NUMA_OK;
 }
 
-// Autotuner: time the right-hand side for each threads-per-CTA candidate and the stage
-// for each columns-per-CTA candidate on the ensemble (rest state), keep the fastest.
+// Autotuner: for every order group, time its right-hand side for each threads-per-CTA
+// candidate and its stage for each columns-per-CTA candidate on the ensemble (rest
+// state), and keep the fastest.
 int autotune(numa_batch* b) {
   cudaEvent_t e0, e1;
   NUMA_BCK(b, cudaEventCreate(&e0));
   NUMA_BCK(b, cudaEventCreate(&e1));
   NUMA_BCK(b, cudaMemsetAsync(b->d_state, 0, b->total * sizeof(double), b->stream));
   const EosSeries S = eos_series();
+  k_batch_pressure<<<b->grid_node, 256, 0, b->stream>>>(b->d_md, b->node_list.dev(), 0, b->d_state, S);
   auto time_it = [&](auto launch, float* ms) -> int {
     for (int r = 0; r < 2; ++r) launch();
     NUMA_BCK(b, cudaEventRecord(e0, b->stream));
@@ -314,35 +369,36 @@ int autotune(numa_batch* b) {
     return NUMA_OK;
   };
   int rc = NUMA_OK;
-  k_batch_pressure<<<b->grid_node, 256, 0, b->stream>>>(b->d_md, b->node_list.dev(), 0, b->d_state, S);
-  const int rhs_c[2] = {128, 256};
-  float best = 1e30f;
-  int best_rt = 256;
-  for (int rt : rhs_c) {
-    b->rhs_threads = rt;
-    if ((rc = build_lists(b))) break;
-    float ms = 0;
-    rc = time_it([&] { k_batch_rhs<<<b->grid_rhs, rt, 0, b->stream>>>(b->d_md, b->rhs_list.dev(), 0, 0, b->d_state, b->d_state); }, &ms);
+  for (auto& g : b->groups) {
+    if (g.members.empty()) continue;
+    float best = 1e30f;
+    int best_rt = 256;
+    for (int rt : {128, 256}) {
+      g.rhs_threads = rt;
+      if ((rc = build_group(b, g))) break;
+      float ms = 0;
+      rc = time_it([&] { enqueue_rhs_all(b, 0, 0, b->d_state, b->d_state, b->stream); }, &ms);
+      if (rc) break;
+      b->tune_ms.push_back(ms);
+      if (ms < best) { best = ms; best_rt = rt; }
+    }
     if (rc) break;
-    b->tune_ms.push_back(ms);
-    if (ms < best) { best = ms; best_rt = rt; }
+    g.rhs_threads = best_rt;
+    best = 1e30f;
+    int best_ct = 32;
+    for (int ct : {32, 64, 96}) {
+      g.col_tile = ct;
+      if (build_group(b, g)) { b->err.clear(); continue; }     // does not fit: skip
+      float ms = 0;
+      rc = time_it([&] { enqueue_stage_all(b, false, b->d_state, b->stream); }, &ms);
+      if (rc) break;
+      b->tune_ms.push_back(ms);
+      if (ms < best) { best = ms; best_ct = ct; }
+    }
+    if (rc) break;
+    g.col_tile = best_ct;
+    if ((rc = build_group(b, g))) break;
   }
-  b->rhs_threads = best_rt;
-  const int col_c[3] = {32, 64, 96};
-  best = 1e30f;
-  int best_ct = 64;
-  for (int ct : col_c) {
-    if (rc) break;
-    b->col_tile = ct;
-    if ((rc = build_lists(b))) { rc = NUMA_OK; b->err.clear(); continue; }   // does not fit: skip
-    float ms = 0;
-    rc = time_it([&] { k_batch_stage<false><<<b->grid_col, ct, b->stage_smem, b->stream>>>(b->d_md, b->col_list.dev(), b->d_state); }, &ms);
-    if (rc) break;
-    b->tune_ms.push_back(ms);
-    if (ms < best) { best = ms; best_ct = ct; }
-  }
-  b->col_tile = best_ct;
-  if (!rc) rc = build_lists(b);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
@@ -394,6 +450,9 @@ int numa_batch_init(const numa_mesh_desc* meshes, const int* N, const double* dt
     b->total += 5 * c->G.nnode;
   }
   b->soff.push_back(b->total);
+  for (int g = 0; g < 3; ++g) b->groups[g].N = 4 + g;
+  if (rc == NUMA_OK)
+    for (int m = 0; m < nmembers; ++m) b->groups[N[m] - 4].members.push_back(m);
   if (rc == NUMA_OK && (cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
                         cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess))
@@ -423,8 +482,10 @@ void numa_batch_destroy(numa_batch* b) {
   cudaStreamSynchronize(b->stream);
   drop_graphs(b);
   free_list(b->node_list);
-  free_list(b->rhs_list);
-  free_list(b->col_list);
+  for (auto& g : b->groups) {
+    free_list(g.rhs_list);
+    free_list(g.col_list);
+  }
   cudaFree(b->d_md);
   cudaFree(b->d_state);
   if (b->gstream) {
@@ -479,10 +540,11 @@ int numa_batch_step_imex1d(numa_batch* b, const double* q_in, double* q_out, int
   return NUMA_OK;
 }
 
-int numa_batch_tuning(const numa_batch* b, int* rhs_threads, int* col_tile) {
-  if (!b) return NUMA_ERR_ARG;
-  if (rhs_threads) *rhs_threads = b->rhs_threads;
-  if (col_tile) *col_tile = b->col_tile;
+int numa_batch_tuning(const numa_batch* b, int N, int* rhs_threads, int* col_tile) {
+  if (!b || N < 4 || N > 6) return NUMA_ERR_ARG;
+  const OrderGroup& g = b->groups[N - 4];
+  if (rhs_threads) *rhs_threads = g.members.empty() ? 0 : g.rhs_threads;
+  if (col_tile) *col_tile = g.members.empty() ? 0 : g.col_tile;
   return NUMA_OK;
 }
 

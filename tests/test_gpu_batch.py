@@ -38,7 +38,9 @@ def test_batch_matches_single_contexts_exactly():
         assert torch.equal(b.member(out, k), ref), k
         g.close()
     t = b.tuning()
-    assert t["rhs_threads_per_cta"] in (128, 256) and t["stage_columns_per_cta"] in (32, 64, 96)
+    assert sorted(t) == [4, 5, 6]
+    for v in t.values():
+        assert v["rhs_threads_per_cta"] in (128, 256) and v["stage_columns_per_cta"] in (32, 64, 96)
 
 
 def test_graph_replay_equals_direct_launches_and_in_place():
