@@ -26,6 +26,10 @@ algorithm or table:
                     predictor-corrector stage form (Sec. "Linear multi-stage methods").
 * ``rk35``       -- the explicit five-stage third-order SSP comparator
                     (Sec. "Performance of IMEX on manycore processors").
+* ``tangent``    -- tangent-linear and adjoint models of R, of the column solve
+                    (transposed stored LU of Algorithm 9) and of the ARK2 step, and the
+                    gradient of a quadratic misfit of the final theta' (differentiation
+                    form: the chain rule applied to the steps above).
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.  One function has no
 pin beyond its defining formula: see the ``PARITY UNPINNED`` note in ``rk35``.
