@@ -171,7 +171,10 @@ enum {
   NUMA_K_STAGE = 2,     /* fused implicit stage: predictor, Schur RHS, solve, extraction */
   NUMA_K_SOLVE = 3,     /* stand-alone column solve */
   NUMA_K_FACTOR = 4,    /* probing + banded LU */
-  NUMA_K_NKINDS = 5
+  NUMA_K_RHS_TLM = 5,   /* tangent-linear right-hand side (with its dP' pre-pass) */
+  NUMA_K_RHS_ADJ = 6,   /* adjoint right-hand side (weights pass + transposed gather) */
+  NUMA_K_STAGE_ADJ = 7, /* adjoint of the fused implicit stage (transposed column solve) */
+  NUMA_K_NKINDS = 8
 };
 int numa_profile(numa_ctx* ctx, int enable);
 int numa_profile_read(numa_ctx* ctx, int kind, double* total_ms, long long* launches);
@@ -204,6 +207,63 @@ int numa_query(const numa_ctx* ctx, int what, long long* out);
 
 /* One-line message of the last failing call on this context ("" if none). */
 const char* numa_last_error(const numa_ctx* ctx);
+
+/* ---- differentiation form -------------------------------------------------------------
+ * Tangent-linear (TLM) and adjoint models of the HEVI 1D-IMEX step.  The paper integrates
+ * forward only; these calls apply the chain rule to its steps: R of Sec. "Equation Set2NC"
+ * (Algorithm 2, Sec. "Direct stiffness summation"), the column solve of Eqs. utteqn and
+ * helm2nc with the stored factors of Algorithm 9, and the ARK2 step of Table 1 in the stage
+ * form of Sec. "Linear multi-stage methods".  The adjoint of a linear map A is its
+ * transpose with respect to the plain Euclidean dot product of the SoA arrays:
+ * <lam, A dq> = <A^T lam, dq>.  All calls need an FP64 context (NUMA_ERR_ARG otherwise),
+ * work in the context's stream, and allocate, on first use, a workspace of 59*nnode
+ * doubles owned by the context (NUMA_ERR_OOM if that fails).  The adjoint right-hand side
+ * gathers rather than scatters (no atomics): results are bitwise reproducible.  The
+ * implicit stage is linear in its inputs, so its TLM is numa_imex_stage applied to the
+ * perturbations. */
+
+/* dR = R'(q) dq.  q, dq, dR: device SoA arrays of 5*nnode doubles; dR must not overlap q
+ * or dq.  Uses the context's R workspace. */
+int numa_rhs_tlm(numa_ctx* ctx, const double* q, const double* dq, double* dR);
+
+/* q_adj = R'(q)^T lam (overwritten).  q, lam, q_adj: device arrays of 5*nnode doubles;
+ * q_adj must not overlap q or lam. */
+int numa_rhs_adjoint(numa_ctx* ctx, const double* q, const double* lam, double* q_adj);
+
+/* Solve S^T x = b for every column with the stored factors S = L U (U^T forward, then L^T
+ * backward substitution).  Layout as numa_solve_columns; x == b (in place) allowed.
+ * NUMA_ERR_NOT_FACTORED before numa_factor_columns. */
+int numa_solve_columns_transposed(numa_ctx* ctx, const double* b, double* x);
+
+/* Adjoint of numa_imex_stage: given lam, the adjoint of the stage output q(i), ADD the
+ * adjoints of its inputs: qn_adj += (dq(i)/dq^n)^T lam, R1_adj += (dq(i)/dR1)^T lam, and for
+ * stage 3 R2_adj and q2_adj likewise (stage 2: R2_adj and q2_adj are ignored and may be
+ * NULL).  All arrays 5*nnode doubles on the device; the outputs must not overlap lam or
+ * each other. */
+int numa_imex_stage_adjoint(numa_ctx* ctx, int stage, const double* lam, double* qn_adj,
+                            double* R1_adj, double* R2_adj, double* q2_adj);
+
+/* nsteps >= 1 HEVI steps of the state and of its tangent: q_out = q^{n+nsteps} and
+ * dq_out = (dq^{n+nsteps}/dq^n) dq.  In place (q_out == q, dq_out == dq) allowed. */
+int numa_step_imex1d_tlm(numa_ctx* ctx, const double* q, const double* dq, double* q_out,
+                         double* dq_out, int nsteps);
+
+/* Adjoint of one HEVI step taken from state q: lam = (dq^{n+1}/dq^n)^T lam_next.  The
+ * step's stage states are recomputed from q.  lam == lam_next (in place) allowed. */
+int numa_step_imex1d_adjoint(numa_ctx* ctx, const double* q, const double* lam_next,
+                             double* lam);
+
+/* Checkpointed forward run: nsteps HEVI steps from q0 to qT, storing the state before step
+ * s in ckpt[s/every] for every s that is a multiple of every.  ckpt: device array of
+ * ceil(nsteps/every) * 5*nnode doubles.  q0 is not modified; qT must not overlap q0. */
+int numa_imex1d_forward_checkpointed(numa_ctx* ctx, const double* q0, double* qT, int nsteps,
+                                     int every, double* ckpt);
+
+/* Adjoint of that run: lam0 = (dq^T/dq^0)^T lamT.  Segments are processed last to first;
+ * each is recomputed from its checkpoint into work (every * 5*nnode doubles) and the steps
+ * are then run backwards with numa_step_imex1d_adjoint.  lam0 == lamT allowed. */
+int numa_imex1d_adjoint_checkpointed(numa_ctx* ctx, const double* ckpt, int nsteps, int every,
+                                     const double* lamT, double* lam0, double* work);
 
 /* ---- ensembles ("batching form") -------------------------------------------------------
  * An ensemble of independent members, each with its own uniform box mesh, polynomial order

@@ -237,6 +237,23 @@ def step_stages(hevi, q):
     return Q
 
 
+def stage_adjoint(hevi, i, lam, cmap=None):
+    """Adjoint of stage i in {1, 2} (rows 2 and 3 of Table 1; q(i+1) in the paper's
+    numbering) as a linear map of its inputs q^n, R_j = R(q(j)) and q(j), j < i:
+
+        q~_e = q^n + dt sum_j a_ij R_j + sum_j c_ij q(j),  q~ = solve(q~_e),
+        q(i) = q~ - sum_j c_ij q(j),  with q(0) = q^n.
+
+    Returns (qn*, [R_j*], [q(j)*]) for j < i; the q(0)* term is already in qn*."""
+    dt = hevi.dt
+    cmap = ColumnMap(hevi) if cmap is None else cmap
+    a, _, c = _stage_coefs(i)
+    qta = cmap.apply_T(lam)
+    Ra = [dt * a[i, j] * qta for j in range(i)]
+    Qa = [c[j] * (qta - lam) for j in range(i)]
+    return qta + Qa[0], Ra, [None] + Qa[1:]
+
+
 def step_adjoint(hevi, q, lam, cmap=None):
     """Adjoint of one ARK2 step at q^n: given lam = dJ/dq^{n+1}, returns dJ/dq^n."""
     mesh, col, dt = hevi.mesh, hevi.col, hevi.dt
@@ -247,17 +264,14 @@ def step_adjoint(hevi, q, lam, cmap=None):
     Ra = [dt * b[i] * lam for i in range(3)]
     Qa = [np.zeros_like(qa) for _ in range(3)]
     for i in (2, 1):
-        a, _, c = _stage_coefs(i)
         Qa[i] = Qa[i] + rhs_adjoint(mesh, col, Q[i], Ra[i], hevi.l2g, hevi.mass)
-        for j in range(i):                                    # Q_i = q~ - sum_j c_ij Q_j
-            Qa[j] = Qa[j] - c[j] * Qa[i]
-        qta = cmap.apply_T(Qa[i])                             # q~ = solve(q~_e)
-        for j in range(i):                                    # q~_e = q + dt sum a R + sum c Q
-            Qa[j] = Qa[j] + c[j] * qta
-            Ra[j] = Ra[j] + dt * a[i, j] * qta
-        qa = qa + qta
-    Qa[0] = Qa[0] + rhs_adjoint(mesh, col, Q[0], Ra[0], hevi.l2g, hevi.mass)
-    return qa + Qa[0]
+        qn_a, Rj_a, Qj_a = stage_adjoint(hevi, i, Qa[i], cmap)
+        qa = qa + qn_a
+        for j in range(i):
+            Ra[j] = Ra[j] + Rj_a[j]
+            if j > 0:
+                Qa[j] = Qa[j] + Qj_a[j]
+    return qa + rhs_adjoint(mesh, col, Q[0], Ra[0], hevi.l2g, hevi.mass)
 
 
 def misfit(qT, target):

@@ -32,8 +32,11 @@ EXPORTS = (
     "numa_rhs_explicit_static", "numa_batch_init", "numa_batch_destroy", "numa_batch_layout",
     "numa_batch_step_imex1d", "numa_batch_set_graph", "numa_batch_tuning",
     "numa_batch_member_query", "numa_batch_reference_levels", "numa_batch_last_error",
+    "numa_rhs_tlm", "numa_rhs_adjoint", "numa_solve_columns_transposed", "numa_imex_stage_adjoint",
+    "numa_step_imex1d_tlm", "numa_step_imex1d_adjoint", "numa_imex1d_forward_checkpointed",
+    "numa_imex1d_adjoint_checkpointed",
 )
-K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR = range(5)
+K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ = range(8)
 
 
 class Options(ctypes.Structure):
@@ -91,6 +94,14 @@ def lib():
             "numa_batch_member_query": (I, [P, I, I, ctypes.POINTER(LL)]),
             "numa_batch_reference_levels": (I, [P, I, P]),
             "numa_batch_last_error": (ctypes.c_char_p, [P]),
+            "numa_rhs_tlm": (I, [P, P, P, P]),
+            "numa_rhs_adjoint": (I, [P, P, P, P]),
+            "numa_solve_columns_transposed": (I, [P, P, P]),
+            "numa_imex_stage_adjoint": (I, [P, I, P, P, P, P, P]),
+            "numa_step_imex1d_tlm": (I, [P, P, P, P, P, I]),
+            "numa_step_imex1d_adjoint": (I, [P, P, P, P]),
+            "numa_imex1d_forward_checkpointed": (I, [P, P, P, I, I, P]),
+            "numa_imex1d_adjoint_checkpointed": (I, [P, P, I, I, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -225,6 +236,94 @@ class Numa:
                     "numa_profile_read")
         return t.value, n.value
 
+    # -- differentiation form -------------------------------------------------------
+    def rhs_tlm(self, q, dq, out=None):
+        """R'(q) dq."""
+        self._state(q)
+        self._state(dq)
+        out = self._torch.empty_like(q) if out is None else self._state(out)
+        self._check(lib().numa_rhs_tlm(self._h, _ptr(q), _ptr(dq), _ptr(out)), "numa_rhs_tlm")
+        return out
+
+    def rhs_adjoint(self, q, lam, out=None):
+        """R'(q)^T lam."""
+        self._state(q)
+        self._state(lam)
+        out = self._torch.empty_like(q) if out is None else self._state(out)
+        self._check(lib().numa_rhs_adjoint(self._h, _ptr(q), _ptr(lam), _ptr(out)),
+                    "numa_rhs_adjoint")
+        return out
+
+    def solve_columns_transposed(self, b, x=None):
+        n = self.ncol * self.M
+        self._state(b, n)
+        x = self._torch.empty_like(b) if x is None else self._state(x, n)
+        self._check(lib().numa_solve_columns_transposed(self._h, _ptr(b), _ptr(x)),
+                    "numa_solve_columns_transposed")
+        return x
+
+    def imex_stage_adjoint(self, stage, lam, qn_adj, R1_adj, R2_adj=None, q2_adj=None):
+        """Adds the adjoints of the stage's inputs to qn_adj, R1_adj (and R2_adj, q2_adj)."""
+        for t in (lam, qn_adj, R1_adj, R2_adj, q2_adj):
+            if t is not None:
+                self._state(t)
+        self._check(lib().numa_imex_stage_adjoint(self._h, int(stage), _ptr(lam), _ptr(qn_adj),
+                                                  _ptr(R1_adj), _ptr(R2_adj), _ptr(q2_adj)),
+                    "numa_imex_stage_adjoint")
+
+    def step_imex1d_tlm(self, q, dq, nsteps=1, q_out=None, dq_out=None):
+        """(q^{n+nsteps}, its tangent along dq)."""
+        self._state(q)
+        self._state(dq)
+        q_out = self._torch.empty_like(q) if q_out is None else self._state(q_out)
+        dq_out = self._torch.empty_like(dq) if dq_out is None else self._state(dq_out)
+        self._check(lib().numa_step_imex1d_tlm(self._h, _ptr(q), _ptr(dq), _ptr(q_out),
+                                               _ptr(dq_out), int(nsteps)), "numa_step_imex1d_tlm")
+        return q_out, dq_out
+
+    def step_imex1d_adjoint(self, q, lam_next, lam=None):
+        """(dq^{n+1}/dq^n)^T lam_next for the step taken from q."""
+        self._state(q)
+        self._state(lam_next)
+        lam = self._torch.empty_like(q) if lam is None else self._state(lam)
+        self._check(lib().numa_step_imex1d_adjoint(self._h, _ptr(q), _ptr(lam_next), _ptr(lam)),
+                    "numa_step_imex1d_adjoint")
+        return lam
+
+    def forward_checkpointed(self, q0, nsteps, every, qT=None):
+        """(q^T, checkpoints) of nsteps steps, the state kept before every `every`-th step."""
+        self._state(q0)
+        qT = self._torch.empty_like(q0) if qT is None else self._state(qT)
+        nck = (int(nsteps) + int(every) - 1) // int(every)
+        ckpt = self._torch.empty(nck, 5, self.nnode, dtype=self._torch.float64, device="cuda")
+        self._check(lib().numa_imex1d_forward_checkpointed(self._h, _ptr(q0), _ptr(qT), int(nsteps),
+                                                           int(every), _ptr(ckpt)),
+                    "numa_imex1d_forward_checkpointed")
+        return qT, ckpt
+
+    def adjoint_checkpointed(self, ckpt, nsteps, every, lamT, lam0=None):
+        """(dq^T/dq^0)^T lamT from the checkpoints of forward_checkpointed."""
+        self._state(lamT)
+        lam0 = self._torch.empty_like(lamT) if lam0 is None else self._state(lam0)
+        work = self._torch.empty(int(every), 5, self.nnode, dtype=self._torch.float64,
+                                 device="cuda")
+        self._check(lib().numa_imex1d_adjoint_checkpointed(self._h, _ptr(ckpt), int(nsteps),
+                                                           int(every), _ptr(lamT), _ptr(lam0),
+                                                           _ptr(work)),
+                    "numa_imex1d_adjoint_checkpointed")
+        return lam0
+
+    def rhs_autograd(self, q):
+        """R(q) as a differentiable torch operation: reverse mode through the adjoint
+        kernels, forward mode (torch.autograd.forward_ad) through the TLM kernels."""
+        return _functions()[0].apply(q, self)
+
+    def trajectory(self, q0, nsteps, every=5):
+        """q^T after nsteps HEVI steps as a differentiable torch operation.  Reverse mode
+        keeps a checkpoint every `every` steps and recomputes each segment during the
+        adjoint sweep; forward mode runs the TLM alongside the trajectory."""
+        return _functions()[1].apply(q0, self, int(nsteps), int(every))
+
     # -- inspection -------------------------------------------------------------------
     def connectivity(self):
         torch = self._torch
@@ -258,6 +357,60 @@ class Numa:
         s = ctypes.c_int()
         self._check(lib().numa_status(self._h, ctypes.byref(s)), "numa_status")
         return s.value
+
+
+_FUNCTIONS = None
+
+
+def _functions():
+    """The torch.autograd.Function classes (built on first use so that importing the
+    binding does not import torch)."""
+    global _FUNCTIONS
+    if _FUNCTIONS is not None:
+        return _FUNCTIONS
+    import torch
+
+    def _c(t):
+        return t.contiguous() if t.dtype == torch.float64 else t.double().contiguous()
+
+    class RHS(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, q, numa):
+            ctx.numa = numa
+            ctx.save_for_backward(q)
+            ctx.save_for_forward(q)
+            return numa.rhs_explicit(_c(q))
+
+        @staticmethod
+        def backward(ctx, lam):
+            q, = ctx.saved_tensors
+            return ctx.numa.rhs_adjoint(_c(q), _c(lam)), None
+
+        @staticmethod
+        def jvp(ctx, dq, _numa):
+            q, = ctx.saved_tensors
+            return ctx.numa.rhs_tlm(_c(q), _c(dq))
+
+    class Trajectory(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, q0, numa, nsteps, every):
+            qT, ckpt = numa.forward_checkpointed(_c(q0), nsteps, every)
+            ctx.numa, ctx.nsteps, ctx.every, ctx.ckpt = numa, nsteps, every, ckpt
+            ctx.save_for_forward(q0)
+            return qT
+
+        @staticmethod
+        def backward(ctx, lamT):
+            lam0 = ctx.numa.adjoint_checkpointed(ctx.ckpt, ctx.nsteps, ctx.every, _c(lamT))
+            return lam0, None, None, None
+
+        @staticmethod
+        def jvp(ctx, dq0, *_):
+            q0, = ctx.saved_tensors
+            return ctx.numa.step_imex1d_tlm(_c(q0), _c(dq0), ctx.nsteps)[1]
+
+    _FUNCTIONS = (RHS, Trajectory)
+    return _FUNCTIONS
 
 
 class Batch:

@@ -122,6 +122,8 @@ int cuda_fail(numa_ctx* ctx, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
+}  // namespace
+
 // Event pair around one launch when profiling is on (index into ctx->prof, or -1).
 long prof_begin(numa_ctx* c, int kind) {
   if (!c->prof_on) return -1;
@@ -140,6 +142,8 @@ void prof_end(numa_ctx* c, long idx) {
   if (idx >= 0) cudaEventRecord(c->prof[idx].b, c->stream);
 }
 
+namespace {
+
 void free_all(numa_ctx* c) {
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
@@ -157,6 +161,8 @@ void free_all(numa_ctx* c) {
   cudaFree(c->d_status);
   cudaFree(c->d_count);
   cudaFree(c->d_hoststate);
+  cudaFree(c->d_adj);
+  cudaFree(c->d_adjtab);
 }
 
 // Host reference state and the column derivative (Sec. "Equation Set2NC",

@@ -35,6 +35,10 @@ struct numa_ctx {
   unsigned* d_status = nullptr;
   unsigned long long* d_count = nullptr;
   double* d_hoststate = nullptr;
+  // differentiation form (allocated on first use): 59 x nnode doubles of workspace and the
+  // transposed derivative tap tables of the three axes
+  double* d_adj = nullptr;
+  void* d_adjtab = nullptr;
   size_t factor_bytes = 0, work_bytes = 0;
   // per-kernel event timing
   struct ProfRec { int kind; cudaEvent_t a, b; };
@@ -43,6 +47,11 @@ struct numa_ctx {
   bool prof_on = false;
 };
 
+
+// Event pair around one launch of kernel kind `kind` when profiling is on (returns the
+// record index, or -1); prof_end records the closing event.
+long prof_begin(numa_ctx* c, int kind);
+void prof_end(numa_ctx* c, long idx);
 
 // Coefficients of IMEX stage 2 or 3 for the context's dt (Table 1 with b = b~).
 StageCoef numa_stage_coef(const numa_ctx* c, int stage);
