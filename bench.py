@@ -276,7 +276,8 @@ def run_gpu(args):
     nnode = g.nnode
     shares = {k: v[0] for k, v in kt.items()}
     names = {pkg.K_PRESSURE: "k_pressure", pkg.K_RHS: "k_rhs", pkg.K_STAGE: "k_stage"}
-    srcs = {pkg.K_PRESSURE: "rhs.cu", pkg.K_RHS: "rhs.cu", pkg.K_STAGE: "column.cu"}
+    srcs = {pkg.K_PRESSURE: ("rhs.cu", "rhs_device.cuh"), pkg.K_RHS: ("rhs.cu", "rhs_device.cuh"),
+            pkg.K_STAGE: ("column.cu", "column_device.cuh")}
     top = max(shares, key=shares.get)
     tot_ms, launches = kt[top]
     per_launch_ms = tot_ms / max(launches, 1)
@@ -287,7 +288,7 @@ def run_gpu(args):
     else:
         flops = 40 * nnode
     achieved = flops / (per_launch_ms / 1e3) / 1e12
-    sha = source_sha(srcs[top], "numa_internal.cuh")
+    sha = source_sha(*srcs[top], "numa_internal.cuh")
     traffic = recorded_traffic(names[top], sha)
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
@@ -334,6 +335,7 @@ def run_gpu(args):
         out["batching_form"] = batching_form(pkg, torch, min(args.steps, 10), args.warmup)
         out["batching_form_small_members"] = batching_form(pkg, torch, min(args.steps, 20), args.warmup,
                                                            64, (8, 8), (6, 6), (4, 4), 4500)
+        out["differentiation_form"] = differentiation_form(pkg, torch, args.warmup)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     g.close()
@@ -484,6 +486,93 @@ def batching_form(pkg, torch, steps, warmup, nmembers=64, h_range=(8, 48), v_ran
                                       "launches_per_step": 8 * nmembers},
             "speedup": round(ms_seq / ms_batch, 3), "identical_to_single_contexts": same,
             "finite": finite}
+
+
+def differentiation_form(pkg, torch, warmup, reps=5, nsteps=20, every=5):
+    """Gradient of J(q0) = 1/2 sum (theta'_T - target)^2 after nsteps HEVI 1D-IMEX steps at
+    C = 15 on 16 x 16 x 8 elements of order 4 over 600 x 600 x 10 km (the box size is not
+    given; this one keeps C_H = 0.5), FP64, checkpoints every `every` steps.  Times the
+    checkpointed forward run, the adjoint sweep (segment recomputation included) and the
+    tangent-linear run, reports the adjoint kernels' own times and checks the gradient by a
+    dot-product test and by centred finite differences with step 1e-6."""
+    import synthetic
+    nex, nez, n, L, Lz, C = 16, 8, 4, 600e3, 10e3, 15.0
+    xi = lgl_nodes()
+    fmin = (xi[1] + 1.0) / 2.0
+    dt = C * fmin * (Lz / nez) / C_S
+    g = pkg.Numa(nex, nex, nez, L, L, Lz, n, dt)
+    lev = g.reference_levels()
+    h = L / nex
+    ax = np.concatenate([e * h + (1.0 + xi[:-1]) * h / 2.0 for e in range(nex)] + [[L]])
+
+    def state(seed, **kw):
+        return torch.from_numpy(synthetic.random_state(ax, ax, lev["z"], L, L, Lz, lev["rho0"],
+                                                       lev["theta0"], seed, **kw)).cuda()
+    q0 = state(5001, vel=5.0)
+    target = state(5002)[4].contiguous()
+    dq, lam = state(5003, vel=3.0), state(5004, vel=2.0)
+
+    def misfit(q):
+        qT = g.trajectory(q, nsteps, every)
+        return 0.5 * ((qT[4] - target) ** 2).sum()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = bwd = tlm = 0.0
+    for r in range(warmup + reps):
+        x = q0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        ev[0].record()
+        J = misfit(x)
+        ev[1].record()
+        J.backward()
+        ev[2].record()
+        ev[2].synchronize()
+        if r >= warmup:
+            fwd += ev[0].elapsed_time(ev[1]) / reps
+            bwd += ev[1].elapsed_time(ev[2]) / reps
+    grad = x.grad
+    for r in range(warmup + reps):
+        torch.cuda.synchronize()
+        ev[0].record()
+        _, dqT = g.step_imex1d_tlm(q0, dq, nsteps)
+        ev[1].record()
+        ev[1].synchronize()
+        if r >= warmup:
+            tlm += ev[0].elapsed_time(ev[1]) / reps
+    # per-kernel times of one adjoint sweep
+    qT, ckpt = g.forward_checkpointed(q0, nsteps, every)
+    g.profile(True)
+    lam0 = g.adjoint_checkpointed(ckpt, nsteps, every, lam)
+    kern = {}
+    for name, kind in (("k_rhs_adj (weights + gather)", pkg.K_RHS_ADJ),
+                       ("k_stage_adj", pkg.K_STAGE_ADJ), ("k_rhs (recompute)", pkg.K_RHS),
+                       ("k_stage (recompute)", pkg.K_STAGE)):
+        t, cnt = g.profile_read(kind)
+        kern[name] = {"launches": cnt, "ms_per_launch": round(t / max(cnt, 1), 5)}
+    g.profile(False)
+    # checks: dot product of the run, centred differences of J
+    a = float((lam * dqT).sum())
+    b = float((lam0 * dq).sum())
+    eps = 1e-6
+    d = state(5005, vel=3.0)
+    with torch.no_grad():
+        fd = (float(misfit(q0 + eps * d)) - float(misfit(q0 - eps * d))) / (2 * eps)
+    ad = float((grad * d).sum())
+    sim = nsteps * dt
+    nodes = g.nnode
+    g.close()
+    return {"workload": "16x16x8 hex elements over 600x600x10 km, N=4 (65x65 columns x 33 levels), "
+                        "%d HEVI 1D-IMEX ARK2 steps at C=15, checkpoints every %d" % (nsteps, every),
+            "nodes": int(nodes), "dt_s": round(dt, 4),
+            "forward_checkpointed_ms": round(fwd, 3), "adjoint_ms": round(bwd, 3),
+            "gradient_ms": round(fwd + bwd, 3), "adjoint_over_forward": round(bwd / fwd, 3),
+            "tlm_run_ms": round(tlm, 3),
+            "gradients_per_s": round(1e3 / (fwd + bwd), 2),
+            "sim_s_per_wall_s_of_gradient": round(sim / ((fwd + bwd) / 1e3), 1),
+            "kernels": kern,
+            "dot_product_rel_diff": float("%.3g" % (abs(a - b) / abs(a))),
+            "fd_rel_diff_step_1e-6": float("%.3g" % (abs(fd - ad) / abs(ad))),
+            "finite": bool(torch.isfinite(grad).all().item())}
 
 
 def oracle_sample_step(window_elems, nsteps_min, seconds):

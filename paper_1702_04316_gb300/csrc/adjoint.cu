@@ -238,20 +238,29 @@ __device__ __forceinline__ double col_dzT(const double* v, int T, int j, int M, 
 // Solve S^T x = b in place for one column (stride T), S = L U in the stored layout:
 // U^T y = b by forward substitution (row i of U^T is stored column i of U: the entries
 // U(i-k, i), k = 1..HB, and 1/U(i,i)), then L^T x = y by back substitution (row i of L^T is
-// stored column i of L).  The last HB values of the recurrence stay in registers.
+// stored column i of L).  The last HB values of the recurrence stay in registers, and the
+// factor row of the next step is loaded while the current one is used.
 template <int HB>
 __device__ __forceinline__ void col_solve_T(double* x, int T, int M, const double* __restrict__ L,
                                             const double* __restrict__ U, long long nc,
                                             long long col) {
-  double z[HB];
+  double z[HB], f[HB + 1], fn[HB + 1];
 #pragma unroll
   for (int k = 0; k < HB; ++k) z[k] = 0.0;          // z[k] = y_{i-1-k}
+#pragma unroll
+  for (int k = 0; k <= HB; ++k) fn[k] = __ldg(U + (long long)k * nc + col);
   for (int i = 0; i < M; ++i) {
-    const double* Uc = U + (long long)i * (HB + 1) * nc + col;
+#pragma unroll
+    for (int k = 0; k <= HB; ++k) f[k] = fn[k];
+    if (i + 1 < M) {
+      const double* Uc = U + (long long)(i + 1) * (HB + 1) * nc + col;
+#pragma unroll
+      for (int k = 0; k <= HB; ++k) fn[k] = __ldg(Uc + (long long)k * nc);
+    }
     double acc = x[i * T];
 #pragma unroll
-    for (int k = 1; k <= HB; ++k) acc = fma(-__ldg(Uc + (long long)k * nc), z[k - 1], acc);
-    const double y = acc * __ldg(Uc);
+    for (int k = 1; k <= HB; ++k) acc = fma(-f[k], z[k - 1], acc);
+    const double y = acc * f[0];
     x[i * T] = y;
 #pragma unroll
     for (int k = HB - 1; k > 0; --k) z[k] = z[k - 1];
@@ -259,11 +268,22 @@ __device__ __forceinline__ void col_solve_T(double* x, int T, int M, const doubl
   }
 #pragma unroll
   for (int k = 0; k < HB; ++k) z[k] = 0.0;          // z[k] = x_{i+1+k}
+  {
+    const double* Lc = L + (long long)(M - 1) * HB * nc + col;
+#pragma unroll
+    for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * nc);
+  }
   for (int i = M - 1; i >= 0; --i) {
-    const double* Lc = L + (long long)i * HB * nc + col;
+#pragma unroll
+    for (int k = 0; k < HB; ++k) f[k] = fn[k];
+    if (i > 0) {
+      const double* Lc = L + (long long)(i - 1) * HB * nc + col;
+#pragma unroll
+      for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * nc);
+    }
     double acc = x[i * T];
 #pragma unroll
-    for (int k = 1; k <= HB; ++k) acc = fma(-__ldg(Lc + (long long)(k - 1) * nc), z[k - 1], acc);
+    for (int k = 1; k <= HB; ++k) acc = fma(-f[k - 1], z[k - 1], acc);
     x[i * T] = acc;
 #pragma unroll
     for (int k = HB - 1; k > 0; --k) z[k] = z[k - 1];
@@ -271,15 +291,17 @@ __device__ __forceinline__ void col_solve_T(double* x, int T, int M, const doubl
   }
 }
 
+// S^T x = b for T columns per CTA (blockDim.x >= T threads; the first T solve).
 template <int N>
-__global__ void k_solve_T(const double* __restrict__ b, double* __restrict__ x, Geom G, Factors F) {
+__global__ void k_solve_T(const double* __restrict__ b, double* __restrict__ x, Geom G, Factors F,
+                          int T) {
   extern __shared__ double sm[];
-  const int T = blockDim.x, M = G.M;
+  const int NT = blockDim.x, M = G.M;
   const long long col0 = blockIdx.x * (long long)T;
   const int ncols = (int)min((long long)T, G.ncol - col0);
   const long long base = col0 * M;
   const int cnt = ncols * M;
-  for (int j = threadIdx.x; j < cnt; j += T) {
+  for (int j = threadIdx.x; j < cnt; j += NT) {
     const int c = j / M, lev = j - c * M;
     sm[lev * T + c] = b[base + j];
   }
@@ -287,7 +309,7 @@ __global__ void k_solve_T(const double* __restrict__ b, double* __restrict__ x, 
   if ((int)threadIdx.x < ncols)
     col_solve_T<2 * N>(sm + threadIdx.x, T, M, F.L, F.U, G.ncol, col0 + threadIdx.x);
   __syncthreads();
-  for (int j = threadIdx.x; j < cnt; j += T) {
+  for (int j = threadIdx.x; j < cnt; j += NT) {
     const int c = j / M, lev = j - c * M;
     x[base + j] = sm[lev * T + c];
   }
@@ -301,12 +323,15 @@ __global__ void k_solve_T(const double* __restrict__ b, double* __restrict__ x, 
 //   b = P_e - kF w_a - kD D_z w_a,  P = S^-1 b,  w_p = kp1 D_z P + kp2 P
 //   w = w_a - w_p,  theta = theta~_e - kth w,  rho = invG0 P - H0G0 theta
 //   q(i) = (rho, w, theta) - c1 q^n (- c2 q(2))
-// Shared memory: four columns of M levels (T columns per CTA).
+// Shared memory: four columns of M levels for each of the CTA's T columns; blockDim.x >= T
+// threads share the coalesced phases, the first T run the column phase.
 template <int N, bool S3>
-__global__ void k_stage_adj(const double* __restrict__ lam, double* qa, double* R1a, double* R2a,
-                            double* q2a, Geom G, RefLev R, Factors F, StageCoef sc, StageTab tb) {
+__global__ void k_stage_adj(const double* __restrict__ lam, double* __restrict__ qa,
+                            double* __restrict__ R1a, double* __restrict__ R2a,
+                            double* __restrict__ q2a, Geom G, RefLev R, Factors F, StageCoef sc,
+                            StageTab tb, int T) {
   extern __shared__ double sm[];
-  const int T = blockDim.x, M = G.M;
+  const int NT = blockDim.x, M = G.M;
   const long long nn = G.nnode;
   const long long col0 = blockIdx.x * (long long)T;
   const int ncols = (int)min((long long)T, G.ncol - col0);
@@ -320,7 +345,8 @@ __global__ void k_stage_adj(const double* __restrict__ lam, double* qa, double* 
   const double c1 = sc.c[0], c2 = sc.c[1];
 
   // phase 3 backwards (coalesced): u, v directly; theta*, w*, P* and kp1 w_p* per level
-  for (int j = threadIdx.x; j < cnt; j += T) {
+#pragma unroll 2
+  for (int j = threadIdx.x; j < cnt; j += NT) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
 #pragma unroll
@@ -357,7 +383,8 @@ __global__ void k_stage_adj(const double* __restrict__ lam, double* qa, double* 
   __syncthreads();
 
   // phase 1 backwards (coalesced)
-  for (int j = threadIdx.x; j < cnt; j += T) {
+#pragma unroll 2
+  for (int j = threadIdx.x; j < cnt; j += NT) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
     const double bs = P[lev * T + c];
@@ -404,22 +431,26 @@ cudaError_t rhs_adj_n(const double* q, const double* Pp, const double* lam, cons
   return cudaGetLastError();
 }
 
-// Columns per CTA of the adjoint column kernels: 32, fewer when M is so large that four
-// columns of 32 would not fit in shared memory.
-int adj_cols(int M) {
+// Columns per CTA of the adjoint column kernels: 32, or 16 when that leaves fewer CTAs than
+// SMs, and fewer when four columns of M levels each would not fit in shared memory.  The
+// CTAs have kAdjThreads threads for the coalesced phases.
+const int kAdjThreads = 128;
+
+int adj_cols(const Geom& G) {
   int T = 32;
-  while (T > 1 && (size_t)4 * M * T * sizeof(double) > 200 * 1024) T /= 2;
+  if ((G.ncol + T - 1) / T < 152) T = 16;
+  while (T > 1 && (size_t)4 * G.M * T * sizeof(double) > 200 * 1024) T /= 2;
   return T;
 }
 
 template <int N>
 cudaError_t solve_T_n(const double* b, double* x, const Geom& G, const Factors& F, cudaStream_t s) {
-  const int T = adj_cols(G.M);
+  const int T = adj_cols(G);
   const size_t smem = (size_t)G.M * T * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_solve_T<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_solve_T<N><<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(b, x, G, F);
+  k_solve_T<N><<<(unsigned)((G.ncol + T - 1) / T), kAdjThreads, smem, s>>>(b, x, G, F, T);
   return cudaGetLastError();
 }
 
@@ -427,13 +458,13 @@ template <int N, bool S3>
 cudaError_t stage_adj_nt(const double* lam, double* qa, double* R1a, double* R2a, double* q2a,
                          const Geom& G, const RefLev& R, const Factors& F, const StageCoef& sc,
                          const StageTab& tb, cudaStream_t s) {
-  const int T = adj_cols(G.M);
+  const int T = adj_cols(G);
   const size_t smem = (size_t)4 * G.M * T * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_stage_adj<N, S3>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_stage_adj<N, S3><<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(lam, qa, R1a, R2a, q2a, G,
-                                                                      R, F, sc, tb);
+  k_stage_adj<N, S3><<<(unsigned)((G.ncol + T - 1) / T), kAdjThreads, smem, s>>>(
+      lam, qa, R1a, R2a, q2a, G, R, F, sc, tb, T);
   return cudaGetLastError();
 }
 

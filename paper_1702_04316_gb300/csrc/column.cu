@@ -14,6 +14,9 @@
 // row is one FMA and the factors are read by column (the layout numa_internal.cuh gives).
 #include "numa_internal.cuh"
 
+#include <algorithm>
+#include <cstdlib>
+
 #include "column_device.cuh"
 
 namespace {
@@ -111,14 +114,31 @@ template <int N, bool S3, bool MIXED, typename RT>
 __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
                         const RT* __restrict__ R2, const double* __restrict__ q2,
                         double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
-                        StageTab tb, int iters) {
+                        StageTab tb, int iters, int T) {
   extern __shared__ double sm[];
-  stage_body<N, S3, MIXED, RT>(blockIdx.x * (long long)blockDim.x, sm, qn, R1, R2, q2, out, G, R,
-                               F, sc, tb, iters);
+  stage_body<N, S3, MIXED, RT>(blockIdx.x * (long long)T, T, sm, qn, R1, R2, q2, out, G, R, F, sc,
+                               tb, iters);
 }
 
 size_t stage_smem(int M, int T, bool mixed, int iters) {
   return col_smem_per_level(mixed, iters) * M * T;
+}
+
+// Threads per CTA of the fused stage for T columns: kStageThreadsPerColumn x T (capped at
+// 1024); NUMA_STAGE_THREADS (a multiple of 32, at least T) overrides, for tuning.
+const int kStageMinThreads = 128;
+
+int stage_threads(int T) {
+  static int env = -1;
+  if (env < 0) {
+    env = 0;
+    if (const char* t = std::getenv("NUMA_STAGE_THREADS")) {
+      const int v = std::atoi(t);
+      if (v >= 32 && v <= 1024 && v % 32 == 0) env = v;
+    }
+  }
+  if (env >= T) return env;
+  return std::min(1024, std::max(T, kStageMinThreads));
 }
 
 template <int N, bool MIXED>
@@ -141,8 +161,8 @@ cudaError_t launch_stage_k(const double* qn, const RT* R1, const RT* R2, const d
   cudaError_t e = cudaFuncSetAttribute(k_stage<N, S3, MIXED, RT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_stage<N, S3, MIXED, RT><<<(unsigned)((G.ncol + T - 1) / T), T, smem, s>>>(
-      qn, R1, R2, q2, out, G, R, F, sc, tb, iters);
+  k_stage<N, S3, MIXED, RT><<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T), smem, s>>>(
+      qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T);
   return cudaGetLastError();
 }
 

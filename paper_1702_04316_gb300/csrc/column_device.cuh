@@ -179,15 +179,17 @@ __host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
 //   kept in shared memory, which doubles the resident columns), then
 //   q(i) = q~ - sum_j c_ij q(j).
 // RT: type of R1, R2 (double, or float in the mixed form).
-// col0: first column of this block (T = blockDim.x columns); sm: dynamic shared memory of
+// col0: first column of this block, T columns (T <= blockDim.x: all threads share phases 1
+// and 3, the first T run phase 2); sm: dynamic shared memory of
 // col_smem_per_level(MIXED, iters) * M * T bytes.
 template <int N, bool S3, bool MIXED, typename RT>
-__device__ __forceinline__ void stage_body(long long col0, double* sm, const double* __restrict__ qn,
+__device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
+                                           const double* __restrict__ qn,
                                            const RT* __restrict__ R1, const RT* __restrict__ R2,
                                            const double* __restrict__ q2, double* __restrict__ out,
                                            const Geom& G, const RefLev& R, const Factors& F,
                                            const StageCoef& sc, const StageTab& tb, int iters) {
-  const int T = blockDim.x, M = G.M;
+  const int NT = blockDim.x, M = G.M;
   const long long nn = G.nnode;
   const int ncols = (int)min((long long)T, G.ncol - col0);
   const long long base = col0 * M;
@@ -213,7 +215,7 @@ __device__ __forceinline__ void stage_body(long long col0, double* sm, const dou
 
   // phase 1
 #pragma unroll 2
-  for (int j = threadIdx.x; j < cnt; j += T) {
+  for (int j = threadIdx.x; j < cnt; j += NT) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
     out[nn + g] = pred(1, nn + g);
@@ -241,7 +243,7 @@ __device__ __forceinline__ void stage_body(long long col0, double* sm, const dou
 
   // phase 3
 #pragma unroll 2
-  for (int j = threadIdx.x; j < cnt; j += T) {
+  for (int j = threadIdx.x; j < cnt; j += NT) {
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
     const long long orr = g, ow = 3 * nn + g, oth = 4 * nn + g;

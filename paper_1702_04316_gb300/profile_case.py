@@ -6,7 +6,11 @@ workload shape on a smaller box: ``--nex`` x ``--nex`` x 12 elements of order 4 
 gives a 164 MB state (larger than the 129 MB L2) and about 1.7 GB of device memory.
 Every step reads the same input and writes a separate output.
 
-  python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0] [--precision mixed]
+  python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0] [--adj 0]
+                                                [--precision mixed]
+
+--adj K also runs K adjoint steps (numa_step_imex1d_adjoint) and K tangent-linear steps from
+the same input, for captures of the differentiation form's kernels.
 """
 import argparse
 import os
@@ -24,6 +28,7 @@ def main():
     ap.add_argument("--nex", type=int, default=72)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--rk", type=int, default=0)
+    ap.add_argument("--adj", type=int, default=0)
     ap.add_argument("--C", type=float, default=15.0)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     a = ap.parse_args()
@@ -47,11 +52,16 @@ def main():
         g.step_imex1d(q0, q1, 1)
     for _ in range(a.rk):
         g.step_explicit_rk(q0, dt / a.C, q1, 1)
+    if a.adj:
+        lam = torch.empty_like(q0).copy_(q0)
+        for _ in range(a.adj):
+            g.step_imex1d_adjoint(q0, lam, q1)
+        g.step_imex1d_tlm(q0, lam, a.adj, q1, torch.empty_like(q0))
     torch.cuda.synchronize()
     assert g.count_nonfinite(q1) == 0
     assert g.status() == pkg.NUMA_OK
     g.close()
-    print("profile_case ok: nex=%d steps=%d rk=%d" % (nex, a.steps, a.rk))
+    print("profile_case ok: nex=%d steps=%d rk=%d adj=%d" % (nex, a.steps, a.rk, a.adj))
 
 
 if __name__ == "__main__":
