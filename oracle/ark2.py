@@ -27,7 +27,8 @@ import math
 
 import numpy as np
 
-from .column import implicit_solve, lu_nopivot_banded
+from .column import (implicit_solve, implicit_solve_standard, lu_nopivot_banded,
+                     standard_half_band, standard_interleaved)
 from .rhs import rhs
 
 SQ2 = math.sqrt(2.0)
@@ -75,13 +76,20 @@ def ark_step(q, dt, R, solve):
 
 
 class HEVI:
-    """The 1D-IMEX (HEVI) ARK2 integrator on a box mesh (oracle)."""
+    """The 1D-IMEX (HEVI) ARK2 integrator on a box mesh (oracle).  form: "schur" (the
+    paper's method) or "standard" (the non-Schur column system, same step otherwise)."""
 
-    def __init__(self, mesh, col, dt):
-        self.mesh, self.col, self.dt = mesh, col, dt
+    def __init__(self, mesh, col, dt, form="schur"):
+        if form not in ("schur", "standard"):
+            raise ValueError("form must be 'schur' or 'standard'")
+        self.mesh, self.col, self.dt, self.form = mesh, col, dt, form
         _, at, _, _ = tableau()
         self.lam = at[1, 1] * dt                     # SDIRK: one lam for every stage
-        self.LU = lu_nopivot_banded(col.jacobian_by_probing(self.lam), col.half_band)
+        if form == "schur":
+            self.LU = lu_nopivot_banded(col.jacobian_by_probing(self.lam), col.half_band)
+        else:
+            self.LU = lu_nopivot_banded(standard_interleaved(col, self.lam),
+                                        standard_half_band(mesh))
         self.l2g = mesh.l2g()
         self.mass = mesh.global_mass(self.l2g)
 
@@ -92,7 +100,9 @@ class HEVI:
         assert abs(lam - self.lam) <= 1e-15 * abs(self.lam)
         shape = q_e.shape
         qc = q_e.reshape(5, self.mesh.ncol, self.mesh.M)
-        return implicit_solve(self.col, self.LU, qc, lam).reshape(shape)
+        if self.form == "schur":
+            return implicit_solve(self.col, self.LU, qc, lam).reshape(shape)
+        return implicit_solve_standard(self.col, self.LU, qc, lam).reshape(shape)
 
     def step(self, q, nsteps=1):
         for _ in range(nsteps):

@@ -24,6 +24,11 @@ direction r is z here, Sec. "IMEX time integration", Eq. sieqn1d):
   theta' = theta'_e - lam w d(theta0)/dz,  rho' = (P - H0 theta') / G0; u, v unchanged.
 * the Jacobian of S by probing with unit vectors (Algorithm 7, BuildJacobian) and its
   banded LU without pivoting (Algorithm 9, LUdecompose), then forward/back substitution.
+* the standard (non-Schur) column form the paper contrasts with the Schur form in memory
+  and speed (Sec. "Performance of IMEX on manycore processors", comparison of the forms
+  with a direct solver): the 3M x 3M system I - lam L_V on (rho', w, theta') itself,
+  unknowns ordered level by level so that the matrix is banded (half-bandwidth 3N + 1),
+  factored by the same banded LU without pivoting.
 
 Readings where the paper defers to work not at hand: the "modified Jacobian for DSS"
 (Sec. "Direct stiffness summation") is taken to be the composition above (gradient, DSS,
@@ -214,3 +219,34 @@ def implicit_solve(col, LU, q_e, lam):
     P = lu_solve_banded(LU, col.half_band, b)
     rho, w, th = col.extract(P, wa, th_e, lam)
     return np.stack([rho, u_e, v_e, w, th])
+
+
+def standard_interleaved(col, lam):
+    """``Column.standard_matrix`` with the unknowns ordered level by level, (rho', w,
+    theta') at each level: unknown 3*m + v is variable v at level m."""
+    K = col.standard_matrix(lam)
+    M = col.M
+    perm = np.array([v * M + m for m in range(M) for v in range(3)])
+    return K[np.ix_(perm, perm)]
+
+
+def standard_half_band(mesh):
+    """Half-bandwidth of the interleaved standard matrix: rho' and theta' couple to w over
+    the N levels on either side (the D_z stencil), 3 unknowns per level: 3N + 1."""
+    return 3 * mesh.N + 1
+
+
+def implicit_solve_standard(col, LUs, q_e, lam):
+    """Solve q = q_e + lam L_V(q) for every column with the standard form: the banded LU
+    ``LUs`` of ``standard_interleaved(col, lam)`` and forward/back substitution.  The w
+    equations of the two end nodes are the wall condition w = 0 (as in the Schur form, where
+    w_a and w_p vanish there).  Shapes as ``implicit_solve``."""
+    rho_e, u_e, v_e, w_e, th_e = q_e
+    M = col.M
+    rhs = np.stack([rho_e, w_e, th_e], axis=-1)          # (..., M, 3)
+    rhs[..., 0, 1] = 0.0
+    rhs[..., M - 1, 1] = 0.0
+    x = lu_solve_banded(LUs, 3 * col.mesh.N + 1, rhs.reshape(rhs.shape[:-2] + (3 * M,)))
+    x = x.reshape(x.shape[:-1] + (M, 3))
+    return np.stack([x[..., 0], u_e, v_e, x[..., 1], x[..., 2]])
+

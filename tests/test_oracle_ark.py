@@ -163,3 +163,15 @@ def test_hevi_bounded_at_large_vertical_courant(C, L):
     q = H.step(q0, 10)
     assert np.isfinite(q).all()
     assert np.abs(q[3]).max() < 1.0 and np.abs(q[4]).max() < 1.0
+
+
+@pytest.mark.parametrize("C", [15, 150])
+def test_standard_form_step_equals_schur_step(C):
+    """The standard (non-Schur) column system gives the same HEVI steps."""
+    m, col, dt1 = _box(nex=2, nez=3, L=2000e3)
+    xg, yg, zg = m.coords()
+    q0 = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Lx, m.Lz, col.rho0, col.theta0, 13)
+    a = ark2.HEVI(m, col, C * dt1).step(q0, 3)
+    b = ark2.HEVI(m, col, C * dt1, form="standard").step(q0, 3)
+    for f in range(5):
+        assert np.abs(a[f] - b[f]).max() <= 1e-10 * max(np.abs(a[f]).max(), 1e-300)

@@ -122,3 +122,35 @@ def test_lowest_acoustic_mode_of_short_column():
     T = np.sum(0.5 * (inv_c[1:] + inv_c[:-1]) * np.diff(zz))
     assert abs(osc.min() - np.pi / T) < 2e-5 * np.pi / T
     assert np.abs(ev.real).max() < 1e-6 * np.abs(ev).max()   # non-dissipative
+
+
+# ---- standard (non-Schur) column form ---------------------------------------------------
+@pytest.mark.parametrize("N,nez", [(2, 5), (4, 3), (7, 2)])
+def test_interleaved_standard_matrix_is_banded(N, nez):
+    from oracle.column import standard_half_band, standard_interleaved
+    m = BoxMesh(1, 1, nez, N, 1e3, 1e3, 10e3)
+    col = Column(m, 300.0, 0.01)
+    K = standard_interleaved(col, 3.0)
+    i, j = np.nonzero(K)
+    assert np.abs(i - j).max() == standard_half_band(m) == 3 * N + 1
+
+
+@pytest.mark.parametrize("n_bv", [0.0, 0.02])
+@pytest.mark.parametrize("C", [1, 15, 150])
+def test_standard_form_solve_equals_schur_solve(C, n_bv):
+    """Banded no-pivot LU of the standard system and the Schur path give the same
+    columns; w is zero at the walls in both (non-zero w_e there is overridden)."""
+    from oracle.column import (implicit_solve_standard, standard_half_band,
+                               standard_interleaved)
+    m, col = _col(n_bv=n_bv)
+    lam = _lam(col, m, C)
+    rng = np.random.default_rng(10 + C)
+    q_e = rng.standard_normal((5, 4, m.M))
+    q_e[0] *= 1e-3 * col.rho0
+    LU = lu_nopivot_banded(col.jacobian_by_probing(lam), col.half_band)
+    LUs = lu_nopivot_banded(standard_interleaved(col, lam), standard_half_band(m))
+    a = implicit_solve(col, LU, q_e, lam)
+    b = implicit_solve_standard(col, LUs, q_e, lam)
+    assert np.abs(b[3][:, [0, -1]]).max() == 0.0
+    for f in range(5):
+        assert np.abs(a[f] - b[f]).max() <= 1e-12 * C * np.abs(a[f]).max()
