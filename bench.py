@@ -336,6 +336,7 @@ def run_gpu(args):
         out["batching_form_small_members"] = batching_form(pkg, torch, min(args.steps, 20), args.warmup,
                                                            64, (8, 8), (6, 6), (4, 4), 4500)
         out["differentiation_form"] = differentiation_form(pkg, torch, args.warmup)
+        out["column_forms"] = column_forms(pkg, torch, q0, min(args.steps, 10), args.warmup)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     g.close()
@@ -486,6 +487,58 @@ def batching_form(pkg, torch, steps, warmup, nmembers=64, h_range=(8, 48), v_ran
                                       "launches_per_step": 8 * nmembers},
             "speedup": round(ms_seq / ms_batch, 3), "identical_to_single_contexts": same,
             "finite": finite}
+
+
+def column_forms(pkg, torch, q0, steps, warmup, nsteps_cmp=1):
+    """The paper's memory / speed contrast of the two 1D column systems on the headline
+    workload (96 x 96 x 12 elements, N = 4, C = 15): the Schur form (M x M, half-band 2N)
+    and the standard form (3M x 3M on rho', w, theta', half-band 3N + 1), both FP64 with
+    banded LU stored per column.  Times the factorisation and one HEVI step of each, and
+    states how far the standard form's step is from the Schur form's (one step: this
+    workload has C_H = 9, so longer runs do not stay bounded)."""
+    dt = dt_for(C_MAIN)
+    res = {}
+    for form in ("schur", "standard"):
+        g = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, 0.0, column_form=form)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        g.factor_columns(dt)
+        e1.record()
+        e1.synchronize()
+        fact_ms = e0.elapsed_time(e1)
+        q1 = torch.empty_like(q0)
+        for _ in range(warmup):
+            g.step_imex1d(q0, q1, 1)
+        g.profile(True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            g.step_imex1d(q0, q1, 1)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st_ms, st_n = g.profile_read(pkg.K_STAGE)
+        g.profile(False)
+        qr = q0.clone()
+        g.step_imex1d(qr, None, nsteps_cmp)
+        torch.cuda.synchronize()
+        res[form] = {"factor_bytes": g.query(pkg.Q_FACTOR_BYTES), "half_band": g.query(pkg.Q_HALF_BAND),
+                     "factor_ms": round(fact_ms, 3), "ms_per_step": round(ms, 4),
+                     "sim_s_per_wall_s": round(dt / (ms / 1e3), 2),
+                     "stage_ms_per_launch": round(st_ms / max(st_n, 1), 4)}, qr
+        g.close()
+    a, qa = res["schur"]
+    b, qb = res["standard"]
+    diff = {name: float(torch.linalg.norm(qb[f] - qa[f]) / torch.linalg.norm(qa[f]))
+            for f, name in ((0, "rho"), (3, "w"), (4, "theta"))}
+    return {"workload": "96x96x12 hex elements over 200x200x15 km, N=4 (385x385 columns x 49 levels), "
+                        "HEVI 1D-IMEX ARK2 at C=15, FP64",
+            "schur": a, "standard": b,
+            "standard_over_schur": {"factor_bytes": round(b["factor_bytes"] / a["factor_bytes"], 3),
+                                    "step_time": round(b["ms_per_step"] / a["ms_per_step"], 3),
+                                    "stage_time": round(b["stage_ms_per_launch"] / a["stage_ms_per_launch"], 3)},
+            "rel_l2_standard_vs_schur_after_%d_steps" % nsteps_cmp: diff}
 
 
 def differentiation_form(pkg, torch, warmup, reps=5, nsteps=20, every=5):

@@ -72,12 +72,14 @@ enum {
   NUMA_Q_M = 1,             /* nodes per column */
   NUMA_Q_NNODE = 2,         /* global nodes */
   NUMA_Q_NELEM = 3,         /* elements */
-  NUMA_Q_HALF_BAND = 4,     /* half-bandwidth 2N of the column Schur matrix */
+  NUMA_Q_HALF_BAND = 4,     /* half-bandwidth of the stored column matrix: 2N (Schur form) or
+                               3N + 1 (standard form) */
   NUMA_Q_FACTOR_BYTES = 5,  /* bytes of stored LU factors */
   NUMA_Q_WORKSPACE_BYTES = 6, /* bytes of step workspace */
   NUMA_Q_FACTORED = 7,      /* 1 once numa_factor_columns succeeded */
   NUMA_Q_N = 8,             /* polynomial order */
-  NUMA_Q_PRECISION = 9      /* NUMA_PREC_FP64 or NUMA_PREC_MIXED */
+  NUMA_Q_PRECISION = 9,     /* NUMA_PREC_FP64 or NUMA_PREC_MIXED */
+  NUMA_Q_COLUMN_FORM = 10   /* NUMA_COLUMN_SCHUR or NUMA_COLUMN_STANDARD */
 };
 
 /* Options of numa_init_ex.
@@ -88,11 +90,21 @@ enum {
  *            solved in FP32 with refine_iters sweeps of FP64 iterative refinement (FP64
  *            residual with the matrix-free Schur operator), FP64 state accumulation.
  * refine_iters: FP64 refinement sweeps per solve in the mixed form (0..8; numa_init_ex with
- *               opt = NULL uses 1). */
+ *               opt = NULL uses 1).
+ * column_form: NUMA_COLUMN_SCHUR (default) -- the paper's Schur-complement column system in
+ *              the pressure, M x M with half-bandwidth 2N per column;
+ *              NUMA_COLUMN_STANDARD -- the standard (non-Schur) column system the paper
+ *              contrasts it with (Sec. "Performance of IMEX on manycore processors"): the
+ *              3M x 3M matrix I - lam L_V on (rho', w, theta') itself, unknowns ordered level
+ *              by level (half-bandwidth 3N + 1), factored by the same banded LU without
+ *              pivoting; M*3*(6N+3) doubles per column instead of M*(4N+1).  FP64 only;
+ *              numa_solve_columns and the differentiation form need the Schur form. */
 enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1 };
+enum { NUMA_COLUMN_SCHUR = 0, NUMA_COLUMN_STANDARD = 1 };
 typedef struct numa_options {
   int precision;
   int refine_iters;
+  int column_form;
 } numa_options;
 
 /* Create a context: validates the mesh, builds the LGL nodes/weights/derivative matrix
@@ -191,6 +203,8 @@ int numa_connectivity(numa_ctx* ctx, int32_t* l2g, int32_t* g2l);
  * stored (entries b < 2N hold L, b >= 2N hold U).  The mixed form's FP32 factors are
  * widened to double.  Synchronous. */
 int numa_column_factors(numa_ctx* ctx, long long col, double* host_out);
+/* (standard form: 3M rows of 2(3N+1)+1 = 6N+3 band entries, the level-interleaved unknowns
+ * 3 l + v, v = 0 rho', 1 w, 2 theta') */
 
 /* Host copy of the per-level reference tables, 8*M doubles in the order
  * z, rho0, theta0, P0, G0, H0, d(rho0)/dz, d(theta0)/dz.  Synchronous. */

@@ -19,8 +19,9 @@ ERRORS = {
     5: "NUMA_ERR_PIVOT", 6: "NUMA_ERR_NONFINITE", 7: "NUMA_ERR_TIMEOUT", 8: "NUMA_ERR_SCRATCH",
 }
 Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_FACTORED, Q_N, \
-    Q_PRECISION = range(10)
+    Q_PRECISION, Q_COLUMN_FORM = range(11)
 PRECISIONS = {"fp64": 0, "mixed": 1}
+COLUMN_FORMS = {"schur": 0, "standard": 1}
 
 # Every symbol include/numa.h declares (checked by tests/test_abi.py).
 EXPORTS = (
@@ -40,7 +41,8 @@ K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("refine_iters", ctypes.c_int)]
+    _fields_ = [("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
+                ("column_form", ctypes.c_int)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -123,7 +125,7 @@ class Numa:
     """One mesh, one reference state, one IMEX time step size (a numa_ctx)."""
 
     def __init__(self, nex, ney, nez, Lx, Ly, Lz, N, dt=0.0, theta_s=300.0, n_bv=0.0,
-                 stream=None, precision="fp64", refine_iters=1):
+                 stream=None, precision="fp64", refine_iters=1, column_form="schur"):
         import torch
         self._torch = torch
         L = lib()
@@ -131,7 +133,7 @@ class Numa:
         s = torch.cuda.current_stream() if stream is None else stream
         self._stream = s
         h = ctypes.c_void_p()
-        self._opt = Options(PRECISIONS[precision], int(refine_iters))
+        self._opt = Options(PRECISIONS[precision], int(refine_iters), COLUMN_FORMS[column_form])
         rc = L.numa_init_ex(ctypes.byref(self._desc), N, float(dt), ctypes.byref(self._opt),
                             ctypes.c_void_p(s.cuda_stream), ctypes.byref(h))
         if rc != NUMA_OK:
@@ -140,6 +142,7 @@ class Numa:
         self.N = N
         self.dt = float(dt)
         self.precision = precision
+        self.column_form = column_form
         self.ncol = self.query(Q_NCOL)
         self.M = self.query(Q_M)
         self.nnode = self.query(Q_NNODE)
@@ -334,8 +337,11 @@ class Numa:
         return l2g.view(self.nelem, self.N + 1, self.N + 1, self.N + 1), g2l.view(self.nnode, 8)
 
     def column_factors(self, col):
-        W = 4 * self.N + 1
-        out = np.empty((self.M, W), dtype=np.float64)
+        """Band of one column's stored factors: (M, 4N+1) for the Schur form, (3M, 6N+3)
+        for the standard form (level-interleaved unknowns)."""
+        hb = self.query(Q_HALF_BAND)
+        n = 3 * self.M if self.column_form == "standard" else self.M
+        out = np.empty((n, 2 * hb + 1), dtype=np.float64)
         self._check(lib().numa_column_factors(self._h, int(col), out.ctypes.data_as(ctypes.c_void_p)),
                     "numa_column_factors")
         return out

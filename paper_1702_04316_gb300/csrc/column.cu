@@ -28,6 +28,43 @@ using namespace numa_dev;
 //   S e_m = e_m - lam F0z w_p - lam rho0 G0 D_z w_p,
 // assembled in FP64 and stored as FT, then Algorithm 9 (LUdecompose): banded LU without
 // pivoting, in place, in FT arithmetic.
+// Zero the band storage of one column (n unknowns, half-bandwidth hb).
+template <typename FT>
+__device__ void band_zero(FT* Lf, FT* Uf, int n, int hb, long long nc, long long col) {
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < hb; ++k) Lf[((long long)i * hb + k) * nc + col] = (FT)0;
+    for (int k = 0; k <= hb; ++k) Uf[((long long)i * (hb + 1) + k) * nc + col] = (FT)0;
+  }
+}
+
+// Algorithm 9 (LUdecompose): banded LU without pivoting of one column's n x n matrix, in
+// place in FT arithmetic; the diagonal of U is stored inverted (the solves multiply).  A
+// zero or non-finite pivot latches NUMA_ST_PIVOT (and is replaced by 1 so the column stays
+// finite).
+template <typename FT>
+__device__ void band_lu(const Band<FT>& A, int n, int hb, unsigned* status) {
+  for (int k = 0; k < n; ++k) {
+    FT piv = A.at(k, k);
+    if (!(fabs((double)piv) > 0.0) || !isfinite((double)piv)) {
+      atomicOr(status, NUMA_ST_PIVOT);
+      piv = (FT)1;
+    }
+    const FT ip = (FT)1 / piv;
+    const int E = min(k + hb, n - 1);
+    for (int i = k + 1; i <= E; ++i) {
+      const FT l = A.at(i, k) * ip;
+      A.at(i, k) = l;
+      for (int j = k + 1; j <= E; ++j) A.at(i, j) = fma(-l, A.at(k, j), A.at(i, j));
+    }
+    A.at(k, k) = ip;
+  }
+}
+
+// Algorithm 7 (BuildJacobian) for the Schur form, one column per thread: column m of
+// S(lam) is the left-hand side applied to the unit vector e_m,
+//   w_p = A^-1 lam (D_z e_m / rho0 + g e_m / (G0 rho0))   (zero at the two walls)
+//   S e_m = e_m - lam F0z w_p - lam rho0 G0 D_z w_p,
+// assembled in FP64 and stored as FT, then Algorithm 9 (band_lu) in FT arithmetic.
 template <typename FT>
 __global__ void k_factor(Geom G, RefLev R, double lam, FT* Lf, FT* Uf, int hb, unsigned* status) {
   const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -35,10 +72,7 @@ __global__ void k_factor(Geom G, RefLev R, double lam, FT* Lf, FT* Uf, int hb, u
   const int M = G.M, N = G.N, W = 2 * N + 1;
   const long long nc = G.ncol;
   Band<FT> A{Lf, Uf, hb, nc, col};
-  for (int i = 0; i < M; ++i) {
-    for (int k = 0; k < hb; ++k) Lf[((long long)i * hb + k) * nc + col] = (FT)0;
-    for (int k = 0; k <= hb; ++k) Uf[((long long)i * (hb + 1) + k) * nc + col] = (FT)0;
-  }
+  band_zero(Lf, Uf, M, hb, nc, col);
   auto dz = [&](int l, int j) -> double {   // D_z(l, j), |l - j| <= N
     return __ldg(R.dz_band + (long long)l * W + (j - l + N));
   };
@@ -62,21 +96,49 @@ __global__ void k_factor(Geom G, RefLev R, double lam, FT* Lf, FT* Uf, int hb, u
       A.at(i, m) = (FT)s;
     }
   }
-  for (int k = 0; k < M; ++k) {
-    FT piv = A.at(k, k);
-    if (!(fabs((double)piv) > 0.0) || !isfinite((double)piv)) {
-      atomicOr(status, NUMA_ST_PIVOT);
-      piv = (FT)1;
-    }
-    const FT ip = (FT)1 / piv;
-    const int E = min(k + hb, M - 1);
-    for (int i = k + 1; i <= E; ++i) {
-      const FT l = A.at(i, k) * ip;
-      A.at(i, k) = l;
-      for (int j = k + 1; j <= E; ++j) A.at(i, j) = fma(-l, A.at(k, j), A.at(i, j));
-    }
-    A.at(k, k) = ip;   // the solve multiplies by 1/U(k,k)
+  band_lu(A, M, hb, status);
+}
+
+// Entry (i, m) of the standard column system I - lam L_V (the non-Schur form), unknowns
+// ordered level by level: unknown 3 l + v is variable v (0 rho', 1 w, 2 theta') at level l.
+//   rho' rows:   rho' + lam (d(rho0)/dz w + rho0 D_z w)
+//   w rows:      w + lam (D_z (G0 rho' + H0 theta') + g rho') / rho0   (w = 0 at the walls)
+//   theta' rows: theta' + lam d(theta0)/dz w
+__device__ double standard_entry(int i, int m, const Geom& G, const RefLev& R, double lam) {
+  const int N = G.N, M = G.M, W = 2 * N + 1;
+  const int li = i / 3, a = i - 3 * li, lj = m / 3, b = m - 3 * lj;
+  if (abs(li - lj) > N) return 0.0;
+  const bool same = li == lj;
+  const double dz = __ldg(R.dz_band + (long long)li * W + (lj - li + N));
+  if (a == 0) {
+    if (b == 0) return same ? 1.0 : 0.0;
+    if (b == 1) return lam * ((same ? R.drho0[li] : 0.0) + R.rho0[li] * dz);
+    return 0.0;
   }
+  if (a == 1) {
+    if (li == 0 || li == M - 1) return (b == 1 && same) ? 1.0 : 0.0;
+    if (b == 0) return lam * (dz * R.G0[lj] + (same ? NUMA_GRAV : 0.0)) * R.inv_rho0[li];
+    if (b == 1) return same ? 1.0 : 0.0;
+    return lam * dz * R.H0[lj] * R.inv_rho0[li];
+  }
+  if (b == 1) return same ? lam * R.dtheta0[li] : 0.0;
+  return (b == 2 && same) ? 1.0 : 0.0;
+}
+
+// Standard form: assemble the 3M x 3M band (half-bandwidth hb = 3N + 1) of one column per
+// thread and factor it with band_lu.
+__global__ void k_factor_standard(Geom G, RefLev R, double lam, double* Lf, double* Uf, int hb,
+                                  unsigned* status) {
+  const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (col >= G.ncol) return;
+  const int n = 3 * G.M;
+  const long long nc = G.ncol;
+  Band<double> A{Lf, Uf, hb, nc, col};
+  band_zero(Lf, Uf, n, hb, nc, col);
+  for (int m = 0; m < n; ++m)
+    for (int i = max(0, m - hb); i <= min(n - 1, m + hb); ++i)
+      A.at(i, m) = standard_entry(i, m, G, R, lam);
+  band_lu(A, n, hb, status);
 }
 
 template <int N, bool MIXED>
@@ -118,6 +180,63 @@ __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1
   extern __shared__ double sm[];
   stage_body<N, S3, MIXED, RT>(blockIdx.x * (long long)T, T, sm, qn, R1, R2, q2, out, G, R, F, sc,
                                tb, iters);
+}
+
+// Fused stage with the standard column system (rows 2 or 3 of Table 1).  Phase 1: the
+// predictor and the shift q~_e (u, v final), with (rho~_e, w~_e, theta~_e) stored level by
+// level in shared memory (3M values per column; w~_e = 0 at the walls, the wall condition).
+// Phase 2 (one thread per column): the banded solve with half-bandwidth 3N + 1.  Phase 3:
+// q(i) = q~ - sum_j c_ij q(j).  T columns per CTA, blockDim.x >= T threads.
+template <int N, bool S3>
+__global__ void k_stage_standard(const double* __restrict__ qn, const double* __restrict__ R1,
+                                 const double* __restrict__ R2, const double* __restrict__ q2,
+                                 double* __restrict__ out, Geom G, Factors F, StageCoef sc, int T) {
+  extern __shared__ double sm[];
+  const int NT = blockDim.x, M = G.M;
+  const long long nn = G.nnode;
+  const long long col0 = blockIdx.x * (long long)T;
+  const int ncols = (int)min((long long)T, G.ncol - col0);
+  const long long base = col0 * M;
+  const int cnt = ncols * M;
+  const double a1dt = sc.a[0] * sc.dt, a2dt = sc.a[1] * sc.dt;
+  const double c1 = sc.c[0], c2 = sc.c[1];
+  auto pred = [&](int f, long long o) -> double {
+    const double qv = qn[o];
+    double v = fma(a1dt, R1[o], qv);
+    if (S3) v = fma(a2dt, R2[o], v);
+    if (f == 1 || f == 2) return v;
+    v = fma(c1, qv, v);
+    if (S3) v = fma(c2, q2[o], v);
+    return v;
+  };
+#pragma unroll 2
+  for (int j = threadIdx.x; j < cnt; j += NT) {
+    const long long g = base + j;
+    const int c = j / M, lev = j - c * M;
+    out[nn + g] = pred(1, nn + g);
+    out[2 * nn + g] = pred(2, 2 * nn + g);
+    sm[(3 * lev) * T + c] = pred(0, g);
+    sm[(3 * lev + 1) * T + c] = (lev == 0 || lev == M - 1) ? 0.0 : pred(3, 3 * nn + g);
+    sm[(3 * lev + 2) * T + c] = pred(4, 4 * nn + g);
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < ncols)
+    col_solve<3 * N + 1, double, double>(sm + threadIdx.x, T, 3 * M, F.L, F.U, G.ncol,
+                                         col0 + threadIdx.x);
+  __syncthreads();
+#pragma unroll 2
+  for (int j = threadIdx.x; j < cnt; j += NT) {
+    const long long g = base + j;
+    const int c = j / M, lev = j - c * M;
+    const int fl[3] = {0, 3, 4};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const long long o = fl[k] * nn + g;
+      double v = fma(-c1, qn[o], sm[(3 * lev + k) * T + c]);
+      if (S3) v = fma(-c2, q2[o], v);
+      out[o] = v;
+    }
+  }
 }
 
 size_t stage_smem(int M, int T, bool mixed, int iters) {
@@ -172,6 +291,23 @@ cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const vo
                            const Factors& F, const StageCoef& sc, const StageTab& tb, int T,
                            bool r_float, cudaStream_t s) {
   const int it = F.refine_iters;
+  if (F.standard) {
+    const size_t smem = (size_t)3 * G.M * T * sizeof(double);
+    const unsigned nb = (unsigned)((G.ncol + T - 1) / T);
+    const double* a = (const double*)R1;
+    const double* b = (const double*)R2;
+    cudaError_t e;
+    if (stage == 3) {
+      e = cudaFuncSetAttribute(k_stage_standard<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_stage_standard<N, true><<<nb, stage_threads(T), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
+    } else {
+      e = cudaFuncSetAttribute(k_stage_standard<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_stage_standard<N, false><<<nb, stage_threads(T), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
+    }
+    return cudaGetLastError();
+  }
   if (F.mixed && !r_float) {
     const double* a = (const double*)R1;
     const double* b = (const double*)R2;
@@ -196,7 +332,8 @@ cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
                           unsigned* status, cudaStream_t s) {
   const int bs = 128;
   const unsigned nb = (unsigned)((G.ncol + bs - 1) / bs);
-  if (F.mixed) k_factor<float><<<nb, bs, 0, s>>>(G, R, lam, F.L32, F.U32, F.hb, status);
+  if (F.standard) k_factor_standard<<<nb, bs, 0, s>>>(G, R, lam, F.L, F.U, F.hb, status);
+  else if (F.mixed) k_factor<float><<<nb, bs, 0, s>>>(G, R, lam, F.L32, F.U32, F.hb, status);
   else k_factor<double><<<nb, bs, 0, s>>>(G, R, lam, F.L, F.U, F.hb, status);
   return cudaGetLastError();
 }

@@ -358,7 +358,10 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   if (!out) return NUMA_ERR_ARG;
   const int precision = opt ? opt->precision : NUMA_PREC_FP64;
   const int refine = opt ? opt->refine_iters : 1;
-  if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED) || refine < 0 || refine > 8) {
+  const int form = opt ? opt->column_form : NUMA_COLUMN_SCHUR;
+  if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED) || refine < 0 || refine > 8 ||
+      (form != NUMA_COLUMN_SCHUR && form != NUMA_COLUMN_STANDARD) ||
+      (form == NUMA_COLUMN_STANDARD && precision != NUMA_PREC_FP64)) {
     *out = nullptr;
     return NUMA_ERR_ARG;
   }
@@ -384,6 +387,7 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   c->precision = precision;
   c->F.mixed = precision == NUMA_PREC_MIXED;
   c->F.refine_iters = refine;
+  c->F.standard = form == NUMA_COLUMN_STANDARD;
   c->theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
   {
     // columns per CTA of the column kernels: 64, or 32 when 64 would leave SMs without a
@@ -403,11 +407,12 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   set_axis(c->C.z, N, w, D, mesh->Lz / mesh->nez);
   build_levels(c, xi, w, D, mesh->Lz / mesh->nez);
   int rc = upload_levels(c);
-  const int hb = 2 * N;
+  const int hb = c->F.standard ? 3 * N + 1 : 2 * N;      // half-bandwidth
+  const size_t nu = c->F.standard ? 3 * (size_t)G.M : (size_t)G.M;   // unknowns per column
   c->F.hb = hb;
   const bool mixed = c->F.mixed;
   const size_t fsz = mixed ? sizeof(float) : sizeof(double);
-  c->factor_bytes = (size_t)G.M * (2 * hb + 1) * G.ncol * fsz;
+  c->factor_bytes = nu * (2 * hb + 1) * G.ncol * fsz;
   c->work_bytes = mixed ? (size_t)(2 * 5) * G.nnode * sizeof(double) +
                               (size_t)(6 + 2 * 5) * G.nnode * sizeof(float)
                         : (size_t)(1 + 4 * 5) * G.nnode * sizeof(double);
@@ -419,8 +424,8 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
       ok = cudaMalloc(&c->F.L32, (size_t)G.M * hb * G.ncol * sizeof(float)) == cudaSuccess &&
            cudaMalloc(&c->F.U32, (size_t)G.M * (hb + 1) * G.ncol * sizeof(float)) == cudaSuccess;
     else if (ok)
-      ok = cudaMalloc(&c->F.L, (size_t)G.M * hb * G.ncol * sizeof(double)) == cudaSuccess &&
-           cudaMalloc(&c->F.U, (size_t)G.M * (hb + 1) * G.ncol * sizeof(double)) == cudaSuccess;
+      ok = cudaMalloc(&c->F.L, nu * hb * G.ncol * sizeof(double)) == cudaSuccess &&
+           cudaMalloc(&c->F.U, nu * (hb + 1) * G.ncol * sizeof(double)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       rc = NUMA_ERR_OOM;
@@ -520,6 +525,8 @@ int numa_solve_columns(numa_ctx* ctx, const double* b, double* x) {
   int rc;
   if ((rc = check_ptr(ctx, b, "b")) || (rc = check_ptr(ctx, x, "x"))) return rc;
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  if (ctx->F.standard)
+    return fail(ctx, NUMA_ERR_ARG, "the stand-alone solve is the Schur system (column_form 0)");
   long p = prof_begin(ctx, NUMA_K_SOLVE);
   NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->R, ctx->T, ctx->col_tile, ctx->stream));
   prof_end(ctx, p);
@@ -671,7 +678,8 @@ int numa_column_factors(numa_ctx* ctx, long long col, double* host_out) {
   if (!ctx) return NUMA_ERR_ARG;
   if (!host_out || col < 0 || col >= ctx->G.ncol) return fail(ctx, NUMA_ERR_ARG, "bad column");
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
-  const int M = ctx->G.M, hb = ctx->F.hb, W = 2 * hb + 1;
+  const int M = ctx->F.standard ? 3 * ctx->G.M : ctx->G.M;   // unknowns per column
+  const int hb = ctx->F.hb, W = 2 * hb + 1;
   std::vector<double> L((size_t)M * hb), U((size_t)M * (hb + 1));
   if (ctx->F.mixed) {
     const size_t pitch = (size_t)ctx->G.ncol * sizeof(float);
@@ -744,12 +752,13 @@ int numa_query(const numa_ctx* ctx, int what, long long* out) {
     case NUMA_Q_M: *out = G.M; break;
     case NUMA_Q_NNODE: *out = G.nnode; break;
     case NUMA_Q_NELEM: *out = (long long)G.nex * G.ney * G.nez; break;
-    case NUMA_Q_HALF_BAND: *out = 2 * G.N; break;
+    case NUMA_Q_HALF_BAND: *out = ctx->F.hb; break;
     case NUMA_Q_FACTOR_BYTES: *out = (long long)ctx->factor_bytes; break;
     case NUMA_Q_WORKSPACE_BYTES: *out = (long long)ctx->work_bytes; break;
     case NUMA_Q_FACTORED: *out = ctx->factored ? 1 : 0; break;
     case NUMA_Q_N: *out = G.N; break;
     case NUMA_Q_PRECISION: *out = ctx->precision; break;
+    case NUMA_Q_COLUMN_FORM: *out = ctx->F.standard ? NUMA_COLUMN_STANDARD : NUMA_COLUMN_SCHUR; break;
     default: return NUMA_ERR_ARG;
   }
   return NUMA_OK;

@@ -73,6 +73,8 @@ struct RefLev {
 // hb = 2N.  Entries outside the matrix are stored as zero.
 // The mixed-precision form stores the same layout in float (L32, U32) and refines each
 // solve refine_iters times with the FP64 operator.
+// The standard column form (standard = 1) stores the 3M x 3M level-interleaved system
+// I - lam L_V in the same layout with n = 3M unknowns per column and hb = 3N + 1.
 struct Factors {
   double* L;
   double* U;
@@ -81,6 +83,7 @@ struct Factors {
   int hb;
   int mixed;
   int refine_iters;
+  int standard;
 };
 
 // Coefficients of one IMEX stage (Table 1 with b = b~).
