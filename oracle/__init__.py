@@ -24,6 +24,8 @@ algorithm or table:
                     utteqn, helm2nc; Algorithms 4-5).
 * ``ark2``       -- the ARK2 double Butcher tableau (Table 1) and the SDIRK
                     predictor-corrector stage form (Sec. "Linear multi-stage methods").
+* ``ark3``       -- a third-order ARK tableau (ARK3(2)4L[2]SA) for the paper's ARK3 runs,
+                    whose tableau the paper does not print (reading stated there).
 * ``rk35``       -- the explicit five-stage third-order SSP comparator
                     (Sec. "Performance of IMEX on manycore processors").
 * ``tangent``    -- tangent-linear and adjoint models of R, of the column solve

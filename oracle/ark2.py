@@ -54,13 +54,14 @@ def printed_b():
     return np.array([-1.0 / (2.0 * SQ2), -1.0 / (2.0 * SQ2), 1.0 - 1.0 / (2.0 * SQ2)])
 
 
-def ark_step(q, dt, R, solve):
-    """One ARK2 step for dq/dt = R(q) = N(q) + L(q).
+def ark_step(q, dt, R, solve, tab=None):
+    """One ARK step for dq/dt = R(q) = N(q) + L(q) (ARK2 unless tab = (a, at, b, c) of
+    another scheme with a~_11 = 0, one implicit diagonal and b = b~, such as ARK3).
 
     R(q) is the full right-hand side; solve(rhs, lam) returns x with x = rhs + lam L(x).
     """
-    a, at, b, _ = tableau()
-    s = 3
+    a, at, b, _ = tableau() if tab is None else tab
+    s = len(b)
     Q = [q]
     Rs = [R(q)]
     for i in range(1, s):
@@ -76,15 +77,23 @@ def ark_step(q, dt, R, solve):
 
 
 class HEVI:
-    """The 1D-IMEX (HEVI) ARK2 integrator on a box mesh (oracle).  form: "schur" (the
-    paper's method) or "standard" (the non-Schur column system, same step otherwise)."""
+    """The 1D-IMEX (HEVI) integrator on a box mesh (oracle).  form: "schur" (the paper's
+    method) or "standard" (the non-Schur column system, same step otherwise); scheme:
+    "ark2" (Table 1) or "ark3" (``oracle.ark3``)."""
 
-    def __init__(self, mesh, col, dt, form="schur"):
+    def __init__(self, mesh, col, dt, form="schur", scheme="ark2"):
         if form not in ("schur", "standard"):
             raise ValueError("form must be 'schur' or 'standard'")
-        self.mesh, self.col, self.dt, self.form = mesh, col, dt, form
-        _, at, _, _ = tableau()
-        self.lam = at[1, 1] * dt                     # SDIRK: one lam for every stage
+        if scheme not in ("ark2", "ark3"):
+            raise ValueError("scheme must be 'ark2' or 'ark3'")
+        self.mesh, self.col, self.dt, self.form, self.scheme = mesh, col, dt, form, scheme
+        if scheme == "ark2":
+            self.tab = tableau()
+        else:
+            from . import ark3
+            self.tab = ark3.tableau()
+        at = self.tab[1]
+        self.lam = at[1, 1] * dt                     # one implicit diagonal for every stage
         if form == "schur":
             self.LU = lu_nopivot_banded(col.jacobian_by_probing(self.lam), col.half_band)
         else:
@@ -106,5 +115,5 @@ class HEVI:
 
     def step(self, q, nsteps=1):
         for _ in range(nsteps):
-            q = ark_step(q, self.dt, self.R, self.solve)
+            q = ark_step(q, self.dt, self.R, self.solve, self.tab)
         return q

@@ -175,3 +175,88 @@ def test_standard_form_step_equals_schur_step(C):
     b = ark2.HEVI(m, col, C * dt1, form="standard").step(q0, 3)
     for f in range(5):
         assert np.abs(a[f] - b[f]).max() <= 1e-10 * max(np.abs(a[f]).max(), 1e-300)
+
+
+# ---- ARK3 (ARK3(2)4L[2]SA; the paper prints no ARK3 tableau) ------------------------------
+def test_ark3_order_conditions_exact():
+    """Third order for the explicit and implicit tableaux and their coupling, c = c~,
+    stiffly accurate (b = last implicit row), one implicit diagonal: checked in exact
+    rational arithmetic (the published rationals approximate irrational coefficients to
+    about 1e-26)."""
+    from fractions import Fraction as F
+    from oracle import ark3
+    a, at, b, c = ark3.rational_tableau()
+    s = 4
+    tol = F(1, 10 ** 20)
+    ct = [sum(F(x) for x in row) for row in at]
+    assert all(abs(c[i] - ct[i]) < tol for i in range(s))
+    assert tuple(b) == tuple(at[3])
+    assert at[0][0] == 0 and all(at[i][i] == ark3.GAMMA for i in range(1, s))
+    conds = [
+        (sum(b), 1),
+        (sum(b[i] * c[i] for i in range(s)), F(1, 2)),
+        (sum(b[i] * c[i] ** 2 for i in range(s)), F(1, 3)),
+    ]
+    for A1 in (a, at):
+        for A2 in (a, at):
+            conds.append((sum(b[i] * A1[i][j] * c[j] for i in range(s) for j in range(s)), F(1, 6)))
+            conds.append((sum(b[i] * A1[i][j] * sum(F(x) for x in A2[j]) for i in range(s)
+                              for j in range(s)), F(1, 6)))
+    for got, want in conds:
+        assert abs(F(got) - want) < tol
+
+
+def _ark_direct_tab(y, dt, Nmat, Lmat, tab):
+    a, at, b, _ = tab
+    n, s = len(y), len(b)
+    Y = []
+    for i in range(s):
+        rhs = y + dt * sum(a[i, j] * Nmat @ Y[j] + at[i, j] * Lmat @ Y[j] for j in range(i))
+        Y.append(np.linalg.solve(np.eye(n) - dt * at[i, i] * Lmat, rhs))
+    return y + dt * sum(b[i] * (Nmat + Lmat) @ Y[i] for i in range(s))
+
+
+def test_ark3_predictor_corrector_form_equals_double_tableau():
+    from oracle import ark3
+    Nmat, Lmat = _split_system(seed=4)
+    y = np.random.default_rng(5).standard_normal(6)
+    R = lambda q: (Nmat + Lmat) @ q
+    solve = lambda r, lam: np.linalg.solve(np.eye(6) - lam * Lmat, r)
+    tab = ark3.tableau()
+    for dt in (0.01, 0.3, 3.0):
+        np.testing.assert_allclose(ark2.ark_step(y, dt, R, solve, tab),
+                                   _ark_direct_tab(y, dt, Nmat, Lmat, tab), rtol=1e-12, atol=1e-12)
+
+
+def test_ark3_third_order():
+    from oracle import ark3
+    Nmat, Lmat = _split_system(seed=6)
+    y0 = np.random.default_rng(7).standard_normal(6)
+    R = lambda q: (Nmat + Lmat) @ q
+    solve = lambda r, lam: np.linalg.solve(np.eye(6) - lam * Lmat, r)
+    T = 1.0
+    exact = expm((Nmat + Lmat) * T) @ y0
+    tab = ark3.tableau()
+    errs = []
+    for n in (40, 80, 160):
+        y = y0.copy()
+        for _ in range(n):
+            y = ark2.ark_step(y, T / n, R, solve, tab)
+        errs.append(np.linalg.norm(y - exact))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 2.8), rates
+
+
+def test_hevi_ark3_matches_ark2_at_small_dt():
+    """Both schemes approach the same solution: at a small step their states agree far
+    better than either scheme's own step-halving difference at the larger step."""
+    m, col, dt1 = _box(nex=2, nez=3, L=2000e3)
+    xg, yg, zg = m.coords()
+    q0 = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Lx, m.Lz, col.rho0, col.theta0, 14)
+    T = 20 * dt1
+    q2 = ark2.HEVI(m, col, T / 20).step(q0, 20)
+    q3 = ark2.HEVI(m, col, T / 20, scheme="ark3").step(q0, 20)
+    q3f = ark2.HEVI(m, col, T / 40, scheme="ark3").step(q0, 40)
+    e3 = np.linalg.norm(q3[3] - q3f[3])
+    e2 = np.linalg.norm(q2[3] - q3f[3])
+    assert e3 < e2 / 5.0, (e3, e2)
