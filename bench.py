@@ -330,6 +330,17 @@ def run_gpu(args):
     gm.close()
     out["imex_c15_mixed"] = {"sim_s_per_wall_s": round(sps(dt15, ms_mx), 3), "ms_per_step": round(ms_mx, 4),
                              "form": "FP32 RHS over FP64 reference, FP32 LU + 1 FP64 refinement sweep"}
+    # ARK3 (ARK3(2)4L[2]SA: four stages, 4 RHS + 3 column stages per step), same workload
+    ark3 = {}
+    for C, dtc in ((15, dt15), (150, dt150)):
+        g3 = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dtc, scheme="ark3")
+        for _ in range(args.warmup):
+            g3.step_imex1d(q0, q1, 1)
+        ms3 = time_steps(lambda: g3.step_imex1d(q0, q1, 1), args.steps) / args.steps
+        g3.close()
+        ark3["C%d" % C] = {"sim_s_per_wall_s": round(sps(dtc, ms3), 3), "ms_per_step": round(ms3, 4),
+                           "speedup_vs_explicit_c1": round(sps(dtc, ms3) / sps(dt1, ms_rk), 3)}
+    out["imex_ark3"] = dict(ark3, scheme="ARK3(2)4L[2]SA, FP64, Schur form")
     if not args.no_forms:
         out["precision_form"] = precision_form(pkg, torch, min(args.steps, 20), args.warmup)
         out["batching_form"] = batching_form(pkg, torch, min(args.steps, 10), args.warmup)

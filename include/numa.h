@@ -79,7 +79,8 @@ enum {
   NUMA_Q_FACTORED = 7,      /* 1 once numa_factor_columns succeeded */
   NUMA_Q_N = 8,             /* polynomial order */
   NUMA_Q_PRECISION = 9,     /* NUMA_PREC_FP64 or NUMA_PREC_MIXED */
-  NUMA_Q_COLUMN_FORM = 10   /* NUMA_COLUMN_SCHUR or NUMA_COLUMN_STANDARD */
+  NUMA_Q_COLUMN_FORM = 10,  /* NUMA_COLUMN_SCHUR or NUMA_COLUMN_STANDARD */
+  NUMA_Q_SCHEME = 11        /* NUMA_SCHEME_ARK2 or NUMA_SCHEME_ARK3 */
 };
 
 /* Options of numa_init_ex.
@@ -98,13 +99,21 @@ enum {
  *              3M x 3M matrix I - lam L_V on (rho', w, theta') itself, unknowns ordered level
  *              by level (half-bandwidth 3N + 1), factored by the same banded LU without
  *              pivoting; M*3*(6N+3) doubles per column instead of M*(4N+1).  FP64 only;
- *              numa_solve_columns and the differentiation form need the Schur form. */
+ *              numa_solve_columns and the differentiation form need the Schur form.
+ * scheme: NUMA_SCHEME_ARK2 (default) -- the second-order ARK of Table 1 (b = b~);
+ *         NUMA_SCHEME_ARK3 -- a third-order ARK for the paper's higher-order runs, whose
+ *         tableau the paper does not print: ARK3(2)4L[2]SA of Kennedy and Carpenter (2003),
+ *         four stages, one implicit diagonal gamma = 0.4358665215084590 (the factors are
+ *         formed at lam = gamma dt), b = b~ (numa_ark3_tableau).  FP64 Schur form only;
+ *         the differentiation form and ensembles use ARK2. */
 enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1 };
 enum { NUMA_COLUMN_SCHUR = 0, NUMA_COLUMN_STANDARD = 1 };
+enum { NUMA_SCHEME_ARK2 = 0, NUMA_SCHEME_ARK3 = 1 };
 typedef struct numa_options {
   int precision;
   int refine_iters;
   int column_form;
+  int scheme;
 } numa_options;
 
 /* Create a context: validates the mesh, builds the LGL nodes/weights/derivative matrix
@@ -345,6 +354,9 @@ int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const double* q,
  * NULL. */
 void numa_rk35_coefficients(double* alpha, double* beta);
 void numa_ark2_tableau(double* a, double* at, double* b);
+/* The ARK3 tableau (a[16], at[16], b[4], row-major 4x4) of NUMA_SCHEME_ARK3.  Host only; any
+ * pointer may be NULL. */
+void numa_ark3_tableau(double* a, double* at, double* b);
 
 #ifdef __cplusplus
 }

@@ -19,9 +19,10 @@ ERRORS = {
     5: "NUMA_ERR_PIVOT", 6: "NUMA_ERR_NONFINITE", 7: "NUMA_ERR_TIMEOUT", 8: "NUMA_ERR_SCRATCH",
 }
 Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_FACTORED, Q_N, \
-    Q_PRECISION, Q_COLUMN_FORM = range(11)
+    Q_PRECISION, Q_COLUMN_FORM, Q_SCHEME = range(12)
 PRECISIONS = {"fp64": 0, "mixed": 1}
 COLUMN_FORMS = {"schur": 0, "standard": 1}
+SCHEMES = {"ark2": 0, "ark3": 1}
 
 # Every symbol include/numa.h declares (checked by tests/test_abi.py).
 EXPORTS = (
@@ -35,14 +36,14 @@ EXPORTS = (
     "numa_batch_member_query", "numa_batch_reference_levels", "numa_batch_last_error",
     "numa_rhs_tlm", "numa_rhs_adjoint", "numa_solve_columns_transposed", "numa_imex_stage_adjoint",
     "numa_step_imex1d_tlm", "numa_step_imex1d_adjoint", "numa_imex1d_forward_checkpointed",
-    "numa_imex1d_adjoint_checkpointed",
+    "numa_imex1d_adjoint_checkpointed", "numa_ark3_tableau",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ = range(8)
 
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
-                ("column_form", ctypes.c_int)]
+                ("column_form", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -86,6 +87,7 @@ def lib():
             "numa_last_error": (ctypes.c_char_p, [P]),
             "numa_rk35_coefficients": (None, [P, P]),
             "numa_ark2_tableau": (None, [P, P, P]),
+            "numa_ark3_tableau": (None, [P, P, P]),
             "numa_rhs_explicit_static": (I, [ctypes.POINTER(MeshDesc), I, P, P, P]),
             "numa_batch_init": (I, [ctypes.POINTER(MeshDesc), P, P, I, P, ctypes.POINTER(P)]),
             "numa_batch_destroy": (None, [P]),
@@ -125,7 +127,8 @@ class Numa:
     """One mesh, one reference state, one IMEX time step size (a numa_ctx)."""
 
     def __init__(self, nex, ney, nez, Lx, Ly, Lz, N, dt=0.0, theta_s=300.0, n_bv=0.0,
-                 stream=None, precision="fp64", refine_iters=1, column_form="schur"):
+                 stream=None, precision="fp64", refine_iters=1, column_form="schur",
+                 scheme="ark2"):
         import torch
         self._torch = torch
         L = lib()
@@ -133,7 +136,8 @@ class Numa:
         s = torch.cuda.current_stream() if stream is None else stream
         self._stream = s
         h = ctypes.c_void_p()
-        self._opt = Options(PRECISIONS[precision], int(refine_iters), COLUMN_FORMS[column_form])
+        self._opt = Options(PRECISIONS[precision], int(refine_iters), COLUMN_FORMS[column_form],
+                            SCHEMES[scheme])
         rc = L.numa_init_ex(ctypes.byref(self._desc), N, float(dt), ctypes.byref(self._opt),
                             ctypes.c_void_p(s.cuda_stream), ctypes.byref(h))
         if rc != NUMA_OK:
@@ -143,6 +147,7 @@ class Numa:
         self.dt = float(dt)
         self.precision = precision
         self.column_form = column_form
+        self.scheme = scheme
         self.ncol = self.query(Q_NCOL)
         self.M = self.query(Q_M)
         self.nnode = self.query(Q_NNODE)
@@ -520,3 +525,10 @@ def ark2_tableau():
     lib().numa_ark2_tableau(a.ctypes.data_as(ctypes.c_void_p), at.ctypes.data_as(ctypes.c_void_p),
                             b.ctypes.data_as(ctypes.c_void_p))
     return a.reshape(3, 3), at.reshape(3, 3), b
+
+
+def ark3_tableau():
+    a, at, b = np.empty(16), np.empty(16), np.empty(4)
+    lib().numa_ark3_tableau(a.ctypes.data_as(ctypes.c_void_p), at.ctypes.data_as(ctypes.c_void_p),
+                            b.ctypes.data_as(ctypes.c_void_p))
+    return a.reshape(4, 4), at.reshape(4, 4), b

@@ -118,7 +118,7 @@ __global__ void k_batch_stage(const MemberDev* __restrict__ md, WorkList W, cons
     const int k = find_slot(W, item);
     const MemberDev& d = md[W.order[k]];
     const long long col0 = (item - W.start[k]) * blockDim.x;
-    stage_body<N, S3, false, double>(col0, blockDim.x, sm, qin + d.soff, d.R1, d.R2, d.q2, S3 ? d.q3 : d.q2,
+    stage_body<N, S3 ? 2 : 1, false, double>(col0, blockDim.x, sm, qin + d.soff, d.R1, d.R2, d.q2, S3 ? d.q3 : d.q2,
                                      d.G, d.R, d.F, S3 ? d.s3 : d.s2, d.tb, 0);
     __syncthreads();
   }

@@ -172,14 +172,16 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
   }
 }
 
-template <int N, bool S3, bool MIXED, typename RT>
+// NP previous stages (see stage_body); R3 and q3 are read only when NP = 3.
+template <int N, int NP, bool MIXED, typename RT>
 __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
                         const RT* __restrict__ R2, const double* __restrict__ q2,
                         double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
-                        StageTab tb, int iters, int T) {
+                        StageTab tb, int iters, int T, const RT* __restrict__ R3,
+                        const double* __restrict__ q3) {
   extern __shared__ double sm[];
-  stage_body<N, S3, MIXED, RT>(blockIdx.x * (long long)T, T, sm, qn, R1, R2, q2, out, G, R, F, sc,
-                               tb, iters);
+  stage_body<N, NP, MIXED, RT>(blockIdx.x * (long long)T, T, sm, qn, R1, R2, q2, out, G, R, F, sc,
+                               tb, iters, R3, q3);
 }
 
 // Fused stage with the standard column system (rows 2 or 3 of Table 1).  Phase 1: the
@@ -271,17 +273,17 @@ cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, const Fact
   return cudaGetLastError();
 }
 
-template <int N, bool S3, bool MIXED, typename RT>
+template <int N, int NP, bool MIXED, typename RT>
 cudaError_t launch_stage_k(const double* qn, const RT* R1, const RT* R2, const double* q2,
                            double* out, const Geom& G, const RefLev& R, const Factors& F,
                            const StageCoef& sc, const StageTab& tb, int T, int iters,
-                           cudaStream_t s) {
+                           cudaStream_t s, const RT* R3 = nullptr, const double* q3 = nullptr) {
   const size_t smem = stage_smem(G.M, T, MIXED, iters);
-  cudaError_t e = cudaFuncSetAttribute(k_stage<N, S3, MIXED, RT>,
+  cudaError_t e = cudaFuncSetAttribute(k_stage<N, NP, MIXED, RT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_stage<N, S3, MIXED, RT><<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T), smem, s>>>(
-      qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T);
+  k_stage<N, NP, MIXED, RT><<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T), smem, s>>>(
+      qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3);
   return cudaGetLastError();
 }
 
@@ -289,8 +291,13 @@ template <int N>
 cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const void* R2,
                            const double* q2, double* out, const Geom& G, const RefLev& R,
                            const Factors& F, const StageCoef& sc, const StageTab& tb, int T,
-                           bool r_float, cudaStream_t s) {
+                           bool r_float, cudaStream_t s, const double* R3, const double* q3) {
   const int it = F.refine_iters;
+  if (stage == 4) {     // four-stage schemes: FP64 Schur form only
+    if (F.standard || F.mixed || !R3 || !q3) return cudaErrorInvalidValue;
+    return launch_stage_k<N, 3, false>(qn, (const double*)R1, (const double*)R2, q2, out, G, R, F,
+                                       sc, tb, T, it, s, R3, q3);
+  }
   if (F.standard) {
     const size_t smem = (size_t)3 * G.M * T * sizeof(double);
     const unsigned nb = (unsigned)((G.ncol + T - 1) / T);
@@ -311,19 +318,19 @@ cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const vo
   if (F.mixed && !r_float) {
     const double* a = (const double*)R1;
     const double* b = (const double*)R2;
-    return stage == 3 ? launch_stage_k<N, true, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
-                      : launch_stage_k<N, false, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
+    return stage == 3 ? launch_stage_k<N, 2, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
+                      : launch_stage_k<N, 1, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
   }
   if (F.mixed) {
     const float* a = (const float*)R1;
     const float* b = (const float*)R2;
-    return stage == 3 ? launch_stage_k<N, true, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
-                      : launch_stage_k<N, false, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
+    return stage == 3 ? launch_stage_k<N, 2, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
+                      : launch_stage_k<N, 1, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
   }
   const double* a = (const double*)R1;
   const double* b = (const double*)R2;
-  return stage == 3 ? launch_stage_k<N, true, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
-                    : launch_stage_k<N, false, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
+  return stage == 3 ? launch_stage_k<N, 2, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
+                    : launch_stage_k<N, 1, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
 }
 
 }  // namespace
@@ -356,18 +363,15 @@ cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, c
 cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void* R2,
                          const double* q2, double* out, const Geom& G, const RefLev& R,
                          Factors F, const StageCoef& sc, const StageTab& tb, int T,
-                         bool r_float, cudaStream_t s) {
+                         bool r_float, cudaStream_t s, const double* R3, const double* q3) {
+#define NUMA_STAGE_CASE(n) \
+  case n: return launch_stage_n<n>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s, R3, q3);
   switch (G.N) {
-    case 1: return launch_stage_n<1>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
-    case 2: return launch_stage_n<2>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
-    case 3: return launch_stage_n<3>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
-    case 4: return launch_stage_n<4>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
-    case 5: return launch_stage_n<5>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
-    case 6: return launch_stage_n<6>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
-    case 7: return launch_stage_n<7>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
-    case 8: return launch_stage_n<8>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s);
+    NUMA_STAGE_CASE(1) NUMA_STAGE_CASE(2) NUMA_STAGE_CASE(3) NUMA_STAGE_CASE(4)
+    NUMA_STAGE_CASE(5) NUMA_STAGE_CASE(6) NUMA_STAGE_CASE(7) NUMA_STAGE_CASE(8)
     default: return cudaErrorInvalidValue;
   }
+#undef NUMA_STAGE_CASE
 }
 
 size_t stage_smem_bytes(int M, int T, bool mixed, int iters) {

@@ -182,13 +182,17 @@ __host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
 // col0: first column of this block, T columns (T <= blockDim.x: all threads share phases 1
 // and 3, the first T run phase 2); sm: dynamic shared memory of
 // col_smem_per_level(MIXED, iters) * M * T bytes.
-template <int N, bool S3, bool MIXED, typename RT>
+// NP: previous stages read (1: stage 2; 2: stage 3; 3: stage 4 of a four-stage scheme,
+// with R3 and q3).
+template <int N, int NP, bool MIXED, typename RT>
 __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
                                            const double* __restrict__ qn,
                                            const RT* __restrict__ R1, const RT* __restrict__ R2,
                                            const double* __restrict__ q2, double* __restrict__ out,
                                            const Geom& G, const RefLev& R, const Factors& F,
-                                           const StageCoef& sc, const StageTab& tb, int iters) {
+                                           const StageCoef& sc, const StageTab& tb, int iters,
+                                           const RT* __restrict__ R3 = nullptr,
+                                           const double* __restrict__ q3 = nullptr) {
   const int NT = blockDim.x, M = G.M;
   const long long nn = G.nnode;
   const int ncols = (int)min((long long)T, G.ncol - col0);
@@ -199,17 +203,19 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
   double* SXd = sm + 2 * M * T; // mixed form with >= 2 sweeps: FP64 iterate
   float* Tf = (float*)(sm + (iters >= 2 ? 3 : 2) * M * T);
   float* Td = Tf + M * T;
-  const double a1dt = sc.a[0] * sc.dt, a2dt = sc.a[1] * sc.dt;
-  const double c1 = sc.c[0], c2 = sc.c[1];
+  const double a1dt = sc.a[0] * sc.dt, a2dt = sc.a[1] * sc.dt, a3dt = sc.a[2] * sc.dt;
+  const double c1 = sc.c[0], c2 = sc.c[1], c3 = sc.c[2];
 
   // predictor of field f at global offset o (q(i)_e, shifted to q~_e unless u, v)
   auto pred = [&](int f, long long o) -> double {
     const double qv = qn[o];
     double v = fma(a1dt, (double)R1[o], qv);
-    if (S3) v = fma(a2dt, (double)R2[o], v);
+    if (NP >= 2) v = fma(a2dt, (double)R2[o], v);
+    if (NP >= 3) v = fma(a3dt, (double)R3[o], v);
     if (f == 1 || f == 2) return v;
     v = fma(c1, qv, v);
-    if (S3) v = fma(c2, q2[o], v);
+    if (NP >= 2) v = fma(c2, q2[o], v);
+    if (NP >= 3) v = fma(c3, q3[o], v);
     return v;
   };
 
@@ -253,10 +259,15 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     const double thv = fma(-__ldg(tb.kth + lev), wv, te);
     const double rv = fma(-__ldg(tb.H0G0 + lev), thv, __ldg(tb.invG0 + lev) * S0[lev * T + c]);
     double o_r = fma(-c1, qn[orr], rv), o_w = fma(-c1, qn[ow], wv), o_t = fma(-c1, qn[oth], thv);
-    if (S3) {
+    if (NP >= 2) {
       o_r = fma(-c2, q2[orr], o_r);
       o_w = fma(-c2, q2[ow], o_w);
       o_t = fma(-c2, q2[oth], o_t);
+    }
+    if (NP >= 3) {
+      o_r = fma(-c3, q3[orr], o_r);
+      o_w = fma(-c3, q3[ow], o_w);
+      o_t = fma(-c3, q3[oth], o_t);
     }
     out[orr] = o_r;
     out[ow] = o_w;

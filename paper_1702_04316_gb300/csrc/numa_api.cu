@@ -30,6 +30,61 @@ struct Ark2 {
   }
 };
 
+// ARK3: the ARK3(2)4L[2]SA scheme of Kennedy and Carpenter (2003), the third-order member
+// of the ARK family (the paper runs ARK3 but prints no tableau).  Explicit / ESDIRK pair,
+// four stages, implicit diagonal gamma, b = b~ = the last implicit row.  Published
+// rational coefficients, each evaluated as one correctly rounded division.
+struct Ark3 {
+  double a[4][4], at[4][4], b[4];
+  Ark3() {
+    std::memset(this, 0, sizeof(*this));
+    const double g = 1767732205903.0 / 4055673282236.0;
+    at[1][0] = at[1][1] = g;
+    at[2][0] = 2746238789719.0 / 10658868560708.0;
+    at[2][1] = -640167445237.0 / 6845629431997.0;
+    at[2][2] = g;
+    at[3][0] = 1471266399579.0 / 7840856788654.0;
+    at[3][1] = -4482444167858.0 / 7529755066697.0;
+    at[3][2] = 11266239266428.0 / 11593286722821.0;
+    at[3][3] = g;
+    a[1][0] = 1767732205903.0 / 2027836641118.0;
+    a[2][0] = 5535828885825.0 / 10492691773637.0;
+    a[2][1] = 788022342437.0 / 10882634858940.0;
+    a[3][0] = 6485989280629.0 / 16251701735622.0;
+    a[3][1] = -4246266847089.0 / 9704473918619.0;
+    a[3][2] = 10755448449292.0 / 10357097424841.0;
+    for (int i = 0; i < 4; ++i) b[i] = at[3][i];
+  }
+};
+
+// The scheme of a context as one s-stage table (s = 3 or 4).
+struct ArkTab {
+  int s = 3;
+  double a[4][4] = {}, at[4][4] = {}, b[4] = {};
+};
+
+ArkTab ark_tab(int scheme) {
+  ArkTab t;
+  if (scheme == NUMA_SCHEME_ARK3) {
+    static const Ark3 k;
+    t.s = 4;
+    std::memcpy(t.a, k.a, sizeof(t.a));
+    std::memcpy(t.at, k.at, sizeof(t.at));
+    std::memcpy(t.b, k.b, sizeof(t.b));
+  } else {
+    static const Ark2 k;
+    t.s = 3;
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) {
+        t.a[i][j] = k.a[i][j];
+        t.at[i][j] = k.at[i][j];
+      }
+      t.b[i] = k.b[i];
+    }
+  }
+  return t;
+}
+
 // ---- RK35: five-stage third-order SSP, two-register Shu-Osher form -------------------
 //   u_i = alpha_i u_0 + (1 - alpha_i) u_{i-1} + beta_i dt F(u_{i-1});  beta_1 = beta_5 =
 //   0.46, alpha_2 = alpha_3 = alpha_5 = 0, the rest the real root of the third-order
@@ -330,12 +385,12 @@ int enqueue_stage(numa_ctx* c, int stage, const double* qn, const void* R1, cons
 }  // namespace
 
 StageCoef numa_stage_coef(const numa_ctx* c, int stage) {
-  static const Ark2 t;
+  const ArkTab t = ark_tab(c->scheme);
   StageCoef sc{};
   const int i = stage - 1;
   sc.dt = c->dt;
   sc.lam = t.at[i][i] * c->dt;
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < 3; ++j) {
     sc.a[j] = (j < i) ? t.a[i][j] : 0.0;
     sc.c[j] = (j < i) ? (t.at[i][j] - t.a[i][j]) / t.at[i][i] : 0.0;
   }
@@ -359,9 +414,12 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   const int precision = opt ? opt->precision : NUMA_PREC_FP64;
   const int refine = opt ? opt->refine_iters : 1;
   const int form = opt ? opt->column_form : NUMA_COLUMN_SCHUR;
+  const int scheme = opt ? opt->scheme : NUMA_SCHEME_ARK2;
   if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED) || refine < 0 || refine > 8 ||
       (form != NUMA_COLUMN_SCHUR && form != NUMA_COLUMN_STANDARD) ||
-      (form == NUMA_COLUMN_STANDARD && precision != NUMA_PREC_FP64)) {
+      (form == NUMA_COLUMN_STANDARD && precision != NUMA_PREC_FP64) ||
+      (scheme != NUMA_SCHEME_ARK2 && scheme != NUMA_SCHEME_ARK3) ||
+      (scheme == NUMA_SCHEME_ARK3 && (precision != NUMA_PREC_FP64 || form != NUMA_COLUMN_SCHUR))) {
     *out = nullptr;
     return NUMA_ERR_ARG;
   }
@@ -388,6 +446,7 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   c->F.mixed = precision == NUMA_PREC_MIXED;
   c->F.refine_iters = refine;
   c->F.standard = form == NUMA_COLUMN_STANDARD;
+  c->scheme = scheme;
   c->theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
   {
     // columns per CTA of the column kernels: 64, or 32 when 64 would leave SMs without a
@@ -415,7 +474,8 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   c->factor_bytes = nu * (2 * hb + 1) * G.ncol * fsz;
   c->work_bytes = mixed ? (size_t)(2 * 5) * G.nnode * sizeof(double) +
                               (size_t)(6 + 2 * 5) * G.nnode * sizeof(float)
-                        : (size_t)(1 + 4 * 5) * G.nnode * sizeof(double);
+                        : (size_t)(1 + (scheme == NUMA_SCHEME_ARK3 ? 6 : 4) * 5) * G.nnode *
+                              sizeof(double);
   if (rc == NUMA_OK) {
     bool ok = cudaMalloc(&c->d_work, c->work_bytes) == cudaSuccess &&
               cudaMalloc(&c->d_status, sizeof(unsigned)) == cudaSuccess &&
@@ -459,6 +519,10 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
       c->R2 = c->R1 + n5;
       c->q2 = c->R2 + n5;
       c->q3 = c->q2 + n5;
+      if (scheme == NUMA_SCHEME_ARK3) {
+        c->R3 = c->q3 + n5;
+        c->q4 = c->R3 + n5;
+      }
     }
     if (cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = NUMA_ERR_CUDA;
   }
@@ -508,7 +572,7 @@ int numa_rhs_explicit(numa_ctx* ctx, const double* q, double* rhs) {
 int numa_factor_columns(numa_ctx* ctx, double dt) {
   if (!ctx) return NUMA_ERR_ARG;
   if (!(dt > 0) || !std::isfinite(dt)) return fail(ctx, NUMA_ERR_ARG, "dt must be > 0");
-  const double lam = (1.0 - 1.0 / std::sqrt(2.0)) * dt;
+  const double lam = ark_tab(ctx->scheme).at[1][1] * dt;   // the one implicit diagonal
   int rc = upload_stage_tables(ctx, lam);
   if (rc) return rc;
   long p = prof_begin(ctx, NUMA_K_FACTOR);
@@ -559,9 +623,38 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
                                    ctx->stream));
     return NUMA_OK;
   }
-  static const Ark2 t;
+  const ArkTab t = ark_tab(ctx->scheme);
   const StageCoef s2 = numa_stage_coef(ctx, 2), s3 = numa_stage_coef(ctx, 3);
   const bool mixed = ctx->precision == NUMA_PREC_MIXED;
+  if (t.s == 4) {       // ARK3: four stages, FP64 Schur form
+    const StageCoef s4 = numa_stage_coef(ctx, 4);
+    const double* cur = q_in;
+    for (int s = 0; s < nsteps; ++s) {
+      RhsEpilogue e0{};
+      if ((rc = enqueue_rhs(ctx, cur, ctx->R1, e0))) return rc;
+      if ((rc = enqueue_stage(ctx, 2, cur, ctx->R1, nullptr, nullptr, ctx->q2, s2))) return rc;
+      if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0))) return rc;
+      if ((rc = enqueue_stage(ctx, 3, cur, ctx->R1, ctx->R2, ctx->q2, ctx->q3, s3))) return rc;
+      if ((rc = enqueue_rhs(ctx, ctx->q3, ctx->R3, e0))) return rc;
+      long p = prof_begin(ctx, NUMA_K_STAGE);
+      NUMA_CK(ctx, launch_stage(4, cur, ctx->R1, ctx->R2, ctx->q2, ctx->q4, ctx->G, ctx->R, ctx->F,
+                                s4, ctx->T, ctx->col_tile, false, ctx->stream, ctx->R3, ctx->q3));
+      prof_end(ctx, p);
+      RhsEpilogue ef{};
+      ef.mode = 3;
+      ef.b1dt = t.b[0] * ctx->dt;
+      ef.b2dt = t.b[1] * ctx->dt;
+      ef.b3dt = t.b[2] * ctx->dt;
+      ef.b4dt = t.b[3] * ctx->dt;
+      ef.u0 = cur;
+      ef.R1 = ctx->R1;
+      ef.R2 = ctx->R2;
+      ef.R3 = ctx->R3;
+      if ((rc = enqueue_rhs(ctx, ctx->q4, q_out, ef))) return rc;
+      cur = q_out;
+    }
+    return NUMA_OK;
+  }
   void* R1 = mixed ? (void*)ctx->R1f : (void*)ctx->R1;
   void* R2 = mixed ? (void*)ctx->R2f : (void*)ctx->R2;
   const double* cur = q_in;
@@ -759,6 +852,7 @@ int numa_query(const numa_ctx* ctx, int what, long long* out) {
     case NUMA_Q_N: *out = G.N; break;
     case NUMA_Q_PRECISION: *out = ctx->precision; break;
     case NUMA_Q_COLUMN_FORM: *out = ctx->F.standard ? NUMA_COLUMN_STANDARD : NUMA_COLUMN_SCHUR; break;
+    case NUMA_Q_SCHEME: *out = ctx->scheme; break;
     default: return NUMA_ERR_ARG;
   }
   return NUMA_OK;
@@ -770,6 +864,17 @@ void numa_rk35_coefficients(double* alpha, double* beta) {
   for (int i = 0; i < 5; ++i) {
     if (alpha) alpha[i] = kRkAlpha[i];
     if (beta) beta[i] = kRkBeta[i];
+  }
+}
+
+void numa_ark3_tableau(double* a, double* at, double* b) {
+  static const Ark3 t;
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      if (a) a[i * 4 + j] = t.a[i][j];
+      if (at) at[i * 4 + j] = t.at[i][j];
+    }
+    if (b) b[i] = t.b[i];
   }
 }
 

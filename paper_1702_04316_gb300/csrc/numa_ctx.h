@@ -25,8 +25,10 @@ struct numa_ctx {
   StageTab T{};
   double* d_stage_tab = nullptr;
   Factors F{};
-  double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (each 5*nnode except Pp)
+  double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (+ R3, q4 for ARK3), each 5*nnode but Pp
   double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
+  double *R3 = nullptr, *q4 = nullptr;     // ARK3 only
+  int scheme = NUMA_SCHEME_ARK2;
   // mixed-precision form: FP32 stencil fields (6 x nnode) and FP32 R1, R2 (5 x nnode each)
   float *F32 = nullptr, *R1f = nullptr, *R2f = nullptr;
   int precision = NUMA_PREC_FP64;

@@ -86,12 +86,13 @@ struct Factors {
   int standard;
 };
 
-// Coefficients of one IMEX stage (Table 1 with b = b~).
+// Coefficients of one IMEX stage i (a row of Table 1 with b = b~, or of the ARK3 tableau):
+// the stage reads the i-1 previous stages.
 struct StageCoef {
   double dt;
   double lam;       // a~_ii dt
-  double a[2];      // a_i1, a_i2 (explicit)
-  double c[2];      // c_ij = (a~_ij - a_ij) / a~_ii
+  double a[3];      // a_i1 .. a_i3 (explicit; zero beyond i-1)
+  double c[3];      // c_ij = (a~_ij - a_ij) / a~_ii
 };
 
 // Per-level coefficient tables of one lam for the fused stage (length M each):
@@ -109,15 +110,17 @@ struct StageTab {
 cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const RefLev& R,
                             cudaStream_t s);
 // MODE 0: out = R(q);  MODE 1 (RK stage): out = alpha*u0 + (1-alpha)*q + beta*dt*R(q);
-// MODE 2 (ARK final): out = qn + dt*(b1*R1 + b2*R2 + b3*R(q)).
+// MODE 2 (ARK2 final): out = qn + dt*(b1*R1 + b2*R2 + b3*R(q));
+// MODE 3 (four-stage ARK final, FP64 only): out = qn + dt*(b1*R1 + b2*R2 + b3*R3 + b4*R(q)).
 struct RhsEpilogue {
   int mode;
   int use_u0;                     // mode 1: alpha != 0
   double alpha, one_minus_alpha, beta_dt;   // mode 1
-  double b1dt, b2dt, b3dt;        // mode 2
-  const double* u0;               // mode 1: u0; mode 2: qn
-  const void* R1;                 // mode 2: double (FP64 method) or float (mixed form)
+  double b1dt, b2dt, b3dt, b4dt;  // modes 2, 3
+  const double* u0;               // mode 1: u0; modes 2, 3: qn
+  const void* R1;                 // modes 2, 3: double (FP64 method) or float (mixed form)
   const void* R2;
+  const void* R3;                 // mode 3 (double)
 };
 // perm: class-sorted thread order from build_rhs_perm (nthreads entries), or NULL for the
 // natural node order (nthreads = nnode; correct, but warps then mix node classes).
@@ -145,10 +148,13 @@ cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
 // r_float (the mixed form's internal tendencies), else double arrays.
 cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, const RefLev& R,
                          const StageTab& tb, int T, cudaStream_t s);
+// stage i in {2, 3, 4} reads R1..R(i-1) and q2..q(i-1); stage 4 (four-stage schemes) is
+// FP64 Schur form only and takes R3, q3.
 cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void* R2,
                          const double* q2, double* out, const Geom& G, const RefLev& R,
                          Factors F, const StageCoef& sc, const StageTab& tb, int T,
-                         bool r_float, cudaStream_t s);
+                         bool r_float, cudaStream_t s, const double* R3 = nullptr,
+                         const double* q3 = nullptr);
 size_t stage_smem_bytes(int M, int T, bool mixed, int iters);
 
 // misc.cu

@@ -194,13 +194,23 @@ __device__ __forceinline__ void rhs_node(long long tid, const double* __restrict
       if (ep.use_u0) val = fma(ep.alpha, ep.u0[f * nn + g], val);
       out[f * nn + g] = val;
     }
-  } else {
+  } else if (ep.mode == 2) {
     const OT* R1 = (const OT*)ep.R1;
     const OT* R2 = (const OT*)ep.R2;
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       const long long o = f * nn + g;
       out[o] = fma(ep.b3dt, (double)t[f], fma(ep.b2dt, (double)R2[o], fma(ep.b1dt, (double)R1[o], ep.u0[o])));
+    }
+  } else {
+    const double* R1 = (const double*)ep.R1;
+    const double* R2 = (const double*)ep.R2;
+    const double* R3 = (const double*)ep.R3;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const long long o = f * nn + g;
+      out[o] = fma(ep.b4dt, (double)t[f],
+                   fma(ep.b3dt, R3[o], fma(ep.b2dt, R2[o], fma(ep.b1dt, R1[o], ep.u0[o]))));
     }
   }
 }

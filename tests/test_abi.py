@@ -61,3 +61,14 @@ def test_host_tableaux_match_the_oracle(pkg):
     al, be = pkg.rk35_coefficients()
     np.testing.assert_array_equal(al, rk35.ALPHA)
     np.testing.assert_array_equal(be, rk35.BETA)
+
+
+def test_ark3_tableau_matches_the_oracle_bitwise():
+    """The host ARK3 tableau (each coefficient one correctly rounded division of the
+    published rationals) equals the oracle's float tableau bit for bit."""
+    import numpy as np
+    import paper_1702_04316_gb300 as pkg
+    from oracle import ark3
+    a, at, b = pkg.ark3_tableau()
+    A, AT, B, _ = ark3.tableau()
+    assert np.array_equal(a, A) and np.array_equal(at, AT) and np.array_equal(b, B)
