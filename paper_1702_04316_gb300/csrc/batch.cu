@@ -111,15 +111,18 @@ __global__ void k_batch_rhs(const MemberDev* __restrict__ md, WorkList W, int sr
   }
 }
 
+// T columns per work item; blockDim.x >= T threads share the stage's coalesced phases.
 template <int N, bool S3>
-__global__ void k_batch_stage(const MemberDev* __restrict__ md, WorkList W, const double* qin) {
+__global__ void k_batch_stage(const MemberDev* __restrict__ md, WorkList W, const double* qin,
+                              int T) {
   extern __shared__ double sm[];
   for (long long item = blockIdx.x; item < W.nitems; item += gridDim.x) {
     const int k = find_slot(W, item);
     const MemberDev& d = md[W.order[k]];
-    const long long col0 = (item - W.start[k]) * blockDim.x;
-    stage_body<N, S3 ? 2 : 1, false, double>(col0, blockDim.x, sm, qin + d.soff, d.R1, d.R2, d.q2, S3 ? d.q3 : d.q2,
-                                     d.G, d.R, d.F, S3 ? d.s3 : d.s2, d.tb, 0);
+    const long long col0 = (item - W.start[k]) * T;
+    stage_body<N, S3 ? 2 : 1, false, double>(col0, T, sm, qin + d.soff, d.R1, d.R2, d.q2,
+                                              S3 ? d.q3 : d.q2, d.G, d.R, d.F, S3 ? d.s3 : d.s2,
+                                              d.tb, 0);
     __syncthreads();
   }
 }
@@ -143,6 +146,8 @@ struct OrderGroup {
   int rhs_threads = 256, col_tile = 64;
   int grid_rhs = 0, grid_col = 0;
   size_t stage_smem = 0;
+  // threads per CTA of the stage: the column tile, at least 128 (the coalesced phases)
+  int stage_threads() const { return std::max(col_tile, 128); }
 };
 
 struct numa_batch {
@@ -210,7 +215,7 @@ int group_shapes(numa_batch* b, OrderGroup& g, int nsm) {
   NUMA_BCK(b, cudaFuncSetAttribute(k_batch_stage<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.stage_smem));
   NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_rhs<N>, g.rhs_threads, 0));
   g.grid_rhs = nsm * std::max(per, 1);
-  NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_stage<N, true>, g.col_tile, g.stage_smem));
+  NUMA_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_stage<N, true>, g.stage_threads(), g.stage_smem));
   if (per < 1) return bfail(b, NUMA_ERR_ARG, "stage tile does not fit in shared memory");
   g.grid_col = nsm * per;
   return NUMA_OK;
@@ -275,8 +280,8 @@ void launch_group_rhs(numa_batch* b, const OrderGroup& g, int src, int mode, con
 template <int N>
 void launch_group_stage(numa_batch* b, const OrderGroup& g, bool s3, const double* qin,
                         cudaStream_t s) {
-  if (s3) k_batch_stage<N, true><<<g.grid_col, g.col_tile, g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin);
-  else k_batch_stage<N, false><<<g.grid_col, g.col_tile, g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin);
+  if (s3) k_batch_stage<N, true><<<g.grid_col, g.stage_threads(), g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin, g.col_tile);
+  else k_batch_stage<N, false><<<g.grid_col, g.stage_threads(), g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin, g.col_tile);
 }
 
 void enqueue_rhs_all(numa_batch* b, int src, int mode, const double* qin, double* qout, cudaStream_t s) {
