@@ -28,6 +28,10 @@ algorithm or table:
                     whose tableau the paper does not print (reading stated there).
 * ``rk35``       -- the explicit five-stage third-order SSP comparator
                     (Sec. "Performance of IMEX on manycore processors").
+* ``schur3d``    -- 3D-IMEX in the Schur form: the 3D Schur operator and right-hand side,
+                    the extraction (Eqs. utteqn, helm2nc with the full gradient), BiCGstab
+                    with a polynomial preconditioner (Algorithm "BiCGstabPBNO"; Chebyshev
+                    coefficients as the reading of PBNO) and the 3D-IMEX ARK2 integrator.
 * ``tangent``    -- tangent-linear and adjoint models of R, of the column solve
                     (transposed stored LU of Algorithm 9) and of the ARK2 step, and the
                     gradient of a quadratic misfit of the final theta' (differentiation
