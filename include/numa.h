@@ -80,7 +80,8 @@ enum {
   NUMA_Q_N = 8,             /* polynomial order */
   NUMA_Q_PRECISION = 9,     /* NUMA_PREC_FP64 or NUMA_PREC_MIXED */
   NUMA_Q_COLUMN_FORM = 10,  /* NUMA_COLUMN_SCHUR or NUMA_COLUMN_STANDARD */
-  NUMA_Q_SCHEME = 11        /* NUMA_SCHEME_ARK2 or NUMA_SCHEME_ARK3 */
+  NUMA_Q_SCHEME = 11,       /* NUMA_SCHEME_ARK2 or NUMA_SCHEME_ARK3 */
+  NUMA_Q_IMEX = 12          /* NUMA_IMEX_1D or NUMA_IMEX_3D */
 };
 
 /* Options of numa_init_ex.
@@ -105,15 +106,41 @@ enum {
  *         tableau the paper does not print: ARK3(2)4L[2]SA of Kennedy and Carpenter (2003),
  *         four stages, one implicit diagonal gamma = 0.4358665215084590 (the factors are
  *         formed at lam = gamma dt), b = b~ (numa_ark3_tableau).  FP64 Schur form only;
- *         the differentiation form and ensembles use ARK2. */
+ *         the differentiation form and ensembles use ARK2.
+ * imex: NUMA_IMEX_1D (default) -- the paper's 1D-IMEX (HEVI) method with stored column
+ *       factors; NUMA_IMEX_3D -- 3D-IMEX in the Schur form (Eqs. utteqn, helm2nc with the
+ *       full gradient): the whole linear operator implicit, one pressure unknown per node,
+ *       BiCGstab left-preconditioned by a polynomial of degree pbno_order (Algorithm
+ *       "BiCGstabPBNO"), no stored factors; stepped by numa_step_imex3d.  The paper's PBNO
+ *       coefficients come from a least-squares fit it does not reproduce; these are the
+ *       Chebyshev minimax polynomial on [1, l_max], l_max estimated by power iteration when
+ *       the time step is set.  FP64 Schur form only.
+ * pbno_order: polynomial degree P of the 3D preconditioner (0..NUMA_MAX_PBNO_ORDER; 0 in
+ *             the struct means the default 2).
+ * krylov_max_iters, krylov_tol: BiCGstab stops when the preconditioned residual's 2-norm
+ *             has dropped by krylov_tol (default 1e-12; 0 means the default), or fails with
+ *             NUMA_ERR_TIMEOUT after krylov_max_iters (default 500; 0 means the default).
+ * precond: left preconditioner of the 3D solve: NUMA_PRECOND_PBNO (default; the paper's
+ *          polynomial, Chebyshev reading) or NUMA_PRECOND_COLUMN -- the 1D-IMEX column Schur
+ *          matrix of the same lam, factored and stored per column as for 1D-IMEX, solved
+ *          exactly as a vertical-line preconditioner (a choice beyond the paper: the stiffest
+ *          part of S is vertical when C_V > C_H; the converged solution is the same). */
 enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1 };
 enum { NUMA_COLUMN_SCHUR = 0, NUMA_COLUMN_STANDARD = 1 };
 enum { NUMA_SCHEME_ARK2 = 0, NUMA_SCHEME_ARK3 = 1 };
+enum { NUMA_IMEX_1D = 0, NUMA_IMEX_3D = 1 };
+enum { NUMA_PRECOND_PBNO = 0, NUMA_PRECOND_COLUMN = 1 };
+#define NUMA_MAX_PBNO_ORDER 8
 typedef struct numa_options {
   int precision;
   int refine_iters;
   int column_form;
   int scheme;
+  int imex;
+  int pbno_order;
+  int krylov_max_iters;
+  double krylov_tol;
+  int precond;
 } numa_options;
 
 /* Create a context: validates the mesh, builds the LGL nodes/weights/derivative matrix
@@ -195,7 +222,8 @@ enum {
   NUMA_K_RHS_TLM = 5,   /* tangent-linear right-hand side (with its dP' pre-pass) */
   NUMA_K_RHS_ADJ = 6,   /* adjoint right-hand side (weights pass + transposed gather) */
   NUMA_K_STAGE_ADJ = 7, /* adjoint of the fused implicit stage (transposed column solve) */
-  NUMA_K_NKINDS = 8
+  NUMA_K_SCHUR3D = 8,   /* one application of the 3D Schur operator (gradient + divergence) */
+  NUMA_K_NKINDS = 9
 };
 int numa_profile(numa_ctx* ctx, int enable);
 int numa_profile_read(numa_ctx* ctx, int kind, double* total_ms, long long* launches);
@@ -287,6 +315,37 @@ int numa_imex1d_forward_checkpointed(numa_ctx* ctx, const double* q0, double* qT
  * are then run backwards with numa_step_imex1d_adjoint.  lam0 == lamT allowed. */
 int numa_imex1d_adjoint_checkpointed(numa_ctx* ctx, const double* ckpt, int nsteps, int every,
                                      const double* lamT, double* lam0, double* work);
+
+/* ---- 3D-IMEX (Schur form, BiCGstab + polynomial preconditioner) -------------------------
+ * Calls for a context made with options.imex = NUMA_IMEX_3D (NUMA_ERR_ARG otherwise; the 1D
+ * entry points numa_step_imex1d, numa_imex_stage, numa_solve_columns and the
+ * differentiation form reject a 3D context).  numa_factor_columns(ctx, dt) sets the step,
+ * forms the per-level tables and the preconditioner (power iteration on S, about 60
+ * operator applications).  The workspace (20 x nnode doubles) is allocated on first use. */
+
+/* SP = S(P) = P - lam F0 . u_p(P) - lam rho0 G0 div u_p(P), the 3D Schur operator (Eq.
+ * helm2nc, left side).  P, SP: device arrays of nnode doubles, not overlapping. */
+int numa_schur3d_apply(numa_ctx* ctx, const double* P, double* SP);
+
+/* Solve S(x) = b by preconditioned BiCGstab from x = 0; *iters (may be NULL) receives the
+ * iteration count.  b, x: nnode doubles, not overlapping.  NUMA_ERR_TIMEOUT when the
+ * tolerance is not reached within krylov_max_iters. */
+int numa_solve_schur3d(numa_ctx* ctx, const double* b, double* x, int* iters);
+
+/* One 3D-IMEX stage i in {2, 3} (as numa_imex_stage, with the 3D implicit solve); *iters
+ * (may be NULL) receives the BiCGstab iterations. */
+int numa_imex3d_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1,
+                      const double* R2, const double* q2, double* q_out, int* iters);
+
+/* nsteps 3D-IMEX steps (the context's scheme, ARK2 or ARK3) from q_in to q_out (in place
+ * allowed). */
+int numa_step_imex3d(numa_ctx* ctx, const double* q_in, double* q_out, int nsteps);
+
+/* The preconditioner of a 3D context: l_max (spectrum bound used), lam_bar = 2/(1 + l_max),
+ * coeffs[0..pbno_order] (c_i of the PBNO recursion), and the total BiCGstab iterations of
+ * the last numa_step_imex3d call.  Any output pointer may be NULL. */
+int numa_imex3d_info(const numa_ctx* ctx, double* l_max, double* lam_bar, double* coeffs,
+                     long long* iters_last_step);
 
 /* ---- ensembles ("batching form") -------------------------------------------------------
  * An ensemble of independent members, each with its own uniform box mesh, polynomial order

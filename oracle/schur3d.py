@@ -154,7 +154,11 @@ def bicgstab_pbno(apply, b, c, lam_bar, tol=1e-12, maxit=500):
     """BiCGstab left-preconditioned by PBNO (Algorithm "BiCGstabPBNO"); x0 = 0.  Returns
     (x, iterations).  Converged when the preconditioned residual's 2-norm has dropped by
     tol."""
-    M = lambda v: pbno_apply(apply, v, c, lam_bar)
+    return bicgstab(apply, b, lambda v: pbno_apply(apply, v, c, lam_bar), tol, maxit)
+
+
+def bicgstab(apply, b, M, tol=1e-12, maxit=500):
+    """The iteration of Algorithm "BiCGstabPBNO" with any left preconditioner M."""
     x = np.zeros_like(b)
     rn = M(b)
     r0n = np.linalg.norm(rn)
@@ -179,12 +183,20 @@ def bicgstab_pbno(apply, b, c, lam_bar, tol=1e-12, maxit=500):
 
 
 class HEVI3D:
-    """3D-IMEX ARK2 integrator with the Schur form and BiCGstab + polynomial preconditioner
-    (oracle).  order: polynomial degree P; tol: relative preconditioned-residual drop."""
+    """3D-IMEX integrator with the Schur form and BiCGstab + polynomial preconditioner
+    (oracle).  order: polynomial degree P; tol: relative preconditioned-residual drop;
+    scheme: "ark2" (Table 1) or "ark3" (``oracle.ark3``); precond: "pbno" (the paper's
+    polynomial preconditioner, Chebyshev reading) or "column" (the 1D column Schur LU as a
+    vertical-line preconditioner, a choice beyond the paper)."""
 
-    def __init__(self, mesh, col, dt, order=2, tol=1e-12):
+    def __init__(self, mesh, col, dt, order=2, tol=1e-12, scheme="ark2", precond="pbno"):
         self.mesh, self.col, self.dt = mesh, col, dt
-        _, at, _, _ = tableau()
+        if scheme == "ark2":
+            self.tab = tableau()
+        else:
+            from . import ark3
+            self.tab = ark3.tableau()
+        at = self.tab[1]
         self.lam = at[1, 1] * dt
         self.op = Schur3D(mesh, col)
         self.l_min = 1.0
@@ -192,6 +204,19 @@ class HEVI3D:
         self.c, self.lam_bar = chebyshev_pbno(order, self.l_min, self.l_max)
         self.tol = tol
         self.iters = []
+        self.precond = precond
+        if precond == "column":
+            # the 1D-IMEX column Schur matrix of the same lam, factored by Algorithm 9: the
+            # vertical (stiffest) part of S solved exactly, column by column
+            from .column import lu_nopivot_banded, lu_solve_banded
+            LU = lu_nopivot_banded(col.jacobian_by_probing(self.lam), col.half_band)
+            hb, sh = col.half_band, (mesh.ncol, mesh.M)
+            self.M = lambda v: lu_solve_banded(LU, hb, v.reshape(sh)).ravel()
+        elif precond == "pbno":
+            self.M = lambda v: pbno_apply(lambda x: self.op.apply(x, self.lam), v, self.c,
+                                          self.lam_bar)
+        else:
+            raise ValueError("precond must be 'pbno' or 'column'")
 
     def R(self, q):
         return rhs(self.mesh, self.col, q, self.op.l2g, self.op.mass)
@@ -199,11 +224,11 @@ class HEVI3D:
     def solve(self, q_e, lam):
         assert abs(lam - self.lam) <= 1e-15 * abs(self.lam)
         b, ua = self.op.rhs(q_e, lam)
-        P, it = bicgstab_pbno(lambda x: self.op.apply(x, lam), b, self.c, self.lam_bar, self.tol)
+        P, it = bicgstab(lambda x: self.op.apply(x, lam), b, self.M, self.tol)
         self.iters.append(it)
         return self.op.extract(P, ua, q_e[4], lam)
 
     def step(self, q, nsteps=1):
         for _ in range(nsteps):
-            q = ark_step(q, self.dt, self.R, self.solve)
+            q = ark_step(q, self.dt, self.R, self.solve, self.tab)
         return q

@@ -19,10 +19,12 @@ ERRORS = {
     5: "NUMA_ERR_PIVOT", 6: "NUMA_ERR_NONFINITE", 7: "NUMA_ERR_TIMEOUT", 8: "NUMA_ERR_SCRATCH",
 }
 Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_FACTORED, Q_N, \
-    Q_PRECISION, Q_COLUMN_FORM, Q_SCHEME = range(12)
+    Q_PRECISION, Q_COLUMN_FORM, Q_SCHEME, Q_IMEX = range(13)
 PRECISIONS = {"fp64": 0, "mixed": 1}
 COLUMN_FORMS = {"schur": 0, "standard": 1}
 SCHEMES = {"ark2": 0, "ark3": 1}
+IMEX = {"1d": 0, "3d": 1}
+PRECONDS = {"pbno": 0, "column": 1}
 
 # Every symbol include/numa.h declares (checked by tests/test_abi.py).
 EXPORTS = (
@@ -36,14 +38,17 @@ EXPORTS = (
     "numa_batch_member_query", "numa_batch_reference_levels", "numa_batch_last_error",
     "numa_rhs_tlm", "numa_rhs_adjoint", "numa_solve_columns_transposed", "numa_imex_stage_adjoint",
     "numa_step_imex1d_tlm", "numa_step_imex1d_adjoint", "numa_imex1d_forward_checkpointed",
-    "numa_imex1d_adjoint_checkpointed", "numa_ark3_tableau",
+    "numa_imex1d_adjoint_checkpointed", "numa_ark3_tableau", "numa_schur3d_apply",
+    "numa_solve_schur3d", "numa_imex3d_stage", "numa_step_imex3d", "numa_imex3d_info",
 )
-K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ = range(8)
+K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ, K_SCHUR3D = range(9)
 
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
-                ("column_form", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("column_form", ctypes.c_int), ("scheme", ctypes.c_int), ("imex", ctypes.c_int),
+                ("pbno_order", ctypes.c_int), ("krylov_max_iters", ctypes.c_int),
+                ("krylov_tol", ctypes.c_double), ("precond", ctypes.c_int)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -88,6 +93,11 @@ def lib():
             "numa_rk35_coefficients": (None, [P, P]),
             "numa_ark2_tableau": (None, [P, P, P]),
             "numa_ark3_tableau": (None, [P, P, P]),
+            "numa_schur3d_apply": (I, [P, P, P]),
+            "numa_solve_schur3d": (I, [P, P, P, ctypes.POINTER(I)]),
+            "numa_imex3d_stage": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I)]),
+            "numa_step_imex3d": (I, [P, P, P, I]),
+            "numa_imex3d_info": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), P, ctypes.POINTER(LL)]),
             "numa_rhs_explicit_static": (I, [ctypes.POINTER(MeshDesc), I, P, P, P]),
             "numa_batch_init": (I, [ctypes.POINTER(MeshDesc), P, P, I, P, ctypes.POINTER(P)]),
             "numa_batch_destroy": (None, [P]),
@@ -128,7 +138,8 @@ class Numa:
 
     def __init__(self, nex, ney, nez, Lx, Ly, Lz, N, dt=0.0, theta_s=300.0, n_bv=0.0,
                  stream=None, precision="fp64", refine_iters=1, column_form="schur",
-                 scheme="ark2"):
+                 scheme="ark2", imex="1d", pbno_order=2, krylov_tol=1e-12, krylov_max_iters=500,
+                 precond="pbno"):
         import torch
         self._torch = torch
         L = lib()
@@ -137,7 +148,8 @@ class Numa:
         self._stream = s
         h = ctypes.c_void_p()
         self._opt = Options(PRECISIONS[precision], int(refine_iters), COLUMN_FORMS[column_form],
-                            SCHEMES[scheme])
+                            SCHEMES[scheme], IMEX[imex], int(pbno_order), int(krylov_max_iters),
+                            float(krylov_tol), PRECONDS[precond])
         rc = L.numa_init_ex(ctypes.byref(self._desc), N, float(dt), ctypes.byref(self._opt),
                             ctypes.c_void_p(s.cuda_stream), ctypes.byref(h))
         if rc != NUMA_OK:
@@ -148,6 +160,8 @@ class Numa:
         self.precision = precision
         self.column_form = column_form
         self.scheme = scheme
+        self.imex = imex
+        self.pbno_order = int(pbno_order)
         self.ncol = self.query(Q_NCOL)
         self.M = self.query(Q_M)
         self.nnode = self.query(Q_NNODE)
@@ -331,6 +345,47 @@ class Numa:
         keeps a checkpoint every `every` steps and recomputes each segment during the
         adjoint sweep; forward mode runs the TLM alongside the trajectory."""
         return _functions()[1].apply(q0, self, int(nsteps), int(every))
+
+    # -- 3D-IMEX (Schur form, BiCGstab + polynomial preconditioner) -----------------------
+    def schur3d_apply(self, P, out=None):
+        self._state(P, self.nnode)
+        out = self._torch.empty_like(P) if out is None else self._state(out, self.nnode)
+        self._check(lib().numa_schur3d_apply(self._h, _ptr(P), _ptr(out)), "numa_schur3d_apply")
+        return out
+
+    def solve_schur3d(self, b, x=None):
+        """(x, iterations) with S(x) = b."""
+        self._state(b, self.nnode)
+        x = self._torch.empty_like(b) if x is None else self._state(x, self.nnode)
+        it = ctypes.c_int()
+        self._check(lib().numa_solve_schur3d(self._h, _ptr(b), _ptr(x), ctypes.byref(it)),
+                    "numa_solve_schur3d")
+        return x, it.value
+
+    def imex3d_stage(self, stage, qn, R1, R2=None, q2=None, out=None):
+        """(q(stage), BiCGstab iterations)."""
+        out = self._torch.empty_like(qn) if out is None else self._state(out)
+        it = ctypes.c_int()
+        self._check(lib().numa_imex3d_stage(self._h, int(stage), _ptr(qn), _ptr(R1), _ptr(R2),
+                                            _ptr(q2), _ptr(out), ctypes.byref(it)),
+                    "numa_imex3d_stage")
+        return out, it.value
+
+    def step_imex3d(self, q_in, q_out=None, nsteps=1):
+        self._state(q_in)
+        q_out = q_in if q_out is None else self._state(q_out)
+        self._check(lib().numa_step_imex3d(self._h, _ptr(q_in), _ptr(q_out), int(nsteps)),
+                    "numa_step_imex3d")
+        return q_out
+
+    def imex3d_info(self):
+        """{"l_max", "lam_bar", "coeffs", "iters_last_step"}."""
+        lm, lb, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        c = np.zeros(self.pbno_order + 1)
+        self._check(lib().numa_imex3d_info(self._h, ctypes.byref(lm), ctypes.byref(lb),
+                                           c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it)),
+                    "numa_imex3d_info")
+        return {"l_max": lm.value, "lam_bar": lb.value, "coeffs": c, "iters_last_step": it.value}
 
     # -- inspection -------------------------------------------------------------------
     def connectivity(self):

@@ -628,7 +628,7 @@ int adj_work(numa_ctx* c, AdjWork& w) {
 }
 
 int check_diff(numa_ctx* c, bool need_factors) {
-  if (c->precision != NUMA_PREC_FP64 || c->F.standard || c->scheme != NUMA_SCHEME_ARK2)
+  if (c->precision != NUMA_PREC_FP64 || c->F.standard || c->scheme != NUMA_SCHEME_ARK2 || c->imex3d)
     return afail(c, NUMA_ERR_ARG, "the differentiation form needs an FP64 Schur-form ARK2 context");
   if (need_factors && !c->factored)
     return afail(c, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");

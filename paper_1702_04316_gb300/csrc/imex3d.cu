@@ -1,0 +1,629 @@
+// 3D-IMEX in the Schur form: the implicit part of the ARK step is the whole linear operator
+// L of Set2NC (Sec. "Equation Set2NC", Eqs. imex2nc, 2ncp, utteqn, helm2nc), reduced to one
+// unknown P per node, and solved by BiCGstab left-preconditioned by a polynomial in the
+// Schur operator (Algorithm "BiCGstabPBNO" with its PBNO procedure).
+//
+// On the box, grad rho0, grad theta0 and F0 are vertical, so with the per-level tables of
+// the 1D stage (kp1 = lam/(A rho0), kp2 = lam g/(A G0 rho0), kF = lam F0z, kD = lam rho0 G0,
+// wa_s = 1/A, wa_th = lam g/theta0, all zero-at-wall where w vanishes):
+//   u_p = lam D_x P / rho0,  v_p = lam D_y P / rho0,  w_p = kp1 D_z P + kp2 P
+//   S(P) = P - kF w_p - kD (D_x u_p + D_y v_p + D_z w_p)
+//   b    = P_e - kF w_a - kD (D_x u_a + D_y v_a + D_z w_a),  u_a = u_e, v_a = v_e,
+//          w_a = wa_s (w_e + wa_th theta_e)
+//   u = u_a - u_p(P),  theta' = theta'_e - lam w d(theta0)/dz,  rho' = (P - H0 theta')/G0
+// D_x, D_y, D_z are the DSS'd derivatives of the explicit right-hand side (the same tap
+// rows); each velocity component is zero on the walls normal to it.  The operator is
+// matrix-free: a gradient pass (P -> u_p, v_p, w_p) and a divergence pass.
+//
+// Preconditioner: the paper's PBNO coefficients come from a least-squares fit that it does
+// not reproduce.  Here they make y q(y) the Chebyshev minimax approximation of 1 on the
+// scaled spectrum interval [1 - delta, 1 + delta], y = lam_bar S, lam_bar = 2/(l_min +
+// l_max), l_min = 1, l_max from a power iteration at start-up (times 1.05).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "numa.h"
+#include "numa_ctx.h"
+#include "rhs_device.cuh"
+
+namespace {
+using namespace numa_dev;
+
+const int kRedBlocks = 152 * 4;   // blocks of the dot-product reduction
+const int kRedThreads = 256;
+
+// D_a f at node g for one field f (the tap rows of the explicit right-hand side), with the
+// exact tap count of the node's class (uniform across a warp in the class-sorted order).
+template <int N>
+__device__ __forceinline__ double deriv1(const double* __restrict__ f, long long g, long long stride,
+                                         int cls, const Taps<N, double>& T) {
+  const double* p = f + g;
+  double a0 = T.c[0] * __ldg(p + T.o[0] * stride), a1 = 0.0;
+  if (cls == CLS_IFACE) {
+#pragma unroll
+    for (int t = 1; t < 2 * N; ++t) {
+      if (t & 1) a1 = fma(T.c[t], __ldg(p + T.o[t] * stride), a1);
+      else a0 = fma(T.c[t], __ldg(p + T.o[t] * stride), a0);
+    }
+  } else if (cls == CLS_WALL) {
+#pragma unroll
+    for (int t = 1; t <= N; ++t) {
+      if (t & 1) a1 = fma(T.c[t], __ldg(p + T.o[t] * stride), a1);
+      else a0 = fma(T.c[t], __ldg(p + T.o[t] * stride), a0);
+    }
+  } else {
+#pragma unroll
+    for (int t = 1; t < N; ++t) {
+      if (t & 1) a1 = fma(T.c[t], __ldg(p + T.o[t] * stride), a1);
+      else a0 = fma(T.c[t], __ldg(p + T.o[t] * stride), a0);
+    }
+  }
+  return a0 + a1;
+}
+
+struct NodeIdx {
+  long long g;
+  int ix, iy, iz;
+};
+
+__device__ __forceinline__ NodeIdx node_idx(long long g, const Geom& G) {
+  NodeIdx n;
+  n.g = g;
+  const long long col = g / G.M;
+  n.iz = (int)(g - col * G.M);
+  n.iy = (int)(col / G.nxg);
+  n.ix = (int)(col - (long long)n.iy * G.nxg);
+  return n;
+}
+
+// (u_p, v_p, w_p) of P into U3 (3 x nnode).
+// Thread tid of the class-sorted order (perm, nthreads entries, -1 = padding) -> node g.
+__device__ __forceinline__ long long sorted_node(const int* __restrict__ perm, long long nthreads) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= nthreads) return -1;
+  return perm[tid];
+}
+
+template <int N>
+__global__ void k_s3_grad(const double* __restrict__ P, double* __restrict__ U3, Geom G, Coef3 C,
+                          RefLev R, StageTab tb, double lam, const int* __restrict__ perm,
+                          long long nthreads) {
+  constexpr int Nq = N + 1;
+  __shared__ double sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
+  load_rows<N, double>(C, sD, sDl, sDr);
+  __syncthreads();
+  const long long g = sorted_node(perm, nthreads);
+  if (g < 0) return;
+  const NodeIdx n = node_idx(g, G);
+  const long long nn = G.nnode, sx = G.M, sy = (long long)G.nxg * G.M;
+  Taps<N, double> T;
+  int cls = axis_taps<N, double>(n.ix, G.nex, sD, sDl, sDr, T);
+  const double dx = deriv1<N>(P, g, sx, cls, T);
+  cls = axis_taps<N, double>(n.iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
+  const double dy = deriv1<N>(P, g, sy, cls, T);
+  cls = axis_taps<N, double>(n.iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
+  const double dz = deriv1<N>(P, g, 1, cls, T);
+  const double k = lam * R.inv_rho0[n.iz];
+  const bool xw = (n.ix == 0 || n.ix == G.nxg - 1), yw = (n.iy == 0 || n.iy == G.nyg - 1);
+  U3[g] = xw ? 0.0 : k * dx;
+  U3[nn + g] = yw ? 0.0 : k * dy;
+  U3[2 * nn + g] = fma(__ldg(tb.kp1 + n.iz), dz, __ldg(tb.kp2 + n.iz) * P[g]);
+}
+
+// out = alpha (base - kF w - kD (D_x u + D_y v + D_z w)) + beta y   (y may be NULL)
+template <int N>
+__global__ void k_s3_div(const double* __restrict__ U3, const double* __restrict__ base,
+                         const double* __restrict__ y, double* __restrict__ out, double alpha,
+                         double beta, Geom G, Coef3 C, StageTab tb, const int* __restrict__ perm,
+                         long long nthreads) {
+  constexpr int Nq = N + 1;
+  __shared__ double sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
+  load_rows<N, double>(C, sD, sDl, sDr);
+  __syncthreads();
+  const long long g = sorted_node(perm, nthreads);
+  if (g < 0) return;
+  const NodeIdx n = node_idx(g, G);
+  const long long nn = G.nnode, sx = G.M, sy = (long long)G.nxg * G.M;
+  Taps<N, double> T;
+  int cls = axis_taps<N, double>(n.ix, G.nex, sD, sDl, sDr, T);
+  const double du = deriv1<N>(U3, g, sx, cls, T);
+  cls = axis_taps<N, double>(n.iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
+  const double dv = deriv1<N>(U3 + nn, g, sy, cls, T);
+  cls = axis_taps<N, double>(n.iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
+  const double dw = deriv1<N>(U3 + 2 * nn, g, 1, cls, T);
+  double v = base[g] - __ldg(tb.kF + n.iz) * U3[2 * nn + g] - __ldg(tb.kD + n.iz) * (du + dv + dw);
+  v *= alpha;
+  if (y) v = fma(beta, y[g], v);
+  out[g] = v;
+}
+
+struct StageIn {
+  const double* qn;
+  const double* R[3];
+  const double* Q[3];    // Q[0] unused (q^n), Q[1] = q(2), Q[2] = q(3)
+};
+
+// q~_e of all five fields, then E5 = (P_e, u_a, v_a, w_a, theta~_e).
+template <int NP>
+__global__ void k_s3_pred(StageIn in, double* __restrict__ E5, Geom G, StageTab tb, StageCoef sc) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= G.nnode) return;
+  const NodeIdx n = node_idx(g, G);
+  const long long nn = G.nnode;
+  double e[5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    const long long o = f * nn + g;
+    const double qv = in.qn[o];
+    double v = fma(sc.a[0] * sc.dt, in.R[0][o], qv);
+    if (NP >= 2) v = fma(sc.a[1] * sc.dt, in.R[1][o], v);
+    if (NP >= 3) v = fma(sc.a[2] * sc.dt, in.R[2][o], v);
+    v = fma(sc.c[0], qv, v);
+    if (NP >= 2) v = fma(sc.c[1], in.Q[1][o], v);
+    if (NP >= 3) v = fma(sc.c[2], in.Q[2][o], v);
+    e[f] = v;
+  }
+  const int iz = n.iz;
+  const bool xw = (n.ix == 0 || n.ix == G.nxg - 1), yw = (n.iy == 0 || n.iy == G.nyg - 1);
+  E5[g] = fma(__ldg(tb.G0 + iz), e[0], __ldg(tb.H0 + iz) * e[4]);
+  E5[nn + g] = xw ? 0.0 : e[1];
+  E5[2 * nn + g] = yw ? 0.0 : e[2];
+  E5[3 * nn + g] = fma(__ldg(tb.wa_th + iz), e[4], e[3]) * __ldg(tb.wa_s + iz);
+  E5[4 * nn + g] = e[4];
+}
+
+// q(i) = (rho', u, v, w, theta')(P) - sum_j c_ij q(j), with U3 = u_p(P).
+template <int NP>
+__global__ void k_s3_extract(const double* __restrict__ P, const double* __restrict__ U3,
+                             const double* __restrict__ E5, StageIn in, double* __restrict__ out,
+                             Geom G, StageTab tb, StageCoef sc) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= G.nnode) return;
+  const long long nn = G.nnode;
+  const int iz = (int)(g % G.M);
+  double v[5];
+  v[1] = E5[nn + g] - U3[g];
+  v[2] = E5[2 * nn + g] - U3[nn + g];
+  v[3] = E5[3 * nn + g] - U3[2 * nn + g];
+  v[4] = fma(-__ldg(tb.kth + iz), v[3], E5[4 * nn + g]);
+  v[0] = fma(-__ldg(tb.H0G0 + iz), v[4], __ldg(tb.invG0 + iz) * P[g]);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    const long long o = f * nn + g;
+    double r = fma(-sc.c[0], in.qn[o], v[f]);
+    if (NP >= 2) r = fma(-sc.c[1], in.Q[1][o], r);
+    if (NP >= 3) r = fma(-sc.c[2], in.Q[2][o], r);
+    out[o] = r;
+  }
+}
+
+// Partial sums of nd <= 3 dot products, in a fixed order (deterministic).
+struct DotArgs {
+  const double* a[3];
+  const double* b[3];
+  int nd;
+};
+
+__global__ void k_dots(DotArgs d, long long n, double* __restrict__ part) {
+  __shared__ double sh[3][kRedThreads];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < d.nd) acc[k] = fma(d.a[k][i], d.b[k][i], acc[k]);
+  for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) part[k * gridDim.x + blockIdx.x] = sh[k][0];
+}
+
+__global__ void k_dots_final(const double* __restrict__ part, int nblk, double* __restrict__ res) {
+  __shared__ double sh[3][kRedThreads];
+  for (int k = 0; k < 3; ++k) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[k * nblk + i];
+    sh[k][threadIdx.x] = acc;
+  }
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) res[k] = sh[k][0];
+}
+
+// out = a x + b y + c z over n entries (y, z may be NULL).
+__global__ void k_lincomb(double* __restrict__ out, double a, const double* __restrict__ x,
+                          double b, const double* __restrict__ y, double c,
+                          const double* __restrict__ z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = a * x[i];
+    if (y) v = fma(b, y[i], v);
+    if (z) v = fma(c, z[i], v);
+    out[i] = v;
+  }
+}
+
+// A start vector for the power iteration: a counter-based hash of the index in [-1, 1).
+__global__ void k_hash_fill(double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------------
+int fail3(numa_ctx* c, int code, const char* m) {
+  c->err = m;
+  return code;
+}
+
+#define NUMA_3CK(c, call)                                                  \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+      return NUMA_ERR_CUDA;                                                \
+    }                                                                      \
+  } while (0)
+
+// 3D workspace: E5 (5), U3 (3) and 12 Krylov vectors, each nnode; reduction partials.
+struct W3 {
+  double *E5, *U3, *b, *x, *rn, *ro, *p, *Ap, *s, *As, *t, *vr, *ra, *rb;
+  double *part, *res;
+};
+
+int w3(numa_ctx* c, W3& w) {
+  const long long nn = c->G.nnode;
+  if (!c->d_w3) {
+    const size_t bytes = ((size_t)20 * nn + 3 * kRedBlocks + 8) * sizeof(double);
+    if (cudaMalloc(&c->d_w3, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_w3 = nullptr;
+      return fail3(c, NUMA_ERR_OOM, "3D-IMEX workspace");
+    }
+  }
+  double* p = c->d_w3;
+  w.E5 = p; p += 5 * nn;
+  w.U3 = p; p += 3 * nn;
+  double** v[12] = {&w.b, &w.x, &w.rn, &w.ro, &w.p, &w.Ap, &w.s, &w.As, &w.t, &w.vr, &w.ra, &w.rb};
+  for (int k = 0; k < 12; ++k) {
+    *v[k] = p;
+    p += nn;
+  }
+  w.part = p;
+  w.res = p + 3 * kRedBlocks;
+  return NUMA_OK;
+}
+
+unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+#define NUMA_3D_DISPATCH(kern, grid, block, stream, ...)                       \
+  switch (c->G.N) {                                                            \
+    case 1: kern<1><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    case 2: kern<2><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    case 3: kern<3><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    case 4: kern<4><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    case 5: kern<5><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    case 6: kern<6><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    case 7: kern<7><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    case 8: kern<8><<<grid, block, 0, stream>>>(__VA_ARGS__); break;           \
+    default: return fail3(c, NUMA_ERR_ARG, "polynomial order out of range");   \
+  }
+
+// U3 = u_p(P)
+int grad(numa_ctx* c, const double* P, double* U3) {
+  NUMA_3D_DISPATCH(k_s3_grad, nblk(c->nperm, 128), 128, c->stream, P, U3, c->G, c->C, c->R,
+                   c->T, c->lam, c->d_perm, c->nperm)
+  NUMA_3CK(c, cudaGetLastError());
+  return NUMA_OK;
+}
+
+// out = alpha (base - kF w - kD div U3) + beta y
+int divg(numa_ctx* c, const double* U3, const double* base, const double* y, double* out,
+         double alpha, double beta) {
+  NUMA_3D_DISPATCH(k_s3_div, nblk(c->nperm, 128), 128, c->stream, U3, base, y, out, alpha, beta,
+                   c->G, c->C, c->T, c->d_perm, c->nperm)
+  NUMA_3CK(c, cudaGetLastError());
+  return NUMA_OK;
+}
+
+// out = alpha S(P) + beta y
+int lhs(numa_ctx* c, const W3& w, const double* P, double* out, double alpha = 1.0,
+        double beta = 0.0, const double* y = nullptr) {
+  long p = prof_begin(c, NUMA_K_SCHUR3D);
+  int rc;
+  if ((rc = grad(c, P, w.U3))) return rc;
+  rc = divg(c, w.U3, P, y, out, alpha, beta);
+  prof_end(c, p);
+  return rc;
+}
+
+int lincomb(numa_ctx* c, double* out, double a, const double* x, double b = 0.0,
+            const double* y = nullptr, double cc = 0.0, const double* z = nullptr) {
+  k_lincomb<<<kRedBlocks, kRedThreads, 0, c->stream>>>(out, a, x, b, y, cc, z, c->G.nnode);
+  NUMA_3CK(c, cudaGetLastError());
+  return NUMA_OK;
+}
+
+// nd dot products a_k . b_k, read back to the host (synchronises the stream).
+int dots(numa_ctx* c, const W3& w, int nd, const double* a0, const double* b0, double* out,
+         const double* a1 = nullptr, const double* b1 = nullptr, const double* a2 = nullptr,
+         const double* b2 = nullptr) {
+  DotArgs d{{a0, a1, a2}, {b0, b1, b2}, nd};
+  k_dots<<<kRedBlocks, kRedThreads, 0, c->stream>>>(d, c->G.nnode, w.part);
+  NUMA_3CK(c, cudaGetLastError());
+  k_dots_final<<<1, kRedThreads, 0, c->stream>>>(w.part, kRedBlocks, w.res);
+  NUMA_3CK(c, cudaGetLastError());
+  NUMA_3CK(c, cudaMemcpyAsync(out, w.res, nd * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  NUMA_3CK(c, cudaStreamSynchronize(c->stream));
+  return NUMA_OK;
+}
+
+// out = s(S) in, the polynomial preconditioner (PBNO procedure): r = lam_bar in;
+// r* = c_0 r; r* = lam_bar S(r*) + c_i r, i = 1..P.  Uses vr, ra, rb; out may alias none.
+int pbno(numa_ctx* c, const W3& w, const double* in, double* out) {
+  const int P = c->pbno_order;
+  const double lb = c->lam_bar;
+  int rc;
+  if (P == 0) return lincomb(c, out, c->pbno_c[0] * lb, in);
+  if ((rc = lincomb(c, w.vr, lb, in))) return rc;
+  if ((rc = lincomb(c, w.ra, c->pbno_c[0], w.vr))) return rc;
+  double* cur = w.ra;
+  double* nxt = w.rb;
+  for (int i = 1; i <= P; ++i) {
+    double* dst = (i == P) ? out : nxt;
+    if ((rc = lhs(c, w, cur, dst, lb, c->pbno_c[i], w.vr))) return rc;
+    std::swap(cur, nxt);
+  }
+  return NUMA_OK;
+}
+
+// out = M^-1 in: the polynomial (PBNO procedure) or the stored column Schur LU solve.
+int precond(numa_ctx* c, const W3& w, const double* in, double* out) {
+  if (c->precond == NUMA_PRECOND_COLUMN) {
+    NUMA_3CK(c, launch_solve(in, out, c->G, c->F, c->R, c->T, c->col_tile, c->stream));
+    return NUMA_OK;
+  }
+  return pbno(c, w, in, out);
+}
+
+// BiCGstab left-preconditioned by the polynomial, x0 = 0 (Algorithm "BiCGstabPBNO").
+// Converged when the preconditioned residual's 2-norm has dropped by krylov_tol.
+int bicgstab(numa_ctx* c, const W3& w, const double* b, double* x, int* iters) {
+  const long long nn = c->G.nnode;
+  int rc;
+  NUMA_3CK(c, cudaMemsetAsync(x, 0, nn * sizeof(double), c->stream));
+  if ((rc = precond(c, w, b, w.rn))) return rc;
+  double d[3];
+  if ((rc = dots(c, w, 1, w.rn, w.rn, d))) return rc;
+  const double r0 = std::sqrt(d[0]);
+  *iters = 0;
+  if (!(r0 > 0.0)) return NUMA_OK;
+  NUMA_3CK(c, cudaMemcpyAsync(w.p, w.rn, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  NUMA_3CK(c, cudaMemcpyAsync(w.ro, w.rn, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  double rn_ro = d[0];
+  for (int it = 1; it <= c->krylov_max_iters; ++it) {
+    if ((rc = lhs(c, w, w.p, w.t)) || (rc = precond(c, w, w.t, w.Ap))) return rc;
+    if ((rc = dots(c, w, 1, w.Ap, w.ro, d))) return rc;
+    const double ar = rn_ro / d[0];
+    if ((rc = lincomb(c, w.s, 1.0, w.rn, -ar, w.Ap))) return rc;
+    if ((rc = lhs(c, w, w.s, w.t)) || (rc = precond(c, w, w.t, w.As))) return rc;
+    if ((rc = dots(c, w, 2, w.As, w.s, d, w.As, w.As))) return rc;
+    const double wr = d[0] / d[1];
+    if ((rc = lincomb(c, x, 1.0, x, ar, w.p, wr, w.s))) return rc;
+    if ((rc = lincomb(c, w.rn, 1.0, w.s, -wr, w.As))) return rc;          // r_e, kept in rn
+    if ((rc = dots(c, w, 2, w.rn, w.rn, d, w.rn, w.ro))) return rc;
+    *iters = it;
+    if (!std::isfinite(d[0])) return fail3(c, NUMA_ERR_NONFINITE, "BiCGstab diverged");
+    if (std::sqrt(d[0]) / r0 <= c->krylov_tol) return NUMA_OK;
+    const double br = d[1] / rn_ro * ar / wr;
+    if ((rc = lincomb(c, w.p, 1.0, w.rn, br, w.p, -br * wr, w.Ap))) return rc;
+    rn_ro = d[1];
+  }
+  return fail3(c, NUMA_ERR_TIMEOUT, "BiCGstab did not converge within krylov_max_iters");
+}
+
+// One 3D-IMEX stage i (NP = i - 1 previous stages).
+template <int NP>
+int stage3(numa_ctx* c, const W3& w, const StageIn& in, double* out, const StageCoef& sc,
+           int* iters) {
+  const unsigned nb = nblk(c->G.nnode, 256);
+  k_s3_pred<NP><<<nb, 256, 0, c->stream>>>(in, w.E5, c->G, c->T, sc);
+  NUMA_3CK(c, cudaGetLastError());
+  int rc;
+  if ((rc = divg(c, w.E5 + c->G.nnode, w.E5, nullptr, w.b, 1.0, 0.0))) return rc;
+  if ((rc = bicgstab(c, w, w.b, w.x, iters))) return rc;
+  if ((rc = grad(c, w.x, w.U3))) return rc;
+  k_s3_extract<NP><<<nb, 256, 0, c->stream>>>(w.x, w.U3, w.E5, in, out, c->G, c->T, sc);
+  NUMA_3CK(c, cudaGetLastError());
+  return NUMA_OK;
+}
+
+int stage3_any(numa_ctx* c, const W3& w, int stage, const StageIn& in, double* out, int* iters) {
+  const StageCoef sc = numa_stage_coef(c, stage);
+  if (stage == 2) return stage3<1>(c, w, in, out, sc, iters);
+  if (stage == 3) return stage3<2>(c, w, in, out, sc, iters);
+  return stage3<3>(c, w, in, out, sc, iters);
+}
+
+int check3(numa_ctx* c) {
+  if (!c->imex3d) return fail3(c, NUMA_ERR_ARG, "not a 3D-IMEX context (option imex)");
+  if (!c->factored) return fail3(c, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  return NUMA_OK;
+}
+
+// Monomial coefficients (ascending) of T_k(t) for k <= 9.
+void cheb_mono(int k, double* out) {
+  double tm[10] = {1.0}, tc[10] = {0.0, 1.0}, tn[10];
+  if (k == 0) {
+    std::memcpy(out, tm, sizeof(tm));
+    return;
+  }
+  for (int j = 1; j < k; ++j) {
+    for (int i = 0; i < 10; ++i) tn[i] = -tm[i] + (i > 0 ? 2.0 * tc[i - 1] : 0.0);
+    std::memcpy(tm, tc, sizeof(tm));
+    std::memcpy(tc, tn, sizeof(tc));
+  }
+  std::memcpy(out, tc, sizeof(tc));
+}
+
+}  // namespace
+
+// The preconditioner of a 3D context for lam: spectrum estimate (power iteration on S,
+// 60 iterations) and the Chebyshev coefficients.  Called by numa_factor_columns.
+int numa_imex3d_setup(numa_ctx* c) {
+  W3 w;
+  int rc;
+  if ((rc = w3(c, w))) return rc;
+  if (c->precond == NUMA_PRECOND_COLUMN) {      // no polynomial to set up
+    c->l_max = 0.0;
+    c->lam_bar = 0.0;
+    return NUMA_OK;
+  }
+  const long long nn = c->G.nnode;
+  k_hash_fill<<<kRedBlocks, kRedThreads, 0, c->stream>>>(w.ra, nn);
+  NUMA_3CK(c, cudaGetLastError());
+  double d[3];
+  if ((rc = dots(c, w, 1, w.ra, w.ra, d))) return rc;
+  if ((rc = lincomb(c, w.ra, 1.0 / std::sqrt(d[0]), w.ra))) return rc;
+  double lam_est = 1.0;
+  for (int it = 0; it < 60; ++it) {
+    if ((rc = lhs(c, w, w.ra, w.rb))) return rc;
+    if ((rc = dots(c, w, 2, w.ra, w.rb, d, w.rb, w.rb))) return rc;
+    lam_est = d[0];
+    if (!(d[1] > 0.0) || !std::isfinite(d[1])) return fail3(c, NUMA_ERR_NONFINITE, "power iteration");
+    if ((rc = lincomb(c, w.ra, 1.0 / std::sqrt(d[1]), w.rb))) return rc;
+  }
+  const double lmin = 1.0, lmax = std::max(1.05 * lam_est, 1.0 + 1e-6);
+  c->l_max = lmax;
+  c->lam_bar = 2.0 / (lmin + lmax);
+  const double delta = (lmax - lmin) / (lmax + lmin);
+  const int P = c->pbno_order;
+  // residual r(y) = T_{P+1}((1 - y)/delta) / T_{P+1}(1/delta) in powers of y, then
+  // q(y) = (1 - r(y)) / y; c_i multiplies y^(P - i)
+  double T[10];
+  cheb_mono(P + 1, T);
+  const double T1 = std::cosh((P + 1) * std::acosh(1.0 / delta));
+  double r[11] = {0.0};
+  // (1 - y)^k / delta^k expanded
+  for (int k = 0; k <= P + 1; ++k) {
+    double binom = 1.0;
+    for (int j = 0; j <= k; ++j) {
+      if (j > 0) binom = binom * (k - j + 1) / j;
+      r[j] += T[k] * binom * ((j & 1) ? -1.0 : 1.0) / std::pow(delta, k);
+    }
+  }
+  for (int j = 0; j <= P + 1; ++j) r[j] /= T1;
+  for (int i = 0; i <= P; ++i) c->pbno_c[i] = -r[P - i + 1];      // (1 - r)/y: drop y^0
+  return NUMA_OK;
+}
+
+extern "C" {
+
+int numa_schur3d_apply(numa_ctx* ctx, const double* P, double* SP) {
+  if (!ctx || !P || !SP || P == SP) return NUMA_ERR_ARG;
+  int rc;
+  W3 w;
+  if ((rc = check3(ctx)) || (rc = w3(ctx, w))) return rc;
+  return lhs(ctx, w, P, SP);
+}
+
+int numa_solve_schur3d(numa_ctx* ctx, const double* b, double* x, int* iters) {
+  if (!ctx || !b || !x || b == x) return NUMA_ERR_ARG;
+  int rc;
+  W3 w;
+  if ((rc = check3(ctx)) || (rc = w3(ctx, w))) return rc;
+  int it = 0;
+  NUMA_3CK(ctx, cudaMemcpyAsync(w.b, b, ctx->G.nnode * sizeof(double), cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+  rc = bicgstab(ctx, w, w.b, x, &it);
+  if (iters) *iters = it;
+  return rc;
+}
+
+int numa_imex3d_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1,
+                      const double* R2, const double* q2, double* q_out, int* iters) {
+  if (!ctx || !qn || !R1 || !q_out || (stage != 2 && stage != 3)) return NUMA_ERR_ARG;
+  if (stage == 3 && (!R2 || !q2)) return NUMA_ERR_ARG;
+  int rc;
+  W3 w;
+  if ((rc = check3(ctx)) || (rc = w3(ctx, w))) return rc;
+  StageIn in{qn, {R1, R2, nullptr}, {nullptr, q2, nullptr}};
+  int it = 0;
+  rc = stage3_any(ctx, w, stage, in, q_out, &it);
+  if (iters) *iters = it;
+  return rc;
+}
+
+int numa_step_imex3d(numa_ctx* ctx, const double* q_in, double* q_out, int nsteps) {
+  if (!ctx || !q_in || !q_out || nsteps < 0) return NUMA_ERR_ARG;
+  int rc;
+  W3 w;
+  if ((rc = check3(ctx)) || (rc = w3(ctx, w))) return rc;
+  const long long n5 = 5 * ctx->G.nnode;
+  if (nsteps == 0) {
+    if (q_in != q_out)
+      NUMA_3CK(ctx, cudaMemcpyAsync(q_out, q_in, n5 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+    return NUMA_OK;
+  }
+  double b[4];
+  const bool ark3 = ctx->scheme == NUMA_SCHEME_ARK3;
+  if (ark3) numa_ark3_tableau(nullptr, nullptr, b);
+  else numa_ark2_tableau(nullptr, nullptr, b);
+  ctx->krylov_last = 0;
+  const double* cur = q_in;
+  for (int s = 0; s < nsteps; ++s) {
+    int it = 0;
+    if ((rc = numa_rhs_explicit(ctx, cur, ctx->R1))) return rc;
+    StageIn in2{cur, {ctx->R1, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    if ((rc = stage3_any(ctx, w, 2, in2, ctx->q2, &it))) return rc;
+    ctx->krylov_last += it;
+    if ((rc = numa_rhs_explicit(ctx, ctx->q2, ctx->R2))) return rc;
+    StageIn in3{cur, {ctx->R1, ctx->R2, nullptr}, {nullptr, ctx->q2, nullptr}};
+    if ((rc = stage3_any(ctx, w, 3, in3, ctx->q3, &it))) return rc;
+    ctx->krylov_last += it;
+    const double* last = ctx->q3;
+    if (ark3) {
+      if ((rc = numa_rhs_explicit(ctx, ctx->q3, ctx->R3))) return rc;
+      StageIn in4{cur, {ctx->R1, ctx->R2, ctx->R3}, {nullptr, ctx->q2, ctx->q3}};
+      if ((rc = stage3_any(ctx, w, 4, in4, ctx->q4, &it))) return rc;
+      ctx->krylov_last += it;
+      last = ctx->q4;
+    }
+    // q^{n+1} = q^n + dt sum_i b_i R(q(i)): the last stage's R goes to t-sized scratch
+    // through the final-update epilogue of the explicit right-hand side
+    if ((rc = numa_rhs_final(ctx, last, cur, q_out, b))) return rc;
+    cur = q_out;
+  }
+  return NUMA_OK;
+}
+
+int numa_imex3d_info(const numa_ctx* ctx, double* l_max, double* lam_bar, double* coeffs,
+                     long long* iters_last_step) {
+  if (!ctx || !ctx->imex3d) return NUMA_ERR_ARG;
+  if (l_max) *l_max = ctx->l_max;
+  if (lam_bar) *lam_bar = ctx->lam_bar;
+  if (coeffs)
+    for (int i = 0; i <= ctx->pbno_order; ++i) coeffs[i] = ctx->pbno_c[i];
+  if (iters_last_step) *iters_last_step = ctx->krylov_last;
+  return NUMA_OK;
+}
+
+}  // extern "C"

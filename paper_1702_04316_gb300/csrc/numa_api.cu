@@ -218,6 +218,7 @@ void free_all(numa_ctx* c) {
   cudaFree(c->d_hoststate);
   cudaFree(c->d_adj);
   cudaFree(c->d_adjtab);
+  cudaFree(c->d_w3);
 }
 
 // Host reference state and the column derivative (Sec. "Equation Set2NC",
@@ -384,6 +385,22 @@ int enqueue_stage(numa_ctx* c, int stage, const double* qn, const void* R1, cons
 
 }  // namespace
 
+int numa_rhs_final(numa_ctx* c, const double* q_last, const double* qn, double* q_out,
+                   const double* b) {
+  RhsEpilogue ef{};
+  const bool four = c->scheme == NUMA_SCHEME_ARK3;
+  ef.mode = four ? 3 : 2;
+  ef.b1dt = b[0] * c->dt;
+  ef.b2dt = b[1] * c->dt;
+  ef.b3dt = b[2] * c->dt;
+  ef.b4dt = four ? b[3] * c->dt : 0.0;
+  ef.u0 = qn;
+  ef.R1 = c->R1;
+  ef.R2 = c->R2;
+  ef.R3 = four ? c->R3 : nullptr;
+  return enqueue_rhs(c, q_last, q_out, ef);
+}
+
 StageCoef numa_stage_coef(const numa_ctx* c, int stage) {
   const ArkTab t = ark_tab(c->scheme);
   StageCoef sc{};
@@ -415,6 +432,21 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   const int refine = opt ? opt->refine_iters : 1;
   const int form = opt ? opt->column_form : NUMA_COLUMN_SCHUR;
   const int scheme = opt ? opt->scheme : NUMA_SCHEME_ARK2;
+  const int imex = opt ? opt->imex : NUMA_IMEX_1D;
+  const int pbno_order = (opt && opt->pbno_order > 0) ? opt->pbno_order : 2;
+  const int kmax = (opt && opt->krylov_max_iters > 0) ? opt->krylov_max_iters : 500;
+  const double ktol = (opt && opt->krylov_tol > 0) ? opt->krylov_tol : 1e-12;
+  const int precond = opt ? opt->precond : NUMA_PRECOND_PBNO;
+  if (precond != NUMA_PRECOND_PBNO && precond != NUMA_PRECOND_COLUMN) {
+    *out = nullptr;
+    return NUMA_ERR_ARG;
+  }
+  if ((imex != NUMA_IMEX_1D && imex != NUMA_IMEX_3D) || pbno_order > NUMA_MAX_PBNO_ORDER ||
+      (imex == NUMA_IMEX_3D && (precision != NUMA_PREC_FP64 || form != NUMA_COLUMN_SCHUR)) ||
+      !std::isfinite(ktol)) {
+    *out = nullptr;
+    return NUMA_ERR_ARG;
+  }
   if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED) || refine < 0 || refine > 8 ||
       (form != NUMA_COLUMN_SCHUR && form != NUMA_COLUMN_STANDARD) ||
       (form == NUMA_COLUMN_STANDARD && precision != NUMA_PREC_FP64) ||
@@ -447,6 +479,11 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   c->F.refine_iters = refine;
   c->F.standard = form == NUMA_COLUMN_STANDARD;
   c->scheme = scheme;
+  c->imex3d = imex == NUMA_IMEX_3D;
+  c->pbno_order = pbno_order;
+  c->krylov_max_iters = kmax;
+  c->krylov_tol = ktol;
+  c->precond = precond;
   c->theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
   {
     // columns per CTA of the column kernels: 64, or 32 when 64 would leave SMs without a
@@ -471,7 +508,9 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   c->F.hb = hb;
   const bool mixed = c->F.mixed;
   const size_t fsz = mixed ? sizeof(float) : sizeof(double);
-  c->factor_bytes = nu * (2 * hb + 1) * G.ncol * fsz;
+  // 3D-IMEX stores column factors only for the column preconditioner
+  const bool need_factors = !c->imex3d || c->precond == NUMA_PRECOND_COLUMN;
+  c->factor_bytes = need_factors ? nu * (2 * hb + 1) * G.ncol * fsz : 0;
   c->work_bytes = mixed ? (size_t)(2 * 5) * G.nnode * sizeof(double) +
                               (size_t)(6 + 2 * 5) * G.nnode * sizeof(float)
                         : (size_t)(1 + (scheme == NUMA_SCHEME_ARK3 ? 6 : 4) * 5) * G.nnode *
@@ -480,7 +519,9 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
     bool ok = cudaMalloc(&c->d_work, c->work_bytes) == cudaSuccess &&
               cudaMalloc(&c->d_status, sizeof(unsigned)) == cudaSuccess &&
               cudaMalloc(&c->d_count, sizeof(unsigned long long)) == cudaSuccess;
-    if (ok && mixed)
+    if (!need_factors) {
+      // 3D-IMEX with the polynomial preconditioner keeps no column factors
+    } else if (ok && mixed)
       ok = cudaMalloc(&c->F.L32, (size_t)G.M * hb * G.ncol * sizeof(float)) == cudaSuccess &&
            cudaMalloc(&c->F.U32, (size_t)G.M * (hb + 1) * G.ncol * sizeof(float)) == cudaSuccess;
     else if (ok)
@@ -575,11 +616,21 @@ int numa_factor_columns(numa_ctx* ctx, double dt) {
   const double lam = ark_tab(ctx->scheme).at[1][1] * dt;   // the one implicit diagonal
   int rc = upload_stage_tables(ctx, lam);
   if (rc) return rc;
+  ctx->dt = dt;
+  ctx->lam = lam;
+  if (ctx->imex3d) {
+    if (ctx->precond == NUMA_PRECOND_COLUMN)
+      NUMA_CK(ctx, launch_factor(ctx->G, ctx->R, lam, ctx->F, ctx->d_status, ctx->stream));
+    ctx->factored = true;            // the stage tables; the preconditioner needs lam
+    if ((rc = numa_imex3d_setup(ctx))) {
+      ctx->factored = false;
+      return rc;
+    }
+    return NUMA_OK;
+  }
   long p = prof_begin(ctx, NUMA_K_FACTOR);
   NUMA_CK(ctx, launch_factor(ctx->G, ctx->R, lam, ctx->F, ctx->d_status, ctx->stream));
   prof_end(ctx, p);
-  ctx->dt = dt;
-  ctx->lam = lam;
   ctx->factored = true;
   return NUMA_OK;
 }
@@ -589,8 +640,8 @@ int numa_solve_columns(numa_ctx* ctx, const double* b, double* x) {
   int rc;
   if ((rc = check_ptr(ctx, b, "b")) || (rc = check_ptr(ctx, x, "x"))) return rc;
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
-  if (ctx->F.standard)
-    return fail(ctx, NUMA_ERR_ARG, "the stand-alone solve is the Schur system (column_form 0)");
+  if (ctx->F.standard || ctx->imex3d)
+    return fail(ctx, NUMA_ERR_ARG, "the stand-alone column solve needs a 1D-IMEX Schur-form context");
   long p = prof_begin(ctx, NUMA_K_SOLVE);
   NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->R, ctx->T, ctx->col_tile, ctx->stream));
   prof_end(ctx, p);
@@ -607,6 +658,7 @@ int numa_imex_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1
     return rc;
   if (stage == 3 && ((rc = check_ptr(ctx, R2, "R2")) || (rc = check_ptr(ctx, q2, "q2")))) return rc;
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  if (ctx->imex3d) return fail(ctx, NUMA_ERR_ARG, "3D-IMEX context: use numa_imex3d_stage");
   return enqueue_stage(ctx, stage, qn, R1, R2, q2, q_out, numa_stage_coef(ctx, stage));
 }
 
@@ -616,6 +668,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
   if ((rc = check_ptr(ctx, q_in, "q_in")) || (rc = check_ptr(ctx, q_out, "q_out"))) return rc;
   if (nsteps < 0) return fail(ctx, NUMA_ERR_ARG, "nsteps < 0");
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  if (ctx->imex3d) return fail(ctx, NUMA_ERR_ARG, "3D-IMEX context: use numa_step_imex3d");
   const long long n5 = 5 * ctx->G.nnode;
   if (nsteps == 0) {
     if (q_in != q_out)
@@ -771,6 +824,7 @@ int numa_column_factors(numa_ctx* ctx, long long col, double* host_out) {
   if (!ctx) return NUMA_ERR_ARG;
   if (!host_out || col < 0 || col >= ctx->G.ncol) return fail(ctx, NUMA_ERR_ARG, "bad column");
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  if (ctx->imex3d) return fail(ctx, NUMA_ERR_ARG, "a 3D-IMEX context stores no column factors");
   const int M = ctx->F.standard ? 3 * ctx->G.M : ctx->G.M;   // unknowns per column
   const int hb = ctx->F.hb, W = 2 * hb + 1;
   std::vector<double> L((size_t)M * hb), U((size_t)M * (hb + 1));
@@ -853,6 +907,7 @@ int numa_query(const numa_ctx* ctx, int what, long long* out) {
     case NUMA_Q_PRECISION: *out = ctx->precision; break;
     case NUMA_Q_COLUMN_FORM: *out = ctx->F.standard ? NUMA_COLUMN_STANDARD : NUMA_COLUMN_SCHUR; break;
     case NUMA_Q_SCHEME: *out = ctx->scheme; break;
+    case NUMA_Q_IMEX: *out = ctx->imex3d ? NUMA_IMEX_3D : NUMA_IMEX_1D; break;
     default: return NUMA_ERR_ARG;
   }
   return NUMA_OK;

@@ -29,6 +29,13 @@ struct numa_ctx {
   double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
   double *R3 = nullptr, *q4 = nullptr;     // ARK3 only
   int scheme = NUMA_SCHEME_ARK2;
+  // 3D-IMEX (Schur form, BiCGstab + polynomial preconditioner)
+  bool imex3d = false;
+  int pbno_order = 2, krylov_max_iters = 500, precond = NUMA_PRECOND_PBNO;
+  double krylov_tol = 1e-12, l_max = 0.0, lam_bar = 0.0;
+  double pbno_c[NUMA_MAX_PBNO_ORDER + 1] = {};
+  long long krylov_last = 0;            // BiCGstab iterations of the last 3D-IMEX step
+  double* d_w3 = nullptr;               // 3D-IMEX workspace (20 x nnode + reduction)
   // mixed-precision form: FP32 stencil fields (6 x nnode) and FP32 R1, R2 (5 x nnode each)
   float *F32 = nullptr, *R1f = nullptr, *R2f = nullptr;
   int precision = NUMA_PREC_FP64;
@@ -54,6 +61,13 @@ struct numa_ctx {
 // record index, or -1); prof_end records the closing event.
 long prof_begin(numa_ctx* c, int kind);
 void prof_end(numa_ctx* c, long idx);
+
+// 3D-IMEX start-up (imex3d.cu): spectrum estimate and preconditioner coefficients.
+int numa_imex3d_setup(numa_ctx* c);
+// q_out = qn + dt sum_i b_i R(q(i)) with the stored R1, R2 (and R3 for four-stage schemes)
+// and R of q_last evaluated in the epilogue of the explicit right-hand side (numa_api.cu).
+int numa_rhs_final(numa_ctx* c, const double* q_last, const double* qn, double* q_out,
+                   const double* b);
 
 // Coefficients of IMEX stage 2 or 3 for the context's dt (Table 1 with b = b~).
 StageCoef numa_stage_coef(const numa_ctx* c, int stage);
