@@ -146,8 +146,8 @@ struct OrderGroup {
   int rhs_threads = 256, col_tile = 64;
   int grid_rhs = 0, grid_col = 0;
   size_t stage_smem = 0;
-  // threads per CTA of the stage: the column tile, at least 128 (the coalesced phases)
-  int stage_threads() const { return std::max(col_tile, 128); }
+  // threads per CTA of the stage: the column tile, at least 256 (the level-parallel steps)
+  int stage_threads() const { return std::max(col_tile, 256); }
 };
 
 struct numa_batch {

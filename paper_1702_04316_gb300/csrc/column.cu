@@ -178,10 +178,10 @@ __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1
                         const RT* __restrict__ R2, const double* __restrict__ q2,
                         double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
                         StageTab tb, int iters, int T, const RT* __restrict__ R3,
-                        const double* __restrict__ q3) {
+                        const double* __restrict__ q3, double* __restrict__ Pp_out, EosSeries eos) {
   extern __shared__ double sm[];
   stage_body<N, NP, MIXED, RT>(blockIdx.x * (long long)T, T, sm, qn, R1, R2, q2, out, G, R, F, sc,
-                               tb, iters, R3, q3);
+                               tb, iters, R3, q3, Pp_out, &eos);
 }
 
 // Fused stage with the standard column system (rows 2 or 3 of Table 1).  Phase 1: the
@@ -245,9 +245,11 @@ size_t stage_smem(int M, int T, bool mixed, int iters) {
   return col_smem_per_level(mixed, iters) * M * T;
 }
 
-// Threads per CTA of the fused stage for T columns: kStageThreadsPerColumn x T (capped at
-// 1024); NUMA_STAGE_THREADS (a multiple of 32, at least T) overrides, for tuning.
-const int kStageMinThreads = 128;
+// Threads per CTA of the fused stage for T columns: at least kStageMinThreads (the coalesced
+// phases and the level-parallel steps of the column phase share them; only the substitutions
+// run one thread per column); NUMA_STAGE_THREADS (a multiple of 32, at least T) overrides,
+// for tuning.
+const int kStageMinThreads = 256;
 
 int stage_threads(int T) {
   static int env = -1;
@@ -277,13 +279,14 @@ template <int N, int NP, bool MIXED, typename RT>
 cudaError_t launch_stage_k(const double* qn, const RT* R1, const RT* R2, const double* q2,
                            double* out, const Geom& G, const RefLev& R, const Factors& F,
                            const StageCoef& sc, const StageTab& tb, int T, int iters,
-                           cudaStream_t s, const RT* R3 = nullptr, const double* q3 = nullptr) {
+                           cudaStream_t s, const RT* R3 = nullptr, const double* q3 = nullptr,
+                           double* Pp_out = nullptr) {
   const size_t smem = stage_smem(G.M, T, MIXED, iters);
   cudaError_t e = cudaFuncSetAttribute(k_stage<N, NP, MIXED, RT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_stage<N, NP, MIXED, RT><<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T), smem, s>>>(
-      qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3);
+      qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3, Pp_out, eos_series());
   return cudaGetLastError();
 }
 
@@ -291,13 +294,15 @@ template <int N>
 cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const void* R2,
                            const double* q2, double* out, const Geom& G, const RefLev& R,
                            const Factors& F, const StageCoef& sc, const StageTab& tb, int T,
-                           bool r_float, cudaStream_t s, const double* R3, const double* q3) {
+                           bool r_float, cudaStream_t s, const double* R3, const double* q3,
+                           double* Pp_out) {
   const int it = F.refine_iters;
   if (stage == 4) {     // four-stage schemes: FP64 Schur form only
     if (F.standard || F.mixed || !R3 || !q3) return cudaErrorInvalidValue;
     return launch_stage_k<N, 3, false>(qn, (const double*)R1, (const double*)R2, q2, out, G, R, F,
-                                       sc, tb, T, it, s, R3, q3);
+                                       sc, tb, T, it, s, R3, q3, Pp_out);
   }
+  if (Pp_out && (F.standard || F.mixed)) return cudaErrorInvalidValue;
   if (F.standard) {
     const size_t smem = (size_t)3 * G.M * T * sizeof(double);
     const unsigned nb = (unsigned)((G.ncol + T - 1) / T);
@@ -329,8 +334,10 @@ cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const vo
   }
   const double* a = (const double*)R1;
   const double* b = (const double*)R2;
-  return stage == 3 ? launch_stage_k<N, 2, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
-                    : launch_stage_k<N, 1, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
+  return stage == 3 ? launch_stage_k<N, 2, false, double>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s,
+                                                  nullptr, nullptr, Pp_out)
+                    : launch_stage_k<N, 1, false, double>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s,
+                                                  nullptr, nullptr, Pp_out);
 }
 
 }  // namespace
@@ -363,9 +370,10 @@ cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, c
 cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void* R2,
                          const double* q2, double* out, const Geom& G, const RefLev& R,
                          Factors F, const StageCoef& sc, const StageTab& tb, int T,
-                         bool r_float, cudaStream_t s, const double* R3, const double* q3) {
+                         bool r_float, cudaStream_t s, const double* R3, const double* q3,
+                         double* Pp_out) {
 #define NUMA_STAGE_CASE(n) \
-  case n: return launch_stage_n<n>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s, R3, q3);
+  case n: return launch_stage_n<n>(stage, qn, R1, R2, q2, out, G, R, F, sc, tb, T, r_float, s, R3, q3, Pp_out);
   switch (G.N) {
     NUMA_STAGE_CASE(1) NUMA_STAGE_CASE(2) NUMA_STAGE_CASE(3) NUMA_STAGE_CASE(4)
     NUMA_STAGE_CASE(5) NUMA_STAGE_CASE(6) NUMA_STAGE_CASE(7) NUMA_STAGE_CASE(8)

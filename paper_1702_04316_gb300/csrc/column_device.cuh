@@ -3,6 +3,7 @@
 // See column.cu for the method.
 #pragma once
 #include "numa_internal.cuh"
+#include "rhs_device.cuh"
 
 namespace numa_dev {
 
@@ -183,7 +184,8 @@ __host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
 // and 3, the first T run phase 2); sm: dynamic shared memory of
 // col_smem_per_level(MIXED, iters) * M * T bytes.
 // NP: previous stages read (1: stage 2; 2: stage 3; 3: stage 4 of a four-stage scheme,
-// with R3 and q3).
+// with R3 and q3).  Pp_out (optional): receives P'(q(i)) (the pre-pass of the next right-hand
+// side fused into phase 3; eos: the series coefficients).
 template <int N, int NP, bool MIXED, typename RT>
 __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
                                            const double* __restrict__ qn,
@@ -192,7 +194,9 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
                                            const Geom& G, const RefLev& R, const Factors& F,
                                            const StageCoef& sc, const StageTab& tb, int iters,
                                            const RT* __restrict__ R3 = nullptr,
-                                           const double* __restrict__ q3 = nullptr) {
+                                           const double* __restrict__ q3 = nullptr,
+                                           double* __restrict__ Pp_out = nullptr,
+                                           const EosSeries* eos = nullptr) {
   const int NT = blockDim.x, M = G.M;
   const long long nn = G.nnode;
   const int ncols = (int)min((long long)T, G.ncol - col0);
@@ -232,19 +236,60 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
   }
   __syncthreads();
 
-  // phase 2
-  if ((int)threadIdx.x < ncols) {
-    const int t = threadIdx.x;
-    double* B = S0 + t;
-    double* Wt = S1 + t;
-    for (int lev = 0; lev < M; ++lev) {     // b = P_e - lam F0z w_a - lam rho0 G0 D_z w_a
-      const double dzw = col_dz<N, double>(Wt, T, lev, R);
-      B[lev * T] = fma(-__ldg(tb.kF + lev), Wt[lev * T], fma(-__ldg(tb.kD + lev), dzw, B[lev * T]));
+  // phase 2: the level-parallel steps on all NT threads (level lev of column c, consecutive
+  // threads on consecutive columns), the triangular substitutions one thread per column.
+  // Every (level, column) value is computed by the same arithmetic as in a thread-per-column
+  // sweep, so the results do not depend on NT.
+  const int tid = threadIdx.x;
+  auto level_loop = [&](auto&& body) {
+    for (int j = tid; j < cnt; j += NT) {
+      const int lev = j / ncols;
+      body(lev, j - lev * ncols);
     }
-    col_solve_refined<N, MIXED>(B, Wt, Tf + t, Td + t, SXd + t, T, M, F, G.ncol, col0 + t, R, tb,
-                                iters);
-    for (int lev = 0; lev < M; ++lev) Wt[lev * T] = col_wp<N, double>(B, T, lev, R, tb);
+  };
+  level_loop([&](int lev, int c) {     // b = P_e - lam F0z w_a - lam rho0 G0 D_z w_a
+    const double dzw = col_dz<N, double>(S1 + c, T, lev, R);
+    const double b = fma(-__ldg(tb.kF + lev), S1[lev * T + c],
+                         fma(-__ldg(tb.kD + lev), dzw, S0[lev * T + c]));
+    S0[lev * T + c] = b;
+    if (MIXED) Tf[lev * T + c] = (float)b;
+  });
+  __syncthreads();
+  if (!MIXED) {
+    if (tid < ncols) col_solve<2 * N, double, double>(S0 + tid, T, M, F.L, F.U, G.ncol, col0 + tid);
+    __syncthreads();
+  } else {
+    // FP32 solve, then `iters` sweeps of FP64 refinement (r = b - S X with the FP64
+    // matrix-free operator, correction solved in FP32); S1 is the scratch for w_p(X)
+    if (tid < ncols) col_solve<2 * N, float, float>(Tf + tid, T, M, F.L32, F.U32, G.ncol, col0 + tid);
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+      const bool first = (it == 0), last = (it == iters - 1);
+      level_loop([&](int lev, int c) {
+        S1[lev * T + c] = first ? col_wp<N, float>(Tf + c, T, lev, R, tb)
+                                : col_wp<N, double>(SXd + c, T, lev, R, tb);
+      });
+      __syncthreads();
+      level_loop([&](int lev, int c) {
+        const double xl = first ? (double)Tf[lev * T + c] : SXd[lev * T + c];
+        Td[lev * T + c] = (float)col_residual<N>(S0 + c, S1 + c, T, lev, R, tb, xl);
+      });
+      __syncthreads();
+      if (tid < ncols) col_solve<2 * N, float, float>(Td + tid, T, M, F.L32, F.U32, G.ncol, col0 + tid);
+      __syncthreads();
+      level_loop([&](int lev, int c) {
+        const double x = (first ? (double)Tf[lev * T + c] : SXd[lev * T + c]) + (double)Td[lev * T + c];
+        if (last) S0[lev * T + c] = x;
+        else SXd[lev * T + c] = x;
+      });
+      __syncthreads();
+    }
+    if (iters == 0) {
+      level_loop([&](int lev, int c) { S0[lev * T + c] = (double)Tf[lev * T + c]; });
+      __syncthreads();
+    }
   }
+  level_loop([&](int lev, int c) { S1[lev * T + c] = col_wp<N, double>(S0 + c, T, lev, R, tb); });
   __syncthreads();
 
   // phase 3
@@ -272,6 +317,9 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     out[orr] = o_r;
     out[ow] = o_w;
     out[oth] = o_t;
+    // P'(q(i)) for the next right-hand side, by the arithmetic of its pre-pass (eos_node)
+    if (Pp_out)
+      Pp_out[g] = R.P0[lev] * eos_rel(o_r, o_t, R.inv_rho0[lev], R.inv_theta0[lev], NUMA_GAMMA, *eos);
   }
 }
 

@@ -357,12 +357,16 @@ int check_ptr(numa_ctx* c, const void* p, const char* name) {
 
 // One right-hand side.  FP64 method: P' pre-pass, FP64 kernel.  Mixed form: FP64 P' and
 // FP32 field copies, FP32 kernel; in mode 0, out32 receives the FP32 tendencies.
+// pp_ready: c->Pp already holds P'(q) (written by the stage that produced q).
 int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep,
-                float* out32 = nullptr) {
-  long p = prof_begin(c, NUMA_K_PRESSURE);
-  if (c->precision == NUMA_PREC_MIXED) NUMA_CK(c, launch_prep32(q, c->F32, c->G, c->R, c->stream));
-  else NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
-  prof_end(c, p);
+                float* out32 = nullptr, bool pp_ready = false) {
+  long p = -1;
+  if (!pp_ready || c->precision == NUMA_PREC_MIXED) {
+    p = prof_begin(c, NUMA_K_PRESSURE);
+    if (c->precision == NUMA_PREC_MIXED) NUMA_CK(c, launch_prep32(q, c->F32, c->G, c->R, c->stream));
+    else NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
+    prof_end(c, p);
+  }
   p = prof_begin(c, NUMA_K_RHS);
   if (c->precision == NUMA_PREC_MIXED)
     NUMA_CK(c, launch_rhs32(q, c->F32, out32, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep,
@@ -374,13 +378,20 @@ int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep
 }
 
 // r_float: R1, R2 are the mixed form's internal FP32 tendencies (else FP64 arrays).
+// Pp_out: optional, receives P'(stage value) (FP64 Schur form).
 int enqueue_stage(numa_ctx* c, int stage, const double* qn, const void* R1, const void* R2,
-                  const double* q2, double* out, const StageCoef& sc, bool r_float = false) {
+                  const double* q2, double* out, const StageCoef& sc, bool r_float = false,
+                  double* Pp_out = nullptr) {
   long p = prof_begin(c, NUMA_K_STAGE);
   NUMA_CK(c, launch_stage(stage, qn, R1, R2, q2, out, c->G, c->R, c->F, sc, c->T, c->col_tile,
-                          r_float, c->stream));
+                          r_float, c->stream, nullptr, nullptr, Pp_out));
   prof_end(c, p);
   return NUMA_OK;
+}
+
+// The stage can hand the next right-hand side its P' (FP64 Schur-form 1D-IMEX).
+bool fuse_pressure(const numa_ctx* c) {
+  return c->precision == NUMA_PREC_FP64 && !c->F.standard && !c->imex3d;
 }
 
 }  // namespace
@@ -685,13 +696,14 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
     for (int s = 0; s < nsteps; ++s) {
       RhsEpilogue e0{};
       if ((rc = enqueue_rhs(ctx, cur, ctx->R1, e0))) return rc;
-      if ((rc = enqueue_stage(ctx, 2, cur, ctx->R1, nullptr, nullptr, ctx->q2, s2))) return rc;
-      if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0))) return rc;
-      if ((rc = enqueue_stage(ctx, 3, cur, ctx->R1, ctx->R2, ctx->q2, ctx->q3, s3))) return rc;
-      if ((rc = enqueue_rhs(ctx, ctx->q3, ctx->R3, e0))) return rc;
+      if ((rc = enqueue_stage(ctx, 2, cur, ctx->R1, nullptr, nullptr, ctx->q2, s2, false, ctx->Pp))) return rc;
+      if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0, nullptr, true))) return rc;
+      if ((rc = enqueue_stage(ctx, 3, cur, ctx->R1, ctx->R2, ctx->q2, ctx->q3, s3, false, ctx->Pp))) return rc;
+      if ((rc = enqueue_rhs(ctx, ctx->q3, ctx->R3, e0, nullptr, true))) return rc;
       long p = prof_begin(ctx, NUMA_K_STAGE);
       NUMA_CK(ctx, launch_stage(4, cur, ctx->R1, ctx->R2, ctx->q2, ctx->q4, ctx->G, ctx->R, ctx->F,
-                                s4, ctx->T, ctx->col_tile, false, ctx->stream, ctx->R3, ctx->q3));
+                                s4, ctx->T, ctx->col_tile, false, ctx->stream, ctx->R3, ctx->q3,
+                                ctx->Pp));
       prof_end(ctx, p);
       RhsEpilogue ef{};
       ef.mode = 3;
@@ -703,7 +715,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
       ef.R1 = ctx->R1;
       ef.R2 = ctx->R2;
       ef.R3 = ctx->R3;
-      if ((rc = enqueue_rhs(ctx, ctx->q4, q_out, ef))) return rc;
+      if ((rc = enqueue_rhs(ctx, ctx->q4, q_out, ef, nullptr, true))) return rc;
       cur = q_out;
     }
     return NUMA_OK;
@@ -711,12 +723,14 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
   void* R1 = mixed ? (void*)ctx->R1f : (void*)ctx->R1;
   void* R2 = mixed ? (void*)ctx->R2f : (void*)ctx->R2;
   const double* cur = q_in;
+  const bool fuse = fuse_pressure(ctx);
+  double* Pp_next = fuse ? ctx->Pp : nullptr;
   for (int s = 0; s < nsteps; ++s) {
     RhsEpilogue e0{};
     if ((rc = enqueue_rhs(ctx, cur, ctx->R1, e0, ctx->R1f))) return rc;
-    if ((rc = enqueue_stage(ctx, 2, cur, R1, nullptr, nullptr, ctx->q2, s2, mixed))) return rc;
-    if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0, ctx->R2f))) return rc;
-    if ((rc = enqueue_stage(ctx, 3, cur, R1, R2, ctx->q2, ctx->q3, s3, mixed))) return rc;
+    if ((rc = enqueue_stage(ctx, 2, cur, R1, nullptr, nullptr, ctx->q2, s2, mixed, Pp_next))) return rc;
+    if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0, ctx->R2f, fuse))) return rc;
+    if ((rc = enqueue_stage(ctx, 3, cur, R1, R2, ctx->q2, ctx->q3, s3, mixed, Pp_next))) return rc;
     RhsEpilogue ef{};
     ef.mode = 2;
     ef.b1dt = t.b[0] * ctx->dt;
@@ -725,7 +739,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
     ef.u0 = cur;
     ef.R1 = R1;
     ef.R2 = R2;
-    if ((rc = enqueue_rhs(ctx, ctx->q3, q_out, ef))) return rc;
+    if ((rc = enqueue_rhs(ctx, ctx->q3, q_out, ef, nullptr, fuse))) return rc;
     cur = q_out;
   }
   return NUMA_OK;

@@ -149,12 +149,13 @@ cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
 cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, const RefLev& R,
                          const StageTab& tb, int T, cudaStream_t s);
 // stage i in {2, 3, 4} reads R1..R(i-1) and q2..q(i-1); stage 4 (four-stage schemes) is
-// FP64 Schur form only and takes R3, q3.
+// FP64 Schur form only and takes R3, q3.  Pp_out (FP64 Schur form only; NULL to skip)
+// receives P'(q(i)), the equation-of-state pre-pass of the next right-hand side.
 cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void* R2,
                          const double* q2, double* out, const Geom& G, const RefLev& R,
                          Factors F, const StageCoef& sc, const StageTab& tb, int T,
                          bool r_float, cudaStream_t s, const double* R3 = nullptr,
-                         const double* q3 = nullptr);
+                         const double* q3 = nullptr, double* Pp_out = nullptr);
 size_t stage_smem_bytes(int M, int T, bool mixed, int iters);
 
 // misc.cu
