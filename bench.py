@@ -330,6 +330,13 @@ def run_gpu(args):
     gm.close()
     out["imex_c15_mixed"] = {"sim_s_per_wall_s": round(sps(dt15, ms_mx), 3), "ms_per_step": round(ms_mx, 4),
                              "form": "FP32 RHS over FP64 reference, FP32 LU + 1 FP64 refinement sweep"}
+    g32 = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dt15, precision="rhs32")
+    for _ in range(args.warmup):
+        g32.step_imex1d(q0, q1, 1)
+    ms_32 = time_steps(lambda: g32.step_imex1d(q0, q1, 1), args.steps) / args.steps
+    g32.close()
+    out["imex_c15_rhs32"] = {"sim_s_per_wall_s": round(sps(dt15, ms_32), 3), "ms_per_step": round(ms_32, 4),
+                             "form": "FP32 RHS over FP64 reference, FP64 column LU"}
     # ARK3 (ARK3(2)4L[2]SA: four stages, 4 RHS + 3 column stages per step), same workload
     ark3 = {}
     for C, dtc in ((15, dt15), (150, dt150)):
@@ -380,7 +387,7 @@ def precision_form(pkg, torch, steps, warmup, nsteps_err=200):
                        "HEVI 1D-IMEX ARK2 at C=15",
            "dt_s": round(dt, 4), "C_H": round(C_S * dt / (fmin * L / nex), 3), "amp_K": round(amp, 4)}
     res = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "rhs32"):
         g = pkg.Numa(nex, nex, nez, L, L, Lz, n, dt, precision=prec, refine_iters=1)
         lev = g.reference_levels()
         h = L / nex
@@ -405,8 +412,10 @@ def precision_form(pkg, torch, steps, warmup, nsteps_err=200):
         g.close()
     ms64, q64, fb64 = res["fp64"]
     msmx, qmx, fbmx = res["mixed"]
-    def rel(f):
-        return float(torch.linalg.norm(qmx[f] - q64[f]) / torch.linalg.norm(q64[f]))
+    ms32, q32, fb32 = res["rhs32"]
+    def rel(f, q=None):
+        q = qmx if q is None else q
+        return float(torch.linalg.norm(q[f] - q64[f]) / torch.linalg.norm(q64[f]))
     out.update({
         "fp64": {"ms_per_step": round(ms64, 4), "sim_s_per_wall_s": round(dt / (ms64 / 1e3), 2),
                  "factor_bytes": fb64},
@@ -414,7 +423,13 @@ def precision_form(pkg, torch, steps, warmup, nsteps_err=200):
                   "factor_bytes": fbmx, "refine_iters": 1},
         "speedup_mixed_vs_fp64": round(ms64 / msmx, 3),
         "rel_l2_vs_fp64_after_%d_steps" % nsteps_err: {"theta": rel(4), "w": rel(3), "rho": rel(0)},
-        "finite": bool(torch.isfinite(qmx).all().item() and torch.isfinite(q64).all().item()),
+        "rhs32": {"ms_per_step": round(ms32, 4), "sim_s_per_wall_s": round(dt / (ms32 / 1e3), 2),
+                  "factor_bytes": fb32, "speedup_vs_fp64": round(ms64 / ms32, 3),
+                  "form": "FP32 RHS, FP64 column factors and solve",
+                  "rel_l2_vs_fp64_after_%d_steps" % nsteps_err:
+                      {"theta": rel(4, q32), "w": rel(3, q32), "rho": rel(0, q32)}},
+        "finite": bool(torch.isfinite(qmx).all().item() and torch.isfinite(q64).all().item()
+                       and torch.isfinite(q32).all().item()),
     })
     return out
 

@@ -332,6 +332,12 @@ cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const vo
     return stage == 3 ? launch_stage_k<N, 2, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
                       : launch_stage_k<N, 1, true>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
   }
+  if (r_float) {         // FP32 tendencies with FP64 factors (NUMA_PREC_RHS32)
+    const float* a = (const float*)R1;
+    const float* b = (const float*)R2;
+    return stage == 3 ? launch_stage_k<N, 2, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s)
+                      : launch_stage_k<N, 1, false>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s);
+  }
   const double* a = (const double*)R1;
   const double* b = (const double*)R2;
   return stage == 3 ? launch_stage_k<N, 2, false, double>(qn, a, b, q2, out, G, R, F, sc, tb, T, it, s,

@@ -361,14 +361,15 @@ int check_ptr(numa_ctx* c, const void* p, const char* name) {
 int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep,
                 float* out32 = nullptr, bool pp_ready = false) {
   long p = -1;
-  if (!pp_ready || c->precision == NUMA_PREC_MIXED) {
+  const bool rhs32 = c->precision != NUMA_PREC_FP64;
+  if (!pp_ready || rhs32) {
     p = prof_begin(c, NUMA_K_PRESSURE);
-    if (c->precision == NUMA_PREC_MIXED) NUMA_CK(c, launch_prep32(q, c->F32, c->G, c->R, c->stream));
+    if (rhs32) NUMA_CK(c, launch_prep32(q, c->F32, c->G, c->R, c->stream));
     else NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
     prof_end(c, p);
   }
   p = prof_begin(c, NUMA_K_RHS);
-  if (c->precision == NUMA_PREC_MIXED)
+  if (rhs32)
     NUMA_CK(c, launch_rhs32(q, c->F32, out32, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep,
                             c->stream));
   else
@@ -458,7 +459,8 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
     *out = nullptr;
     return NUMA_ERR_ARG;
   }
-  if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED) || refine < 0 || refine > 8 ||
+  if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED && precision != NUMA_PREC_RHS32) ||
+      refine < 0 || refine > 8 ||
       (form != NUMA_COLUMN_SCHUR && form != NUMA_COLUMN_STANDARD) ||
       (form == NUMA_COLUMN_STANDARD && precision != NUMA_PREC_FP64) ||
       (scheme != NUMA_SCHEME_ARK2 && scheme != NUMA_SCHEME_ARK3) ||
@@ -517,12 +519,13 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   const int hb = c->F.standard ? 3 * N + 1 : 2 * N;      // half-bandwidth
   const size_t nu = c->F.standard ? 3 * (size_t)G.M : (size_t)G.M;   // unknowns per column
   c->F.hb = hb;
-  const bool mixed = c->F.mixed;
+  const bool mixed = c->F.mixed;                         // FP32 factors
+  const bool rhs32 = precision != NUMA_PREC_FP64;        // FP32 right-hand side
   const size_t fsz = mixed ? sizeof(float) : sizeof(double);
   // 3D-IMEX stores column factors only for the column preconditioner
   const bool need_factors = !c->imex3d || c->precond == NUMA_PRECOND_COLUMN;
   c->factor_bytes = need_factors ? nu * (2 * hb + 1) * G.ncol * fsz : 0;
-  c->work_bytes = mixed ? (size_t)(2 * 5) * G.nnode * sizeof(double) +
+  c->work_bytes = rhs32 ? (size_t)(2 * 5) * G.nnode * sizeof(double) +
                               (size_t)(6 + 2 * 5) * G.nnode * sizeof(float)
                         : (size_t)(1 + (scheme == NUMA_SCHEME_ARK3 ? 6 : 4) * 5) * G.nnode *
                               sizeof(double);
@@ -557,7 +560,7 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   }
   if (rc == NUMA_OK) {
     const long long n5 = 5 * G.nnode;
-    if (mixed) {
+    if (rhs32) {
       c->R1 = c->R2 = nullptr;
       c->Pp = nullptr;
       c->q2 = c->d_work;
@@ -609,7 +612,7 @@ int numa_rhs_explicit(numa_ctx* ctx, const double* q, double* rhs) {
   if (q == rhs) return fail(ctx, NUMA_ERR_ARG, "q and rhs must not overlap");
   RhsEpilogue ep{};
   ep.mode = 0;
-  if (ctx->precision == NUMA_PREC_MIXED) {
+  if (ctx->precision != NUMA_PREC_FP64) {
     long p = prof_begin(ctx, NUMA_K_PRESSURE);
     NUMA_CK(ctx, launch_prep32(q, ctx->F32, ctx->G, ctx->R, ctx->stream));
     prof_end(ctx, p);
@@ -689,7 +692,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
   }
   const ArkTab t = ark_tab(ctx->scheme);
   const StageCoef s2 = numa_stage_coef(ctx, 2), s3 = numa_stage_coef(ctx, 3);
-  const bool mixed = ctx->precision == NUMA_PREC_MIXED;
+  const bool mixed = ctx->precision != NUMA_PREC_FP64;    // FP32 tendencies
   if (t.s == 4) {       // ARK3: four stages, FP64 Schur form
     const StageCoef s4 = numa_stage_coef(ctx, 4);
     const double* cur = q_in;

@@ -103,3 +103,38 @@ def test_mixed_rk35_run():
     out = g.step_explicit_rk(torch.from_numpy(q0).cuda(), dt, g.empty_state(), 10).cpu().numpy()
     e = rel_l2(out, ref)
     assert np.all(e[[0, 3, 4]] < 1e-4), e
+
+
+# ---- FP32 right-hand side with the FP64 column factors (NUMA_PREC_RHS32) ------------------
+def ctx32(case, dt=0.0):
+    import paper_1702_04316_gb300 as pkg
+    nex, ney, nez, Lx, Ly, Lz, N = case.args
+    return pkg.Numa(nex, ney, nez, Lx, Ly, Lz, N, dt, 300.0, case.n_bv, precision="rhs32")
+
+
+def test_rhs32_factors_are_fp64():
+    import paper_1702_04316_gb300 as pkg
+    case = Case(3, 3, 3, 4, 6e3, 6e3, 6e3)
+    dt = case.dt_for(15.0)
+    a = ctx32(case, dt)
+    b = pkg.Numa(*case.args[:6], case.args[6], dt)
+    assert a.query(pkg.Q_PRECISION) == 2
+    assert a.query(pkg.Q_FACTOR_BYTES) == b.query(pkg.Q_FACTOR_BYTES)
+    np.testing.assert_array_equal(a.column_factors(7), b.column_factors(7))
+
+
+@pytest.mark.parametrize("C,L", [(15, 300e3), (150, 3000e3)])
+def test_rhs32_run_error_is_stated(C, L):
+    """Ten steps on the horizontally wide box: only the FP32 right-hand sides differ from
+    the FP64 method; errors of the same size as the mixed form's."""
+    import torch
+    from oracle import ark2
+    case = Case(4, 4, 4, 4, L, L, 10e3)
+    dt = case.dt_for(C)
+    q0 = case.state(31, kind="balanced")
+    ref = ark2.HEVI(case.mesh, case.col, dt).step(q0, 10)
+    g = ctx32(case, dt)
+    out = g.step_imex1d(torch.from_numpy(q0).cuda(), g.empty_state(), 10).cpu().numpy()
+    e = rel_l2(out, ref)
+    print("rhs32 relative L2 after 10 steps, C=%d:" % C, e)
+    assert np.all(e[[0, 3, 4]] < 1e-4), e
