@@ -337,6 +337,25 @@ def run_gpu(args):
     g32.close()
     out["imex_c15_rhs32"] = {"sim_s_per_wall_s": round(sps(dt15, ms_32), 3), "ms_per_step": round(ms_32, 4),
                              "form": "FP32 RHS over FP64 reference, FP64 column LU"}
+    gdf = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dt15, precision="df")
+    for _ in range(args.warmup):
+        gdf.step_imex1d(q0, q1, 1)
+    ms_df = time_steps(lambda: gdf.step_imex1d(q0, q1, 1), args.steps) / args.steps
+    gdf.profile(True)
+    gdf.step_imex1d(q0, q1, 1)
+    t_df, n_df = gdf.profile_read(pkg.K_RHS)
+    t_pd, n_pd = gdf.profile_read(pkg.K_PRESSURE)
+    gdf.profile(False)
+    r64 = g.rhs_explicit(q0)
+    rdf = gdf.rhs_explicit(q0)
+    rel = [float(torch.linalg.norm(rdf[f] - r64[f]) / torch.linalg.norm(r64[f])) for f in range(5)]
+    gdf.close()
+    out["imex_c15_df"] = {"sim_s_per_wall_s": round(sps(dt15, ms_df), 3), "ms_per_step": round(ms_df, 4),
+                          "rhs_ms_per_launch": round(t_df / max(n_df, 1), 4),
+                          "prepass_ms_per_launch": round(t_pd / max(n_pd, 1), 4),
+                          "rhs_rel_l2_vs_fp64_kernel": [float("%.3g" % x) for x in rel],
+                          "form": "double-float (FP32-pair) derivative sums, FP64 pointwise terms, "
+                                  "EOS, column LU and state"}
     # ARK3 (ARK3(2)4L[2]SA: four stages, 4 RHS + 3 column stages per step), same workload
     ark3 = {}
     for C, dtc in ((15, dt15), (150, dt150)):

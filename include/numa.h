@@ -78,7 +78,7 @@ enum {
   NUMA_Q_WORKSPACE_BYTES = 6, /* bytes of step workspace */
   NUMA_Q_FACTORED = 7,      /* 1 once numa_factor_columns succeeded */
   NUMA_Q_N = 8,             /* polynomial order */
-  NUMA_Q_PRECISION = 9,     /* NUMA_PREC_FP64, NUMA_PREC_MIXED or NUMA_PREC_RHS32 */
+  NUMA_Q_PRECISION = 9,     /* NUMA_PREC_FP64, NUMA_PREC_MIXED, NUMA_PREC_RHS32 or NUMA_PREC_DF */
   NUMA_Q_COLUMN_FORM = 10,  /* NUMA_COLUMN_SCHUR or NUMA_COLUMN_STANDARD */
   NUMA_Q_SCHEME = 11,       /* NUMA_SCHEME_ARK2 or NUMA_SCHEME_ARK3 */
   NUMA_Q_IMEX = 12          /* NUMA_IMEX_1D or NUMA_IMEX_3D */
@@ -96,6 +96,12 @@ enum {
  *            is faster than FP32 substitutions plus an FP64 refinement residual (the
  *            substitutions are latency bound and the residual costs about what the FP64
  *            solve costs), so this keeps the FP32 part where it pays.
+ *            NUMA_PREC_DF -- the right-hand side's DSS'd derivative sums in double-float
+ *            arithmetic (each value an unevaluated sum of two FP32 numbers, about 48
+ *            significant bits; products by Dekker's method, sums by Knuth's TwoSum), its
+ *            pointwise terms, the equation of state, the column solves and the state in
+ *            FP64.  Accurate to the FP64 method's parity bars; it moves the bulk of the
+ *            right-hand side off GB300's narrow FP64 pipe onto the FP32 pipe.
  * refine_iters: FP64 refinement sweeps per solve in the mixed form (0..8; numa_init_ex with
  *               opt = NULL uses 1).
  * column_form: NUMA_COLUMN_SCHUR (default) -- the paper's Schur-complement column system in
@@ -130,7 +136,7 @@ enum {
  *          matrix of the same lam, factored and stored per column as for 1D-IMEX, solved
  *          exactly as a vertical-line preconditioner (a choice beyond the paper: the stiffest
  *          part of S is vertical when C_V > C_H; the converged solution is the same). */
-enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1, NUMA_PREC_RHS32 = 2 };
+enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1, NUMA_PREC_RHS32 = 2, NUMA_PREC_DF = 3 };
 enum { NUMA_COLUMN_SCHUR = 0, NUMA_COLUMN_STANDARD = 1 };
 enum { NUMA_SCHEME_ARK2 = 0, NUMA_SCHEME_ARK3 = 1 };
 enum { NUMA_IMEX_1D = 0, NUMA_IMEX_3D = 1 };

@@ -20,7 +20,7 @@ ERRORS = {
 }
 Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_FACTORED, Q_N, \
     Q_PRECISION, Q_COLUMN_FORM, Q_SCHEME, Q_IMEX = range(13)
-PRECISIONS = {"fp64": 0, "mixed": 1, "rhs32": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1, "rhs32": 2, "df": 3}
 COLUMN_FORMS = {"schur": 0, "standard": 1}
 SCHEMES = {"ark2": 0, "ark3": 1}
 IMEX = {"1d": 0, "3d": 1}

@@ -219,6 +219,7 @@ void free_all(numa_ctx* c) {
   cudaFree(c->d_adj);
   cudaFree(c->d_adjtab);
   cudaFree(c->d_w3);
+  cudaFree(c->F2);
 }
 
 // Host reference state and the column derivative (Sec. "Equation Set2NC",
@@ -361,15 +362,19 @@ int check_ptr(numa_ctx* c, const void* p, const char* name) {
 int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep,
                 float* out32 = nullptr, bool pp_ready = false) {
   long p = -1;
-  const bool rhs32 = c->precision != NUMA_PREC_FP64;
-  if (!pp_ready || rhs32) {
+  const bool rhs32 = c->precision == NUMA_PREC_MIXED || c->precision == NUMA_PREC_RHS32;
+  const bool df = c->precision == NUMA_PREC_DF;
+  if (!pp_ready || rhs32 || df) {
     p = prof_begin(c, NUMA_K_PRESSURE);
     if (rhs32) NUMA_CK(c, launch_prep32(q, c->F32, c->G, c->R, c->stream));
+    else if (df) NUMA_CK(c, launch_prep_df(q, c->F2, c->G, c->R, c->stream));
     else NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
     prof_end(c, p);
   }
   p = prof_begin(c, NUMA_K_RHS);
-  if (rhs32)
+  if (df)
+    NUMA_CK(c, launch_rhs_df(q, c->F2, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep, c->stream));
+  else if (rhs32)
     NUMA_CK(c, launch_rhs32(q, c->F32, out32, out, c->d_perm, c->nperm, c->G, c->C, c->R, ep,
                             c->stream));
   else
@@ -459,7 +464,8 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
     *out = nullptr;
     return NUMA_ERR_ARG;
   }
-  if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED && precision != NUMA_PREC_RHS32) ||
+  if ((precision != NUMA_PREC_FP64 && precision != NUMA_PREC_MIXED && precision != NUMA_PREC_RHS32 &&
+       precision != NUMA_PREC_DF) ||
       refine < 0 || refine > 8 ||
       (form != NUMA_COLUMN_SCHUR && form != NUMA_COLUMN_STANDARD) ||
       (form == NUMA_COLUMN_STANDARD && precision != NUMA_PREC_FP64) ||
@@ -520,7 +526,7 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   const size_t nu = c->F.standard ? 3 * (size_t)G.M : (size_t)G.M;   // unknowns per column
   c->F.hb = hb;
   const bool mixed = c->F.mixed;                         // FP32 factors
-  const bool rhs32 = precision != NUMA_PREC_FP64;        // FP32 right-hand side
+  const bool rhs32 = precision == NUMA_PREC_MIXED || precision == NUMA_PREC_RHS32;  // FP32 RHS
   const size_t fsz = mixed ? sizeof(float) : sizeof(double);
   // 3D-IMEX stores column factors only for the column preconditioner
   const bool need_factors = !c->imex3d || c->precond == NUMA_PRECOND_COLUMN;
@@ -579,7 +585,13 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
         c->q4 = c->R3 + n5;
       }
     }
-    if (cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = NUMA_ERR_CUDA;
+    if (precision == NUMA_PREC_DF &&
+        cudaMalloc(&c->F2, (size_t)6 * G.nnode * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      c->F2 = nullptr;
+      rc = NUMA_ERR_OOM;
+    }
+    if (rc == NUMA_OK && cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = NUMA_ERR_CUDA;
   }
   if (rc == NUMA_OK && dt > 0) rc = numa_factor_columns(c, dt);
   if (rc == NUMA_OK) rc = (cudaDeviceSynchronize() == cudaSuccess) ? NUMA_OK : NUMA_ERR_CUDA;
@@ -612,7 +624,7 @@ int numa_rhs_explicit(numa_ctx* ctx, const double* q, double* rhs) {
   if (q == rhs) return fail(ctx, NUMA_ERR_ARG, "q and rhs must not overlap");
   RhsEpilogue ep{};
   ep.mode = 0;
-  if (ctx->precision != NUMA_PREC_FP64) {
+  if (ctx->precision == NUMA_PREC_MIXED || ctx->precision == NUMA_PREC_RHS32) {
     long p = prof_begin(ctx, NUMA_K_PRESSURE);
     NUMA_CK(ctx, launch_prep32(q, ctx->F32, ctx->G, ctx->R, ctx->stream));
     prof_end(ctx, p);
@@ -692,7 +704,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
   }
   const ArkTab t = ark_tab(ctx->scheme);
   const StageCoef s2 = numa_stage_coef(ctx, 2), s3 = numa_stage_coef(ctx, 3);
-  const bool mixed = ctx->precision != NUMA_PREC_FP64;    // FP32 tendencies
+  const bool mixed = ctx->precision == NUMA_PREC_MIXED || ctx->precision == NUMA_PREC_RHS32;  // FP32 tendencies
   if (t.s == 4) {       // ARK3: four stages, FP64 Schur form
     const StageCoef s4 = numa_stage_coef(ctx, 4);
     const double* cur = q_in;

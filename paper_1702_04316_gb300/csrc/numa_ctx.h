@@ -38,6 +38,8 @@ struct numa_ctx {
   double* d_w3 = nullptr;               // 3D-IMEX workspace (20 x nnode + reduction)
   // mixed-precision form: FP32 stencil fields (6 x nnode) and FP32 R1, R2 (5 x nnode each)
   float *F32 = nullptr, *R1f = nullptr, *R2f = nullptr;
+  // double-float form: (hi, lo) FP32 pairs of the six stencil fields (6 x nnode)
+  float2* F2 = nullptr;
   int precision = NUMA_PREC_FP64;
   int* d_perm = nullptr;        // class-sorted thread order of the right-hand side
   long long nperm = 0;

@@ -132,6 +132,14 @@ cudaError_t launch_rhs(const double* q, const double* Pp, double* out, const int
 // and R2 given as float arrays).
 cudaError_t launch_prep32(const double* q, float* F32, const Geom& G, const RefLev& R,
                           cudaStream_t s);
+// rhs_df.cu: the double-float variant -- P' and the (hi, lo) FP32 pairs of the six stencil
+// fields (6 x nnode float2), then the right-hand side with double-float derivative sums and
+// FP64 pointwise terms (epilogue modes as launch_rhs, FP64 arrays).
+cudaError_t launch_prep_df(const double* q, float2* F2, const Geom& G, const RefLev& R,
+                           cudaStream_t s);
+cudaError_t launch_rhs_df(const double* q, const float2* F2, double* out, const int* perm,
+                          long long nthreads, const Geom& G, const Coef3& C, const RefLev& R,
+                          const RhsEpilogue& ep, cudaStream_t s);
 cudaError_t launch_rhs32(const double* q, const float* F32, float* out32, double* out,
                          const int* perm, long long nthreads, const Geom& G, const Coef3& C,
                          const RefLev& R, const RhsEpilogue& ep, cudaStream_t s);

@@ -131,45 +131,24 @@ __device__ __forceinline__ void axis_derivs(const RT* const* F, long long g, lon
   }
 }
 
-// One node of the right-hand side (thread index tid of the class-sorted order, or of the
-// natural order when perm is NULL).  sD, sDl, sDr: the three axes' derivative rows
-// (axis a at sD + a*(N+1)^2, sDl + a*(N+1), sDr + a*(N+1)), normally in shared memory.
-// RT: type of the stencil fields and of the arithmetic (double: the FP64 method, fields =
-// the state and P'; float: the mixed-precision form, fields = the FP32 copies from
-// k_prep32).  fld holds rho', u, v, w, theta' (stride nnode), fp holds P'.  OT: type
-// written in mode 0.  Modes 1 and 2 read and write the FP64 state; R1, R2 are OT arrays.
-template <int N, typename RT, typename OT>
-__device__ __forceinline__ void rhs_node(long long tid, const double* __restrict__ q,
-                                         const RT* __restrict__ fld, const RT* __restrict__ fp,
-                                         OT* out0, double* out, const int* __restrict__ perm,
-                                         long long nthreads, const Geom& G, const RefLev& R,
-                                         const RhsEpilogue& ep, const RT* sD, const RT* sDl,
-                                         const RT* sDr) {
-  constexpr int Nq = N + 1;
-  if (tid >= nthreads) return;
-  const int gi = perm ? perm[tid] : (int)tid;
-  if (gi < 0) return;                       // padding of a class group
-  const long long g = gi;
-  const long long nn = G.nnode;
-  const long long col = g / G.M;
-  const int iz = (int)(g - col * G.M);
-  const int iy = (int)(col / G.nxg);
-  const int ix = (int)(col - (long long)iy * G.nxg);
-  const long long sxs = G.M, sys = (long long)G.nxg * G.M;
+// The Set2NC tendencies at node g from the DSS'd derivatives of the six fields (dx, dy, dz:
+// rho', u, v, w, theta', P'), and the epilogue.  RT: arithmetic type; fld: the fields read at
+// g (rho', u, v, w; stride nnode); OT: type written in mode 0.  Modes 1 and 2 read and
+// write the FP64 state; R1, R2 are OT arrays.
+template <typename RT, typename OT, typename FT>
+__device__ __forceinline__ void rhs_point(long long g, int ix, int iy, int iz, const double* __restrict__ q,
+                                          const FT* __restrict__ fld, const RT* dx, const RT* dy,
+                                          const RT* dz, OT* out0, double* out, const Geom& G,
+                                          const RefLev& R, const RhsEpilogue& ep);
 
-  // fields: 0 rho', 1 u, 2 v, 3 w, 4 theta', 5 P'
-  const RT* Fld[6] = {fld, fld + nn, fld + 2 * nn, fld + 3 * nn, fld + 4 * nn, fp};
-  RT dx[6], dy[6], dz[6];
-  {
-    Taps<N, RT> T;
-    int cls = axis_taps<N, RT>(ix, G.nex, sD, sDl, sDr, T);
-    axis_derivs<N, RT>(Fld, g, sxs, cls, T, dx);
-    cls = axis_taps<N, RT>(iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
-    axis_derivs<N, RT>(Fld, g, sys, cls, T, dy);
-    cls = axis_taps<N, RT>(iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
-    axis_derivs<N, RT>(Fld, g, 1, cls, T, dz);
-  }
-  const RT r_ = fld[g], u_ = fld[nn + g], v_ = fld[2 * nn + g], w_ = fld[3 * nn + g];
+// The same with rho', u, v, w at g given as values.
+template <typename RT, typename OT>
+__device__ __forceinline__ void rhs_point_v(long long g, int ix, int iy, int iz,
+                                            const double* __restrict__ q, RT r_, RT u_, RT v_,
+                                            RT w_, const RT* dx, const RT* dy, const RT* dz,
+                                            OT* out0, double* out, const Geom& G, const RefLev& R,
+                                            const RhsEpilogue& ep) {
+  const long long nn = G.nnode;
   const RT rho = (RT)R.rho0[iz] + r_;
   const RT irho = (RT)1 / rho;
   const RT grav = (RT)NUMA_GRAV;
@@ -213,6 +192,57 @@ __device__ __forceinline__ void rhs_node(long long tid, const double* __restrict
                    fma(ep.b3dt, R3[o], fma(ep.b2dt, R2[o], fma(ep.b1dt, R1[o], ep.u0[o]))));
     }
   }
+}
+
+template <typename RT, typename OT, typename FT>
+__device__ __forceinline__ void rhs_point(long long g, int ix, int iy, int iz, const double* __restrict__ q,
+                                          const FT* __restrict__ fld, const RT* dx, const RT* dy,
+                                          const RT* dz, OT* out0, double* out, const Geom& G,
+                                          const RefLev& R, const RhsEpilogue& ep) {
+  const long long nn = G.nnode;
+  rhs_point_v<RT, OT>(g, ix, iy, iz, q, (RT)fld[g], (RT)fld[nn + g], (RT)fld[2 * nn + g],
+                      (RT)fld[3 * nn + g], dx, dy, dz, out0, out, G, R, ep);
+}
+
+// One node of the right-hand side (thread index tid of the class-sorted order, or of the
+// natural order when perm is NULL).  sD, sDl, sDr: the three axes' derivative rows
+// (axis a at sD + a*(N+1)^2, sDl + a*(N+1), sDr + a*(N+1)), normally in shared memory.
+// RT: type of the stencil fields and of the arithmetic (double: the FP64 method, fields =
+// the state and P'; float: the mixed-precision form, fields = the FP32 copies from
+// k_prep32).  fld holds rho', u, v, w, theta' (stride nnode), fp holds P'.  OT: type
+// written in mode 0.  Modes 1 and 2 read and write the FP64 state; R1, R2 are OT arrays.
+template <int N, typename RT, typename OT>
+__device__ __forceinline__ void rhs_node(long long tid, const double* __restrict__ q,
+                                         const RT* __restrict__ fld, const RT* __restrict__ fp,
+                                         OT* out0, double* out, const int* __restrict__ perm,
+                                         long long nthreads, const Geom& G, const RefLev& R,
+                                         const RhsEpilogue& ep, const RT* sD, const RT* sDl,
+                                         const RT* sDr) {
+  constexpr int Nq = N + 1;
+  if (tid >= nthreads) return;
+  const int gi = perm ? perm[tid] : (int)tid;
+  if (gi < 0) return;                       // padding of a class group
+  const long long g = gi;
+  const long long nn = G.nnode;
+  const long long col = g / G.M;
+  const int iz = (int)(g - col * G.M);
+  const int iy = (int)(col / G.nxg);
+  const int ix = (int)(col - (long long)iy * G.nxg);
+  const long long sxs = G.M, sys = (long long)G.nxg * G.M;
+
+  // fields: 0 rho', 1 u, 2 v, 3 w, 4 theta', 5 P'
+  const RT* Fld[6] = {fld, fld + nn, fld + 2 * nn, fld + 3 * nn, fld + 4 * nn, fp};
+  RT dx[6], dy[6], dz[6];
+  {
+    Taps<N, RT> T;
+    int cls = axis_taps<N, RT>(ix, G.nex, sD, sDl, sDr, T);
+    axis_derivs<N, RT>(Fld, g, sxs, cls, T, dx);
+    cls = axis_taps<N, RT>(iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
+    axis_derivs<N, RT>(Fld, g, sys, cls, T, dy);
+    cls = axis_taps<N, RT>(iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
+    axis_derivs<N, RT>(Fld, g, 1, cls, T, dz);
+  }
+  rhs_point<RT, OT, RT>(g, ix, iy, iz, q, fld, dx, dy, dz, out0, out, G, R, ep);
 }
 
 // The three axes' derivative rows of C into shared memory (cast to RT).

@@ -1,0 +1,181 @@
+// Double-float ("DF") variant of the explicit right-hand side (precision NUMA_PREC_DF).
+//
+// GB300 issues FP64 at 2 FMA per clock per SM and FP32 at 128, and the FP64 right-hand side
+// is bound by the FP64 pipe (93 % busy).  Its bulk is the DSS'd derivative sums (about 90
+// multiply-adds per node at N = 4).  Here those sums run in double-float arithmetic: every
+// value is an unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits), the
+// products by Dekker's method (the exact residual of a product from one fused
+// multiply-add) and the sums by Knuth's TwoSum, with the low-order parts accumulated
+// without renormalisation and the pair rounded to FP64 once per derivative.  The pointwise
+// Set2NC terms, the equation of state and the state stay FP64 (rhs_point).
+//
+// A pre-pass writes every stencil field -- rho', u, v, w, theta' and P' from the FP64
+// equation of state -- as a (hi, lo) pair of FP32 numbers (see split): 8 bytes per value, as
+// a double, so the stencil reads the same bytes as the FP64 kernel.  The derivative rows are
+// split the same way, once per CTA, into shared memory.
+#include "numa_internal.cuh"
+#include "rhs_device.cuh"
+
+namespace {
+using namespace numa_dev;
+
+// TwoSum (Knuth): s + e = a + b exactly.  The round-to-nearest intrinsics keep the compiler
+// from fusing or reassociating the steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (ah, al) += (ch + cl) (fh + fl): the product's high part ph = fl32(ch fh) with its exact
+// residual ch fh - ph from one fused multiply-add (Dekker), the cross terms ch fl + cl fh
+// added to it (cl fl, below 2^-48 relative, is dropped), ph added to ah by TwoSum and all
+// low-order parts to al.
+__device__ __forceinline__ void df_mac(float ch, float cl, float fh, float fl, float& ah,
+                                       float& al) {
+  const float ph = __fmul_rn(ch, fh);
+  const float pe = __fmaf_rn(ch, fh, -ph);
+  const float pl = __fmaf_rn(ch, fl, __fmaf_rn(cl, fh, pe));
+  float s, e;
+  two_sum(ah, ph, s, e);
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(e, pl));
+}
+
+// On GB300 the FP64 <-> FP32 conversion instructions run at about the FP64 pipe's rate, so
+// the splits and recombinations below work on the IEEE-754 bit patterns with integer
+// instructions instead.
+//
+// split: hi = x with its significand truncated to 24 bits, lo = the remaining 29 bits,
+// truncated to a 24-bit float: x - hi - lo is below 2^-47 |x|.  Magnitudes below 2^-100 are
+// taken as 0; magnitudes from 2^128 up and non-finite values become NaN, so that a state
+// gone bad stays visible (the model's fields lie far inside both bounds).
+__device__ __forceinline__ float2 split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned s = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;                 // unbiased exponent
+  if (e < -100) return make_float2(0.0f, 0.0f);
+  if (e > 127) return make_float2(__uint_as_float(0x7fc00000u), 0.0f);   // beyond FP32, or not finite: NaN
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;           // 52-bit fraction
+  const float hi = __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+  const unsigned low = (unsigned)(m & 0x1FFFFFFFull);            // 29 bits below hi
+  if (low == 0) return make_float2(hi, 0.0f);
+  const int p = 31 - __clz(low);                                 // leading one of low
+  const int el = e - 52 + p;                                     // its exponent
+  if (el < -126) return make_float2(hi, 0.0f);
+  const unsigned frac = low ^ (1u << p);
+  const unsigned f23 = (p >= 23) ? (frac >> (p - 23)) : (frac << (23 - p));
+  return make_float2(hi, __uint_as_float(s | ((unsigned)(el + 127) << 23) | f23));
+}
+
+// The double equal to a normal float (exact), or 0 for a zero or subnormal float.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0) return 0.0;
+  if (ef == 255) return __longlong_as_double(0x7ff8000000000000ll);     // not finite: NaN
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ef - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// The six fields' derivatives along one axis with K taps (the class's exact count).
+template <int K, int N>
+__device__ __forceinline__ void derivs_df(const float2* const* F, long long g, long long stride,
+                                          const Taps<N, float2>& T, double* d) {
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const float2* p = F[f] + g;
+    float ah = 0.0f, al = 0.0f;
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+      const float2 v = __ldg(p + T.o[t] * stride);
+      df_mac(T.c[t].x, T.c[t].y, v.x, v.y, ah, al);
+    }
+    d[f] = widen(ah) + widen(al);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void axis_derivs_df(const float2* const* F, long long g, long long stride,
+                                               int cls, const Taps<N, float2>& T, double* d) {
+  if (cls == CLS_IFACE) derivs_df<2 * N, N>(F, g, stride, T, d);
+  else if (cls == CLS_WALL) derivs_df<N + 1, N>(F, g, stride, T, d);
+  else derivs_df<N, N>(F, g, stride, T, d);
+}
+
+// P' from the FP64 equation of state, and the (hi, lo) pairs of the six stencil fields.
+__global__ void k_prep_df(const double* __restrict__ q, float2* __restrict__ F2, Geom G, RefLev R,
+                          EosSeries S) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= G.nnode) return;
+  const long long nn = G.nnode;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) F2[f * nn + g] = split(q[f * nn + g]);
+  F2[5 * nn + g] = split(eos_node(q, g, G, R, S));
+}
+
+template <int N>
+__global__ void k_rhs_df(const double* __restrict__ q, const float2* __restrict__ F2, double* out0,
+                         double* out, const int* __restrict__ perm, long long nthreads, Geom G,
+                         Coef3 C, RefLev R, RhsEpilogue ep) {
+  constexpr int Nq = N + 1;
+  __shared__ float2 sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
+  for (int t = threadIdx.x; t < Nq * Nq; t += blockDim.x) {
+    sD[t] = split(C.x.D[t]);
+    sD[Nq * Nq + t] = split(C.y.D[t]);
+    sD[2 * Nq * Nq + t] = split(C.z.D[t]);
+  }
+  for (int t = threadIdx.x; t < Nq; t += blockDim.x) {
+    sDl[t] = split(C.x.Dl[t]); sDr[t] = split(C.x.Dr[t]);
+    sDl[Nq + t] = split(C.y.Dl[t]); sDr[Nq + t] = split(C.y.Dr[t]);
+    sDl[2 * Nq + t] = split(C.z.Dl[t]); sDr[2 * Nq + t] = split(C.z.Dr[t]);
+  }
+  __syncthreads();
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= nthreads) return;
+  const int gi = perm[tid];
+  if (gi < 0) return;
+  const long long g = gi;
+  const long long nn = G.nnode;
+  const long long col = g / G.M;
+  const int iz = (int)(g - col * G.M);
+  const int iy = (int)(col / G.nxg);
+  const int ix = (int)(col - (long long)iy * G.nxg);
+  const float2* Fld[6] = {F2, F2 + nn, F2 + 2 * nn, F2 + 3 * nn, F2 + 4 * nn, F2 + 5 * nn};
+  double dx[6], dy[6], dz[6];
+  {
+    Taps<N, float2> T;
+    int cls = axis_taps<N, float2>(ix, G.nex, sD, sDl, sDr, T);
+    axis_derivs_df<N>(Fld, g, G.M, cls, T, dx);
+    cls = axis_taps<N, float2>(iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
+    axis_derivs_df<N>(Fld, g, (long long)G.nxg * G.M, cls, T, dy);
+    cls = axis_taps<N, float2>(iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
+    axis_derivs_df<N>(Fld, g, 1, cls, T, dz);
+  }
+  rhs_point<double, double, double>(g, ix, iy, iz, q, q, dx, dy, dz, out0, out, G, R, ep);
+}
+
+}  // namespace
+
+cudaError_t launch_prep_df(const double* q, float2* F2, const Geom& G, const RefLev& R,
+                           cudaStream_t s) {
+  k_prep_df<<<(unsigned)((G.nnode + 255) / 256), 256, 0, s>>>(q, F2, G, R, eos_series());
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_df(const double* q, const float2* F2, double* out, const int* perm,
+                          long long nthreads, const Geom& G, const Coef3& C, const RefLev& R,
+                          const RhsEpilogue& ep, cudaStream_t s) {
+  const unsigned nb = (unsigned)((nthreads + 127) / 128);
+#define NUMA_DF_CASE(n) \
+  case n: k_rhs_df<n><<<nb, 128, 0, s>>>(q, F2, out, out, perm, nthreads, G, C, R, ep); break;
+  switch (G.N) {
+    NUMA_DF_CASE(1) NUMA_DF_CASE(2) NUMA_DF_CASE(3) NUMA_DF_CASE(4)
+    NUMA_DF_CASE(5) NUMA_DF_CASE(6) NUMA_DF_CASE(7) NUMA_DF_CASE(8)
+    default: return cudaErrorInvalidValue;
+  }
+#undef NUMA_DF_CASE
+  return cudaGetLastError();
+}

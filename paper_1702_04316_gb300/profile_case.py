@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--rk", type=int, default=0)
     ap.add_argument("--adj", type=int, default=0)
     ap.add_argument("--C", type=float, default=15.0)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "rhs32", "df"])
     a = ap.parse_args()
     import torch
     import paper_1702_04316_gb300 as pkg
