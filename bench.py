@@ -178,6 +178,22 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------------------
+def max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks of the job (x itself when running alone)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(dt, ms_step, world):
+    """Whole-job sim-s/wall-s of `world` independent replicas whose slowest step took
+    ms_step: the simulated time all of them advanced, over that wall time."""
+    return dt / (ms_step / 1e3) * world
+
+
 def run_gpu(args):
     import torch
     import paper_1702_04316_gb300 as pkg
@@ -221,12 +237,7 @@ def run_gpu(args):
         b.synchronize()
         torch.cuda.synchronize()
         barrier()
-        ms = a.elapsed_time(b)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(a.elapsed_time(b), dist, dev)
 
     imex = lambda: g.step_imex1d(q0, q1, 1)
     for _ in range(args.warmup):
@@ -240,7 +251,7 @@ def run_gpu(args):
     clk = clocks.stop()
     kt = {k: g.profile_read(k) for k in (pkg.K_PRESSURE, pkg.K_RHS, pkg.K_STAGE)}
     ms_step = ms / args.steps
-    value = dt15 / (ms_step / 1e3) * world
+    value = replica_value(dt15, ms_step, world)
     assert g.count_nonfinite(q1) == 0, "non-finite output"
     assert g.status() == pkg.NUMA_OK
 
@@ -266,11 +277,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         g.run_host(0, qin, 1, 0.0, qout)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
 
     # roofline of the dominant kernel (by measured share of the step)
     nnode = g.nnode
