@@ -89,3 +89,74 @@ def test_rk35_step_sampled(setup):
     gi, wi = window_nodes(s["case"].mesh, 40, 40, 11, 5)
     e = rel_l2(out[:, gi], ref[:, wi])
     assert np.all(e <= 1e-9), e
+
+
+# ---- the forms and variants at the same full size -----------------------------------------
+def test_tlm_and_adjoint_rhs_sampled(setup):
+    """R'(q) dq and R'(q)^T lam are as local as R (one element): margin 1 (the adjoint's
+    transposed stencil reaches the same neighbours), 7 x 7 windows."""
+    from oracle.column import Column
+    from oracle.tangent import rhs_adjoint, rhs_tlm
+    s = setup
+    torch = s["torch"]
+    case = s["case"]
+    dq = case.state(2011, kind="random", amp=0.3)
+    lam = case.state(2012, kind="random", amp=0.2)
+    t = s["g"].rhs_tlm(s["qg"], torch.from_numpy(dq).cuda()).cpu().numpy()
+    a = s["g"].rhs_adjoint(s["qg"], torch.from_numpy(lam).cuda()).cpu().numpy()
+    for ex0, ey0 in WINDOWS[:2]:
+        sub, qs = window(case.mesh, s["q0"], ex0, ey0, W)
+        _, dqs = window(case.mesh, dq, ex0, ey0, W)
+        _, ls = window(case.mesh, lam, ex0, ey0, W)
+        gi, wi = window_nodes(case.mesh, ex0, ey0, W, 2)
+        e = rel_l2(t[:, gi], rhs_tlm(sub, Column(sub), qs, dqs)[:, wi])
+        assert np.all(e <= 1e-11), ("tlm", ex0, ey0, e)
+        e = rel_l2(a[:, gi], rhs_adjoint(sub, Column(sub), qs, ls)[:, wi])
+        assert np.all(e <= 1e-11), ("adjoint", ex0, ey0, e)
+
+
+def test_df_rhs_sampled(setup):
+    from oracle.column import Column
+    from oracle.rhs import rhs
+    s = setup
+    case = s["case"]
+    g = s["pkg"].Numa(NEX, NEX, NEZ, L, L, LZ, N, s["dt"], precision="df")
+    r = g.rhs_explicit(s["qg"]).cpu().numpy()
+    for ex0, ey0 in WINDOWS:
+        sub, qs = window(case.mesh, s["q0"], ex0, ey0, W)
+        gi, wi = window_nodes(case.mesh, ex0, ey0, W, 1)
+        e = rel_l2(r[:, gi], rhs(sub, Column(sub), qs)[:, wi])
+        assert np.all(e <= 1e-11), (ex0, ey0, e)
+    g.close()
+
+
+def test_standard_form_step_sampled(setup):
+    from oracle import ark2
+    from oracle.column import Column
+    s = setup
+    case = s["case"]
+    g = s["pkg"].Numa(NEX, NEX, NEZ, L, L, LZ, N, s["dt"], column_form="standard")
+    out = g.step_imex1d(s["qg"], g.empty_state(), 1).cpu().numpy()
+    g.close()
+    for ex0, ey0 in WINDOWS[:2]:
+        sub, qs = window(case.mesh, s["q0"], ex0, ey0, W)
+        ref = ark2.HEVI(sub, Column(sub), s["dt"], form="standard").step(qs, 1)
+        gi, wi = window_nodes(case.mesh, ex0, ey0, W, 3)
+        e = rel_l2(out[:, gi], ref[:, wi])
+        assert np.all(e <= 1e-9), (ex0, ey0, e)
+
+
+def test_ark3_step_sampled(setup):
+    """An ARK3 step has four RHS evaluations: an 11 x 11 window, margin 5."""
+    from oracle import ark2
+    from oracle.column import Column
+    s = setup
+    case = s["case"]
+    g = s["pkg"].Numa(NEX, NEX, NEZ, L, L, LZ, N, s["dt"], scheme="ark3")
+    out = g.step_imex1d(s["qg"], g.empty_state(), 1).cpu().numpy()
+    g.close()
+    sub, qs = window(case.mesh, s["q0"], 40, 40, 11)
+    ref = ark2.HEVI(sub, Column(sub), s["dt"], scheme="ark3").step(qs, 1)
+    gi, wi = window_nodes(case.mesh, 40, 40, 11, 5)
+    e = rel_l2(out[:, gi], ref[:, wi])
+    assert np.all(e <= 1e-9), e
