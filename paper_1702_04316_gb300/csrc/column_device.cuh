@@ -175,10 +175,10 @@ __host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
 //   P_e = G0 rho~_e + H0 theta~_e and w_a = A^-1 (w~_e + lam g theta~_e / theta0).
 // Phase 2 (one thread per column): Schur right-hand side b (Algorithm 4), the column solve,
 //   and w_p(P) (Eq. utteqn).
-// Phase 3 (coalesced): w~ = w_a - w_p(P), theta~ = theta~_e - lam w~ d(theta0)/dz,
-//   rho~ = (P - H0 theta~) / G0 (w_a and theta~_e recomputed from their sources rather than
-//   kept in shared memory, which doubles the resident columns), then
-//   q(i) = q~ - sum_j c_ij q(j).
+// Phase 3 (coalesced): w~ = w_a - w_p(P) (formed at the end of phase 2 in the FP64 form),
+//   theta~ = theta~_e - lam w~ d(theta0)/dz, rho~ = (P - H0 theta~) / G0 (theta~_e, and in
+//   the mixed form w_a, recomputed from their sources rather than kept in shared memory,
+//   which would cut the resident columns), then q(i) = q~ - sum_j c_ij q(j).
 // RT: type of R1, R2 (double, or float in the mixed form).
 // col0: first column of this block, T columns (T <= blockDim.x: all threads share phases 1
 // and 3, the first T run phase 2); sm: dynamic shared memory of
@@ -289,7 +289,12 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
       __syncthreads();
     }
   }
-  level_loop([&](int lev, int c) { S1[lev * T + c] = col_wp<N, double>(S0 + c, T, lev, R, tb); });
+  // FP64: S1 still holds w_a, so it becomes w = w_a - w_p(P) here; the mixed form used S1 as
+  // scratch and keeps w_p(P) (phase 3 recomputes w_a)
+  level_loop([&](int lev, int c) {
+    const double wp = col_wp<N, double>(S0 + c, T, lev, R, tb);
+    S1[lev * T + c] = MIXED ? wp : S1[lev * T + c] - wp;
+  });
   __syncthreads();
 
   // phase 3
@@ -298,9 +303,14 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
     const long long orr = g, ow = 3 * nn + g, oth = 4 * nn + g;
-    const double te = pred(4, oth), we = pred(3, ow);
-    const double wa = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
-    const double wv = wa - S1[lev * T + c];
+    const double te = pred(4, oth);
+    double wv;
+    if (MIXED) {
+      const double wa = fma(__ldg(tb.wa_th + lev), te, pred(3, ow)) * __ldg(tb.wa_s + lev);
+      wv = wa - S1[lev * T + c];
+    } else {
+      wv = S1[lev * T + c];
+    }
     const double thv = fma(-__ldg(tb.kth + lev), wv, te);
     const double rv = fma(-__ldg(tb.H0G0 + lev), thv, __ldg(tb.invG0 + lev) * S0[lev * T + c]);
     double o_r = fma(-c1, qn[orr], rv), o_w = fma(-c1, qn[ow], wv), o_t = fma(-c1, qn[oth], thv);
