@@ -311,7 +311,8 @@ int numa_step_imex1d_tlm(numa_ctx* ctx, const double* q, const double* dq, doubl
                          double* dq_out, int nsteps);
 
 /* Adjoint of one HEVI step taken from state q: lam = (dq^{n+1}/dq^n)^T lam_next.  The
- * step's stage states are recomputed from q.  lam == lam_next (in place) allowed. */
+ * step is retaken from q (numa_step_imex1d) for its stage states.  lam == lam_next (in
+ * place) allowed. */
 int numa_step_imex1d_adjoint(numa_ctx* ctx, const double* q, const double* lam_next,
                              double* lam);
 
@@ -322,8 +323,10 @@ int numa_imex1d_forward_checkpointed(numa_ctx* ctx, const double* q0, double* qT
                                      int every, double* ckpt);
 
 /* Adjoint of that run: lam0 = (dq^T/dq^0)^T lamT.  Segments are processed last to first;
- * each is recomputed from its checkpoint into work (every * 5*nnode doubles) and the steps
- * are then run backwards with numa_step_imex1d_adjoint.  lam0 == lamT allowed. */
+ * each is retaken from its checkpoint, keeping every step's state q^n and stage states q(2),
+ * q(3) in work (device, 3 * every * 5*nnode doubles, caller-owned scratch), and its steps are
+ * then run backwards from those states (numa_step_imex1d_adjoint without the retaken step).
+ * lam0 == lamT allowed. */
 int numa_imex1d_adjoint_checkpointed(numa_ctx* ctx, const double* ckpt, int nsteps, int every,
                                      const double* lamT, double* lam0, double* work);
 

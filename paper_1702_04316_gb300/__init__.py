@@ -327,7 +327,7 @@ class Numa:
         """(dq^T/dq^0)^T lamT from the checkpoints of forward_checkpointed."""
         self._state(lamT)
         lam0 = self._torch.empty_like(lamT) if lam0 is None else self._state(lam0)
-        work = self._torch.empty(int(every), 5, self.nnode, dtype=self._torch.float64,
+        work = self._torch.empty(3 * int(every), 5, self.nnode, dtype=self._torch.float64,
                                  device="cuda")
         self._check(lib().numa_imex1d_adjoint_checkpointed(self._h, _ptr(ckpt), int(nsteps),
                                                            int(every), _ptr(lamT), _ptr(lam0),

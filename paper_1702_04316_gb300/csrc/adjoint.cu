@@ -676,6 +676,34 @@ int scale_into(numa_ctx* c, const double* x, double* y, double a) {
   return NUMA_OK;
 }
 
+// The adjoint of one ARK2 step from its states qn = q^n, q2 = q(2), q3 = q(3):
+// lam = (dq^{n+1}/dq^n)^T lam_next (lam may equal lam_next).  Uses w.B[0..4] and w.B[6].
+int step_adjoint_core(numa_ctx* ctx, const AdjWork& w, const double* qn, const double* q2,
+                      const double* q3, const double* lam_next, double* lam) {
+  int rc;
+  double *R1a = w.B[0], *R2a = w.B[1], *R3a = w.B[2], *q2a = w.B[3], *q3a = w.B[4],
+         *qa = w.B[6];
+  const size_t bytes = 5 * ctx->G.nnode * sizeof(double);
+  double b[3];
+  numa_ark2_tableau(nullptr, nullptr, b);
+  // q^{n+1} = q^n + dt (b1 R1 + b2 R2 + b3 R3)
+  NUMA_ACK(ctx, cudaMemcpyAsync(qa, lam_next, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  if ((rc = scale_into(ctx, lam_next, R1a, b[0] * ctx->dt))) return rc;
+  if ((rc = scale_into(ctx, lam_next, R2a, b[1] * ctx->dt))) return rc;
+  if ((rc = scale_into(ctx, lam_next, R3a, b[2] * ctx->dt))) return rc;
+  NUMA_ACK(ctx, cudaMemsetAsync(q2a, 0, bytes, ctx->stream));
+  // R3 = R(q(3));  q(3) = stage 3 (q^n, R1, R2, q(2))
+  if ((rc = enqueue_rhs_adj(ctx, w, q3, R3a, q3a, 0))) return rc;
+  if ((rc = enqueue_stage_adj(ctx, 3, q3a, qa, R1a, R2a, q2a))) return rc;
+  // R2 = R(q(2));  q(2) = stage 2 (q^n, R1)
+  if ((rc = enqueue_rhs_adj(ctx, w, q2, R2a, q2a, 1))) return rc;
+  if ((rc = enqueue_stage_adj(ctx, 2, q2a, qa, R1a, nullptr, nullptr))) return rc;
+  // R1 = R(q^n)
+  if ((rc = enqueue_rhs_adj(ctx, w, qn, R1a, qa, 1))) return rc;
+  NUMA_ACK(ctx, cudaMemcpyAsync(lam, qa, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return NUMA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -754,34 +782,12 @@ int numa_step_imex1d_adjoint(numa_ctx* ctx, const double* q, const double* lam_n
   int rc;
   AdjWork w;
   if ((rc = check_diff(ctx, true)) || (rc = adj_work(ctx, w))) return rc;
-  double *R1a = w.B[0], *R2a = w.B[1], *R3a = w.B[2], *q2a = w.B[3], *q3a = w.B[4],
-         *qn = w.B[5], *qa = w.B[6];
+  double* qn = w.B[5];
   const size_t bytes = 5 * ctx->G.nnode * sizeof(double);
-  double b[3];
-  numa_ark2_tableau(nullptr, nullptr, b);
-  // recompute the stage states q(2), q(3) of this step (the last right-hand side of the
-  // step is not needed)
+  // retake the step from q: it leaves its stage states q(2), q(3) in ctx->q2, ctx->q3
   NUMA_ACK(ctx, cudaMemcpyAsync(qn, q, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-  if ((rc = numa_rhs_explicit(ctx, qn, ctx->R1))) return rc;
-  if ((rc = numa_imex_stage(ctx, 2, qn, ctx->R1, nullptr, nullptr, ctx->q2))) return rc;
-  if ((rc = numa_rhs_explicit(ctx, ctx->q2, ctx->R2))) return rc;
-  if ((rc = numa_imex_stage(ctx, 3, qn, ctx->R1, ctx->R2, ctx->q2, ctx->q3))) return rc;
-  // q^{n+1} = q^n + dt (b1 R1 + b2 R2 + b3 R3)
-  NUMA_ACK(ctx, cudaMemcpyAsync(qa, lam_next, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-  if ((rc = scale_into(ctx, lam_next, R1a, b[0] * ctx->dt))) return rc;
-  if ((rc = scale_into(ctx, lam_next, R2a, b[1] * ctx->dt))) return rc;
-  if ((rc = scale_into(ctx, lam_next, R3a, b[2] * ctx->dt))) return rc;
-  NUMA_ACK(ctx, cudaMemsetAsync(q2a, 0, bytes, ctx->stream));
-  // R3 = R(q(3));  q(3) = stage 3 (q^n, R1, R2, q(2))
-  if ((rc = enqueue_rhs_adj(ctx, w, ctx->q3, R3a, q3a, 0))) return rc;
-  if ((rc = enqueue_stage_adj(ctx, 3, q3a, qa, R1a, R2a, q2a))) return rc;
-  // R2 = R(q(2));  q(2) = stage 2 (q^n, R1)
-  if ((rc = enqueue_rhs_adj(ctx, w, ctx->q2, R2a, q2a, 1))) return rc;
-  if ((rc = enqueue_stage_adj(ctx, 2, q2a, qa, R1a, nullptr, nullptr))) return rc;
-  // R1 = R(q^n)
-  if ((rc = enqueue_rhs_adj(ctx, w, qn, R1a, qa, 1))) return rc;
-  NUMA_ACK(ctx, cudaMemcpyAsync(lam, qa, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-  return NUMA_OK;
+  if ((rc = numa_step_imex1d(ctx, qn, w.B[7], 1))) return rc;
+  return step_adjoint_core(ctx, w, qn, ctx->q2, ctx->q3, lam_next, lam);
 }
 
 int numa_imex1d_forward_checkpointed(numa_ctx* ctx, const double* q0, double* qT, int nsteps,
@@ -805,23 +811,27 @@ int numa_imex1d_adjoint_checkpointed(numa_ctx* ctx, const double* ckpt, int nste
                                      const double* lamT, double* lam0, double* work) {
   if (!ctx || !ckpt || !lamT || !lam0 || !work || nsteps < 1 || every < 1) return NUMA_ERR_ARG;
   int rc;
-  if ((rc = check_diff(ctx, true))) return rc;
+  AdjWork w;
+  if ((rc = check_diff(ctx, true)) || (rc = adj_work(ctx, w))) return rc;
   const long long n5 = 5 * ctx->G.nnode;
   const size_t bytes = n5 * sizeof(double);
   if (lam0 != lamT)
     NUMA_ACK(ctx, cudaMemcpyAsync(lam0, lamT, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  // work holds, for step i of the current segment, q at that step and its stage states
+  auto Q = [&](int i, int f) { return work + ((size_t)3 * i + f) * n5; };
   const int nseg = (nsteps + every - 1) / every;
   for (int k = nseg - 1; k >= 0; --k) {
-    const int s0 = k * every, s1 = std::min(nsteps, s0 + every);
-    // recompute the segment's states from its checkpoint: work[s - s0] = q at step s
-    NUMA_ACK(ctx, cudaMemcpyAsync(work, ckpt + (size_t)k * n5, bytes, cudaMemcpyDeviceToDevice,
+    const int s0 = k * every, len = std::min(nsteps, s0 + every) - s0;
+    // retake the segment's steps from its checkpoint
+    NUMA_ACK(ctx, cudaMemcpyAsync(Q(0, 0), ckpt + (size_t)k * n5, bytes, cudaMemcpyDeviceToDevice,
                                   ctx->stream));
-    for (int s = s0; s + 1 < s1; ++s)
-      if ((rc = numa_step_imex1d(ctx, work + (size_t)(s - s0) * n5,
-                                 work + (size_t)(s - s0 + 1) * n5, 1)))
-        return rc;
-    for (int s = s1 - 1; s >= s0; --s)
-      if ((rc = numa_step_imex1d_adjoint(ctx, work + (size_t)(s - s0) * n5, lam0, lam0))) return rc;
+    for (int i = 0; i < len; ++i) {
+      if ((rc = numa_step_imex1d(ctx, Q(i, 0), i + 1 < len ? Q(i + 1, 0) : w.B[7], 1))) return rc;
+      NUMA_ACK(ctx, cudaMemcpyAsync(Q(i, 1), ctx->q2, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      NUMA_ACK(ctx, cudaMemcpyAsync(Q(i, 2), ctx->q3, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    for (int i = len - 1; i >= 0; --i)
+      if ((rc = step_adjoint_core(ctx, w, Q(i, 0), Q(i, 1), Q(i, 2), lam0, lam0))) return rc;
   }
   return NUMA_OK;
 }
