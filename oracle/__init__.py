@@ -24,8 +24,11 @@ algorithm or table:
                     utteqn, helm2nc; Algorithms 4-5).
 * ``ark2``       -- the ARK2 double Butcher tableau (Table 1) and the SDIRK
                     predictor-corrector stage form (Sec. "Linear multi-stage methods").
-* ``ark3``       -- a third-order ARK tableau (ARK3(2)4L[2]SA) for the paper's ARK3 runs,
-                    whose tableau the paper does not print (reading stated there).
+* ``ark3``, ``ark4``, ``ark5`` -- the ARK3(2)4L[2]SA, ARK4(3)6L[2]SA and ARK5(4)8L[2]SA
+                    tableaux for the paper's ARK3 - ARK5 runs, whose tableaux the paper
+                    does not print (readings stated there); ``derive_ark5_row8`` re-derives
+                    two entries of ARK5 from its order conditions.
+* ``ark_order``  -- the bicoloured-tree order conditions of ARK pairs, exact arithmetic.
 * ``rk35``       -- the explicit five-stage third-order SSP comparator
                     (Sec. "Performance of IMEX on manycore processors").
 * ``schur3d``    -- 3D-IMEX in the Schur form: the 3D Schur operator and right-hand side,

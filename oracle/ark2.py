@@ -56,7 +56,7 @@ def printed_b():
 
 def ark_step(q, dt, R, solve, tab=None):
     """One ARK step for dq/dt = R(q) = N(q) + L(q) (ARK2 unless tab = (a, at, b, c) of
-    another scheme with a~_11 = 0, one implicit diagonal and b = b~, such as ARK3).
+    another scheme with a~_11 = 0, one implicit diagonal and b = b~, such as ARK3 - ARK5).
 
     R(q) is the full right-hand side; solve(rhs, lam) returns x with x = rhs + lam L(x).
     """
@@ -76,22 +76,30 @@ def ark_step(q, dt, R, solve, tab=None):
     return q + dt * sum(b[i] * Rs[i] for i in range(s))
 
 
+SCHEMES = ("ark2", "ark3", "ark4", "ark5")
+
+
+def scheme_tableau(scheme):
+    """(a, at, b, c) of "ark2" (Table 1), "ark3", "ark4" or "ark5" (``oracle.ark3``,
+    ``oracle.ark4``, ``oracle.ark5``)."""
+    if scheme not in SCHEMES:
+        raise ValueError("scheme must be one of %s" % (SCHEMES,))
+    if scheme == "ark2":
+        return tableau()
+    import importlib
+    return importlib.import_module("." + scheme, __package__).tableau()
+
+
 class HEVI:
     """The 1D-IMEX (HEVI) integrator on a box mesh (oracle).  form: "schur" (the paper's
     method) or "standard" (the non-Schur column system, same step otherwise); scheme:
-    "ark2" (Table 1) or "ark3" (``oracle.ark3``)."""
+    one of SCHEMES (``scheme_tableau``)."""
 
     def __init__(self, mesh, col, dt, form="schur", scheme="ark2"):
         if form not in ("schur", "standard"):
             raise ValueError("form must be 'schur' or 'standard'")
-        if scheme not in ("ark2", "ark3"):
-            raise ValueError("scheme must be 'ark2' or 'ark3'")
+        self.tab = scheme_tableau(scheme)
         self.mesh, self.col, self.dt, self.form, self.scheme = mesh, col, dt, form, scheme
-        if scheme == "ark2":
-            self.tab = tableau()
-        else:
-            from . import ark3
-            self.tab = ark3.tableau()
         at = self.tab[1]
         self.lam = at[1, 1] * dt                     # one implicit diagonal for every stage
         if form == "schur":

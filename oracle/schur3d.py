@@ -27,7 +27,7 @@ lam^2 times a discrete -rho0 G0 div(grad / rho0) operator; l_max by power iterat
 """
 import numpy as np
 
-from .ark2 import ark_step, tableau
+from .ark2 import ark_step, scheme_tableau
 from .reference import GRAV
 from .rhs import rhs
 
@@ -185,17 +185,13 @@ def bicgstab(apply, b, M, tol=1e-12, maxit=500):
 class HEVI3D:
     """3D-IMEX integrator with the Schur form and BiCGstab + polynomial preconditioner
     (oracle).  order: polynomial degree P; tol: relative preconditioned-residual drop;
-    scheme: "ark2" (Table 1) or "ark3" (``oracle.ark3``); precond: "pbno" (the paper's
+    scheme: one of ``ark2.SCHEMES``; precond: "pbno" (the paper's
     polynomial preconditioner, Chebyshev reading) or "column" (the 1D column Schur LU as a
     vertical-line preconditioner, a choice beyond the paper)."""
 
     def __init__(self, mesh, col, dt, order=2, tol=1e-12, scheme="ark2", precond="pbno"):
         self.mesh, self.col, self.dt = mesh, col, dt
-        if scheme == "ark2":
-            self.tab = tableau()
-        else:
-            from . import ark3
-            self.tab = ark3.tableau()
+        self.tab = scheme_tableau(scheme)
         at = self.tab[1]
         self.lam = at[1, 1] * dt
         self.op = Schur3D(mesh, col)

@@ -264,3 +264,122 @@ def test_hevi_ark3_converges_faster_than_ark2():
     assert err[("ark3", 32)] < err[("ark2", 32)] / 3.0, err
     assert np.log2(err[("ark3", 16)] / err[("ark3", 32)]) > 2.5, err
     assert np.log2(err[("ark2", 16)] / err[("ark2", 32)]) < 2.3, err
+
+
+# ---- ARK4, ARK5 and the order-condition machinery --------------------------------------
+
+def test_bicoloured_tree_counts():
+    """The numbers of rooted trees with two-coloured non-root vertices (oriented rooted
+    trees, OEIS A000151): 1, 2, 7, 26, 107, 458."""
+    from oracle.ark_order import trees
+    assert [len(trees(n)) for n in range(1, 7)] == [1, 2, 7, 26, 107, 458]
+
+
+def test_order_conditions_on_textbook_pairs():
+    """The classical fourth-order Runge-Kutta method used as both halves of a pair is of
+    order exactly 4; the explicit / implicit Euler pair of order exactly 1; a 1e-6 change of
+    one ARK4 entry breaks order 2 or more."""
+    from fractions import Fraction as F
+    from oracle import ark4
+    from oracle.ark_order import residuals
+    h = F(1, 2)
+    rk4 = ((0, 0, 0, 0), (h, 0, 0, 0), (0, h, 0, 0), (0, 0, 1, 0))
+    res = residuals(rk4, rk4, (F(1, 6), F(1, 3), F(1, 3), F(1, 6)), 5)
+    assert all(res[n] == 0 for n in range(1, 5)) and res[5] > F(1, 1000)
+    res = residuals(((0, 0), (1, 0)), ((0, 0), (0, 1)), (0, 1), 2)
+    assert res[1] == 0 and res[2] >= F(1, 2)
+    a, at, b, _ = ark4.rational_tableau()
+    bad = [list(r) for r in a]
+    bad[4][2] += F(1, 10 ** 6)
+    res = residuals(bad, at, b, 4)
+    assert res[1] == 0 and max(res[n] for n in (2, 3, 4)) > F(1, 10 ** 8)
+
+
+@pytest.mark.parametrize("name,p", [("ark3", 3), ("ark4", 4), ("ark5", 5)])
+def test_ark_tableau_order_conditions_exact(name, p):
+    """Every bicoloured-tree condition up to order p holds to the accuracy of the published
+    rationals (<= 1e-25), order p + 1 fails, c = c~, b = the last implicit row, and one
+    implicit diagonal over an explicit first stage."""
+    import importlib
+    from fractions import Fraction as F
+    from oracle.ark_order import residuals
+    m = importlib.import_module("oracle." + name)
+    a, at, b, c = m.rational_tableau()
+    s = len(b)
+    tol = F(1, 10 ** 25)
+    res = residuals(a, at, b, p + 1)
+    assert all(res[n] < tol for n in range(1, p + 1)), res
+    assert res[p + 1] > F(1, 10 ** 4)
+    ct = [sum(F(x) for x in row) for row in at]
+    assert all(abs(F(c[i]) - ct[i]) < tol for i in range(s))
+    assert tuple(b) == tuple(at[-1])
+    assert at[0][0] == 0 and all(at[i][i] == m.GAMMA for i in range(1, s))
+    assert all(a[i][j] == 0 for i in range(s) for j in range(i, s))
+    assert all(at[i][j] == 0 for i in range(s) for j in range(i + 1, s))
+
+
+def test_ark5_row8_is_the_order_condition_solution():
+    """The two derived ARK5 entries are the least-squares solution of the fifth-order
+    conditions: Gauss-Newton started there does not move them."""
+    pytest.importorskip("mpmath")
+    from oracle import ark5, derive_ark5_row8
+    x, r = derive_ark5_row8.solve((float(ark5.A86), float(ark5.A87)), iters=4)
+    assert derive_ark5_row8.rationals(x) == (ark5.A86, ark5.A87)
+    assert float(r) < 1e-25
+
+
+@pytest.mark.parametrize("name", ["ark4", "ark5"])
+def test_ark45_predictor_corrector_form_equals_double_tableau(name):
+    Nmat, Lmat = _split_system(seed=8)
+    y = np.random.default_rng(9).standard_normal(6)
+    R = lambda q: (Nmat + Lmat) @ q
+    solve = lambda r, lam: np.linalg.solve(np.eye(6) - lam * Lmat, r)
+    tab = ark2.scheme_tableau(name)
+    for dt in (0.01, 0.3, 3.0):
+        np.testing.assert_allclose(ark2.ark_step(y, dt, R, solve, tab),
+                                   _ark_direct_tab(y, dt, Nmat, Lmat, tab), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,rate", [("ark2", 1.9), ("ark3", 2.7), ("ark4", 3.8), ("ark5", 4.7)])
+def test_ark_rate_on_a_nonlinear_split_system(name, rate):
+    """y' = N(y) + L y with N nonlinear (sin of a random mixing plus a quadratic) and L a
+    moderately stiff linear part, against an adaptive eighth-order Dormand-Prince solution:
+    the error drops at the scheme's order (nonlinear N exercises the coupling conditions
+    that a linear test cannot)."""
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(11)
+    n = 4
+    Lm = -np.diag([1.0, 3.0, 8.0, 20.0]) + 0.3 * rng.standard_normal((n, n))
+    K = rng.standard_normal((n, n))
+    R = lambda y: np.sin(K @ y) + 0.5 * y[::-1] ** 2 + Lm @ y
+    solve = lambda r, lam: np.linalg.solve(np.eye(n) - lam * Lm, r)
+    y0 = 0.5 * rng.standard_normal(n)
+    ref = solve_ivp(lambda t, y: R(y), (0.0, 1.0), y0, method="DOP853", rtol=3e-14,
+                    atol=1e-15).y[:, -1]
+    tab = ark2.scheme_tableau(name)
+    errs = []
+    for k in (32, 64):
+        y = y0.copy()
+        for _ in range(k):
+            y = ark2.ark_step(y, 1.0 / k, R, solve, tab)
+        errs.append(np.linalg.norm(y - ref))
+    assert np.log2(errs[0] / errs[1]) > rate, errs
+
+
+def test_hevi_ark4_ark5_rates_on_the_box():
+    """HEVI with ARK4 and ARK5 on the Set2NC box with resolved vertical acoustics: against a
+    fine run of the same scheme the error drops at rates above 3.4 and 4.4, and ARK5 is
+    at least 3x more accurate than ARK4 at the same step."""
+    m, col, dt1 = _box(nex=2, nez=3, L=400e3)
+    xg, yg, zg = m.coords()
+    q0 = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Lx, m.Lz, col.rho0, col.theta0, 15)
+    T = 16 * dt1
+    err = {}
+    for s in ("ark4", "ark5"):
+        ref = ark2.HEVI(m, col, T / 64, scheme=s).step(q0, 64)
+        for n in (8, 16):
+            q = ark2.HEVI(m, col, T / n, scheme=s).step(q0, n)
+            err[(s, n)] = np.linalg.norm(q[3] - ref[3]) / np.linalg.norm(ref[3])
+    assert np.log2(err[("ark4", 8)] / err[("ark4", 16)]) > 3.4, err
+    assert np.log2(err[("ark5", 8)] / err[("ark5", 16)]) > 4.4, err
+    assert err[("ark5", 16)] < err[("ark4", 16)] / 3.0, err
