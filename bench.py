@@ -363,17 +363,25 @@ def run_gpu(args):
                           "rhs_rel_l2_vs_fp64_kernel": [float("%.3g" % x) for x in rel],
                           "form": "double-float (FP32-pair) derivative sums, FP64 pointwise terms, "
                                   "EOS, column LU and state"}
-    # ARK3 (ARK3(2)4L[2]SA: four stages, 4 RHS + 3 column stages per step), same workload
-    ark3 = {}
-    for C, dtc in ((15, dt15), (150, dt150)):
-        g3 = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dtc, scheme="ark3")
-        for _ in range(args.warmup):
-            g3.step_imex1d(q0, q1, 1)
-        ms3 = time_steps(lambda: g3.step_imex1d(q0, q1, 1), args.steps) / args.steps
-        g3.close()
-        ark3["C%d" % C] = {"sim_s_per_wall_s": round(sps(dtc, ms3), 3), "ms_per_step": round(ms3, 4),
-                           "speedup_vs_explicit_c1": round(sps(dtc, ms3) / sps(dt1, ms_rk), 3)}
-    out["imex_ark3"] = dict(ark3, scheme="ARK3(2)4L[2]SA, FP64, Schur form")
+    # the higher-order schemes on the same workload: ARK3(2)4L[2]SA (4 RHS + 3 column stages
+    # per step), ARK4(3)6L[2]SA (6 + 5, general fused stage), ARK5(4)8L[2]SA (8 + 7)
+    for scheme, name in (("ark3", "ARK3(2)4L[2]SA"), ("ark4", "ARK4(3)6L[2]SA"),
+                         ("ark5", "ARK5(4)8L[2]SA")):
+        res = {}
+        for C, dtc in ((15, dt15), (150, dt150)):
+            gs = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dtc, scheme=scheme)
+            for _ in range(args.warmup):
+                gs.step_imex1d(q0, q1, 1)
+            mss = time_steps(lambda: gs.step_imex1d(q0, q1, 1), args.steps) / args.steps
+            gs.profile(True)
+            gs.step_imex1d(q0, q1, 1)
+            t_st, n_st = gs.profile_read(pkg.K_STAGE)
+            gs.profile(False)
+            gs.close()
+            res["C%d" % C] = {"sim_s_per_wall_s": round(sps(dtc, mss), 3), "ms_per_step": round(mss, 4),
+                              "stage_ms_per_launch": round(t_st / max(n_st, 1), 4),
+                              "speedup_vs_explicit_c1": round(sps(dtc, mss) / sps(dt1, ms_rk), 3)}
+        out["imex_" + scheme] = dict(res, scheme=name + ", FP64, Schur form")
     if not args.no_forms:
         out["imex3d"] = imex3d_form(pkg, torch, q0, ms_rk, args.warmup)
     if not args.no_forms:

@@ -80,7 +80,7 @@ enum {
   NUMA_Q_N = 8,             /* polynomial order */
   NUMA_Q_PRECISION = 9,     /* NUMA_PREC_FP64, NUMA_PREC_MIXED, NUMA_PREC_RHS32 or NUMA_PREC_DF */
   NUMA_Q_COLUMN_FORM = 10,  /* NUMA_COLUMN_SCHUR or NUMA_COLUMN_STANDARD */
-  NUMA_Q_SCHEME = 11,       /* NUMA_SCHEME_ARK2 or NUMA_SCHEME_ARK3 */
+  NUMA_Q_SCHEME = 11,       /* NUMA_SCHEME_ARK2 .. NUMA_SCHEME_ARK5 */
   NUMA_Q_IMEX = 12          /* NUMA_IMEX_1D or NUMA_IMEX_3D */
 };
 
@@ -116,8 +116,13 @@ enum {
  *         NUMA_SCHEME_ARK3 -- a third-order ARK for the paper's higher-order runs, whose
  *         tableau the paper does not print: ARK3(2)4L[2]SA of Kennedy and Carpenter (2003),
  *         four stages, one implicit diagonal gamma = 0.4358665215084590 (the factors are
- *         formed at lam = gamma dt), b = b~ (numa_ark3_tableau).  FP64 Schur form only;
- *         the differentiation form and ensembles use ARK2.
+ *         formed at lam = gamma dt), b = b~ (numa_ark3_tableau);
+ *         NUMA_SCHEME_ARK4, NUMA_SCHEME_ARK5 -- fourth- and fifth-order ARKs for the same
+ *         runs: ARK4(3)6L[2]SA (six stages, gamma = 1/4) and ARK5(4)8L[2]SA (eight stages,
+ *         gamma = 41/200) of Kennedy and Carpenter (2003), b = b~; ARK5's explicit a_86,
+ *         a_87 are the solution of its fifth-order conditions given the other published
+ *         entries (numa_ark_tableau).  ARK3 - ARK5: FP64 Schur form; ARK4 and ARK5 with
+ *         1D-IMEX only.  The differentiation form and ensembles use ARK2.
  * imex: NUMA_IMEX_1D (default) -- the paper's 1D-IMEX (HEVI) method with stored column
  *       factors; NUMA_IMEX_3D -- 3D-IMEX in the Schur form (Eqs. utteqn, helm2nc with the
  *       full gradient): the whole linear operator implicit, one pressure unknown per node,
@@ -138,7 +143,8 @@ enum {
  *          part of S is vertical when C_V > C_H; the converged solution is the same). */
 enum { NUMA_PREC_FP64 = 0, NUMA_PREC_MIXED = 1, NUMA_PREC_RHS32 = 2, NUMA_PREC_DF = 3 };
 enum { NUMA_COLUMN_SCHUR = 0, NUMA_COLUMN_STANDARD = 1 };
-enum { NUMA_SCHEME_ARK2 = 0, NUMA_SCHEME_ARK3 = 1 };
+enum { NUMA_SCHEME_ARK2 = 0, NUMA_SCHEME_ARK3 = 1, NUMA_SCHEME_ARK4 = 2, NUMA_SCHEME_ARK5 = 3 };
+#define NUMA_MAX_STAGES 8   /* stages of the longest scheme (ARK5) */
 enum { NUMA_IMEX_1D = 0, NUMA_IMEX_3D = 1 };
 enum { NUMA_PRECOND_PBNO = 0, NUMA_PRECOND_COLUMN = 1 };
 #define NUMA_MAX_PBNO_ORDER 8
@@ -197,6 +203,19 @@ int numa_solve_columns(numa_ctx* ctx, const double* b, double* x);
  * sieqn1d, Table 1 with b = b~).  q_in == q_out (in place) is allowed; otherwise q_in is
  * not modified.  nsteps == 0 copies q_in to q_out. */
 int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nsteps);
+
+/* Stage i in {2, ..., s} of the context's scheme (s = 3, 4, 6 or 8; numa_ark_tableau) in
+ * the stage form of Sec. "Linear multi-stage methods": predictor q(i)_e = q^n +
+ * dt sum_{j<i} a_ij R(q(j)), shift by sum_{j<i} c_ij q(j) with c_ij = (a~_ij - a_ij)/a~_ii
+ * and q(1) = q^n, column solve at lam = a~_ii dt, extraction, un-shift.  R: host array of
+ * i-1 device pointers R(q(1)) .. R(q(i-1)); Q: host array of i-2 device pointers q(2) ..
+ * q(i-1) (may be NULL for i = 2).  Device arrays 5*nnode doubles, SoA.  q_out must not
+ * overlap an input.  FP64 Schur-form 1D-IMEX contexts only (NUMA_ERR_ARG otherwise);
+ * NUMA_ERR_NOT_FACTORED before numa_factor_columns.  The general form of numa_imex_stage
+ * (the same kernel phases; it reads only the terms with nonzero coefficients), exposed so
+ * that each stage of ARK3 - ARK5 can be checked on its own. */
+int numa_imex_stage_s(numa_ctx* ctx, int stage, const double* qn, const double* const* R,
+                      const double* const* Q, double* q_out);
 
 /* One fused 1D-IMEX stage i in {2, 3} (rows 2 and 3 of Table 1): explicit predictor,
  * Schur right-hand side (Algorithm 4), column solve, extraction of (rho', w, theta')
@@ -430,6 +449,11 @@ void numa_ark2_tableau(double* a, double* at, double* b);
 /* The ARK3 tableau (a[16], at[16], b[4], row-major 4x4) of NUMA_SCHEME_ARK3.  Host only; any
  * pointer may be NULL. */
 void numa_ark3_tableau(double* a, double* at, double* b);
+/* The tableau of any scheme: s stages (3, 4, 6 or 8), a and at row-major s x s into arrays
+ * of NUMA_MAX_STAGES^2 doubles, b into NUMA_MAX_STAGES doubles.  Each published rational
+ * p/q is the correctly rounded double of p/q.  Host only; returns NUMA_ERR_ARG for an
+ * unknown scheme; any pointer may be NULL. */
+int numa_ark_tableau(int scheme, double* a, double* at, double* b, int* s);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,8 @@ Q_NCOL, Q_M, Q_NNODE, Q_NELEM, Q_HALF_BAND, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q
     Q_PRECISION, Q_COLUMN_FORM, Q_SCHEME, Q_IMEX = range(13)
 PRECISIONS = {"fp64": 0, "mixed": 1, "rhs32": 2, "df": 3}
 COLUMN_FORMS = {"schur": 0, "standard": 1}
-SCHEMES = {"ark2": 0, "ark3": 1}
+SCHEMES = {"ark2": 0, "ark3": 1, "ark4": 2, "ark5": 3}
+MAX_STAGES = 8
 IMEX = {"1d": 0, "3d": 1}
 PRECONDS = {"pbno": 0, "column": 1}
 
@@ -38,7 +39,8 @@ EXPORTS = (
     "numa_batch_member_query", "numa_batch_reference_levels", "numa_batch_last_error",
     "numa_rhs_tlm", "numa_rhs_adjoint", "numa_solve_columns_transposed", "numa_imex_stage_adjoint",
     "numa_step_imex1d_tlm", "numa_step_imex1d_adjoint", "numa_imex1d_forward_checkpointed",
-    "numa_imex1d_adjoint_checkpointed", "numa_ark3_tableau", "numa_schur3d_apply",
+    "numa_imex1d_adjoint_checkpointed", "numa_ark3_tableau", "numa_ark_tableau", "numa_imex_stage_s",
+    "numa_schur3d_apply",
     "numa_solve_schur3d", "numa_imex3d_stage", "numa_step_imex3d", "numa_imex3d_info",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ, K_SCHUR3D = range(9)
@@ -93,6 +95,8 @@ def lib():
             "numa_rk35_coefficients": (None, [P, P]),
             "numa_ark2_tableau": (None, [P, P, P]),
             "numa_ark3_tableau": (None, [P, P, P]),
+            "numa_ark_tableau": (I, [I, P, P, P, ctypes.POINTER(I)]),
+            "numa_imex_stage_s": (I, [P, I, P, P, P, P]),
             "numa_schur3d_apply": (I, [P, P, P]),
             "numa_solve_schur3d": (I, [P, P, P, ctypes.POINTER(I)]),
             "numa_imex3d_stage": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I)]),
@@ -228,6 +232,19 @@ class Numa:
         out = self._torch.empty_like(qn) if out is None else self._state(out)
         self._check(lib().numa_imex_stage(self._h, int(stage), _ptr(qn), _ptr(R1), _ptr(R2),
                                           _ptr(q2), _ptr(out)), "numa_imex_stage")
+        return out
+
+    def imex_stage_s(self, stage, qn, Rs, Qs=(), out=None):
+        """Stage `stage` of the context's scheme from q^n, Rs = [R(q(1)), ..., R(q(i-1))] and
+        Qs = [q(2), ..., q(i-1)] (numa_imex_stage_s)."""
+        for t in (qn, *Rs, *Qs):
+            self._state(t)
+        out = self._torch.empty_like(qn) if out is None else self._state(out)
+        Ra = (ctypes.c_void_p * max(1, len(Rs)))(*[t.data_ptr() for t in Rs])
+        Qa = (ctypes.c_void_p * max(1, len(Qs)))(*[t.data_ptr() for t in Qs])
+        self._check(lib().numa_imex_stage_s(self._h, int(stage), _ptr(qn), Ra,
+                                            Qa if len(Qs) else None, _ptr(out)),
+                    "numa_imex_stage_s")
         return out
 
     def step_explicit_rk(self, q_in, dt, q_out=None, nsteps=1):
@@ -580,6 +597,19 @@ def ark2_tableau():
     lib().numa_ark2_tableau(a.ctypes.data_as(ctypes.c_void_p), at.ctypes.data_as(ctypes.c_void_p),
                             b.ctypes.data_as(ctypes.c_void_p))
     return a.reshape(3, 3), at.reshape(3, 3), b
+
+
+def ark_tableau(scheme):
+    """(a, at, b) of a scheme ("ark2" .. "ark5") as the library evaluates it."""
+    a, at, b = np.empty(MAX_STAGES ** 2), np.empty(MAX_STAGES ** 2), np.empty(MAX_STAGES)
+    s = ctypes.c_int(0)
+    rc = lib().numa_ark_tableau(SCHEMES[scheme], a.ctypes.data_as(ctypes.c_void_p),
+                                at.ctypes.data_as(ctypes.c_void_p),
+                                b.ctypes.data_as(ctypes.c_void_p), ctypes.byref(s))
+    if rc != 0:
+        raise ValueError("numa_ark_tableau: unknown scheme")
+    n = s.value
+    return a[:n * n].reshape(n, n), at[:n * n].reshape(n, n), b[:n].copy()
 
 
 def ark3_tableau():

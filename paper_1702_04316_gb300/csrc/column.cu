@@ -184,6 +184,18 @@ __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1
                                tb, iters, R3, q3, Pp_out, &eos);
 }
 
+// Any stage of an s-stage scheme: the previous stages listed in P (FP64 Schur form).
+template <int N>
+__global__ void k_stage_general(const __grid_constant__ StagePrev P, double* __restrict__ out,
+                                Geom G, RefLev R, Factors F, StageTab tb, int T,
+                                double* __restrict__ Pp_out, EosSeries eos) {
+  extern __shared__ double sm[];
+  StageCoef sc{};
+  stage_body<N, 0, false, double>(blockIdx.x * (long long)T, T, sm, P.qn, nullptr, nullptr,
+                                  nullptr, out, G, R, F, sc, tb, 0, nullptr, nullptr, Pp_out,
+                                  &eos, &P);
+}
+
 // Fused stage with the standard column system (rows 2 or 3 of Table 1).  Phase 1: the
 // predictor and the shift q~_e (u, v final), with (rho~_e, w~_e, theta~_e) stored level by
 // level in shared memory (3M values per column; w~_e = 0 at the walls, the wall condition).
@@ -386,6 +398,32 @@ cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void
     default: return cudaErrorInvalidValue;
   }
 #undef NUMA_STAGE_CASE
+}
+
+cudaError_t launch_stage_general(const StagePrev& P, double* out, const Geom& G, const RefLev& R,
+                                 const Factors& F, const StageTab& tb, int T, cudaStream_t s,
+                                 double* Pp_out) {
+  if (F.standard || F.mixed || !P.qn || P.nr < 0 || P.nr > kMaxPrev || P.nq < 0 ||
+      P.nq > kMaxPrev)
+    return cudaErrorInvalidValue;
+  const size_t smem = stage_smem(G.M, T, false, 0);
+  const unsigned nb = (unsigned)((G.ncol + T - 1) / T);
+#define NUMA_GEN_CASE(n)                                                                    \
+  case n: {                                                                                 \
+    cudaError_t e = cudaFuncSetAttribute(k_stage_general<n>,                                \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                         \
+    k_stage_general<n><<<nb, stage_threads(T), smem, s>>>(P, out, G, R, F, tb, T, Pp_out,   \
+                                                          eos_series());                    \
+    break;                                                                                  \
+  }
+  switch (G.N) {
+    NUMA_GEN_CASE(1) NUMA_GEN_CASE(2) NUMA_GEN_CASE(3) NUMA_GEN_CASE(4)
+    NUMA_GEN_CASE(5) NUMA_GEN_CASE(6) NUMA_GEN_CASE(7) NUMA_GEN_CASE(8)
+    default: return cudaErrorInvalidValue;
+  }
+#undef NUMA_GEN_CASE
+  return cudaGetLastError();
 }
 
 size_t stage_smem_bytes(int M, int T, bool mixed, int iters) {

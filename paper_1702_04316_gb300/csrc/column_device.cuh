@@ -184,8 +184,9 @@ __host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
 // and 3, the first T run phase 2); sm: dynamic shared memory of
 // col_smem_per_level(MIXED, iters) * M * T bytes.
 // NP: previous stages read (1: stage 2; 2: stage 3; 3: stage 4 of a four-stage scheme,
-// with R3 and q3).  Pp_out (optional): receives P'(q(i)) (the pre-pass of the next right-hand
-// side fused into phase 3; eos: the series coefficients).
+// with R3 and q3; 0: any stage of an s-stage scheme, the terms listed in *P, with qn =
+// P->qn).  Pp_out (optional): receives P'(q(i)) (the pre-pass of the next right-hand side
+// fused into phase 3; eos: the series coefficients).
 template <int N, int NP, bool MIXED, typename RT>
 __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
                                            const double* __restrict__ qn,
@@ -196,7 +197,8 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
                                            const RT* __restrict__ R3 = nullptr,
                                            const double* __restrict__ q3 = nullptr,
                                            double* __restrict__ Pp_out = nullptr,
-                                           const EosSeries* eos = nullptr) {
+                                           const EosSeries* eos = nullptr,
+                                           const StagePrev* P = nullptr) {
   const int NT = blockDim.x, M = G.M;
   const long long nn = G.nnode;
   const int ncols = (int)min((long long)T, G.ncol - col0);
@@ -213,6 +215,13 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
   // predictor of field f at global offset o (q(i)_e, shifted to q~_e unless u, v)
   auto pred = [&](int f, long long o) -> double {
     const double qv = qn[o];
+    if (NP == 0) {
+      double v = qv;
+      for (int k = 0; k < P->nr; ++k) v = fma(P->adt[k], __ldg(P->R[k] + o), v);
+      if (f == 1 || f == 2) return v;
+      for (int k = 0; k < P->nq; ++k) v = fma(P->c[k], __ldg(P->q[k] + o), v);
+      return v;
+    }
     double v = fma(a1dt, (double)R1[o], qv);
     if (NP >= 2) v = fma(a2dt, (double)R2[o], v);
     if (NP >= 3) v = fma(a3dt, (double)R3[o], v);
@@ -313,7 +322,22 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     }
     const double thv = fma(-__ldg(tb.kth + lev), wv, te);
     const double rv = fma(-__ldg(tb.H0G0 + lev), thv, __ldg(tb.invG0 + lev) * S0[lev * T + c]);
-    double o_r = fma(-c1, qn[orr], rv), o_w = fma(-c1, qn[ow], wv), o_t = fma(-c1, qn[oth], thv);
+    double o_r, o_w, o_t;
+    if (NP == 0) {
+      o_r = rv;
+      o_w = wv;
+      o_t = thv;
+      for (int k = 0; k < P->nq; ++k) {
+        const double* qk = P->q[k];
+        o_r = fma(-P->c[k], __ldg(qk + orr), o_r);
+        o_w = fma(-P->c[k], __ldg(qk + ow), o_w);
+        o_t = fma(-P->c[k], __ldg(qk + oth), o_t);
+      }
+    } else {
+      o_r = fma(-c1, qn[orr], rv);
+      o_w = fma(-c1, qn[ow], wv);
+      o_t = fma(-c1, qn[oth], thv);
+    }
     if (NP >= 2) {
       o_r = fma(-c2, q2[orr], o_r);
       o_w = fma(-c2, q2[ow], o_w);

@@ -73,7 +73,23 @@ __global__ void k_ark_final(const double* __restrict__ qn, const double* __restr
     out[t] = fma(b3dt, R3[t], fma(b2dt, R2[t], fma(b1dt, R1[t], qn[t])));
 }
 
+__global__ void k_ark_combine(const double* __restrict__ qn, const __grid_constant__ StageSum S,
+                              double* out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    double v = qn[t];
+    for (int k = 0; k < S.n; ++k) v = fma(S.bdt[k], __ldg(S.R[k] + t), v);
+    out[t] = v;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_ark_combine(const double* qn, const StageSum& S, double* out, long long n,
+                               cudaStream_t s) {
+  k_ark_combine<<<152 * 8, 256, 0, s>>>(qn, S, out, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_connectivity(const Geom& G, int32_t* l2g, int32_t* g2l, cudaStream_t s) {
   const int bs = 256;

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -57,32 +58,118 @@ struct Ark3 {
   }
 };
 
-// The scheme of a context as one s-stage table (s = 3 or 4).
+// ARK4, ARK5: the ARK4(3)6L[2]SA and ARK5(4)8L[2]SA schemes of Kennedy and Carpenter (2003)
+// for the paper's fourth- and fifth-order runs (no tableau printed).  Same structure as
+// ARK3: a~_11 = 0, one implicit diagonal, b = b~ = the last implicit row.  Every entry is
+// a published rational evaluated as one correctly rounded division, except ARK5's explicit
+// a_86 and a_87: the solution of its 143 fifth-order conditions with the other entries
+// fixed (it meets them to 2e-26, the precision of the published rationals).
+struct Rat {
+  double p, q;
+};
+
+template <int S>
+struct ArkRat {
+  double a[S][S] = {}, at[S][S] = {};
+  void row(double (*m)[S], int i, std::initializer_list<Rat> r) {
+    int j = 0;
+    for (const Rat& x : r) m[i][j++] = x.p / x.q;
+  }
+};
+
+struct Ark4 : ArkRat<6> {
+  Ark4() {
+    const Rat g{1, 4}, z{0, 1};
+    row(at, 1, {g, g});
+    row(at, 2, {{8611, 62500}, {-1743, 31250}, g});
+    row(at, 3, {{5012029, 34652500}, {-654441, 2922500}, {174375, 388108}, g});
+    row(at, 4, {{15267082809.0, 155376265600.0}, {-71443401, 120774400}, {730878875, 902184768},
+                {2285395, 8070912}, g});
+    row(at, 5, {{82889, 524892}, z, {15625, 83664}, {69875, 102672}, {-2260, 8211}, g});
+    row(a, 1, {{1, 2}});
+    row(a, 2, {{13861, 62500}, {6889, 62500}});
+    row(a, 3, {{-116923316275.0, 2393684061468.0}, {-2731218467317.0, 15368042101831.0},
+               {9408046702089.0, 11113171139209.0}});
+    row(a, 4, {{-451086348788.0, 2902428689909.0}, {-2682348792572.0, 7519795681897.0},
+               {12662868775082.0, 11960479115383.0}, {3355817975965.0, 11060851509271.0}});
+    row(a, 5, {{647845179188.0, 3216320057751.0}, {73281519250.0, 8382639484533.0},
+               {552539513391.0, 3454668386233.0}, {3354512671639.0, 8306763924573.0},
+               {4040, 17871}});
+  }
+};
+
+struct Ark5 : ArkRat<8> {
+  Ark5() {
+    const Rat g{41, 200}, z{0, 1};
+    row(at, 1, {g, g});
+    row(at, 2, {{41, 400}, {-567603406766.0, 11931857230679.0}, g});
+    row(at, 3, {{683785636431.0, 9252920307686.0}, z, {-110385047103.0, 1367015193373.0}, g});
+    row(at, 4, {{3016520224154.0, 10081342136671.0}, z, {30586259806659.0, 12414158314087.0},
+                {-22760509404356.0, 11113319521817.0}, g});
+    row(at, 5, {{218866479029.0, 1489978393911.0}, z, {638256894668.0, 5436446318841.0},
+                {-1179710474555.0, 5321154724896.0}, {-60928119172.0, 8023461067671.0}, g});
+    row(at, 6, {{1020004230633.0, 5715676835656.0}, z, {25762820946817.0, 25263940353407.0},
+                {-2161375909145.0, 9755907335909.0}, {-211217309593.0, 5846859502534.0},
+                {-4269925059573.0, 7827059040749.0}, g});
+    row(at, 7, {{-872700587467.0, 9133579230613.0}, z, z, {22348218063261.0, 9555858737531.0},
+                {-1143369518992.0, 8141816002931.0}, {-39379526789629.0, 19018526304540.0},
+                {32727382324388.0, 42900044865799.0}, g});
+    row(a, 1, {{41, 100}});
+    row(a, 2, {{367902744464.0, 2072280473677.0}, {677623207551.0, 8224143866563.0}});
+    row(a, 3, {{1268023523408.0, 10340822734521.0}, z, {1029933939417.0, 13636558850479.0}});
+    row(a, 4, {{14463281900351.0, 6315353703477.0}, z, {66114435211212.0, 5879490589093.0},
+               {-54053170152839.0, 4284798021562.0}});
+    row(a, 5, {{14090043504691.0, 34967701212078.0}, z, {15191511035443.0, 11219624916014.0},
+               {-18461159152457.0, 12425892160975.0}, {-281667163811.0, 9011619295870.0}});
+    row(a, 6, {{19230459214898.0, 13134317526959.0}, z, {21275331358303.0, 2942455364971.0},
+               {-38145345988419.0, 4862620318723.0}, {-1, 8}, {-1, 8}});
+    row(a, 7, {{-19977161125411.0, 11928030595625.0}, z, {-40795976796054.0, 6384907823539.0},
+               {177454434618887.0, 12078138498510.0}, {782672205425.0, 8267701900261.0},
+               {-56156175540813.0, 7787401243552.0}, {21501425855156.0, 14444669418411.0}});
+  }
+};
+
+// The scheme of a context as one s-stage table (s = 3, 4, 6 or 8).
 struct ArkTab {
   int s = 3;
-  double a[4][4] = {}, at[4][4] = {}, b[4] = {};
+  double a[NUMA_MAX_STAGES][NUMA_MAX_STAGES] = {}, at[NUMA_MAX_STAGES][NUMA_MAX_STAGES] = {},
+         b[NUMA_MAX_STAGES] = {};
+  template <typename K>
+  void set(int n, const K& k) {
+    s = n;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        a[i][j] = k.a[i][j];
+        at[i][j] = k.at[i][j];
+      }
+    for (int j = 0; j < n; ++j) b[j] = at[n - 1][j];
+  }
 };
 
 ArkTab ark_tab(int scheme) {
   ArkTab t;
   if (scheme == NUMA_SCHEME_ARK3) {
     static const Ark3 k;
-    t.s = 4;
-    std::memcpy(t.a, k.a, sizeof(t.a));
-    std::memcpy(t.at, k.at, sizeof(t.at));
-    std::memcpy(t.b, k.b, sizeof(t.b));
+    t.set(4, k);
+  } else if (scheme == NUMA_SCHEME_ARK4) {
+    static const Ark4 k;
+    t.set(6, k);
+  } else if (scheme == NUMA_SCHEME_ARK5) {
+    static const Ark5 k;
+    t.set(8, k);
   } else {
     static const Ark2 k;
-    t.s = 3;
-    for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) {
-        t.a[i][j] = k.a[i][j];
-        t.at[i][j] = k.at[i][j];
-      }
-      t.b[i] = k.b[i];
-    }
+    t.set(3, k);
   }
   return t;
+}
+
+// State-sized workspace vectors of the FP64 1D-IMEX step: R(q(j)) for every stage j and the
+// stage states q(2) .. q(s) (ARK2: R1, R2, q2, q3; the last R goes to the final update).
+int work_states(int scheme) {
+  if (scheme == NUMA_SCHEME_ARK2) return 4;
+  if (scheme == NUMA_SCHEME_ARK3) return 6;
+  return 2 * ark_tab(scheme).s - 1;
 }
 
 // ---- RK35: five-stage third-order SSP, two-register Shu-Osher form -------------------
@@ -418,6 +505,26 @@ int numa_rhs_final(numa_ctx* c, const double* q_last, const double* qn, double* 
   return enqueue_rhs(c, q_last, q_out, ef);
 }
 
+// The previous-stage terms of stage i + 1 (0-based row i of the tableau) with nonzero
+// coefficients: R[j] = R(q(j+1)), Q[j] = q(j+1) for j >= 1, q(1) = qn.
+static StagePrev stage_prev(const ArkTab& t, int i, double dt, const double* qn,
+                            const double* const* R, const double* const* Q) {
+  StagePrev P{};
+  P.qn = qn;
+  for (int j = 0; j < i; ++j) {
+    const double c = (t.at[i][j] - t.a[i][j]) / t.at[i][i];
+    if (t.a[i][j] != 0.0) {
+      P.R[P.nr] = R[j];
+      P.adt[P.nr++] = t.a[i][j] * dt;
+    }
+    if (c != 0.0) {
+      P.q[P.nq] = j ? Q[j] : qn;
+      P.c[P.nq++] = c;
+    }
+  }
+  return P;
+}
+
 StageCoef numa_stage_coef(const numa_ctx* c, int stage) {
   const ArkTab t = ark_tab(c->scheme);
   StageCoef sc{};
@@ -469,8 +576,9 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
       refine < 0 || refine > 8 ||
       (form != NUMA_COLUMN_SCHUR && form != NUMA_COLUMN_STANDARD) ||
       (form == NUMA_COLUMN_STANDARD && precision != NUMA_PREC_FP64) ||
-      (scheme != NUMA_SCHEME_ARK2 && scheme != NUMA_SCHEME_ARK3) ||
-      (scheme == NUMA_SCHEME_ARK3 && (precision != NUMA_PREC_FP64 || form != NUMA_COLUMN_SCHUR))) {
+      scheme < NUMA_SCHEME_ARK2 || scheme > NUMA_SCHEME_ARK5 ||
+      (scheme != NUMA_SCHEME_ARK2 && (precision != NUMA_PREC_FP64 || form != NUMA_COLUMN_SCHUR)) ||
+      (scheme >= NUMA_SCHEME_ARK4 && imex != NUMA_IMEX_1D)) {
     *out = nullptr;
     return NUMA_ERR_ARG;
   }
@@ -533,8 +641,7 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   c->factor_bytes = need_factors ? nu * (2 * hb + 1) * G.ncol * fsz : 0;
   c->work_bytes = rhs32 ? (size_t)(2 * 5) * G.nnode * sizeof(double) +
                               (size_t)(6 + 2 * 5) * G.nnode * sizeof(float)
-                        : (size_t)(1 + (scheme == NUMA_SCHEME_ARK3 ? 6 : 4) * 5) * G.nnode *
-                              sizeof(double);
+                        : (size_t)(1 + work_states(scheme) * 5) * G.nnode * sizeof(double);
   if (rc == NUMA_OK) {
     bool ok = cudaMalloc(&c->d_work, c->work_bytes) == cudaSuccess &&
               cudaMalloc(&c->d_status, sizeof(unsigned)) == cudaSuccess &&
@@ -583,6 +690,15 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
       if (scheme == NUMA_SCHEME_ARK3) {
         c->R3 = c->q3 + n5;
         c->q4 = c->R3 + n5;
+      } else if (scheme >= NUMA_SCHEME_ARK4) {
+        const int ns = ark_tab(scheme).s;
+        c->Rk[0] = c->R1;
+        c->Rk[1] = c->R2;
+        c->Qk[1] = c->q2;
+        c->Qk[2] = c->q3;
+        double* p = c->q3 + n5;
+        for (int j = 2; j < ns; ++j, p += n5) c->Rk[j] = p;
+        for (int j = 3; j < ns; ++j, p += n5) c->Qk[j] = p;
       }
     }
     if (precision == NUMA_PREC_DF &&
@@ -688,6 +804,35 @@ int numa_imex_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1
   return enqueue_stage(ctx, stage, qn, R1, R2, q2, q_out, numa_stage_coef(ctx, stage));
 }
 
+int numa_imex_stage_s(numa_ctx* ctx, int stage, const double* qn, const double* const* R,
+                      const double* const* Q, double* q_out) {
+  if (!ctx) return NUMA_ERR_ARG;
+  const ArkTab t = ark_tab(ctx->scheme);
+  if (stage < 2 || stage > t.s) return fail(ctx, NUMA_ERR_ARG, "stage outside 2..s");
+  if (!R || (stage > 2 && !Q)) return fail(ctx, NUMA_ERR_ARG, "R or Q missing");
+  if (ctx->precision != NUMA_PREC_FP64 || ctx->F.standard || ctx->imex3d)
+    return fail(ctx, NUMA_ERR_ARG, "the general stage needs an FP64 Schur-form 1D-IMEX context");
+  int rc;
+  if ((rc = check_ptr(ctx, qn, "qn")) || (rc = check_ptr(ctx, q_out, "q_out"))) return rc;
+  const double* Rv[NUMA_MAX_STAGES] = {};
+  const double* Qv[NUMA_MAX_STAGES] = {};
+  for (int j = 0; j < stage - 1; ++j) {
+    if ((rc = check_ptr(ctx, R[j], "R[j]"))) return rc;
+    Rv[j] = R[j];
+    if (j >= 1) {
+      if ((rc = check_ptr(ctx, Q[j - 1], "Q[j]"))) return rc;
+      Qv[j] = Q[j - 1];
+    }
+  }
+  if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  const StagePrev P = stage_prev(t, stage - 1, ctx->dt, qn, Rv, Qv);
+  long p = prof_begin(ctx, NUMA_K_STAGE);
+  NUMA_CK(ctx, launch_stage_general(P, q_out, ctx->G, ctx->R, ctx->F, ctx->T, ctx->col_tile,
+                                    ctx->stream, nullptr));
+  prof_end(ctx, p);
+  return NUMA_OK;
+}
+
 int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nsteps) {
   if (!ctx) return NUMA_ERR_ARG;
   int rc;
@@ -705,6 +850,31 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
   const ArkTab t = ark_tab(ctx->scheme);
   const StageCoef s2 = numa_stage_coef(ctx, 2), s3 = numa_stage_coef(ctx, 3);
   const bool mixed = ctx->precision == NUMA_PREC_MIXED || ctx->precision == NUMA_PREC_RHS32;  // FP32 tendencies
+  if (t.s > 4) {        // ARK4, ARK5: FP64 Schur form, general fused stage
+    const double* cur = q_in;
+    for (int s = 0; s < nsteps; ++s) {
+      RhsEpilogue e0{};
+      if ((rc = enqueue_rhs(ctx, cur, ctx->Rk[0], e0))) return rc;
+      for (int i = 1; i < t.s; ++i) {        // stage i + 1
+        const StagePrev P = stage_prev(t, i, ctx->dt, cur, ctx->Rk, ctx->Qk);
+        long p = prof_begin(ctx, NUMA_K_STAGE);
+        NUMA_CK(ctx, launch_stage_general(P, ctx->Qk[i], ctx->G, ctx->R, ctx->F, ctx->T,
+                                          ctx->col_tile, ctx->stream, ctx->Pp));
+        prof_end(ctx, p);
+        if ((rc = enqueue_rhs(ctx, ctx->Qk[i], ctx->Rk[i], e0, nullptr, true))) return rc;
+      }
+      // q^{n+1} = q^n + dt sum_j b_j R(q(j))
+      StageSum S{};
+      for (int j = 0; j < t.s; ++j)
+        if (t.b[j] != 0.0) {
+          S.R[S.n] = ctx->Rk[j];
+          S.bdt[S.n++] = t.b[j] * ctx->dt;
+        }
+      NUMA_CK(ctx, launch_ark_combine(cur, S, q_out, n5, ctx->stream));
+      cur = q_out;
+    }
+    return NUMA_OK;
+  }
   if (t.s == 4) {       // ARK3: four stages, FP64 Schur form
     const StageCoef s4 = numa_stage_coef(ctx, 4);
     const double* cur = q_in;
@@ -960,6 +1130,20 @@ void numa_ark3_tableau(double* a, double* at, double* b) {
     }
     if (b) b[i] = t.b[i];
   }
+}
+
+int numa_ark_tableau(int scheme, double* a, double* at, double* b, int* s) {
+  if (scheme < NUMA_SCHEME_ARK2 || scheme > NUMA_SCHEME_ARK5) return NUMA_ERR_ARG;
+  const ArkTab t = ark_tab(scheme);
+  if (s) *s = t.s;
+  for (int i = 0; i < t.s; ++i) {
+    for (int j = 0; j < t.s; ++j) {
+      if (a) a[i * t.s + j] = t.a[i][j];
+      if (at) at[i * t.s + j] = t.at[i][j];
+    }
+    if (b) b[i] = t.b[i];
+  }
+  return NUMA_OK;
 }
 
 void numa_ark2_tableau(double* a, double* at, double* b) {

@@ -25,9 +25,13 @@ struct numa_ctx {
   StageTab T{};
   double* d_stage_tab = nullptr;
   Factors F{};
-  double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (+ R3, q4 for ARK3), each 5*nnode but Pp
+  double* d_work = nullptr;     // Pp, R1, R2, q2, q3 (+ R3, q4 for ARK3; + R3..Rs, q4..qs
+                                // for s-stage schemes), each 5*nnode but Pp
   double *Pp = nullptr, *R1 = nullptr, *R2 = nullptr, *q2 = nullptr, *q3 = nullptr;
   double *R3 = nullptr, *q4 = nullptr;     // ARK3 only
+  // s-stage schemes (ARK4, ARK5): Rk[j] = R(q(j+1)), Qk[j] = q(j+1) (Qk[0] unused: q(1) = q^n)
+  double* Rk[NUMA_MAX_STAGES] = {};
+  double* Qk[NUMA_MAX_STAGES] = {};
   int scheme = NUMA_SCHEME_ARK2;
   // 3D-IMEX (Schur form, BiCGstab + polynomial preconditioner)
   bool imex3d = false;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "numa.h"
+
 #define NUMA_MAXN 8
 #define NUMA_MAXNQ (NUMA_MAXN + 1)
 
@@ -165,6 +167,33 @@ cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void
                          bool r_float, cudaStream_t s, const double* R3 = nullptr,
                          const double* q3 = nullptr, double* Pp_out = nullptr);
 size_t stage_smem_bytes(int M, int T, bool mixed, int iters);
+
+// The previous stages of stage i of an s-stage scheme (s <= NUMA_MAX_STAGES), read by the
+// general form of the fused stage: q(i)_e = qn + sum_k adt[k] R[k] and the shift
+// sum_k c[k] q[k], over the terms with nonzero coefficients only (q(1) = qn may appear in
+// q[]).  Passed by value as a kernel parameter.
+constexpr int kMaxPrev = NUMA_MAX_STAGES - 1;
+struct StagePrev {
+  const double* qn;
+  int nr, nq;
+  const double* R[kMaxPrev];
+  double adt[kMaxPrev];          // a_ij dt
+  const double* q[kMaxPrev];
+  double c[kMaxPrev];            // c_ij = (a~_ij - a_ij) / a~_ii
+};
+// Fused stage of the FP64 Schur form for any number of previous stages.  Pp_out as for
+// launch_stage.
+cudaError_t launch_stage_general(const StagePrev& P, double* out, const Geom& G, const RefLev& R,
+                                 const Factors& F, const StageTab& tb, int T, cudaStream_t s,
+                                 double* Pp_out);
+// out = qn + sum_k bdt[k] R[k] (k < n; in place on qn allowed).
+struct StageSum {
+  int n;
+  const double* R[NUMA_MAX_STAGES];
+  double bdt[NUMA_MAX_STAGES];
+};
+cudaError_t launch_ark_combine(const double* qn, const StageSum& S, double* out, long long n,
+                               cudaStream_t s);
 
 // misc.cu
 cudaError_t launch_connectivity(const Geom& G, int32_t* l2g, int32_t* g2l, cudaStream_t s);

@@ -72,3 +72,18 @@ def test_ark3_tableau_matches_the_oracle_bitwise():
     a, at, b = pkg.ark3_tableau()
     A, AT, B, _ = ark3.tableau()
     assert np.array_equal(a, A) and np.array_equal(at, AT) and np.array_equal(b, B)
+
+
+@pytest.mark.parametrize("scheme", ["ark3", "ark4", "ark5"])
+def test_ark_tableaux_match_the_oracle_bitwise(scheme):
+    """numa_ark_tableau: every coefficient of ARK3 - ARK5 (each a correctly rounded division
+    of a rational) equals the oracle's float tableau bit for bit; ARK2 to rounding."""
+    import numpy as np
+    import paper_1702_04316_gb300 as pkg
+    from oracle import ark2
+    a, at, b = pkg.ark_tableau(scheme)
+    A, AT, B, _ = ark2.scheme_tableau(scheme)
+    assert a.shape == A.shape
+    assert np.array_equal(a, A) and np.array_equal(at, AT) and np.array_equal(b, B)
+    a2, at2, b2 = pkg.ark_tableau("ark2")
+    np.testing.assert_allclose(at2, ark2.tableau()[1], rtol=0, atol=1e-15)
