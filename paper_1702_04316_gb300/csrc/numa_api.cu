@@ -303,6 +303,9 @@ void free_all(numa_ctx* c) {
   cudaFree(c->d_status);
   cudaFree(c->d_count);
   cudaFree(c->d_hoststate);
+  for (cudaEvent_t e : c->host_ev) cudaEventDestroy(e);
+  if (c->cs_in) cudaStreamDestroy(c->cs_in);
+  if (c->cs_out) cudaStreamDestroy(c->cs_out);
   cudaFree(c->d_adj);
   cudaFree(c->d_adjtab);
   cudaFree(c->d_w3);
@@ -663,6 +666,7 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
     c->nperm = rhs_perm_size(G);
     std::vector<int> hp((size_t)c->nperm);
     build_rhs_perm(G, hp.data());
+    rhs_perm_rows(G, c->perm_row_off, c->perm_row_y);
     if (cudaMalloc(&c->d_perm, hp.size() * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       rc = NUMA_ERR_OOM;
@@ -967,6 +971,106 @@ int numa_step_explicit_rk(numa_ctx* ctx, const double* q_in, double* q_out, doub
   return NUMA_OK;
 }
 
+namespace {
+
+// Slabs of the pipelined host run: runs of whole tile rows of the RHS thread order.
+const int kHostSlabs = 8;
+
+// FP64 ARK2 1D-IMEX steps from host memory to host memory with the copies overlapped.  The
+// upload is issued slab by slab (node rows [y0, y1) of every field) on cs_in; the first
+// right-hand side of the first step waits for each slab and computes P' and R slab by slab,
+// R of slab k once slab k + 1 (its stencil's far side, at most N node rows away) is on the
+// device.  The final update of the last step is issued slab by slab; each slab goes back
+// to the host on cs_out as soon as it is final.  Steps in between run unchanged.
+int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nsteps) {
+  const Geom& G = ctx->G;
+  const long long nn = G.nnode;
+  const long long plane = (long long)G.nxg * G.M;        // nodes per node row
+  const int rows = (int)ctx->perm_row_y.size() - 1;
+  const int K = std::min(kHostSlabs, rows);
+  if (!ctx->cs_in) {
+    if (cudaStreamCreateWithFlags(&ctx->cs_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cs_out, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(ctx, NUMA_ERR_CUDA, "copy streams");
+  }
+  while ((int)ctx->host_ev.size() < 2 * kHostSlabs + 2) {
+    cudaEvent_t e;
+    NUMA_CK(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->host_ev.push_back(e);
+  }
+  cudaEvent_t* ev_in = ctx->host_ev.data();
+  cudaEvent_t* ev_out = ev_in + kHostSlabs;
+  cudaEvent_t ev_start = ev_in[2 * kHostSlabs], ev_done = ev_in[2 * kHostSlabs + 1];
+  auto r0 = [&](int k) { return (int)((long long)k * rows / K); };       // first tile row
+  auto n0 = [&](int k) { return (long long)ctx->perm_row_y[r0(k)] * plane; };   // first node
+  auto p0 = [&](int k) { return ctx->perm_row_off[r0(k)]; };           // first thread
+  double* q = ctx->d_hoststate;
+  const size_t pitch = nn * sizeof(double);
+  // the upload starts after everything already in the context's stream
+  NUMA_CK(ctx, cudaEventRecord(ev_start, ctx->stream));
+  NUMA_CK(ctx, cudaStreamWaitEvent(ctx->cs_in, ev_start, 0));
+  for (int k = 0; k < K; ++k) {
+    const long long a = n0(k), b = n0(k + 1);
+    NUMA_CK(ctx, cudaMemcpy2DAsync(q + a, pitch, hin + a, pitch, (b - a) * sizeof(double), 5,
+                                   cudaMemcpyHostToDevice, ctx->cs_in));
+    NUMA_CK(ctx, cudaEventRecord(ev_in[k], ctx->cs_in));
+  }
+  const ArkTab t = ark_tab(ctx->scheme);
+  const StageCoef s2 = numa_stage_coef(ctx, 2), s3 = numa_stage_coef(ctx, 3);
+  int rc;
+  for (int s = 0; s < nsteps; ++s) {
+    RhsEpilogue e0{};
+    if (s == 0) {
+      long p = prof_begin(ctx, NUMA_K_RHS);
+      for (int k = 0; k <= K; ++k) {
+        if (k < K) {
+          NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[k], 0));
+          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, n0(k), n0(k + 1), ctx->stream));
+        }
+        if (k >= 1)
+          NUMA_CK(ctx, launch_rhs(q, ctx->Pp, ctx->R1, ctx->d_perm + p0(k - 1), p0(k) - p0(k - 1),
+                                  G, ctx->C, ctx->R, e0, ctx->stream));
+      }
+      prof_end(ctx, p);
+    } else if ((rc = enqueue_rhs(ctx, q, ctx->R1, e0))) {
+      return rc;
+    }
+    if ((rc = enqueue_stage(ctx, 2, q, ctx->R1, nullptr, nullptr, ctx->q2, s2, false, ctx->Pp))) return rc;
+    if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0, nullptr, true))) return rc;
+    if ((rc = enqueue_stage(ctx, 3, q, ctx->R1, ctx->R2, ctx->q2, ctx->q3, s3, false, ctx->Pp))) return rc;
+    RhsEpilogue ef{};
+    ef.mode = 2;
+    ef.b1dt = t.b[0] * ctx->dt;
+    ef.b2dt = t.b[1] * ctx->dt;
+    ef.b3dt = t.b[2] * ctx->dt;
+    ef.u0 = q;
+    ef.R1 = ctx->R1;
+    ef.R2 = ctx->R2;
+    if (s + 1 < nsteps) {
+      if ((rc = enqueue_rhs(ctx, ctx->q3, q, ef, nullptr, true))) return rc;
+      continue;
+    }
+    // last step: final update (in place, node by node) and download, slab by slab
+    long p = prof_begin(ctx, NUMA_K_RHS);
+    for (int k = 0; k < K; ++k) {
+      NUMA_CK(ctx, launch_rhs(ctx->q3, ctx->Pp, q, ctx->d_perm + p0(k), p0(k + 1) - p0(k), G,
+                              ctx->C, ctx->R, ef, ctx->stream));
+      NUMA_CK(ctx, cudaEventRecord(ev_out[k], ctx->stream));
+      NUMA_CK(ctx, cudaStreamWaitEvent(ctx->cs_out, ev_out[k], 0));
+      const long long a = n0(k), b = n0(k + 1);
+      NUMA_CK(ctx, cudaMemcpy2DAsync(hout + a, pitch, q + a, pitch, (b - a) * sizeof(double), 5,
+                                     cudaMemcpyDeviceToHost, ctx->cs_out));
+    }
+    prof_end(ctx, p);
+  }
+  NUMA_CK(ctx, cudaEventRecord(ev_done, ctx->cs_out));
+  NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_done, 0));
+  NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return NUMA_OK;
+}
+
+}  // namespace
+
 int numa_run_host(numa_ctx* ctx, int method, const double* q_in_host, double* q_out_host,
                   int nsteps, double dt) {
   if (!ctx) return NUMA_ERR_ARG;
@@ -979,6 +1083,9 @@ int numa_run_host(numa_ctx* ctx, int method, const double* q_in_host, double* q_
       return fail(ctx, NUMA_ERR_OOM, "host-run state buffer");
     }
   }
+  if (method == 0 && nsteps >= 1 && ctx->factored && !ctx->imex3d && fuse_pressure(ctx) &&
+      ctx->scheme == NUMA_SCHEME_ARK2)
+    return run_host_pipelined(ctx, q_in_host, q_out_host, nsteps);
   NUMA_CK(ctx, cudaMemcpyAsync(ctx->d_hoststate, q_in_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
   int rc = (method == 0) ? numa_step_imex1d(ctx, ctx->d_hoststate, ctx->d_hoststate, nsteps)
                          : numa_step_explicit_rk(ctx, ctx->d_hoststate, ctx->d_hoststate, dt, nsteps);

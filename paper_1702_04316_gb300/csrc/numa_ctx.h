@@ -50,6 +50,12 @@ struct numa_ctx {
   unsigned* d_status = nullptr;
   unsigned long long* d_count = nullptr;
   double* d_hoststate = nullptr;
+  // pipelined host runs (numa_run_host): tile-row offsets of the RHS thread order, the
+  // upload and download streams and their per-slab events
+  std::vector<long long> perm_row_off;
+  std::vector<int> perm_row_y;
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  std::vector<cudaEvent_t> host_ev;
   // differentiation form (allocated on first use): 59 x nnode doubles of workspace and the
   // transposed derivative tap tables of the three axes
   double* d_adj = nullptr;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "numa.h"
 
 #define NUMA_MAXN 8
@@ -111,6 +113,9 @@ struct StageTab {
 // rhs.cu
 cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const RefLev& R,
                             cudaStream_t s);
+// P' for the nodes g0 <= g < g1 only.
+cudaError_t launch_pressure_range(const double* q, double* Pp, const Geom& G, const RefLev& R,
+                                  long long g0, long long g1, cudaStream_t s);
 // MODE 0: out = R(q);  MODE 1 (RK stage): out = alpha*u0 + (1-alpha)*q + beta*dt*R(q);
 // MODE 2 (ARK2 final): out = qn + dt*(b1*R1 + b2*R2 + b3*R(q));
 // MODE 3 (four-stage ARK final, FP64 only): out = qn + dt*(b1*R1 + b2*R2 + b3*R3 + b4*R(q)).
@@ -150,6 +155,11 @@ cudaError_t launch_rhs32d(const double* q, const float* F32, double* out0, const
                           const Coef3& C, const RefLev& R, cudaStream_t s);
 long long rhs_perm_size(const Geom& G);
 void build_rhs_perm(const Geom& G, int* out);
+// The thread order is built one row of tiles at a time (tiles of 4N x 4N node columns, the
+// last row taking the end node): off[r] is the first entry of tile row r, whose node rows
+// start at y0[r]; off and y0 end with the total and nyg.  A run of whole tile rows is one
+// contiguous range of the order.
+void rhs_perm_rows(const Geom& G, std::vector<long long>& off, std::vector<int>& y0);
 
 // column.cu
 cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,

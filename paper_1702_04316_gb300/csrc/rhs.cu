@@ -29,9 +29,9 @@ namespace {
 using namespace numa_dev;
 
 __global__ void k_pressure(const double* __restrict__ q, double* __restrict__ Pp, Geom G,
-                           RefLev R, EosSeries S) {
-  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= G.nnode) return;
+                           RefLev R, EosSeries S, long long g0, long long g1) {
+  const long long g = g0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= g1) return;
   Pp[g] = eos_node(q, g, G, R, S);
 }
 
@@ -106,7 +106,16 @@ cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const Re
                             cudaStream_t s) {
   const int bs = 256;
   const long long nb = (G.nnode + bs - 1) / bs;
-  k_pressure<<<(unsigned)nb, bs, 0, s>>>(q, Pp, G, R, eos_series());
+  k_pressure<<<(unsigned)nb, bs, 0, s>>>(q, Pp, G, R, eos_series(), 0, G.nnode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pressure_range(const double* q, double* Pp, const Geom& G, const RefLev& R,
+                                  long long g0, long long g1, cudaStream_t s) {
+  if (g0 < 0 || g1 > G.nnode || g0 > g1) return cudaErrorInvalidValue;
+  if (g0 == g1) return cudaSuccess;
+  const int bs = 256;
+  k_pressure<<<(unsigned)((g1 - g0 + bs - 1) / bs), bs, 0, s>>>(q, Pp, G, R, eos_series(), g0, g1);
   return cudaGetLastError();
 }
 
@@ -146,14 +155,15 @@ cudaError_t launch_rhs32(const double* q, const float* F32, float* out32, double
 // stencil neighbours are still in L2).
 static const int kTile = 4;
 
-template <typename Emit>
-static void walk_rhs_perm(const Geom& G, Emit emit) {
+template <typename Emit, typename Row>
+static void walk_rhs_perm(const Geom& G, Emit emit, Row row) {
   const int tn = kTile * G.N;
   std::vector<int> cz(G.M);
   for (int iz = 0; iz < G.M; ++iz) cz[iz] = node_class(iz, G.N, G.nez);
   std::vector<long long> bucket[27];
   for (int y0 = 0; y0 < G.nyg; y0 += tn) {
     const int y1 = (G.nyg - y0 <= tn + 1) ? G.nyg : y0 + tn;   // the last tile takes the end node
+    row(y0);
     for (int x0 = 0; x0 < G.nxg; x0 += tn) {
       const int x1 = (G.nxg - x0 <= tn + 1) ? G.nxg : x0 + tn;
       for (auto& b : bucket) b.clear();
@@ -178,11 +188,23 @@ static void walk_rhs_perm(const Geom& G, Emit emit) {
 
 long long rhs_perm_size(const Geom& G) {
   long long n = 0;
-  walk_rhs_perm(G, [&](long long) { ++n; });
+  walk_rhs_perm(G, [&](long long) { ++n; }, [](int) {});
   return n;
 }
 
 void build_rhs_perm(const Geom& G, int* out) {
   long long n = 0;
-  walk_rhs_perm(G, [&](long long g) { out[n++] = (int)g; });
+  walk_rhs_perm(G, [&](long long g) { out[n++] = (int)g; }, [](int) {});
+}
+
+void rhs_perm_rows(const Geom& G, std::vector<long long>& off, std::vector<int>& y0) {
+  off.clear();
+  y0.clear();
+  long long n = 0;
+  walk_rhs_perm(G, [&](long long) { ++n; }, [&](int y) {
+    off.push_back(n);
+    y0.push_back(y);
+  });
+  off.push_back(n);
+  y0.push_back(G.nyg);
 }
