@@ -7,10 +7,11 @@ gives a 164 MB state (larger than the 129 MB L2) and about 1.7 GB of device memo
 Every step reads the same input and writes a separate output.
 
   python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0] [--adj 0]
-                                                [--precision mixed]
+                                                [--precision mixed] [--scheme ark5]
 
 --adj K also runs K adjoint steps (numa_step_imex1d_adjoint) and K tangent-linear steps from
-the same input, for captures of the differentiation form's kernels.
+the same input, for captures of the differentiation form's kernels.  --scheme selects the
+ARK scheme of the steps (ark2 .. ark5; FP64).
 """
 import argparse
 import os
@@ -31,6 +32,7 @@ def main():
     ap.add_argument("--adj", type=int, default=0)
     ap.add_argument("--C", type=float, default=15.0)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "rhs32", "df"])
+    ap.add_argument("--scheme", default="ark2", choices=["ark2", "ark3", "ark4", "ark5"])
     a = ap.parse_args()
     import torch
     import paper_1702_04316_gb300 as pkg
@@ -41,7 +43,7 @@ def main():
     xi = np.array([-1.0, -np.sqrt(3.0 / 7.0), 0.0, np.sqrt(3.0 / 7.0), 1.0])
     c_s = (1004.67 / (1004.67 - 287.17) * 287.17 * 300.0) ** 0.5
     dt = a.C * (xi[1] + 1.0) / 2.0 * (Lz / nez) / c_s
-    g = pkg.Numa(nex, nex, nez, L, L, Lz, N, dt, precision=a.precision)
+    g = pkg.Numa(nex, nex, nez, L, L, Lz, N, dt, precision=a.precision, scheme=a.scheme)
     lev = g.reference_levels()
     h = L / nex
     ax = np.concatenate([e * h + (1.0 + xi[:-1]) * h / 2.0 for e in range(nex)] + [[L]])
@@ -61,7 +63,8 @@ def main():
     assert g.count_nonfinite(q1) == 0
     assert g.status() == pkg.NUMA_OK
     g.close()
-    print("profile_case ok: nex=%d steps=%d rk=%d adj=%d" % (nex, a.steps, a.rk, a.adj))
+    print("profile_case ok: nex=%d steps=%d rk=%d adj=%d scheme=%s" % (nex, a.steps, a.rk, a.adj,
+                                                                       a.scheme))
 
 
 if __name__ == "__main__":

@@ -160,3 +160,22 @@ def test_ark3_step_sampled(setup):
     gi, wi = window_nodes(case.mesh, 40, 40, 11, 5)
     e = rel_l2(out[:, gi], ref[:, wi])
     assert np.all(e <= 1e-9), e
+
+
+@pytest.mark.parametrize("scheme,ex0,ey0,Wn,margin", [("ark4", 40, 40, 15, 7), ("ark5", 0, 77, 19, 9)])
+def test_ark45_step_sampled(setup, scheme, ex0, ey0, Wn, margin):
+    """An ARK4 step has six RHS evaluations and an ARK5 step eight: windows of 15 x 15 and
+    19 x 19 elements, margins 7 and 9 (the ARK5 window touches the west and north walls,
+    where it is exact up to the wall)."""
+    from oracle import ark2
+    from oracle.column import Column
+    s = setup
+    case = s["case"]
+    g = s["pkg"].Numa(NEX, NEX, NEZ, L, L, LZ, N, s["dt"], scheme=scheme)
+    out = g.step_imex1d(s["qg"], g.empty_state(), 1).cpu().numpy()
+    g.close()
+    sub, qs = window(case.mesh, s["q0"], ex0, ey0, Wn)
+    ref = ark2.HEVI(sub, Column(sub), s["dt"], scheme=scheme).step(qs, 1)
+    gi, wi = window_nodes(case.mesh, ex0, ey0, Wn, margin)
+    e = rel_l2(out[:, gi], ref[:, wi])
+    assert np.all(e <= 1e-9), e
