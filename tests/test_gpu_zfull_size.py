@@ -165,8 +165,8 @@ def test_ark3_step_sampled(setup):
 @pytest.mark.parametrize("scheme,ex0,ey0,Wn,margin", [("ark4", 40, 40, 15, 7), ("ark5", 0, 77, 19, 9)])
 def test_ark45_step_sampled(setup, scheme, ex0, ey0, Wn, margin):
     """An ARK4 step has six RHS evaluations and an ARK5 step eight: windows of 15 x 15 and
-    19 x 19 elements, margins 7 and 9 (the ARK5 window touches the west and north walls,
-    where it is exact up to the wall)."""
+    19 x 19 elements, margins 7 and 9 (the ARK5 window lies against the west and north
+    walls)."""
     from oracle import ark2
     from oracle.column import Column
     s = setup
@@ -179,3 +179,64 @@ def test_ark45_step_sampled(setup, scheme, ex0, ey0, Wn, margin):
     gi, wi = window_nodes(case.mesh, ex0, ey0, Wn, margin)
     e = rel_l2(out[:, gi], ref[:, wi])
     assert np.all(e <= 1e-9), e
+
+
+# ---- the precision form at its own full size: 64 x 64 x 10 elements, N = 7 ----------------
+P_NEX, P_NEZ, P_N, P_L, P_LZ = 64, 10, 7, 2000e3, 10e3
+P_WINDOWS = [(0, 0), (30, 41), (57, 57)]
+
+
+@pytest.fixture(scope="module")
+def psetup():
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    case = Case(P_NEX, P_NEX, P_NEZ, P_N, P_L, P_L, P_LZ)
+    dt = case.dt_for(15.0)
+    amp = float(np.random.Generator(np.random.PCG64(3000)).uniform(0.1, 2.0))
+    q0 = case.state(3001, kind="balanced", amp=amp)
+    # small smooth velocities, so that every term of the right-hand side is exercised
+    q0 = q0 + case.state(3002, kind="random", amp=0.1) * np.array([0, 1, 1, 1, 0])[:, None]
+    return dict(torch=torch, pkg=pkg, case=case, dt=dt, q0=q0, qg=torch.from_numpy(q0).cuda())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 5e-6), ("rhs32", 5e-6)])
+def test_precision_form_rhs_sampled(psetup, precision, tol):
+    """R(q) of the FP64, mixed and rhs32 contexts on the precision form's full mesh against
+    the oracle on 7 x 7-element windows (margin 1): FP64 to 1e-11, the FP32 right-hand
+    sides to 5e-6 relative L2 per field.  (At N = 7 the FP32 derivative sums have up to
+    2N = 14 terms and LGL derivative weights up to N(N+1)/4 = 14, against 8 and 5 at N = 4:
+    theta' measured 2.1e-6 here, against below 2e-6 at N = 4.)"""
+    from oracle.rhs import rhs
+    from oracle.column import Column
+    s = psetup
+    case = s["case"]
+    g = s["pkg"].Numa(P_NEX, P_NEX, P_NEZ, P_L, P_L, P_LZ, P_N, s["dt"], precision=precision)
+    r = g.rhs_explicit(s["qg"]).cpu().numpy()
+    g.close()
+    for ex0, ey0 in P_WINDOWS:
+        sub, qs = window(case.mesh, s["q0"], ex0, ey0, 7)
+        ref = rhs(sub, Column(sub), qs)
+        gi, wi = window_nodes(case.mesh, ex0, ey0, 7, 1)
+        e = rel_l2(r[:, gi], ref[:, wi])
+        assert np.all(e <= tol), (ex0, ey0, e)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-5), ("rhs32", 1e-5)])
+def test_precision_form_step_sampled(psetup, precision, tol):
+    """One HEVI step at C = 15 on the precision form's full mesh, against the oracle on
+    7 x 7-element windows (margin 3): FP64 to the run tolerance, the mixed and rhs32 forms to
+    1e-5 relative L2 per field."""
+    from oracle import ark2
+    from oracle.column import Column
+    s = psetup
+    case = s["case"]
+    g = s["pkg"].Numa(P_NEX, P_NEX, P_NEZ, P_L, P_L, P_LZ, P_N, s["dt"], precision=precision,
+                      refine_iters=1)
+    out = g.step_imex1d(s["qg"], g.empty_state(), 1).cpu().numpy()
+    g.close()
+    for ex0, ey0 in P_WINDOWS:
+        sub, qs = window(case.mesh, s["q0"], ex0, ey0, 7)
+        ref = ark2.HEVI(sub, Column(sub), s["dt"]).step(qs, 1)
+        gi, wi = window_nodes(case.mesh, ex0, ey0, 7, 3)
+        e = rel_l2(out[:, gi], ref[:, wi])
+        assert np.all(e <= tol), (ex0, ey0, e)
