@@ -472,14 +472,12 @@ def precision_form(pkg, torch, steps, warmup, nsteps_err=200):
     return out
 
 
-def batching_form(pkg, torch, steps, warmup, nmembers=64, h_range=(8, 48), v_range=(6, 16),
-                  n_range=(4, 6), seed=4000):
-    """Ensemble of nmembers independent members with seeded uneven meshes (horizontal 8x8 to
-    48x48 elements, vertical 6-16, N = 4-6, FP64), each with its own seeded perturbation,
-    advanced by HEVI 1D-IMEX at C = 15 (each member at its own dt).  Box sizes are not given:
-    50 km x 50 km elements horizontally over a 10 km depth (C_H < 0.5).  Compares the
-    ensemble path (persistent launches, CUDA graph per step, autotuned tiles) with stepping
-    the members one context at a time."""
+def ensemble(pkg, torch, nmembers=64, h_range=(8, 48), v_range=(6, 16), n_range=(4, 6),
+             seed=4000):
+    """The batching form's seeded ensemble: nmembers members with uneven meshes (horizontal
+    h_range x h_range elements, vertical v_range, order n_range), 50 km x 50 km elements over
+    a 10 km depth, each at its own C = 15 time step, each with its own balanced perturbation
+    of amplitude in [0.1, 2] K.  Returns (batch, state, meshes, orders, dts, nodes)."""
     import synthetic
     rng = np.random.Generator(np.random.PCG64(seed))
     meshes, Ns, dts, xis = [], [], [], {}
@@ -507,6 +505,18 @@ def batching_form(pkg, torch, steps, warmup, nmembers=64, h_range=(8, 48), v_ran
         st = synthetic.balanced_state(ax, ax, lev["z"], L, L, Lz, lev["rho0"], lev["theta0"], seed + 100 + m, amp)
         b.member(q, m).copy_(torch.from_numpy(st))
         nodes += st.shape[1]
+    return b, q, meshes, Ns, dts, nodes
+
+
+def batching_form(pkg, torch, steps, warmup, nmembers=64, h_range=(8, 48), v_range=(6, 16),
+                  n_range=(4, 6), seed=4000):
+    """Ensemble of nmembers independent members with seeded uneven meshes (horizontal 8x8 to
+    48x48 elements, vertical 6-16, N = 4-6, FP64), each with its own seeded perturbation,
+    advanced by HEVI 1D-IMEX at C = 15 (each member at its own dt).  Box sizes are not given:
+    50 km x 50 km elements horizontally over a 10 km depth (C_H < 0.5).  Compares the
+    ensemble path (persistent launches, CUDA graph per step, autotuned tiles) with stepping
+    the members one context at a time."""
+    b, q, meshes, Ns, dts, nodes = ensemble(pkg, torch, nmembers, h_range, v_range, n_range, seed)
     q1 = b.empty_state()
     for _ in range(warmup):
         b.step_imex1d(q, q1, 1)

@@ -973,8 +973,21 @@ int numa_step_explicit_rk(numa_ctx* ctx, const double* q_in, double* q_out, doub
 
 namespace {
 
-// Slabs of the pipelined host run: runs of whole tile rows of the RHS thread order.
-const int kHostSlabs = 8;
+// Slabs of the pipelined host run: runs of whole tile rows of the RHS thread order.  At
+// most kHostSlabs; NUMA_HOST_SLABS (1..kHostSlabs) overrides, for tuning.
+const int kHostSlabs = 16;
+
+int host_slabs() {
+  static int n = -1;
+  if (n < 0) {
+    n = 8;
+    if (const char* t = std::getenv("NUMA_HOST_SLABS")) {
+      const int v = std::atoi(t);
+      if (v >= 1 && v <= kHostSlabs) n = v;
+    }
+  }
+  return n;
+}
 
 // FP64 ARK2 1D-IMEX steps from host memory to host memory with the copies overlapped.  The
 // upload is issued slab by slab (node rows [y0, y1) of every field) on cs_in; the first
@@ -987,7 +1000,7 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
   const long long nn = G.nnode;
   const long long plane = (long long)G.nxg * G.M;        // nodes per node row
   const int rows = (int)ctx->perm_row_y.size() - 1;
-  const int K = std::min(kHostSlabs, rows);
+  const int K = std::min(host_slabs(), rows);
   if (!ctx->cs_in) {
     if (cudaStreamCreateWithFlags(&ctx->cs_in, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->cs_out, cudaStreamNonBlocking) != cudaSuccess)

@@ -240,3 +240,36 @@ def test_precision_form_step_sampled(psetup, precision, tol):
         gi, wi = window_nodes(case.mesh, ex0, ey0, 7, 3)
         e = rel_l2(out[:, gi], ref[:, wi])
         assert np.all(e <= tol), (ex0, ey0, e)
+
+
+# ---- the batching form at its own full size: 64 seeded uneven members -----------------------
+def test_batching_form_full_ensemble():
+    """The batching form's own workload (the benchmark's 64 seeded members, 8x8 to 48x48 by
+    6-16 elements, N = 4-6, each at its own C = 15 step): after one step of the ensemble path
+    (persistent launches, CUDA graph) every member equals a single-mesh context bit for bit,
+    and the three smallest members match the oracle, run on each whole member, to 1e-9 in
+    rho', w and theta'.  (The members start at rest, so u and v after one step are small;
+    they are held to 1e-9 of |w| instead.)"""
+    import torch
+    import bench
+    import paper_1702_04316_gb300 as pkg
+    from oracle import ark2
+    b, q, meshes, Ns, dts, nodes = bench.ensemble(pkg, torch)
+    out = b.step_imex1d(q, b.empty_state(), 1)
+    for m, (mesh, n, dt) in enumerate(zip(meshes, Ns, dts)):
+        g = pkg.Numa(*mesh[:3], *mesh[3:], n, dt)
+        ref = g.step_imex1d(b.member(q, m).contiguous(), g.empty_state(), 1)
+        assert torch.equal(b.member(out, m), ref), m
+        g.close()
+    sizes = [mesh[0] * mesh[1] * mesh[2] * n ** 3 for mesh, n in zip(meshes, Ns)]
+    for m in np.argsort(sizes)[:3]:
+        nh, _, nz, L, _, Lz = meshes[m]
+        case = Case(nh, nh, nz, Ns[m], L, L, Lz)
+        qm = b.member(q, m).cpu().numpy()
+        ref = ark2.HEVI(case.mesh, case.col, dts[m]).step(qm, 1)
+        got = b.member(out, m).cpu().numpy()
+        e = rel_l2(got, ref)
+        assert np.all(e[[0, 3, 4]] <= 1e-9), (m, e)
+        wn = np.linalg.norm(ref[3])
+        assert np.linalg.norm(got[1:3] - ref[1:3]) <= 1e-9 * wn, (m, e)
+    b.close()
