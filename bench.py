@@ -50,6 +50,16 @@ SEED = 2024
 GAMMA = 1004.67 / (1004.67 - 287.17)
 C_S = (GAMMA * 287.17 * 300.0) ** 0.5          # sound speed at theta0 = 300 K
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of this GPU pool when its record is
+    present, else the earlier GB300 measurement of 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 METRIC = "1D-IMEX sim-seconds/wall-second vs explicit C=1 on 1 GB300; % of HBM roofline"
 WORKLOAD = ("96x96x12 hex elements over 200x200x15 km, N=4 (385x385 columns x 49 levels), FP64, "
             "HEVI 1D-IMEX ARK2 step at C=15")
@@ -329,6 +339,24 @@ def run_gpu(args):
         "gpu_launches": int(sum(v[1] for v in kt.values())),
         "clocks": clk,
     }
+    # the standalone column solve (numa_solve_columns, step a4) against the HBM roofline:
+    # algorithmic bytes = the stored factors + the right-hand side read + the solution written
+    fb = g.query(pkg.Q_FACTOR_BYTES)
+    nn = g.query(pkg.Q_NNODE)
+    bcol = torch.randn(nn, dtype=torch.float64, device="cuda")
+    xcol = torch.empty_like(bcol)
+    for _ in range(args.warmup):
+        g.solve_columns(bcol, xcol)
+    ms_solve = time_steps(lambda: g.solve_columns(bcol, xcol), args.steps) / args.steps
+    solve_bytes = fb + 2 * 8 * nn
+    hbm, hbm_src = hbm_peak()
+    out["column_solve"] = {"ms_per_launch": round(ms_solve, 4), "bytes_per_launch": int(solve_bytes),
+                           "achieved_gbs": round(solve_bytes / (ms_solve * 1e-3) / 1e9, 1),
+                           "hbm_peak_gbs": hbm, "peak_source": hbm_src,
+                           "frac_of_hbm_peak": round(solve_bytes / (ms_solve * 1e-3) / 1e9 / hbm, 4),
+                           "fp64_floor_ms": round(17 * nn / (FP64_PEAK_TFLOPS * 1e12 / 2) * 1e3, 4),
+                           "note": "17 FP64 multiply-adds per unknown (L and U substitutions, half-band 2N)"}
+    del bcol, xcol
     # the mixed-precision form on the same workload
     gm = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dt15, precision="mixed", refine_iters=1)
     for _ in range(args.warmup):

@@ -242,20 +242,22 @@ __device__ __forceinline__ double col_dzT(const double* v, int T, int j, int M, 
 // factor row of the next step is loaded while the current one is used.
 template <int HB>
 __device__ __forceinline__ void col_solve_T(double* x, int T, int M, const double* __restrict__ L,
-                                            const double* __restrict__ U, long long nc,
-                                            long long col) {
+                                            const double* __restrict__ U, long long col) {
+  const double* Lb = L + fac_col_base(col, M, HB);
+  const double* Ub = U + fac_col_base(col, M, HB + 1);
   double z[HB], f[HB + 1], fn[HB + 1];
 #pragma unroll
   for (int k = 0; k < HB; ++k) z[k] = 0.0;          // z[k] = y_{i-1-k}
 #pragma unroll
-  for (int k = 0; k <= HB; ++k) fn[k] = __ldg(U + (long long)k * nc + col);
+  for (int k = 0; k <= HB; ++k) fn[k] = __ldg(Ub + (long long)k * kFacBlk);
+#pragma unroll 1
   for (int i = 0; i < M; ++i) {
 #pragma unroll
     for (int k = 0; k <= HB; ++k) f[k] = fn[k];
     if (i + 1 < M) {
-      const double* Uc = U + (long long)(i + 1) * (HB + 1) * nc + col;
+      const double* Uc = Ub + (long long)(i + 1) * (HB + 1) * kFacBlk;
 #pragma unroll
-      for (int k = 0; k <= HB; ++k) fn[k] = __ldg(Uc + (long long)k * nc);
+      for (int k = 0; k <= HB; ++k) fn[k] = __ldg(Uc + (long long)k * kFacBlk);
     }
     double acc = x[i * T];
 #pragma unroll
@@ -269,17 +271,18 @@ __device__ __forceinline__ void col_solve_T(double* x, int T, int M, const doubl
 #pragma unroll
   for (int k = 0; k < HB; ++k) z[k] = 0.0;          // z[k] = x_{i+1+k}
   {
-    const double* Lc = L + (long long)(M - 1) * HB * nc + col;
+    const double* Lc = Lb + (long long)(M - 1) * HB * kFacBlk;
 #pragma unroll
-    for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * nc);
+    for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * kFacBlk);
   }
+#pragma unroll 1
   for (int i = M - 1; i >= 0; --i) {
 #pragma unroll
     for (int k = 0; k < HB; ++k) f[k] = fn[k];
     if (i > 0) {
-      const double* Lc = L + (long long)(i - 1) * HB * nc + col;
+      const double* Lc = Lb + (long long)(i - 1) * HB * kFacBlk;
 #pragma unroll
-      for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * nc);
+      for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * kFacBlk);
     }
     double acc = x[i * T];
 #pragma unroll
@@ -307,7 +310,7 @@ __global__ void k_solve_T(const double* __restrict__ b, double* __restrict__ x, 
   }
   __syncthreads();
   if ((int)threadIdx.x < ncols)
-    col_solve_T<2 * N>(sm + threadIdx.x, T, M, F.L, F.U, G.ncol, col0 + threadIdx.x);
+    col_solve_T<2 * N>(sm + threadIdx.x, T, M, F.L, F.U, col0 + threadIdx.x);
   __syncthreads();
   for (int j = threadIdx.x; j < cnt; j += NT) {
     const int c = j / M, lev = j - c * M;
@@ -375,7 +378,7 @@ __global__ void k_stage_adj(const double* __restrict__ lam, double* __restrict__
     double* p = P + t;
     for (int lev = 0; lev < M; ++lev)   // P* += kp2 w_p* + D_z^T (kp1 w_p*)
       p[lev * T] += fma(-__ldg(tb.kp2 + lev), wt[lev * T], col_dzT<N>(a, T, lev, M, R));
-    col_solve_T<2 * N>(p, T, M, F.L, F.U, G.ncol, col0 + t);      // b* = S^-T P*
+    col_solve_T<2 * N>(p, T, M, F.L, F.U, col0 + t);      // b* = S^-T P*
     for (int lev = 0; lev < M; ++lev) a[lev * T] = __ldg(tb.kD + lev) * p[lev * T];
     for (int lev = 0; lev < M; ++lev)   // w_a* = w* - kF b* - D_z^T (kD b*)
       wt[lev * T] -= fma(__ldg(tb.kF + lev), p[lev * T], col_dzT<N>(a, T, lev, M, R));

@@ -30,10 +30,12 @@ using namespace numa_dev;
 // pivoting, in place, in FT arithmetic.
 // Zero the band storage of one column (n unknowns, half-bandwidth hb).
 template <typename FT>
-__device__ void band_zero(FT* Lf, FT* Uf, int n, int hb, long long nc, long long col) {
+__device__ void band_zero(FT* Lf, FT* Uf, int n, int hb, long long col) {
+  FT* Lb = Lf + fac_col_base(col, n, hb);
+  FT* Ub = Uf + fac_col_base(col, n, hb + 1);
   for (int i = 0; i < n; ++i) {
-    for (int k = 0; k < hb; ++k) Lf[((long long)i * hb + k) * nc + col] = (FT)0;
-    for (int k = 0; k <= hb; ++k) Uf[((long long)i * (hb + 1) + k) * nc + col] = (FT)0;
+    for (int k = 0; k < hb; ++k) Lb[((long long)i * hb + k) * kFacBlk] = (FT)0;
+    for (int k = 0; k <= hb; ++k) Ub[((long long)i * (hb + 1) + k) * kFacBlk] = (FT)0;
   }
 }
 
@@ -70,9 +72,8 @@ __global__ void k_factor(Geom G, RefLev R, double lam, FT* Lf, FT* Uf, int hb, u
   const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (col >= G.ncol) return;
   const int M = G.M, N = G.N, W = 2 * N + 1;
-  const long long nc = G.ncol;
-  Band<FT> A{Lf, Uf, hb, nc, col};
-  band_zero(Lf, Uf, M, hb, nc, col);
+  Band<FT> A(Lf, Uf, hb, M, col);
+  band_zero(Lf, Uf, M, hb, col);
   auto dz = [&](int l, int j) -> double {   // D_z(l, j), |l - j| <= N
     return __ldg(R.dz_band + (long long)l * W + (j - l + N));
   };
@@ -132,9 +133,8 @@ __global__ void k_factor_standard(Geom G, RefLev R, double lam, double* Lf, doub
   const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (col >= G.ncol) return;
   const int n = 3 * G.M;
-  const long long nc = G.ncol;
-  Band<double> A{Lf, Uf, hb, nc, col};
-  band_zero(Lf, Uf, n, hb, nc, col);
+  Band<double> A(Lf, Uf, hb, n, col);
+  band_zero(Lf, Uf, n, hb, col);
   for (int m = 0; m < n; ++m)
     for (int i = max(0, m - hb); i <= min(n - 1, m + hb); ++i)
       A.at(i, m) = standard_entry(i, m, G, R, lam);
@@ -151,10 +151,6 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
   const long long base = col0 * M;
   const int cnt = ncols * M;
   double* Sb = sm;
-  double* St = sm + M * T;
-  double* Sx = sm + 2 * M * T;                                  // only when iters >= 2
-  float* Tf = (float*)(sm + (iters >= 2 ? 3 : 2) * M * T);
-  float* Td = Tf + M * T;
   for (int j = threadIdx.x; j < cnt; j += T) {
     const int c = j / M, lev = j - c * M;
     Sb[lev * T + c] = b[base + j];
@@ -162,8 +158,18 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
   __syncthreads();
   if ((int)threadIdx.x < ncols) {
     const int t = threadIdx.x;
-    col_solve_refined<N, MIXED>(Sb + t, St + t, Tf + t, Td + t, Sx + t, T, M, F, G.ncol, col0 + t,
-                                R, tb, iters);
+    if constexpr (MIXED) {
+      // scratch columns of the refinement (the FP64 solve allocates only Sb)
+      double* St = sm + M * T;
+      double* Sx = sm + 2 * M * T;                              // only when iters >= 2
+      float* Tf = (float*)(sm + (iters >= 2 ? 3 : 2) * M * T);
+      float* Td = Tf + M * T;
+      col_solve_refined<N, MIXED>(Sb + t, St + t, Tf + t, Td + t, Sx + t, T, M, F, col0 + t, R,
+                                  tb, iters);
+    } else {
+      // the factor stream is this kernel's time: prefetch two factor columns ahead
+      col_solve<2 * N, double, double, 3>(Sb + t, T, M, F.L, F.U, col0 + t);
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < cnt; j += T) {
@@ -235,7 +241,7 @@ __global__ void k_stage_standard(const double* __restrict__ qn, const double* __
   }
   __syncthreads();
   if ((int)threadIdx.x < ncols)
-    col_solve<3 * N + 1, double, double>(sm + threadIdx.x, T, 3 * M, F.L, F.U, G.ncol,
+    col_solve<3 * N + 1, double, double>(sm + threadIdx.x, T, 3 * M, F.L, F.U,
                                          col0 + threadIdx.x);
   __syncthreads();
 #pragma unroll 2
@@ -279,7 +285,8 @@ int stage_threads(int T) {
 template <int N, bool MIXED>
 cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, const Factors& F,
                            const RefLev& R, const StageTab& tb, int T, int iters, cudaStream_t s) {
-  const size_t smem = col_smem_per_level(MIXED, iters) * G.M * T;
+  // the FP64 solve uses only the right-hand-side column (more resident columns per SM)
+  const size_t smem = (MIXED ? col_smem_per_level(MIXED, iters) : sizeof(double)) * G.M * T;
   cudaError_t e = cudaFuncSetAttribute(k_solve<N, MIXED>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

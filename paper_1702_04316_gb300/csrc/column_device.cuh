@@ -9,16 +9,18 @@ namespace numa_dev {
 
 
 // ---- band accessor of the stored factors (column-oriented layout) ----------------------
+// Entry (i, j) of one column's n x n band matrix: L(i, j), j < i, in slot i - j - 1 of stored
+// row j of L; U(i, j), j >= i, in slot j - i of stored row j of U (rows by matrix column).
 template <typename FT>
 struct Band {
-  FT* L;
-  FT* U;
+  FT* L;        // L + fac_col_base(col, n, hb)
+  FT* U;        // U + fac_col_base(col, n, hb + 1)
   int hb;
-  long long nc;
-  long long col;
+  __device__ Band(FT* Lf, FT* Uf, int hb_, int n, long long col)
+      : L(Lf + fac_col_base(col, n, hb_)), U(Uf + fac_col_base(col, n, hb_ + 1)), hb(hb_) {}
   __device__ __forceinline__ FT& at(int i, int j) const {
-    return (j < i) ? L[((long long)j * hb + (i - j) - 1) * nc + col]
-                   : U[((long long)j * (hb + 1) + (j - i)) * nc + col];
+    return (j < i) ? L[((long long)j * hb + (i - j) - 1) * kFacBlk]
+                   : U[((long long)j * (hb + 1) + (j - i)) * kFacBlk];
   }
 };
 
@@ -67,52 +69,124 @@ __device__ __forceinline__ double col_wp(const XT* x, int T, int lev, const RefL
 // Solve L U x = b in place for one column held in shared memory (stride T), VT the value
 // type, FT the factor type.  Forward: y_i = w_0; x_{i+1+k} -= L(i+1+k, i) y_i for k < HB
 // (window w in registers).  Backward: x_i = v_0 / U(i,i); y_{i-1-k} -= U(i-1-k, i) x_i.
-// Factor columns are prefetched one column ahead.
-template <int HB, typename VT, typename FT>
+// NB = 0 (the column kernels that are bound by FP64 issue): the next factor column is
+// loaded before the current one is used, one column of work ahead, in two register
+// buffers.  NB >= 2 (the standalone solve, whose time is the factor stream): the factor
+// columns stream through NB buffers; the level loop is unrolled by NB and each buffer is
+// refilled, NB levels ahead, right after its last use, so no pending load is copied from
+// buffer to buffer (a copy would wait for it) and each load has NB - 1 levels of work to
+// arrive.
+template <int HB, typename VT, typename FT, int NB = 0>
 __device__ __forceinline__ void col_solve(VT* x, int T, int M, const FT* __restrict__ L,
-                                          const FT* __restrict__ U, long long nc, long long col) {
-  VT w[HB], l[HB], ln[HB];
+                                          const FT* __restrict__ U, long long col) {
+  const FT* Lb = L + fac_col_base(col, M, HB);
+  const FT* Ub = U + fac_col_base(col, M, HB + 1);
+  static_assert(NB == 0 || (NB >= 2 && NB <= 4), "NB = 0 or 2 to 4 factor buffers");
+  if constexpr (NB == 0) {
+    VT w[HB], l[HB], ln[HB];
 #pragma unroll
-  for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : (VT)0;
+    for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : (VT)0;
 #pragma unroll
-  for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(L + (long long)k * nc + col);
-  for (int i = 0; i < M; ++i) {
+    for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(Lb + (long long)k * kFacBlk);
+#pragma unroll 1
+    for (int i = 0; i < M; ++i) {
 #pragma unroll
-    for (int k = 0; k < HB; ++k) l[k] = ln[k];
-    if (i + 1 < M) {
-      const FT* Lc = L + (long long)(i + 1) * HB * nc + col;
+      for (int k = 0; k < HB; ++k) l[k] = ln[k];
+      if (i + 1 < M) {
+        const FT* Lc = Lb + (long long)(i + 1) * HB * kFacBlk;
 #pragma unroll
-      for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(Lc + (long long)k * nc);
+        for (int k = 0; k < HB; ++k) ln[k] = (VT)__ldg(Lc + (long long)k * kFacBlk);
+      }
+      const VT y = w[0];
+      x[i * T] = y;
+      const VT nxt = (i + HB < M) ? x[(i + HB) * T] : (VT)0;
+#pragma unroll
+      for (int k = 0; k < HB - 1; ++k) w[k] = fma(-l[k], y, w[k + 1]);
+      w[HB - 1] = fma(-l[HB - 1], y, nxt);
     }
-    const VT y = w[0];
-    x[i * T] = y;
-    const VT nxt = (i + HB < M) ? x[(i + HB) * T] : (VT)0;
+    VT v[HB], u[HB + 1], un[HB + 1];
 #pragma unroll
-    for (int k = 0; k < HB - 1; ++k) w[k] = fma(-l[k], y, w[k + 1]);
-    w[HB - 1] = fma(-l[HB - 1], y, nxt);
-  }
-  VT v[HB], u[HB + 1], un[HB + 1];
+    for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : (VT)0;
+    {
+      const FT* Uc = Ub + (long long)(M - 1) * (HB + 1) * kFacBlk;
 #pragma unroll
-  for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : (VT)0;
-  {
-    const FT* Uc = U + (long long)(M - 1) * (HB + 1) * nc + col;
-#pragma unroll
-    for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * nc);
-  }
-  for (int i = M - 1; i >= 0; --i) {
-#pragma unroll
-    for (int k = 0; k <= HB; ++k) u[k] = un[k];
-    if (i > 0) {
-      const FT* Uc = U + (long long)(i - 1) * (HB + 1) * nc + col;
-#pragma unroll
-      for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * nc);
+      for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * kFacBlk);
     }
-    const VT xi = v[0] * u[0];
-    x[i * T] = xi;
-    const VT nxt = (i - HB >= 0) ? x[(i - HB) * T] : (VT)0;
+#pragma unroll 1
+    for (int i = M - 1; i >= 0; --i) {
 #pragma unroll
-    for (int k = 0; k < HB - 1; ++k) v[k] = fma(-u[k + 1], xi, v[k + 1]);
-    v[HB - 1] = fma(-u[HB], xi, nxt);
+      for (int k = 0; k <= HB; ++k) u[k] = un[k];
+      if (i > 0) {
+        const FT* Uc = Ub + (long long)(i - 1) * (HB + 1) * kFacBlk;
+#pragma unroll
+        for (int k = 0; k <= HB; ++k) un[k] = (VT)__ldg(Uc + (long long)k * kFacBlk);
+      }
+      const VT xi = v[0] * u[0];
+      x[i * T] = xi;
+      const VT nxt = (i - HB >= 0) ? x[(i - HB) * T] : (VT)0;
+#pragma unroll
+      for (int k = 0; k < HB - 1; ++k) v[k] = fma(-u[k + 1], xi, v[k + 1]);
+      v[HB - 1] = fma(-u[HB], xi, nxt);
+    }
+  } else {
+    VT w[HB], rl[NB][HB];
+  #pragma unroll
+    for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : (VT)0;
+  #pragma unroll
+    for (int p = 0; p < NB; ++p)
+      if (p < M) {
+        const FT* Lc = Lb + (long long)p * HB * kFacBlk;
+  #pragma unroll
+        for (int k = 0; k < HB; ++k) rl[p][k] = (VT)__ldg(Lc + (long long)k * kFacBlk);
+      }
+    for (int i0 = 0; i0 < M; i0 += NB) {
+  #pragma unroll
+      for (int p = 0; p < NB; ++p) {
+        const int i = i0 + p;
+        if (i < M) {
+          const VT y = w[0];
+          x[i * T] = y;
+          const VT nxt = (i + HB < M) ? x[(i + HB) * T] : (VT)0;
+  #pragma unroll
+          for (int k = 0; k < HB - 1; ++k) w[k] = fma(-rl[p][k], y, w[k + 1]);
+          w[HB - 1] = fma(-rl[p][HB - 1], y, nxt);
+          if (i + NB < M) {
+            const FT* Lc = Lb + (long long)(i + NB) * HB * kFacBlk;
+  #pragma unroll
+            for (int k = 0; k < HB; ++k) rl[p][k] = (VT)__ldg(Lc + (long long)k * kFacBlk);
+          }
+        }
+      }
+    }
+    VT v[HB], ru[NB][HB + 1];
+  #pragma unroll
+    for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : (VT)0;
+  #pragma unroll
+    for (int p = 0; p < NB; ++p)
+      if (M - 1 - p >= 0) {
+        const FT* Uc = Ub + (long long)(M - 1 - p) * (HB + 1) * kFacBlk;
+  #pragma unroll
+        for (int k = 0; k <= HB; ++k) ru[p][k] = (VT)__ldg(Uc + (long long)k * kFacBlk);
+      }
+    for (int i0 = 0; i0 < M; i0 += NB) {
+  #pragma unroll
+      for (int p = 0; p < NB; ++p) {
+        const int i = M - 1 - (i0 + p);
+        if (i >= 0) {
+          const VT xi = v[0] * ru[p][0];
+          x[i * T] = xi;
+          const VT nxt = (i - HB >= 0) ? x[(i - HB) * T] : (VT)0;
+  #pragma unroll
+          for (int k = 0; k < HB - 1; ++k) v[k] = fma(-ru[p][k + 1], xi, v[k + 1]);
+          v[HB - 1] = fma(-ru[p][HB], xi, nxt);
+          if (i - NB >= 0) {
+            const FT* Uc = Ub + (long long)(i - NB) * (HB + 1) * kFacBlk;
+  #pragma unroll
+            for (int k = 0; k <= HB; ++k) ru[p][k] = (VT)__ldg(Uc + (long long)k * kFacBlk);
+          }
+        }
+      }
+    }
   }
 }
 
@@ -135,14 +209,14 @@ __device__ __forceinline__ double col_residual(const double* B, const double* tm
 template <int N, bool MIXED>
 __device__ __forceinline__ void col_solve_refined(double* B, double* tmp, float* Tf, float* Td,
                                                   double* Xd, int T, int M, const Factors& F,
-                                                  long long nc, long long col, const RefLev& R,
+                                                  long long col, const RefLev& R,
                                                   const StageTab& tb, int iters) {
   if (!MIXED) {
-    col_solve<2 * N, double, double>(B, T, M, F.L, F.U, nc, col);
+    col_solve<2 * N, double, double>(B, T, M, F.L, F.U, col);
     return;
   }
   for (int lev = 0; lev < M; ++lev) Tf[lev * T] = (float)B[lev * T];
-  col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, nc, col);
+  col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, col);
   for (int it = 0; it < iters; ++it) {
     const bool first = (it == 0), last = (it == iters - 1);
     for (int lev = 0; lev < M; ++lev)
@@ -151,7 +225,7 @@ __device__ __forceinline__ void col_solve_refined(double* B, double* tmp, float*
       const double xl = first ? (double)Tf[lev * T] : Xd[lev * T];
       Td[lev * T] = (float)col_residual<N>(B, tmp, T, lev, R, tb, xl);
     }
-    col_solve<2 * N, float, float>(Td, T, M, F.L32, F.U32, nc, col);
+    col_solve<2 * N, float, float>(Td, T, M, F.L32, F.U32, col);
     for (int lev = 0; lev < M; ++lev) {
       const double x = (first ? (double)Tf[lev * T] : Xd[lev * T]) + (double)Td[lev * T];
       if (last) B[lev * T] = x;
@@ -265,12 +339,12 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
   });
   __syncthreads();
   if (!MIXED) {
-    if (tid < ncols) col_solve<2 * N, double, double>(S0 + tid, T, M, F.L, F.U, G.ncol, col0 + tid);
+    if (tid < ncols) col_solve<2 * N, double, double>(S0 + tid, T, M, F.L, F.U, col0 + tid);
     __syncthreads();
   } else {
     // FP32 solve, then `iters` sweeps of FP64 refinement (r = b - S X with the FP64
     // matrix-free operator, correction solved in FP32); S1 is the scratch for w_p(X)
-    if (tid < ncols) col_solve<2 * N, float, float>(Tf + tid, T, M, F.L32, F.U32, G.ncol, col0 + tid);
+    if (tid < ncols) col_solve<2 * N, float, float>(Tf + tid, T, M, F.L32, F.U32, col0 + tid);
     __syncthreads();
     for (int it = 0; it < iters; ++it) {
       const bool first = (it == 0), last = (it == iters - 1);
@@ -284,7 +358,7 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
         Td[lev * T + c] = (float)col_residual<N>(S0 + c, S1 + c, T, lev, R, tb, xl);
       });
       __syncthreads();
-      if (tid < ncols) col_solve<2 * N, float, float>(Td + tid, T, M, F.L32, F.U32, G.ncol, col0 + tid);
+      if (tid < ncols) col_solve<2 * N, float, float>(Td + tid, T, M, F.L32, F.U32, col0 + tid);
       __syncthreads();
       level_loop([&](int lev, int c) {
         const double x = (first ? (double)Tf[lev * T + c] : SXd[lev * T + c]) + (double)Td[lev * T + c];

@@ -652,11 +652,11 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
     if (!need_factors) {
       // 3D-IMEX with the polynomial preconditioner keeps no column factors
     } else if (ok && mixed)
-      ok = cudaMalloc(&c->F.L32, (size_t)G.M * hb * G.ncol * sizeof(float)) == cudaSuccess &&
-           cudaMalloc(&c->F.U32, (size_t)G.M * (hb + 1) * G.ncol * sizeof(float)) == cudaSuccess;
+      ok = cudaMalloc(&c->F.L32, (size_t)G.M * hb * fac_cols(G.ncol) * sizeof(float)) == cudaSuccess &&
+           cudaMalloc(&c->F.U32, (size_t)G.M * (hb + 1) * fac_cols(G.ncol) * sizeof(float)) == cudaSuccess;
     else if (ok)
-      ok = cudaMalloc(&c->F.L, nu * hb * G.ncol * sizeof(double)) == cudaSuccess &&
-           cudaMalloc(&c->F.U, nu * (hb + 1) * G.ncol * sizeof(double)) == cudaSuccess;
+      ok = cudaMalloc(&c->F.L, nu * hb * fac_cols(G.ncol) * sizeof(double)) == cudaSuccess &&
+           cudaMalloc(&c->F.U, nu * (hb + 1) * fac_cols(G.ncol) * sizeof(double)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       rc = NUMA_ERR_OOM;
@@ -1147,21 +1147,23 @@ int numa_column_factors(numa_ctx* ctx, long long col, double* host_out) {
   const int M = ctx->F.standard ? 3 * ctx->G.M : ctx->G.M;   // unknowns per column
   const int hb = ctx->F.hb, W = 2 * hb + 1;
   std::vector<double> L((size_t)M * hb), U((size_t)M * (hb + 1));
+  // in the stored layout one column's entries are kFacBlk elements apart
+  const long long lb = fac_col_base(col, M, hb), ub = fac_col_base(col, M, hb + 1);
   if (ctx->F.mixed) {
-    const size_t pitch = (size_t)ctx->G.ncol * sizeof(float);
+    const size_t pitch = (size_t)kFacBlk * sizeof(float);
     std::vector<float> Lf(L.size()), Uf(U.size());
-    NUMA_CK(ctx, cudaMemcpy2DAsync(Lf.data(), sizeof(float), ctx->F.L32 + col, pitch, sizeof(float),
+    NUMA_CK(ctx, cudaMemcpy2DAsync(Lf.data(), sizeof(float), ctx->F.L32 + lb, pitch, sizeof(float),
                                    (size_t)M * hb, cudaMemcpyDeviceToHost, ctx->stream));
-    NUMA_CK(ctx, cudaMemcpy2DAsync(Uf.data(), sizeof(float), ctx->F.U32 + col, pitch, sizeof(float),
+    NUMA_CK(ctx, cudaMemcpy2DAsync(Uf.data(), sizeof(float), ctx->F.U32 + ub, pitch, sizeof(float),
                                    (size_t)M * (hb + 1), cudaMemcpyDeviceToHost, ctx->stream));
     NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
     for (size_t t = 0; t < L.size(); ++t) L[t] = Lf[t];
     for (size_t t = 0; t < U.size(); ++t) U[t] = Uf[t];
   } else {
-    const size_t pitch = (size_t)ctx->G.ncol * sizeof(double);
-    NUMA_CK(ctx, cudaMemcpy2DAsync(L.data(), sizeof(double), ctx->F.L + col, pitch, sizeof(double),
+    const size_t pitch = (size_t)kFacBlk * sizeof(double);
+    NUMA_CK(ctx, cudaMemcpy2DAsync(L.data(), sizeof(double), ctx->F.L + lb, pitch, sizeof(double),
                                    (size_t)M * hb, cudaMemcpyDeviceToHost, ctx->stream));
-    NUMA_CK(ctx, cudaMemcpy2DAsync(U.data(), sizeof(double), ctx->F.U + col, pitch, sizeof(double),
+    NUMA_CK(ctx, cudaMemcpy2DAsync(U.data(), sizeof(double), ctx->F.U + ub, pitch, sizeof(double),
                                    (size_t)M * (hb + 1), cudaMemcpyDeviceToHost, ctx->stream));
     NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
   }

@@ -79,6 +79,21 @@ struct RefLev {
 // solve refine_iters times with the FP64 operator.
 // The standard column form (standard = 1) stores the 3M x 3M level-interleaved system
 // I - lam L_V in the same layout with n = 3M unknowns per column and hb = 3N + 1.
+// Layout of the stored column factors.  Mesh columns are grouped in blocks of kFacBlk = 32
+// consecutive columns; a block stores, for every band row i and slot k in order, the entry
+// of each of its 32 columns side by side.  A warp whose lanes take consecutive columns
+// then reads each (i, k) as one contiguous line and walks its block's factors front to back.
+// n rows (M, or 3M in the standard form), W slots per row (hb for L, hb + 1 for U); the
+// allocation holds fac_cols(ncol) columns.  Entry (i, k) of column col is at
+// fac_col_base(col, n, W) + (i * W + k) * kFacBlk.
+constexpr int kFacBlk = 32;
+__host__ __device__ inline long long fac_cols(long long ncol) {
+  return (ncol + kFacBlk - 1) / kFacBlk * kFacBlk;
+}
+__host__ __device__ inline long long fac_col_base(long long col, int n, int W) {
+  return (col / kFacBlk) * (long long)n * W * kFacBlk + (col % kFacBlk);
+}
+
 struct Factors {
   double* L;
   double* U;

@@ -8,10 +8,12 @@ Every step reads the same input and writes a separate output.
 
   python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0] [--adj 0]
                                                 [--precision mixed] [--scheme ark5]
+                                                [--solve 0]
 
 --adj K also runs K adjoint steps (numa_step_imex1d_adjoint) and K tangent-linear steps from
 the same input, for captures of the differentiation form's kernels.  --scheme selects the
-ARK scheme of the steps (ark2 .. ark5; FP64).
+ARK scheme of the steps (ark2 .. ark5; FP64).  --solve K runs K standalone column solves
+(numa_solve_columns) of a seeded right-hand side.
 """
 import argparse
 import os
@@ -33,6 +35,7 @@ def main():
     ap.add_argument("--C", type=float, default=15.0)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "rhs32", "df"])
     ap.add_argument("--scheme", default="ark2", choices=["ark2", "ark3", "ark4", "ark5"])
+    ap.add_argument("--solve", type=int, default=0)
     a = ap.parse_args()
     import torch
     import paper_1702_04316_gb300 as pkg
@@ -59,6 +62,13 @@ def main():
         for _ in range(a.adj):
             g.step_imex1d_adjoint(q0, lam, q1)
         g.step_imex1d_tlm(q0, lam, a.adj, q1, torch.empty_like(q0))
+    if a.solve:
+        gen = torch.Generator(device="cuda").manual_seed(11)
+        b = torch.randn(g.ncol * g.M, dtype=torch.float64, device="cuda", generator=gen)
+        x = torch.empty_like(b)
+        for _ in range(a.solve):
+            g.solve_columns(b, x)
+        assert bool(torch.isfinite(x).all())
     torch.cuda.synchronize()
     assert g.count_nonfinite(q1) == 0
     assert g.status() == pkg.NUMA_OK
