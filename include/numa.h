@@ -281,7 +281,11 @@ int numa_reference_levels(const numa_ctx* ctx, double* host_out);
 int numa_count_nonfinite(numa_ctx* ctx, const double* x, long long n, long long* count);
 
 /* Synchronise the stream and return the latched device status (NUMA_OK or the first
- * NUMA_ERR_* a kernel recorded), then clear it. */
+ * NUMA_ERR_* a kernel recorded), then clear it.  NUMA_ERR_PIVOT: a zero or non-finite pivot
+ * in numa_factor_columns.  NUMA_ERR_NONFINITE: a step met a non-finite state -- the
+ * equation-of-state passes (the P' pre-pass of a step's or RK stage's input, the fused P'
+ * of each implicit stage value) and the ARK4/ARK5 final combination test their results; a
+ * non-finite u, v or w reaches them within one step through the coupled tendencies. */
 int numa_status(numa_ctx* ctx, int* status);
 
 int numa_query(const numa_ctx* ctx, int what, long long* out);

@@ -14,6 +14,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnuma.so")
 
 NUMA_OK = 0
+NUMA_ERR_ARG, NUMA_ERR_CUDA, NUMA_ERR_OOM, NUMA_ERR_NOT_FACTORED, NUMA_ERR_PIVOT, \
+    NUMA_ERR_NONFINITE, NUMA_ERR_TIMEOUT, NUMA_ERR_SCRATCH = range(1, 9)
 ERRORS = {
     1: "NUMA_ERR_ARG", 2: "NUMA_ERR_CUDA", 3: "NUMA_ERR_OOM", 4: "NUMA_ERR_NOT_FACTORED",
     5: "NUMA_ERR_PIVOT", 6: "NUMA_ERR_NONFINITE", 7: "NUMA_ERR_TIMEOUT", 8: "NUMA_ERR_SCRATCH",

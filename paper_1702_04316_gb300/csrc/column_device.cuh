@@ -381,6 +381,7 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
   __syncthreads();
 
   // phase 3
+  unsigned bad = 0;
 #pragma unroll 2
   for (int j = threadIdx.x; j < cnt; j += NT) {
     const long long g = base + j;
@@ -426,9 +427,13 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     out[ow] = o_w;
     out[oth] = o_t;
     // P'(q(i)) for the next right-hand side, by the arithmetic of its pre-pass (eos_node)
-    if (Pp_out)
-      Pp_out[g] = R.P0[lev] * eos_rel(o_r, o_t, R.inv_rho0[lev], R.inv_theta0[lev], NUMA_GAMMA, *eos);
+    if (Pp_out) {
+      const double pv = R.P0[lev] * eos_rel(o_r, o_t, R.inv_rho0[lev], R.inv_theta0[lev], NUMA_GAMMA, *eos);
+      Pp_out[g] = pv;
+      bad |= not_finite(pv);
+    }
   }
+  if (bad && tb.status) atomicOr(tb.status, NUMA_ST_NONFINITE);
 }
 
 }  // namespace numa_dev

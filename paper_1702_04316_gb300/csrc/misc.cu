@@ -74,20 +74,23 @@ __global__ void k_ark_final(const double* __restrict__ qn, const double* __restr
 }
 
 __global__ void k_ark_combine(const double* __restrict__ qn, const __grid_constant__ StageSum S,
-                              double* out, long long n) {
+                              double* out, long long n, unsigned* status) {
+  unsigned bad = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     double v = qn[t];
     for (int k = 0; k < S.n; ++k) v = fma(S.bdt[k], __ldg(S.R[k] + t), v);
     out[t] = v;
+    bad |= not_finite(v);
   }
+  if (bad && status) atomicOr(status, NUMA_ST_NONFINITE);
 }
 
 }  // namespace
 
 cudaError_t launch_ark_combine(const double* qn, const StageSum& S, double* out, long long n,
-                               cudaStream_t s) {
-  k_ark_combine<<<152 * 8, 256, 0, s>>>(qn, S, out, n);
+                               unsigned* status, cudaStream_t s) {
+  k_ark_combine<<<152 * 8, 256, 0, s>>>(qn, S, out, n, status);
   return cudaGetLastError();
 }
 

@@ -436,7 +436,7 @@ int upload_stage_tables(numa_ctx* c, double lam) {
   NUMA_CK(c, cudaStreamSynchronize(c->stream));
   const double* d = c->d_stage_tab;
   c->T = StageTab{d, d + M, d + 2 * M, d + 3 * M, d + 4 * M, d + 5 * M,
-                  d + 6 * M, d + 7 * M, d + 8 * M, d + 9 * M, d + 10 * M};
+                  d + 6 * M, d + 7 * M, d + 8 * M, d + 9 * M, d + 10 * M, c->d_status};
   return NUMA_OK;
 }
 
@@ -458,7 +458,7 @@ int enqueue_rhs(numa_ctx* c, const double* q, double* out, const RhsEpilogue& ep
     p = prof_begin(c, NUMA_K_PRESSURE);
     if (rhs32) NUMA_CK(c, launch_prep32(q, c->F32, c->G, c->R, c->stream));
     else if (df) NUMA_CK(c, launch_prep_df(q, c->F2, c->G, c->R, c->stream));
-    else NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream));
+    else NUMA_CK(c, launch_pressure(q, c->Pp, c->G, c->R, c->stream, c->d_status));
     prof_end(c, p);
   }
   p = prof_begin(c, NUMA_K_RHS);
@@ -874,7 +874,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
           S.R[S.n] = ctx->Rk[j];
           S.bdt[S.n++] = t.b[j] * ctx->dt;
         }
-      NUMA_CK(ctx, launch_ark_combine(cur, S, q_out, n5, ctx->stream));
+      NUMA_CK(ctx, launch_ark_combine(cur, S, q_out, n5, ctx->d_status, ctx->stream));
       cur = q_out;
     }
     return NUMA_OK;
@@ -1038,7 +1038,8 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
       for (int k = 0; k <= K; ++k) {
         if (k < K) {
           NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[k], 0));
-          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, n0(k), n0(k + 1), ctx->stream));
+          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, n0(k), n0(k + 1), ctx->stream,
+                                             ctx->d_status));
         }
         if (k >= 1)
           NUMA_CK(ctx, launch_rhs(q, ctx->Pp, ctx->R1, ctx->d_perm + p0(k - 1), p0(k) - p0(k - 1),

@@ -122,15 +122,25 @@ struct StageCoef {
 // with A = 1 + lam^2 (g/theta0) d(theta0)/dz.
 struct StageTab {
   const double *wa_th, *wa_s, *kF, *kD, *kp1, *kp2, *kth, *invG0, *H0G0, *G0, *H0;
+  unsigned* status;   // the fused stage latches NUMA_ST_NONFINITE here when P' of its output
+                      // is not finite (NULL: no check)
 };
+
+// True when x is an infinity or a NaN, from the exponent bits of its high word: integer
+// instructions only, so the check takes no FP64 issue slots.
+__device__ __forceinline__ unsigned not_finite(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) == 0x7ff00000u;
+}
 
 // ---- launchers (return the launch error) ----------------------------------------------
 // rhs.cu
 cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const RefLev& R,
-                            cudaStream_t s);
-// P' for the nodes g0 <= g < g1 only.
+                            cudaStream_t s, unsigned* status = nullptr);
+// P' for the nodes g0 <= g < g1 only.  Both pre-passes latch NUMA_ST_NONFINITE into status
+// (NULL: no check) when a P' is not finite: a non-finite rho' or theta' of the input state.
 cudaError_t launch_pressure_range(const double* q, double* Pp, const Geom& G, const RefLev& R,
-                                  long long g0, long long g1, cudaStream_t s);
+                                  long long g0, long long g1, cudaStream_t s,
+                                  unsigned* status = nullptr);
 // MODE 0: out = R(q);  MODE 1 (RK stage): out = alpha*u0 + (1-alpha)*q + beta*dt*R(q);
 // MODE 2 (ARK2 final): out = qn + dt*(b1*R1 + b2*R2 + b3*R(q));
 // MODE 3 (four-stage ARK final, FP64 only): out = qn + dt*(b1*R1 + b2*R2 + b3*R3 + b4*R(q)).
@@ -211,14 +221,15 @@ struct StagePrev {
 cudaError_t launch_stage_general(const StagePrev& P, double* out, const Geom& G, const RefLev& R,
                                  const Factors& F, const StageTab& tb, int T, cudaStream_t s,
                                  double* Pp_out);
-// out = qn + sum_k bdt[k] R[k] (k < n; in place on qn allowed).
+// out = qn + sum_k bdt[k] R[k] (k < n; in place on qn allowed); a value that is not finite
+// latches NUMA_ST_NONFINITE into status (NULL: no check).
 struct StageSum {
   int n;
   const double* R[NUMA_MAX_STAGES];
   double bdt[NUMA_MAX_STAGES];
 };
 cudaError_t launch_ark_combine(const double* qn, const StageSum& S, double* out, long long n,
-                               cudaStream_t s);
+                               unsigned* status, cudaStream_t s);
 
 // misc.cu
 cudaError_t launch_connectivity(const Geom& G, int32_t* l2g, int32_t* g2l, cudaStream_t s);

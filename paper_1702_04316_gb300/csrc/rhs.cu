@@ -29,10 +29,12 @@ namespace {
 using namespace numa_dev;
 
 __global__ void k_pressure(const double* __restrict__ q, double* __restrict__ Pp, Geom G,
-                           RefLev R, EosSeries S, long long g0, long long g1) {
+                           RefLev R, EosSeries S, long long g0, long long g1, unsigned* status) {
   const long long g = g0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= g1) return;
-  Pp[g] = eos_node(q, g, G, R, S);
+  const double p = eos_node(q, g, G, R, S);
+  Pp[g] = p;
+  if (status && not_finite(p)) atomicOr(status, NUMA_ST_NONFINITE);
 }
 
 // Mixed-precision form: P' in FP64, then FP32 copies of the six stencil fields
@@ -103,19 +105,20 @@ int node_class(int idx, int N, int nel) {
 }  // namespace
 
 cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const RefLev& R,
-                            cudaStream_t s) {
+                            cudaStream_t s, unsigned* status) {
   const int bs = 256;
   const long long nb = (G.nnode + bs - 1) / bs;
-  k_pressure<<<(unsigned)nb, bs, 0, s>>>(q, Pp, G, R, eos_series(), 0, G.nnode);
+  k_pressure<<<(unsigned)nb, bs, 0, s>>>(q, Pp, G, R, eos_series(), 0, G.nnode, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pressure_range(const double* q, double* Pp, const Geom& G, const RefLev& R,
-                                  long long g0, long long g1, cudaStream_t s) {
+                                  long long g0, long long g1, cudaStream_t s, unsigned* status) {
   if (g0 < 0 || g1 > G.nnode || g0 > g1) return cudaErrorInvalidValue;
   if (g0 == g1) return cudaSuccess;
   const int bs = 256;
-  k_pressure<<<(unsigned)((g1 - g0 + bs - 1) / bs), bs, 0, s>>>(q, Pp, G, R, eos_series(), g0, g1);
+  k_pressure<<<(unsigned)((g1 - g0 + bs - 1) / bs), bs, 0, s>>>(q, Pp, G, R, eos_series(), g0, g1,
+                                                                 status);
   return cudaGetLastError();
 }
 
