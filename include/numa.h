@@ -234,7 +234,13 @@ int numa_step_explicit_rk(numa_ctx* ctx, const double* q_in, double* q_out, doub
 /* Host-buffer driver: copies q_in_host (5*nnode doubles, pinned memory recommended) to
  * the device, runs nsteps of method 0 (1D-IMEX, dt of the factors) or 1 (RK35 with the
  * given dt), copies the result into q_out_host (may equal q_in_host) and synchronises.
- * Uses a device state buffer owned by the context (allocated on first use). */
+ * Uses a device state buffer owned by the context (allocated on first use).  For the FP64
+ * ARK2 Schur-form 1D-IMEX the copies are overlapped with the kernels: the upload runs
+ * slab by slab (runs of whole tile rows of the right-hand side's thread order, at most 8
+ * slabs; NUMA_HOST_SLABS overrides) on its own stream while the first right-hand side
+ * consumes the slabs that have arrived, and each slab of the last step's result is
+ * downloaded on a third stream as soon as its final update is done.  The result is bit
+ * for bit that of numa_step_imex1d. */
 int numa_run_host(numa_ctx* ctx, int method, const double* q_in_host, double* q_out_host,
                   int nsteps, double dt);
 
