@@ -34,23 +34,19 @@ __device__ __forceinline__ double col_dz(const XT* f, int T, int lev, const RefL
   const int* o = R.dz_o + (long long)lev * W;
   const int n = __ldg(R.dz_n + lev);
   const XT* p = f + lev * T;
+  // one accumulator: FP64 issue, not latency, bounds the column kernels (a warp-wide FP64
+  // multiply-add occupies the pipe 16 cycles), so a second chain would only add a final add
   if (n == N) {
-    double a0 = __ldg(c) * (double)p[__ldg(o) * T], a1 = 0.0;
+    double acc = __ldg(c) * (double)p[__ldg(o) * T];
 #pragma unroll
-    for (int t = 1; t < N; ++t) {
-      if (t & 1) a1 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a1);
-      else a0 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a0);
-    }
-    return a0 + a1;
+    for (int t = 1; t < N; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);
+    return acc;
   }
   if (n == 2 * N) {
-    double a0 = __ldg(c) * (double)p[__ldg(o) * T], a1 = __ldg(c + 1) * (double)p[__ldg(o + 1) * T];
+    double acc = __ldg(c) * (double)p[__ldg(o) * T];
 #pragma unroll
-    for (int t = 2; t < 2 * N; ++t) {
-      if (t & 1) a1 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a1);
-      else a0 = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], a0);
-    }
-    return a0 + a1;
+    for (int t = 1; t < 2 * N; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);
+    return acc;
   }
   double acc = 0.0;
   for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);

@@ -39,28 +39,20 @@ const int kRedThreads = 256;
 template <int N>
 __device__ __forceinline__ double deriv1(const double* __restrict__ f, long long g, long long stride,
                                          int cls, const Taps<N, double>& T) {
+  // one accumulator: the operator is bound by FP64 issue, not by the chain's latency
   const double* p = f + g;
-  double a0 = T.c[0] * __ldg(p + T.o[0] * stride), a1 = 0.0;
+  double acc = T.c[0] * __ldg(p + T.o[0] * stride);
   if (cls == CLS_IFACE) {
 #pragma unroll
-    for (int t = 1; t < 2 * N; ++t) {
-      if (t & 1) a1 = fma(T.c[t], __ldg(p + T.o[t] * stride), a1);
-      else a0 = fma(T.c[t], __ldg(p + T.o[t] * stride), a0);
-    }
+    for (int t = 1; t < 2 * N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
   } else if (cls == CLS_WALL) {
 #pragma unroll
-    for (int t = 1; t <= N; ++t) {
-      if (t & 1) a1 = fma(T.c[t], __ldg(p + T.o[t] * stride), a1);
-      else a0 = fma(T.c[t], __ldg(p + T.o[t] * stride), a0);
-    }
+    for (int t = 1; t <= N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
   } else {
 #pragma unroll
-    for (int t = 1; t < N; ++t) {
-      if (t & 1) a1 = fma(T.c[t], __ldg(p + T.o[t] * stride), a1);
-      else a0 = fma(T.c[t], __ldg(p + T.o[t] * stride), a0);
-    }
+    for (int t = 1; t < N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
   }
-  return a0 + a1;
+  return acc;
 }
 
 struct NodeIdx {
@@ -133,8 +125,8 @@ __global__ void k_s3_div(const double* __restrict__ U3, const double* __restrict
   const double dv = deriv1<N>(U3 + nn, g, sy, cls, T);
   cls = axis_taps<N, double>(n.iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
   const double dw = deriv1<N>(U3 + 2 * nn, g, 1, cls, T);
-  double v = base[g] - __ldg(tb.kF + n.iz) * U3[2 * nn + g] - __ldg(tb.kD + n.iz) * (du + dv + dw);
-  v *= alpha;
+  double v = fma(-__ldg(tb.kD + n.iz), du + dv + dw, fma(-__ldg(tb.kF + n.iz), U3[2 * nn + g], base[g]));
+  if (alpha != 1.0) v *= alpha;                       // uniform: S itself has alpha = 1
   if (y) v = fma(beta, y[g], v);
   out[g] = v;
 }

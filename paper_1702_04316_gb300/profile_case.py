@@ -8,12 +8,13 @@ Every step reads the same input and writes a separate output.
 
   python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0] [--adj 0]
                                                 [--precision mixed] [--scheme ark5]
-                                                [--solve 0]
+                                                [--solve 0] [--imex3d 0]
 
 --adj K also runs K adjoint steps (numa_step_imex1d_adjoint) and K tangent-linear steps from
 the same input, for captures of the differentiation form's kernels.  --scheme selects the
 ARK scheme of the steps (ark2 .. ark5; FP64).  --solve K runs K standalone column solves
-(numa_solve_columns) of a seeded right-hand side.
+(numa_solve_columns) of a seeded right-hand side.  --imex3d K runs K 3D-IMEX steps of a
+separate 3D context (polynomial preconditioner) from the same input.
 """
 import argparse
 import os
@@ -36,6 +37,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "rhs32", "df"])
     ap.add_argument("--scheme", default="ark2", choices=["ark2", "ark3", "ark4", "ark5"])
     ap.add_argument("--solve", type=int, default=0)
+    ap.add_argument("--imex3d", type=int, default=0)
     a = ap.parse_args()
     import torch
     import paper_1702_04316_gb300 as pkg
@@ -69,6 +71,13 @@ def main():
         for _ in range(a.solve):
             g.solve_columns(b, x)
         assert bool(torch.isfinite(x).all())
+    if a.imex3d:
+        g3 = pkg.Numa(nex, nex, nez, L, L, Lz, N, dt, imex="3d")
+        q3 = torch.empty_like(q0)
+        g3.step_imex3d(q0, q3, a.imex3d)
+        torch.cuda.synchronize()
+        assert g3.count_nonfinite(q3) == 0 and g3.status() == pkg.NUMA_OK
+        g3.close()
     torch.cuda.synchronize()
     assert g.count_nonfinite(q1) == 0
     assert g.status() == pkg.NUMA_OK
