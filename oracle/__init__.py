@@ -40,6 +40,7 @@ algorithm or table:
                     gradient of a quadratic misfit of the final theta' (differentiation
                     form: the chain rule applied to the steps above).
 
-Parity pins for every function live in ``tests/test_oracle_*.py``.  One function has no
-pin beyond its defining formula: see the ``PARITY UNPINNED`` note in ``rk35``.
+Parity pins for every function live in ``tests/test_oracle_*.py``.  Four tableaux are
+pinned only as methods of their order, not as the schemes the paper ran (which it does not
+print): see the ``PARITY UNPINNED`` notes in ``rk35``, ``ark3``, ``ark4`` and ``ark5``.
 """

@@ -11,6 +11,10 @@ factorisation at lam = gamma dt.  The coefficients are the published rationals. 
 in tests/test_oracle_ark.py check the third-order conditions of both tableaux and of
 their coupling in exact rational arithmetic, and third-order convergence on a stiff
 linear split system.
+
+PARITY UNPINNED in the sense of the paper: the paper does not print the tableau it ran, so
+which scheme it used cannot be checked.  The pins fix this tableau only as an ARK pair of
+its order (exact order conditions) and by its convergence rate.
 """
 from fractions import Fraction as F
 

@@ -8,6 +8,10 @@ c = c~ and b = b~ = the last implicit row (stiffly accurate), so it has the stag
 ``ark2.ark_step`` and one column factorisation at lam = dt / 4.  The coefficients are the
 published rationals; tests/test_oracle_ark.py checks every bicoloured-tree condition up
 to order 4 in exact arithmetic and the rate of convergence.
+
+PARITY UNPINNED in the sense of the paper: the paper does not print the tableau it ran, so
+which scheme it used cannot be checked.  The pins fix this tableau only as an ARK pair of
+its order (exact order conditions) and by its convergence rate.
 """
 from fractions import Fraction as F
 

@@ -14,6 +14,10 @@ system that they satisfy to 2e-26, the accuracy of the published rationals, so t
 the published scheme's entries to that accuracy, rounded to rationals with denominators
 below 2e13.  tests/test_oracle_ark.py checks every condition up to order 5 in exact
 arithmetic and the rate of convergence.
+
+PARITY UNPINNED in the sense of the paper: the paper does not print the tableau it ran, so
+which scheme it used cannot be checked.  The pins fix this tableau only as an ARK pair of
+its order (exact order conditions) and by its convergence rate.
 """
 from fractions import Fraction as F
 
