@@ -195,7 +195,13 @@ int numa_factor_columns(numa_ctx* ctx, double dt);
 
 /* Solve S x = b for every column with the stored factors (forward then back
  * substitution).  b, x: device arrays of ncol*M doubles in column order (g = col*M+iz);
- * x == b (in place) is allowed.  NUMA_ERR_NOT_FACTORED before numa_factor_columns. */
+ * x == b (in place) is allowed.  NUMA_ERR_NOT_FACTORED before numa_factor_columns.
+ * FP64 contexts stream the factors into shared memory with bulk (TMA) copies; the right-hand
+ * side and the solution move by bulk copies too when b and x are 16-byte aligned (plain
+ * loads and stores otherwise; the result bits are the same).  A bounded device wait that
+ * gives up (it never should) latches NUMA_ERR_TIMEOUT in the device status and leaves the
+ * affected columns of x unwritten.  The environment variable NUMA_SOLVE=regs, read once per
+ * process, selects the register-pipelined kernel instead (same arithmetic, same bits). */
 int numa_solve_columns(numa_ctx* ctx, const double* b, double* x);
 
 /* nsteps >= 0 HEVI 1D-IMEX ARK2 steps of size dt (the dt of the last
@@ -291,7 +297,9 @@ int numa_count_nonfinite(numa_ctx* ctx, const double* x, long long n, long long*
  * in numa_factor_columns.  NUMA_ERR_NONFINITE: a step met a non-finite state -- the
  * equation-of-state passes (the P' pre-pass of a step's or RK stage's input, the fused P'
  * of each implicit stage value) and the ARK4/ARK5 final combination test their results; a
- * non-finite u, v or w reaches them within one step through the coupled tendencies. */
+ * non-finite u, v or w reaches them within one step through the coupled tendencies.
+ * NUMA_ERR_TIMEOUT: a bounded wait of the FP64 stand-alone column solve on its bulk copies
+ * gave up. */
 int numa_status(numa_ctx* ctx, int* status);
 
 int numa_query(const numa_ctx* ctx, int what, long long* out);

@@ -16,7 +16,9 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <string>
 
+#include "bulk_copy.cuh"
 #include "column_device.cuh"
 
 namespace {
@@ -178,6 +180,183 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
   }
 }
 
+// The stand-alone FP64 column solve with its memory traffic on the TMA engine.
+// One warp owns one block of kFacBlk = 32 consecutive mesh columns, one lane per column.
+// * The block's right-hand side, 32 M contiguous doubles, arrives by one bulk copy and
+//   stays in shared memory in its global layout (lane c reads level i at c M + i: an odd M
+//   gives no bank conflicts); the solution leaves by one bulk store, in place.
+// * The block's factors are one contiguous stream: M rows of L (hb slots x 32 columns, read
+//   front to back), then M rows of U (hb + 1 slots, back to front).  Each stored row is one
+//   chunk, copied into a ring of kSolveStages shared-memory slots of the warp, each
+//   completed on its own mbarrier; a slot is refilled with the chunk kSolveStages rows ahead
+//   as soon as the warp has read it into registers.
+// A short ring leaves room for more warps per SM, which is what the FP64 pipe, the other
+// bound of this kernel, needs.  The arithmetic is col_solve's, in the same order.
+// A bounded wait that gives up latches NUMA_ST_TIMEOUT, drains the warp's copies in flight
+// and leaves the block unwritten.  Where b or x is not 16-byte aligned, or the block's byte
+// count is not a multiple of 16 (an odd M times an odd column count in the last block),
+// plain loads and stores move the block.
+#ifndef NUMA_SOLVE_STAGES
+#define NUMA_SOLVE_STAGES 2
+#endif
+#ifndef NUMA_SOLVE_MAXW
+#define NUMA_SOLVE_MAXW 2
+#endif
+constexpr int kSolveStages = NUMA_SOLVE_STAGES;   // slots in a warp's ring
+constexpr size_t kSmemPerCta = 227 * 1024;           // opt-in shared memory per CTA
+
+// NUMA_SOLVE=regs selects the register-pipelined k_solve for the FP64 stand-alone solve
+// (read once per process).
+inline bool solve_regs_forced() {
+  static const bool f = [] {
+    const char* e = std::getenv("NUMA_SOLVE");
+    return e && std::string(e) == "regs";
+  }();
+  return f;
+}
+
+__host__ __device__ inline size_t solve_bulk_warp_bytes(int hb, int M) {
+  const size_t slots = (size_t)kSolveStages * (hb + 1) * kFacBlk * sizeof(double);
+  const size_t xs = (size_t)M * kFacBlk * sizeof(double);
+  const size_t bars = (kSolveStages + 1) * sizeof(unsigned long long);
+  return (slots + xs + bars + 127) / 128 * 128;
+}
+
+template <int N>
+__global__ void __launch_bounds__(32 * NUMA_SOLVE_MAXW) k_solve_bulk(
+    const double* b, double* x, long long ncol, int M, const double* __restrict__ L,
+    const double* __restrict__ U, unsigned* status) {
+  constexpr int HB = 2 * N;
+  constexpr unsigned LROW = HB * kFacBlk * sizeof(double);
+  constexpr unsigned UROW = (HB + 1) * kFacBlk * sizeof(double);
+  constexpr int S = kSolveStages;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long blk = (long long)blockIdx.x * (blockDim.x >> 5) + wid;
+  const long long col0 = blk * kFacBlk;
+  if (col0 >= ncol) return;                         // whole warp; no CTA-wide sync follows
+  unsigned char* base = smem + (size_t)wid * solve_bulk_warp_bytes(HB, M);
+  double* xs = (double*)(base + (size_t)S * UROW);  // the block's columns, global layout
+  const unsigned slot0 = smem_u32(base);
+  const unsigned bar0 = smem_u32(xs + (size_t)M * kFacBlk);  // S ring barriers, then b's
+  const unsigned barb = bar0 + 8 * S;
+  const double* Lb = L + blk * (long long)M * HB * kFacBlk;
+  const double* Ub = U + blk * (long long)M * (HB + 1) * kFacBlk;
+  const int nch = 2 * M;
+  const int nc = (int)min((long long)kFacBlk, ncol - col0);
+  const unsigned bbytes = (unsigned)(nc * M) * sizeof(double);
+  const bool bulk_io = (bbytes % 16) == 0 && ((unsigned long long)b % 16) == 0 &&
+                       ((unsigned long long)x % 16) == 0;
+  const double* bb = b + col0 * M;
+  double* xb = x + col0 * M;
+
+  // chunk q < M: row q of L; chunk q >= M: row 2M - 1 - q of U
+  auto issue = [&](int q) {
+    const int s = q % S;
+    const bool isL = q < M;
+    const double* src = isL ? Lb + (long long)q * HB * kFacBlk
+                            : Ub + (long long)(nch - 1 - q) * (HB + 1) * kFacBlk;
+    const unsigned bytes = isL ? LROW : UROW;
+    mbar_arrive_expect_tx(bar0 + 8 * s, bytes);
+    bulk_g2s(slot0 + s * UROW, src, bytes, bar0 + 8 * s);
+  };
+  if (lane == 0) {
+    for (int s = 0; s <= S; ++s) mbar_init(bar0 + 8 * s, 1);
+    fence_proxy_async_smem();
+    if (bulk_io) {
+      mbar_arrive_expect_tx(barb, bbytes);
+      bulk_g2s(smem_u32(xs), bb, bbytes, barb);
+    }
+    for (int q = 0; q < S && q < nch; ++q) issue(q);
+  }
+  // on a timeout: latch the status and drain this warp's copies in flight (chunks q0 ..
+  // q0 + S - 1, and b's when it was still pending)
+  auto give_up = [&](int q0, bool b_pending) {
+    if (lane == 0) {
+      atomicOr(status, NUMA_ST_TIMEOUT);
+      if (b_pending) mbar_wait_bounded(barb, 0);
+      for (int r = q0; r < q0 + S && r < nch; ++r) mbar_wait_bounded(bar0 + 8 * (r % S), (r / S) & 1);
+    }
+    __syncwarp();
+  };
+  if (bulk_io) {
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(barb, 0))) {
+      give_up(0, true);
+      return;
+    }
+  } else {
+    for (int j = lane; j < nc * M; j += 32) xs[j] = bb[j];
+    __syncwarp();
+  }
+  double* xc = xs + lane * M;                       // this lane's column
+
+  int q = 0;
+  auto acquire = [&]() -> const double* {
+    const int s = q % S;
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar0 + 8 * s, (q / S) & 1))) {
+      give_up(q, false);
+      return nullptr;
+    }
+    return (const double*)(base + (size_t)s * UROW) + lane;
+  };
+  // the slot just read is refilled: every lane orders its reads of it before the bulk copy
+  // (async proxy) that overwrites it, the warp synchronises, lane 0 issues the copy
+  auto release = [&]() {
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0 && q + S < nch) issue(q + S);
+    ++q;
+  };
+
+  // forward: y_i = w_0; w_k <- w_{k+1} - L(i+1+k, i) y_i
+  double w[HB];
+#pragma unroll
+  for (int k = 0; k < HB; ++k) w[k] = (k < M) ? xc[k] : 0.0;
+  for (int i = 0; i < M; ++i) {
+    const double* sl = acquire();
+    if (!sl) return;
+    double l[HB];
+#pragma unroll
+    for (int k = 0; k < HB; ++k) l[k] = sl[k * kFacBlk];
+    release();
+    const double y = w[0];
+    const double nxt = (i + HB < M) ? xc[i + HB] : 0.0;
+    xc[i] = y;
+#pragma unroll
+    for (int k = 0; k < HB - 1; ++k) w[k] = fma(-l[k], y, w[k + 1]);
+    w[HB - 1] = fma(-l[HB - 1], y, nxt);
+  }
+  // backward: x_i = v_0 / U(i,i); v_k <- v_{k+1} - U(i-1-k, i) x_i
+  double v[HB];
+#pragma unroll
+  for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? xc[M - 1 - k] : 0.0;
+  for (int i = M - 1; i >= 0; --i) {
+    const double* su = acquire();
+    if (!su) return;
+    double u[HB + 1];
+#pragma unroll
+    for (int k = 0; k <= HB; ++k) u[k] = su[k * kFacBlk];
+    release();
+    const double xi = v[0] * u[0];
+    xc[i] = xi;
+    const double nxt = (i - HB >= 0) ? xc[i - HB] : 0.0;
+#pragma unroll
+    for (int k = 0; k < HB - 1; ++k) v[k] = fma(-u[k + 1], xi, v[k + 1]);
+    v[HB - 1] = fma(-u[HB], xi, nxt);
+  }
+  __syncwarp();
+  if (bulk_io) {
+    if (lane == 0) {
+      fence_proxy_async_smem();                     // the lanes' writes, before the store reads
+      bulk_s2g(xb, smem_u32(xs), bbytes);
+      bulk_commit();
+      bulk_wait_read_all();
+    }
+  } else {
+    for (int j = lane; j < nc * M; j += 32) xb[j] = xs[j];
+  }
+}
+
 // NP previous stages (see stage_body); R3 and q3 are read only when NP = 3.
 template <int N, int NP, bool MIXED, typename RT>
 __global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
@@ -282,9 +461,31 @@ int stage_threads(int T) {
   return std::min(1024, std::max(T, kStageMinThreads));
 }
 
+// Warps (32-column blocks) per CTA of k_solve_bulk for M levels at order N; 0 when one
+// warp's slots and column do not fit in shared memory (the register-pipelined k_solve runs).
+inline int solve_bulk_warps(int N, int M) {
+  const size_t wb = solve_bulk_warp_bytes(2 * N, M);
+  if (wb > kSmemPerCta) return 0;
+  return (int)std::min<size_t>(NUMA_SOLVE_MAXW, kSmemPerCta / wb);
+}
+
 template <int N, bool MIXED>
 cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, const Factors& F,
-                           const RefLev& R, const StageTab& tb, int T, int iters, cudaStream_t s) {
+                           const RefLev& R, const StageTab& tb, int T, int iters,
+                           unsigned* status, cudaStream_t s) {
+  if constexpr (!MIXED) {
+    const int nw = solve_bulk_warps(N, G.M);
+    if (nw > 0 && status && !solve_regs_forced()) {
+      const size_t smem = solve_bulk_warp_bytes(2 * N, G.M) * nw;
+      cudaError_t e = cudaFuncSetAttribute(k_solve_bulk<N>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const long long nblk = (G.ncol + kFacBlk - 1) / kFacBlk;
+      k_solve_bulk<N><<<(unsigned)((nblk + nw - 1) / nw), 32 * nw, smem, s>>>(
+          b, x, G.ncol, G.M, F.L, F.U, status);
+      return cudaGetLastError();
+    }
+  }
   // the FP64 solve uses only the right-hand-side column (more resident columns per SM)
   const size_t smem = (MIXED ? col_smem_per_level(MIXED, iters) : sizeof(double)) * G.M * T;
   cudaError_t e = cudaFuncSetAttribute(k_solve<N, MIXED>,
@@ -378,12 +579,12 @@ cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
 }
 
 cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, const RefLev& R,
-                         const StageTab& tb, int T, cudaStream_t s) {
+                         const StageTab& tb, int T, cudaStream_t s, unsigned* status) {
   const int it = F.refine_iters;
 #define NUMA_SOLVE_CASE(n)                                                             \
   case n:                                                                              \
-    return F.mixed ? launch_solve_n<n, true>(b, x, G, F, R, tb, T, it, s)              \
-                   : launch_solve_n<n, false>(b, x, G, F, R, tb, T, it, s);
+    return F.mixed ? launch_solve_n<n, true>(b, x, G, F, R, tb, T, it, status, s)      \
+                   : launch_solve_n<n, false>(b, x, G, F, R, tb, T, it, status, s);
   switch (G.N) {
     NUMA_SOLVE_CASE(1) NUMA_SOLVE_CASE(2) NUMA_SOLVE_CASE(3) NUMA_SOLVE_CASE(4)
     NUMA_SOLVE_CASE(5) NUMA_SOLVE_CASE(6) NUMA_SOLVE_CASE(7) NUMA_SOLVE_CASE(8)

@@ -389,7 +389,8 @@ int pbno(numa_ctx* c, const W3& w, const double* in, double* out) {
 // out = M^-1 in: the polynomial (PBNO procedure) or the stored column Schur LU solve.
 int precond(numa_ctx* c, const W3& w, const double* in, double* out) {
   if (c->precond == NUMA_PRECOND_COLUMN) {
-    NUMA_3CK(c, launch_solve(in, out, c->G, c->F, c->R, c->T, c->col_tile, c->stream));
+    NUMA_3CK(c, launch_solve(in, out, c->G, c->F, c->R, c->T, c->col_tile, c->stream,
+                             c->d_status));
     return NUMA_OK;
   }
   return pbno(c, w, in, out);

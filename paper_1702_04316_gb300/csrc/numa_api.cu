@@ -789,7 +789,8 @@ int numa_solve_columns(numa_ctx* ctx, const double* b, double* x) {
   if (ctx->F.standard || ctx->imex3d)
     return fail(ctx, NUMA_ERR_ARG, "the stand-alone column solve needs a 1D-IMEX Schur-form context");
   long p = prof_begin(ctx, NUMA_K_SOLVE);
-  NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->R, ctx->T, ctx->col_tile, ctx->stream));
+  NUMA_CK(ctx, launch_solve(b, x, ctx->G, ctx->F, ctx->R, ctx->T, ctx->col_tile, ctx->stream,
+                            ctx->d_status));
   prof_end(ctx, p);
   return NUMA_OK;
 }
@@ -1209,7 +1210,10 @@ int numa_status(numa_ctx* ctx, int* status) {
   NUMA_CK(ctx, cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   NUMA_CK(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
   NUMA_CK(ctx, cudaStreamSynchronize(ctx->stream));
-  *status = (h & NUMA_ST_PIVOT) ? NUMA_ERR_PIVOT : (h & NUMA_ST_NONFINITE) ? NUMA_ERR_NONFINITE : NUMA_OK;
+  *status = (h & NUMA_ST_PIVOT)       ? NUMA_ERR_PIVOT
+            : (h & NUMA_ST_NONFINITE) ? NUMA_ERR_NONFINITE
+            : (h & NUMA_ST_TIMEOUT)   ? NUMA_ERR_TIMEOUT
+                                      : NUMA_OK;
   return NUMA_OK;
 }
 

@@ -24,6 +24,7 @@
 // Device status bits latched by kernels (read back by numa_status).
 #define NUMA_ST_PIVOT 1u
 #define NUMA_ST_NONFINITE 2u
+#define NUMA_ST_TIMEOUT 4u
 
 // Mesh sizes (see the conventions in include/numa.h).
 struct Geom {
@@ -191,8 +192,10 @@ cudaError_t launch_factor(const Geom& G, const RefLev& R, double lam, Factors F,
                           unsigned* status, cudaStream_t s);
 // T: columns per CTA (one thread each; a multiple of 32).  R1, R2: float arrays when
 // r_float (the mixed form's internal tendencies), else double arrays.
+// status: device status word; the FP64 solve stages its factor stream with bulk copies
+// only when it is given (a bounded wait that gives up latches NUMA_ST_TIMEOUT there).
 cudaError_t launch_solve(const double* b, double* x, const Geom& G, Factors F, const RefLev& R,
-                         const StageTab& tb, int T, cudaStream_t s);
+                         const StageTab& tb, int T, cudaStream_t s, unsigned* status = nullptr);
 // stage i in {2, 3, 4} reads R1..R(i-1) and q2..q(i-1); stage 4 (four-stage schemes) is
 // FP64 Schur form only and takes R3, q3.  Pp_out (FP64 Schur form only; NULL to skip)
 // receives P'(q(i)), the equation-of-state pre-pass of the next right-hand side.

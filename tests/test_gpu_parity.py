@@ -128,6 +128,76 @@ def test_factors_and_solve(pkg, torch, name, n_bv, C):
     assert g.status() == pkg.NUMA_OK
 
 
+_SOLVE_SCRIPT = r"""
+import hashlib, sys, torch
+import paper_1702_04316_gb300 as pkg
+nex, ney, nez, N = (int(v) for v in sys.argv[1:5])
+g = pkg.Numa(nex, ney, nez, 2e3 * nex, 2e3 * ney, 1.25e3 * nez, N, 9.32)
+nn = g.ncol * g.M
+gen = torch.Generator(device="cuda").manual_seed(5)
+b = torch.randn(nn, dtype=torch.float64, device="cuda", generator=gen)
+x = g.solve_columns(b)
+assert g.status() == pkg.NUMA_OK
+print(hashlib.sha1(x.cpu().numpy().tobytes()).hexdigest())
+"""
+
+
+@pytest.mark.parametrize("mesh", [(4, 4, 4, 4), (3, 5, 2, 3), (2, 3, 2, 7), (21, 19, 6, 4)])
+def test_bulk_copy_solve_equals_register_solve(mesh):
+    """The stand-alone solve stages its factor stream with bulk (TMA) copies; with
+    NUMA_SOLVE=regs it runs the register-pipelined kernel instead.  Both do the same
+    arithmetic in the same order, so the solutions agree bit for bit (ragged last blocks of
+    32 columns included: 3 x 5 x 2 at N = 3 has 16 x 10 columns)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for mode in ("", "regs"):
+        env = dict(os.environ, NUMA_SOLVE=mode, PYTHONPATH=root)
+        r = subprocess.run([sys.executable, "-c", _SOLVE_SCRIPT] + [str(v) for v in mesh],
+                           env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        out[mode] = r.stdout.strip()
+    assert out[""] == out["regs"]
+
+
+def test_bulk_copy_solve_unaligned_buffers(pkg, torch):
+    """Buffers that are 8- but not 16-byte aligned take plain loads and stores for the
+    right-hand side and the solution; the result bits do not change."""
+    case = make("cfg1")
+    g = gpu_ctx(pkg, case, case.dt_for(15))
+    nn = case.mesh.ncol * case.mesh.M
+    b = torch.randn(nn, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(3))
+    x = g.solve_columns(b)
+    bu = torch.empty(nn + 1, dtype=torch.float64, device="cuda")[1:]
+    xu = torch.empty(nn + 1, dtype=torch.float64, device="cuda")[1:]
+    bu.copy_(b)
+    g.solve_columns(bu, xu)
+    assert torch.equal(xu, x)
+    g.solve_columns(bu, bu)                          # in place, unaligned
+    assert torch.equal(bu, x)
+    assert g.status() == pkg.NUMA_OK
+
+
+def test_bulk_copy_solve_is_repeatable(pkg, torch):
+    """Twenty solves of one right-hand side give the same bits (the shared-memory ring of
+    factor rows is refilled while other warps stream: a refill that overtook a read would
+    show here).  N = 7, 169 x 169 columns of 43 levels, half-band 14."""
+    case = Case(24, 24, 6, 7, 48e3, 48e3, 7.5e3)
+    g = gpu_ctx(pkg, case, case.dt_for(15))
+    nn = case.mesh.ncol * case.mesh.M
+    b = torch.randn(nn, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(4))
+    x0 = g.solve_columns(b)
+    x = torch.empty_like(b)
+    for _ in range(20):
+        g.solve_columns(b, x)
+        assert torch.equal(x, x0)
+    assert g.status() == pkg.NUMA_OK
+
+
 @pytest.mark.parametrize("C", [15, 150])
 def test_imex_stages(pkg, torch, C):
     """Rows 2 and 3 of Table 1 on their own, inputs from the oracle."""
