@@ -99,6 +99,20 @@ def stage_flops_per_node(stage):
     return 2 * pred + schur + solve + extract + recomb
 
 
+def alg_bytes_per_node(kernel, hb=2 * N):
+    """Algorithmic HBM bytes per global node and launch, averaged over one ARK2 step.
+    k_rhs: the five state fields and P' read, five tendencies (or the updated state)
+    written.  k_pressure: rho' and theta' read, P' written.  k_stage (mean of stages 2 and
+    3): q^n and R1 (stage 3 also R2 and q(2)) read, 2 hb + 1 factor doubles per unknown read,
+    the stage value and its P' written."""
+    if kernel == "k_rhs":
+        return 8 * (6 + 5)
+    if kernel == "k_pressure":
+        return 8 * (2 + 1)
+    fac = 2 * hb + 1
+    return 8 * (0.5 * ((5 + 5) + (5 + 5 + 5 + 5)) + fac + 6)
+
+
 def source_sha(*names):
     h = hashlib.sha256()
     for n in names:
@@ -311,8 +325,16 @@ def run_gpu(args):
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "kernel": names[top], "per_launch_ms": round(per_launch_ms, 4),
                 "peak_note": "FP64 FMA peak: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (unit counts x max clock)"}
-    kernel_ms = {names[k]: {"total_ms": round(v[0], 3), "launches": v[1],
-                            "share": round(v[0] / max(ms, 1e-9), 4)} for k, v in kt.items()}
+    hbm, hbm_src = hbm_peak()
+    kernel_ms = {}
+    for k, v in kt.items():
+        per = v[0] / max(v[1], 1)
+        gbs = alg_bytes_per_node(names[k]) * nnode / (per * 1e-3) / 1e9
+        kernel_ms[names[k]] = {"total_ms": round(v[0], 3), "launches": v[1],
+                               "share": round(v[0] / max(ms, 1e-9), 4),
+                               "alg_bytes_per_node": alg_bytes_per_node(names[k]),
+                               "achieved_gbs": round(gbs, 1),
+                               "frac_of_hbm_peak": round(gbs / hbm, 4)}
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "sim-s/wall-s", "n_gpus": world,
@@ -349,7 +371,6 @@ def run_gpu(args):
         g.solve_columns(bcol, xcol)
     ms_solve = time_steps(lambda: g.solve_columns(bcol, xcol), args.steps) / args.steps
     solve_bytes = fb + 2 * 8 * nn
-    hbm, hbm_src = hbm_peak()
     out["column_solve"] = {"ms_per_launch": round(ms_solve, 4), "bytes_per_launch": int(solve_bytes),
                            "achieved_gbs": round(solve_bytes / (ms_solve * 1e-3) / 1e9, 1),
                            "hbm_peak_gbs": hbm, "peak_source": hbm_src,
