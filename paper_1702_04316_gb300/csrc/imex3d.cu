@@ -234,6 +234,53 @@ __global__ void k_dots_final(const double* __restrict__ part, int nblk, double* 
     for (int k = 0; k < 3; ++k) res[k] = sh[k][0];
 }
 
+// BiCGstab's scalars kept on the device (slots of the result array after the three dot
+// products), so that an iteration needs the host only for its convergence test.
+enum { KS_RNRO = 3, KS_AR = 4, KS_WR = 5, KS_BR = 6 };
+enum { KU_INIT = 0, KU_ALPHA = 1, KU_OMEGA = 2, KU_BETA = 3 };
+
+// After a k_dots_final: the scalar update of one point of the iteration, with the host
+// code's expressions (IEEE division and products, same order).
+__global__ void k_bicg_scalars(double* __restrict__ res, int what) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double d0 = res[0], d1 = res[1];
+  switch (what) {
+    case KU_INIT: res[KS_RNRO] = d0; break;                     // (r0, r0)
+    case KU_ALPHA: res[KS_AR] = res[KS_RNRO] / d0; break;       // (r, r0) / (A p, r0)
+    case KU_OMEGA: res[KS_WR] = d0 / d1; break;                 // (A s, s) / (A s, A s)
+    default:                                                    // beta; (r, r0) moves on
+      res[KS_BR] = d1 / res[KS_RNRO] * res[KS_AR] / res[KS_WR];
+      res[KS_RNRO] = d1;
+  }
+}
+
+// The vector updates of an iteration with the device scalars sc: out = x + b y + c z with
+//   form 0: s  = r + (-alpha) A p
+//   form 1: x  = x + alpha p + omega s
+//   form 2: r  = s + (-omega) A s
+//   form 3: p  = r + beta p + (-beta omega) A p
+// evaluated as k_lincomb does with a = 1.
+// out may alias x (the x update is in place).
+__global__ void k_lincomb_sc(double* out, const double* x,
+                             const double* __restrict__ y, const double* __restrict__ z,
+                             const double* __restrict__ sc, int form, long long n) {
+  const double ar = __ldg(sc + KS_AR), wr = __ldg(sc + KS_WR), br = __ldg(sc + KS_BR);
+  double b, c = 0.0;
+  switch (form) {
+    case 0: b = -ar; break;
+    case 1: b = ar; c = wr; break;
+    case 2: b = -wr; break;
+    default: b = br; c = -br * wr;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = 1.0 * x[i];
+    v = fma(b, y[i], v);
+    if (z) v = fma(c, z[i], v);
+    out[i] = v;
+  }
+}
+
 // out = a x + b y + c z over n entries (y, z may be NULL).
 __global__ void k_lincomb(double* __restrict__ out, double a, const double* __restrict__ x,
                           double b, const double* __restrict__ y, double c,
@@ -353,17 +400,30 @@ int lincomb(numa_ctx* c, double* out, double a, const double* x, double b = 0.0,
   return NUMA_OK;
 }
 
-// nd dot products a_k . b_k, read back to the host (synchronises the stream).
+// nd dot products a_k . b_k into w.res; then the device scalar update `upd` (-1: none); then,
+// when out is given, the results read back to the host (synchronises the stream).
 int dots(numa_ctx* c, const W3& w, int nd, const double* a0, const double* b0, double* out,
          const double* a1 = nullptr, const double* b1 = nullptr, const double* a2 = nullptr,
-         const double* b2 = nullptr) {
+         const double* b2 = nullptr, int upd = -1) {
   DotArgs d{{a0, a1, a2}, {b0, b1, b2}, nd};
   k_dots<<<kRedBlocks, kRedThreads, 0, c->stream>>>(d, c->G.nnode, w.part);
   NUMA_3CK(c, cudaGetLastError());
   k_dots_final<<<1, kRedThreads, 0, c->stream>>>(w.part, kRedBlocks, w.res);
   NUMA_3CK(c, cudaGetLastError());
+  if (upd >= 0) {
+    k_bicg_scalars<<<1, 32, 0, c->stream>>>(w.res, upd);
+    NUMA_3CK(c, cudaGetLastError());
+  }
+  if (!out) return NUMA_OK;
   NUMA_3CK(c, cudaMemcpyAsync(out, w.res, nd * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   NUMA_3CK(c, cudaStreamSynchronize(c->stream));
+  return NUMA_OK;
+}
+
+int lincomb_sc(numa_ctx* c, const W3& w, double* out, int form, const double* x,
+               const double* y, const double* z = nullptr) {
+  k_lincomb_sc<<<kRedBlocks, kRedThreads, 0, c->stream>>>(out, x, y, z, w.res, form, c->G.nnode);
+  NUMA_3CK(c, cudaGetLastError());
   return NUMA_OK;
 }
 
@@ -403,31 +463,29 @@ int bicgstab(numa_ctx* c, const W3& w, const double* b, double* x, int* iters) {
   int rc;
   NUMA_3CK(c, cudaMemsetAsync(x, 0, nn * sizeof(double), c->stream));
   if ((rc = precond(c, w, b, w.rn))) return rc;
+  // alpha, omega, beta and (r, r0) live on the device (k_bicg_scalars, k_lincomb_sc); the
+  // host reads only |r|^2 once per iteration for the convergence test
   double d[3];
-  if ((rc = dots(c, w, 1, w.rn, w.rn, d))) return rc;
+  if ((rc = dots(c, w, 1, w.rn, w.rn, d, nullptr, nullptr, nullptr, nullptr, KU_INIT))) return rc;
   const double r0 = std::sqrt(d[0]);
   *iters = 0;
   if (!(r0 > 0.0)) return NUMA_OK;
   NUMA_3CK(c, cudaMemcpyAsync(w.p, w.rn, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   NUMA_3CK(c, cudaMemcpyAsync(w.ro, w.rn, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  double rn_ro = d[0];
   for (int it = 1; it <= c->krylov_max_iters; ++it) {
     if ((rc = lhs(c, w, w.p, w.t)) || (rc = precond(c, w, w.t, w.Ap))) return rc;
-    if ((rc = dots(c, w, 1, w.Ap, w.ro, d))) return rc;
-    const double ar = rn_ro / d[0];
-    if ((rc = lincomb(c, w.s, 1.0, w.rn, -ar, w.Ap))) return rc;
+    if ((rc = dots(c, w, 1, w.Ap, w.ro, nullptr, nullptr, nullptr, nullptr, nullptr, KU_ALPHA)))
+      return rc;
+    if ((rc = lincomb_sc(c, w, w.s, 0, w.rn, w.Ap))) return rc;
     if ((rc = lhs(c, w, w.s, w.t)) || (rc = precond(c, w, w.t, w.As))) return rc;
-    if ((rc = dots(c, w, 2, w.As, w.s, d, w.As, w.As))) return rc;
-    const double wr = d[0] / d[1];
-    if ((rc = lincomb(c, x, 1.0, x, ar, w.p, wr, w.s))) return rc;
-    if ((rc = lincomb(c, w.rn, 1.0, w.s, -wr, w.As))) return rc;          // r_e, kept in rn
-    if ((rc = dots(c, w, 2, w.rn, w.rn, d, w.rn, w.ro))) return rc;
+    if ((rc = dots(c, w, 2, w.As, w.s, nullptr, w.As, w.As, nullptr, nullptr, KU_OMEGA))) return rc;
+    if ((rc = lincomb_sc(c, w, x, 1, x, w.p, w.s))) return rc;
+    if ((rc = lincomb_sc(c, w, w.rn, 2, w.s, w.As))) return rc;          // r_e, kept in rn
+    if ((rc = dots(c, w, 2, w.rn, w.rn, d, w.rn, w.ro, nullptr, nullptr, KU_BETA))) return rc;
     *iters = it;
     if (!std::isfinite(d[0])) return fail3(c, NUMA_ERR_NONFINITE, "BiCGstab diverged");
     if (std::sqrt(d[0]) / r0 <= c->krylov_tol) return NUMA_OK;
-    const double br = d[1] / rn_ro * ar / wr;
-    if ((rc = lincomb(c, w.p, 1.0, w.rn, br, w.p, -br * wr, w.Ap))) return rc;
-    rn_ro = d[1];
+    if ((rc = lincomb_sc(c, w, w.p, 3, w.rn, w.p, w.Ap))) return rc;
   }
   return fail3(c, NUMA_ERR_TIMEOUT, "BiCGstab did not converge within krylov_max_iters");
 }
