@@ -990,12 +990,31 @@ int host_slabs() {
   return n;
 }
 
-// FP64 ARK2 1D-IMEX steps from host memory to host memory with the copies overlapped.  The
-// upload is issued slab by slab (node rows [y0, y1) of every field) on cs_in; the first
-// right-hand side of the first step waits for each slab and computes P' and R slab by slab,
-// R of slab k once slab k + 1 (its stencil's far side, at most N node rows away) is on the
-// device.  The final update of the last step is issued slab by slab; each slab goes back
-// to the host on cs_out as soon as it is final.  Steps in between run unchanged.
+// Slab boundaries in tile rows: K slabs over `rows` tile rows, one slab of a single tile row
+// at the front (first_small) or at the back, the others as even as possible.  With fewer
+// than K + 1 tile rows, or K < 3, the slabs are plain even splits.
+std::vector<int> slab_bounds(int rows, int K, bool first_small) {
+  std::vector<int> b(K + 1);
+  if (K < 3 || rows < K + 1) {
+    for (int k = 0; k <= K; ++k) b[k] = (int)((long long)k * rows / K);
+    return b;
+  }
+  const int off = first_small ? 1 : 0;
+  for (int k = 0; k < K; ++k) b[k + off] = off + (int)((long long)k * (rows - 1) / (K - 1));
+  b[0] = 0;
+  b[K] = rows;
+  return b;
+}
+
+// FP64 ARK2 1D-IMEX steps from host memory to host memory with the copies overlapped.
+// * Upload: slab by slab on cs_in, the first slab one tile row.  Each slab goes up in two
+//   pieces, its first N node rows (one element: all that the stencil of the slab before it
+//   reaches) and the rest, with an event after each.
+// * The first right-hand side of the first step follows the pieces: P' of each piece once it
+//   is on the device, and R of slab k once P' of slab k + 1's first piece is done.
+// * The final update of the last step is issued slab by slab, the last slab one tile row;
+//   each slab goes back to the host on cs_out as soon as it is final.
+// * Steps in between run unchanged, and every node's arithmetic is the device run's.
 int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nsteps) {
   const Geom& G = ctx->G;
   const long long nn = G.nnode;
@@ -1007,26 +1026,34 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
         cudaStreamCreateWithFlags(&ctx->cs_out, cudaStreamNonBlocking) != cudaSuccess)
       return fail(ctx, NUMA_ERR_CUDA, "copy streams");
   }
-  while ((int)ctx->host_ev.size() < 2 * kHostSlabs + 2) {
+  while ((int)ctx->host_ev.size() < 3 * kHostSlabs + 2) {
     cudaEvent_t e;
     NUMA_CK(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     ctx->host_ev.push_back(e);
   }
-  cudaEvent_t* ev_in = ctx->host_ev.data();
-  cudaEvent_t* ev_out = ev_in + kHostSlabs;
-  cudaEvent_t ev_start = ev_in[2 * kHostSlabs], ev_done = ev_in[2 * kHostSlabs + 1];
-  auto r0 = [&](int k) { return (int)((long long)k * rows / K); };       // first tile row
-  auto n0 = [&](int k) { return (long long)ctx->perm_row_y[r0(k)] * plane; };   // first node
-  auto p0 = [&](int k) { return ctx->perm_row_off[r0(k)]; };           // first thread
+  cudaEvent_t* ev_head = ctx->host_ev.data();           // first piece of slab k uploaded
+  cudaEvent_t* ev_in = ev_head + kHostSlabs;            // whole slab k uploaded
+  cudaEvent_t* ev_out = ev_in + kHostSlabs;             // slab k final
+  cudaEvent_t ev_start = ev_head[3 * kHostSlabs], ev_done = ev_head[3 * kHostSlabs + 1];
+  const std::vector<int> bu = slab_bounds(rows, K, true), bd = slab_bounds(rows, K, false);
+  auto y0 = [&](const std::vector<int>& bnd, int k) { return (long long)ctx->perm_row_y[bnd[k]]; };
+  auto n0 = [&](const std::vector<int>& bnd, int k) { return y0(bnd, k) * plane; };   // first node
+  auto p0 = [&](const std::vector<int>& bnd, int k) { return ctx->perm_row_off[bnd[k]]; };  // first thread
+  // end of slab k's first piece (node index)
+  auto nh = [&](int k) { return std::min(y0(bu, k) + G.N, y0(bu, k + 1)) * plane; };
   double* q = ctx->d_hoststate;
   const size_t pitch = nn * sizeof(double);
   // the upload starts after everything already in the context's stream
   NUMA_CK(ctx, cudaEventRecord(ev_start, ctx->stream));
   NUMA_CK(ctx, cudaStreamWaitEvent(ctx->cs_in, ev_start, 0));
   for (int k = 0; k < K; ++k) {
-    const long long a = n0(k), b = n0(k + 1);
-    NUMA_CK(ctx, cudaMemcpy2DAsync(q + a, pitch, hin + a, pitch, (b - a) * sizeof(double), 5,
+    const long long a = n0(bu, k), h = nh(k), b = n0(bu, k + 1);
+    NUMA_CK(ctx, cudaMemcpy2DAsync(q + a, pitch, hin + a, pitch, (h - a) * sizeof(double), 5,
                                    cudaMemcpyHostToDevice, ctx->cs_in));
+    NUMA_CK(ctx, cudaEventRecord(ev_head[k], ctx->cs_in));
+    if (b > h)
+      NUMA_CK(ctx, cudaMemcpy2DAsync(q + h, pitch, hin + h, pitch, (b - h) * sizeof(double), 5,
+                                     cudaMemcpyHostToDevice, ctx->cs_in));
     NUMA_CK(ctx, cudaEventRecord(ev_in[k], ctx->cs_in));
   }
   const ArkTab t = ark_tab(ctx->scheme);
@@ -1038,13 +1065,18 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
       long p = prof_begin(ctx, NUMA_K_RHS);
       for (int k = 0; k <= K; ++k) {
         if (k < K) {
-          NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[k], 0));
-          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, n0(k), n0(k + 1), ctx->stream,
+          NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_head[k], 0));
+          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, n0(bu, k), nh(k), ctx->stream,
                                              ctx->d_status));
         }
         if (k >= 1)
-          NUMA_CK(ctx, launch_rhs(q, ctx->Pp, ctx->R1, ctx->d_perm + p0(k - 1), p0(k) - p0(k - 1),
-                                  G, ctx->C, ctx->R, e0, ctx->stream));
+          NUMA_CK(ctx, launch_rhs(q, ctx->Pp, ctx->R1, ctx->d_perm + p0(bu, k - 1),
+                                  p0(bu, k) - p0(bu, k - 1), G, ctx->C, ctx->R, e0, ctx->stream));
+        if (k < K && n0(bu, k + 1) > nh(k)) {
+          NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[k], 0));
+          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, nh(k), n0(bu, k + 1),
+                                             ctx->stream, ctx->d_status));
+        }
       }
       prof_end(ctx, p);
     } else if ((rc = enqueue_rhs(ctx, q, ctx->R1, e0))) {
@@ -1068,11 +1100,11 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
     // last step: final update (in place, node by node) and download, slab by slab
     long p = prof_begin(ctx, NUMA_K_RHS);
     for (int k = 0; k < K; ++k) {
-      NUMA_CK(ctx, launch_rhs(ctx->q3, ctx->Pp, q, ctx->d_perm + p0(k), p0(k + 1) - p0(k), G,
-                              ctx->C, ctx->R, ef, ctx->stream));
+      NUMA_CK(ctx, launch_rhs(ctx->q3, ctx->Pp, q, ctx->d_perm + p0(bd, k), p0(bd, k + 1) - p0(bd, k),
+                              G, ctx->C, ctx->R, ef, ctx->stream));
       NUMA_CK(ctx, cudaEventRecord(ev_out[k], ctx->stream));
       NUMA_CK(ctx, cudaStreamWaitEvent(ctx->cs_out, ev_out[k], 0));
-      const long long a = n0(k), b = n0(k + 1);
+      const long long a = n0(bd, k), b = n0(bd, k + 1);
       NUMA_CK(ctx, cudaMemcpy2DAsync(hout + a, pitch, q + a, pitch, (b - a) * sizeof(double), 5,
                                      cudaMemcpyDeviceToHost, ctx->cs_out));
     }
