@@ -438,6 +438,7 @@ def run_gpu(args):
     if not args.no_forms:
         out["imex3d"] = imex3d_form(pkg, torch, q0, ms_rk, args.warmup)
     if not args.no_forms:
+        out["accuracy_vs_explicit_c1"] = accuracy_vs_explicit(pkg, torch)
         out["precision_form"] = precision_form(pkg, torch, min(args.steps, 20), args.warmup)
         out["batching_form"] = batching_form(pkg, torch, min(args.steps, 10), args.warmup)
         out["batching_form_small_members"] = batching_form(pkg, torch, min(args.steps, 20), args.warmup,
@@ -452,6 +453,57 @@ def run_gpu(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+def accuracy_vs_explicit(pkg, torch, L=40000e3):
+    """The accuracy at which the speedups over explicit RK35 at C = 1 hold.
+
+    Same array shapes as the benchmark (96 x 96 x 12 elements, N = 4, 15 km deep, the same
+    dt at each C_V and so the same cost per step), on a box stretched horizontally to
+    L x L: on the 200 km box C_H = 0.6 C_V, and at C_V = 15 the explicit horizontal part is
+    unstable (C_H = 9).  At L = 40,000 km C_H = 0.45 at C_V = 150, the paper's regime of
+    large aspect ratio.  theta' is the benchmark's recipe (0.5 K) on the stretched box.
+    Reference: RK35 at C = 1 to t = dt(C = 150) = 150 steps; its own error is estimated
+    against RK35 at C = 0.5 (300 steps).  Relative L2 per field of 1D-IMEX ARK2 at C = 15
+    (10 steps) and C = 150 (1 step), FP64 and the two FP32-RHS precision forms, against
+    the reference."""
+    dt1, dt15, dt150 = dt_for(1.0), dt_for(15.0), dt_for(150.0)
+    g = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt15)
+    lev = g.reference_levels()
+    xi = lgl_nodes()
+    import synthetic
+    q0h = synthetic.balanced_state(axis_coords(NEX, L / NEX, xi), axis_coords(NEY, L / NEY, xi),
+                                   lev["z"], L, L, LZ, lev["rho0"], lev["theta0"], SEED, 0.5)
+    q0 = torch.from_numpy(q0h).cuda()
+    names = ("rho", "u", "v", "w", "theta")
+
+    def rel(a, b):
+        out = {}
+        for f, nm in enumerate(names):
+            nb = float(torch.linalg.norm(b[f]))
+            out[nm] = float("%.3g" % (float(torch.linalg.norm(a[f] - b[f])) / nb)) if nb > 0 else None
+        return out
+
+    ref = g.step_explicit_rk(q0, dt1, torch.empty_like(q0), 150)
+    ref_half = g.step_explicit_rk(q0, 0.5 * dt1, torch.empty_like(q0), 300)
+    res = {"box": "96x96x12 elements over %gx%g km x 15 km, N=4" % (L / 1e3, L / 1e3),
+           "C_H_at_C_V_150": round(C_S * dt150 / (dx_min() * L / LX), 3),
+           "t_s": round(dt150, 4),
+           "reference": "RK35 at C=1 (150 steps)",
+           "reference_vs_rk35_c0.5": rel(ref, ref_half)}
+    res["imex_c15_fp64"] = rel(g.step_imex1d(q0, torch.empty_like(q0), 10), ref)
+    g.close()
+    g150 = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt150)
+    res["imex_c150_fp64"] = rel(g150.step_imex1d(q0, torch.empty_like(q0), 1), ref)
+    g150.close()
+    for prec in ("mixed", "rhs32"):
+        gp = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt15, precision=prec)
+        res["imex_c15_" + prec] = rel(gp.step_imex1d(q0, torch.empty_like(q0), 10), ref)
+        gp.close()
+    res["batched"] = ("ensemble members are bitwise equal to single FP64 contexts, so their "
+                      "accuracy is the FP64 form's")
+    return res
 
 
 # ---------------------------------------------------------------------------------------
