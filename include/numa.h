@@ -201,7 +201,10 @@ int numa_factor_columns(numa_ctx* ctx, double dt);
  * loads and stores otherwise; the result bits are the same).  A bounded device wait that
  * gives up (it never should) latches NUMA_ERR_TIMEOUT in the device status and leaves the
  * affected columns of x unwritten.  The environment variable NUMA_SOLVE=regs, read once per
- * process, selects the register-pipelined kernel instead (same arithmetic, same bits). */
+ * process, selects the register-pipelined kernel instead (same arithmetic, same bits).
+ * NUMA_TEST_SOLVE_TIMEOUT=1, read at every call and meant for tests only, arms the first
+ * factor row's barrier of every warp for 16 bytes more than its copy delivers, so that
+ * the wait gives up after its bound and the call latches NUMA_ERR_TIMEOUT. */
 int numa_solve_columns(numa_ctx* ctx, const double* b, double* x);
 
 /* nsteps >= 0 HEVI 1D-IMEX ARK2 steps of size dt (the dt of the last

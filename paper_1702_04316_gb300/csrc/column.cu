@@ -225,7 +225,7 @@ __host__ __device__ inline size_t solve_bulk_warp_bytes(int hb, int M) {
 template <int N>
 __global__ void __launch_bounds__(32 * NUMA_SOLVE_MAXW) k_solve_bulk(
     const double* b, double* x, long long ncol, int M, const double* __restrict__ L,
-    const double* __restrict__ U, unsigned* status) {
+    const double* __restrict__ U, unsigned* status, int plant_timeout) {
   constexpr int HB = 2 * N;
   constexpr unsigned LROW = HB * kFacBlk * sizeof(double);
   constexpr unsigned UROW = (HB + 1) * kFacBlk * sizeof(double);
@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(32 * NUMA_SOLVE_MAXW) k_solve_bulk(
     const double* src = isL ? Lb + (long long)q * HB * kFacBlk
                             : Ub + (long long)(nch - 1 - q) * (HB + 1) * kFacBlk;
     const unsigned bytes = isL ? LROW : UROW;
-    mbar_arrive_expect_tx(bar0 + 8 * s, bytes);
+    // plant_timeout (tests only): the first row's barrier expects 16 bytes more than arrive
+    mbar_arrive_expect_tx(bar0 + 8 * s, bytes + ((plant_timeout && q == 0) ? 16u : 0u));
     bulk_g2s(slot0 + s * UROW, src, bytes, bar0 + 8 * s);
   };
   if (lane == 0) {
@@ -481,8 +482,12 @@ cudaError_t launch_solve_n(const double* b, double* x, const Geom& G, const Fact
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       const long long nblk = (G.ncol + kFacBlk - 1) / kFacBlk;
+      // NUMA_TEST_SOLVE_TIMEOUT=1 (read at every call; tests only) makes the first wait of
+      // every warp run out, to exercise the timeout path without a fault
+      const char* pt = std::getenv("NUMA_TEST_SOLVE_TIMEOUT");
+      const int plant = (pt && std::string(pt) == "1") ? 1 : 0;
       k_solve_bulk<N><<<(unsigned)((nblk + nw - 1) / nw), 32 * nw, smem, s>>>(
-          b, x, G.ncol, G.M, F.L, F.U, status);
+          b, x, G.ncol, G.M, F.L, F.U, status, plant);
       return cudaGetLastError();
     }
   }

@@ -76,3 +76,47 @@ def test_clean_runs_report_ok(pkg, torch):
         g.step_imex1d(q, None, 3)
         assert g.status() == pkg.NUMA_OK, kw
         g.close()
+
+
+_TIMEOUT_SCRIPT = r"""
+import os, time, torch
+import paper_1702_04316_gb300 as pkg
+g = pkg.Numa(4, 4, 4, 10e3, 10e3, 10e3, 4, 9.0)
+b = torch.randn(g.ncol * g.M, dtype=torch.float64, device="cuda",
+                generator=torch.Generator(device="cuda").manual_seed(9))
+x0 = g.solve_columns(b)
+assert g.status() == pkg.NUMA_OK
+os.environ["NUMA_TEST_SOLVE_TIMEOUT"] = "1"
+t0 = time.time()
+g.solve_columns(b, torch.empty_like(b))
+torch.cuda.synchronize()
+elapsed = time.time() - t0
+st = g.status()
+del os.environ["NUMA_TEST_SOLVE_TIMEOUT"]
+x2 = g.solve_columns(b)
+print(st, g.status(), "%.3f" % elapsed, int(torch.equal(x2, x0)))
+"""
+
+
+def test_bulk_copy_wait_gives_up_with_a_status():
+    """The stand-alone solve waits on mbarriers for its bulk copies, every wait bounded (1 s).
+    NUMA_TEST_SOLVE_TIMEOUT=1 arms the first factor row's barrier of every warp for 16 bytes
+    more than its copy delivers, so that wait runs out (no fault: the barrier simply never
+    completes).  The kernel latches NUMA_ERR_TIMEOUT, drains its copies with the same bound
+    and returns; numa_status reports it, and the next solve in the same context is exact
+    again.  Run in a child process so that the switch touches no other test."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root)
+    env.pop("NUMA_TEST_SOLVE_TIMEOUT", None)
+    r = subprocess.run([sys.executable, "-c", _TIMEOUT_SCRIPT], env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    st, st2, elapsed, same = r.stdout.split()
+    import paper_1702_04316_gb300 as p
+    assert int(st) == p.NUMA_ERR_TIMEOUT
+    assert int(st2) == p.NUMA_OK
+    assert 0.9 < float(elapsed) < 60.0                 # the 1 s bound, then the drain
+    assert same == "1"
