@@ -295,7 +295,7 @@ def run_gpu(args):
     # end to end through the host-buffer entry point: H2D of the state, the step, D2H
     qin = torch.from_numpy(q0h).pin_memory()
     qout = torch.empty_like(qin).pin_memory()
-    for _ in range(max(1, args.warmup // 2)):
+    for _ in range(max(3, args.warmup)):
         g.run_host(0, qin, 1, 0.0, qout)
     barrier()
     t0 = time.perf_counter()
