@@ -306,6 +306,7 @@ void free_all(numa_ctx* c) {
   for (cudaEvent_t e : c->host_ev) cudaEventDestroy(e);
   if (c->cs_in) cudaStreamDestroy(c->cs_in);
   if (c->cs_out) cudaStreamDestroy(c->cs_out);
+  if (c->cs_p) cudaStreamDestroy(c->cs_p);
   cudaFree(c->d_adj);
   cudaFree(c->d_adjtab);
   cudaFree(c->d_w3);
@@ -990,19 +991,31 @@ int host_slabs() {
   return n;
 }
 
-// Slab boundaries in tile rows: K slabs over `rows` tile rows, one slab of a single tile row
-// at the front (first_small) or at the back, the others as even as possible.  With fewer
-// than K + 1 tile rows, or K < 3, the slabs are plain even splits.
-std::vector<int> slab_bounds(int rows, int K, bool first_small) {
+// Slab boundaries in tile rows: K slabs over `rows` tile rows.
+// * Upload (taper_end = false): the first slab is one tile row, the others as even as
+//   possible.
+// * Download (taper_end = true): slabs of relative sizes 1, ..., 1, 1/2, 1/4, so that
+//   little download is left after the last kernel.
+// With fewer than K + 2 tile rows, or K < 3, the slabs are plain even splits.
+std::vector<int> slab_bounds(int rows, int K, bool taper_end) {
   std::vector<int> b(K + 1);
-  if (K < 3 || rows < K + 1) {
+  if (K < 3 || rows < K + 2) {
     for (int k = 0; k <= K; ++k) b[k] = (int)((long long)k * rows / K);
     return b;
   }
-  const int off = first_small ? 1 : 0;
-  for (int k = 0; k < K; ++k) b[k + off] = off + (int)((long long)k * (rows - 1) / (K - 1));
   b[0] = 0;
   b[K] = rows;
+  if (!taper_end) {
+    for (int k = 0; k < K; ++k) b[k + 1] = 1 + (int)((long long)k * (rows - 1) / (K - 1));
+    return b;
+  }
+  const double total = (K - 2) + 0.75;
+  double cum = 0.0;
+  for (int k = 1; k < K; ++k) {
+    cum += (k <= K - 2) ? 1.0 : 0.5;
+    const int v = (int)std::lround(cum / total * rows);
+    b[k] = std::min(std::max(v, b[k - 1] + 1), rows - (K - k));   // strictly increasing
+  }
   return b;
 }
 
@@ -1010,10 +1023,11 @@ std::vector<int> slab_bounds(int rows, int K, bool first_small) {
 // * Upload: slab by slab on cs_in, the first slab one tile row.  Each slab goes up in two
 //   pieces, its first N node rows (one element: all that the stencil of the slab before it
 //   reaches) and the rest, with an event after each.
-// * The first right-hand side of the first step follows the pieces: P' of each piece once it
-//   is on the device, and R of slab k once P' of slab k + 1's first piece is done.
-// * The final update of the last step is issued slab by slab, the last slab one tile row;
-//   each slab goes back to the host on cs_out as soon as it is final.
+// * The first right-hand side of the first step follows the pieces: P' of each piece on
+//   cs_p once it is on the device (overlapping the right-hand sides of earlier slabs), and
+//   R of slab k once P' of slab k and of slab k + 1's first piece are done.
+// * The final update of the last step is issued slab by slab, the slabs shrinking to a
+//   quarter at the end; each slab goes back to the host on cs_out as soon as it is final.
 // * Steps in between run unchanged, and every node's arithmetic is the device run's.
 int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nsteps) {
   const Geom& G = ctx->G;
@@ -1026,7 +1040,10 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
         cudaStreamCreateWithFlags(&ctx->cs_out, cudaStreamNonBlocking) != cudaSuccess)
       return fail(ctx, NUMA_ERR_CUDA, "copy streams");
   }
-  while ((int)ctx->host_ev.size() < 3 * kHostSlabs + 2) {
+  if (!ctx->cs_p &&
+      cudaStreamCreateWithFlags(&ctx->cs_p, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(ctx, NUMA_ERR_CUDA, "pre-pass stream");
+  while ((int)ctx->host_ev.size() < 5 * kHostSlabs + 2) {
     cudaEvent_t e;
     NUMA_CK(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     ctx->host_ev.push_back(e);
@@ -1034,8 +1051,10 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
   cudaEvent_t* ev_head = ctx->host_ev.data();           // first piece of slab k uploaded
   cudaEvent_t* ev_in = ev_head + kHostSlabs;            // whole slab k uploaded
   cudaEvent_t* ev_out = ev_in + kHostSlabs;             // slab k final
-  cudaEvent_t ev_start = ev_head[3 * kHostSlabs], ev_done = ev_head[3 * kHostSlabs + 1];
-  const std::vector<int> bu = slab_bounds(rows, K, true), bd = slab_bounds(rows, K, false);
+  cudaEvent_t* ev_ph = ev_out + kHostSlabs;             // P' of slab k's first piece done
+  cudaEvent_t* ev_pr = ev_ph + kHostSlabs;              // P' of all of slab k done
+  cudaEvent_t ev_start = ev_head[5 * kHostSlabs], ev_done = ev_head[5 * kHostSlabs + 1];
+  const std::vector<int> bu = slab_bounds(rows, K, false), bd = slab_bounds(rows, K, true);
   auto y0 = [&](const std::vector<int>& bnd, int k) { return (long long)ctx->perm_row_y[bnd[k]]; };
   auto n0 = [&](const std::vector<int>& bnd, int k) { return y0(bnd, k) * plane; };   // first node
   auto p0 = [&](const std::vector<int>& bnd, int k) { return ctx->perm_row_off[bnd[k]]; };  // first thread
@@ -1063,20 +1082,26 @@ int run_host_pipelined(numa_ctx* ctx, const double* hin, double* hout, int nstep
     RhsEpilogue e0{};
     if (s == 0) {
       long p = prof_begin(ctx, NUMA_K_RHS);
-      for (int k = 0; k <= K; ++k) {
-        if (k < K) {
-          NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_head[k], 0));
-          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, n0(bu, k), nh(k), ctx->stream,
+      // P' piece by piece on cs_p as the pieces arrive; R of slab k on the context's stream
+      // once P' of slab k and of slab k + 1's first piece are done
+      NUMA_CK(ctx, cudaStreamWaitEvent(ctx->cs_p, ev_start, 0));
+      for (int k = 0; k < K; ++k) {
+        NUMA_CK(ctx, cudaStreamWaitEvent(ctx->cs_p, ev_head[k], 0));
+        NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, n0(bu, k), nh(k), ctx->cs_p,
+                                           ctx->d_status));
+        NUMA_CK(ctx, cudaEventRecord(ev_ph[k], ctx->cs_p));
+        if (n0(bu, k + 1) > nh(k)) {
+          NUMA_CK(ctx, cudaStreamWaitEvent(ctx->cs_p, ev_in[k], 0));
+          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, nh(k), n0(bu, k + 1), ctx->cs_p,
                                              ctx->d_status));
         }
-        if (k >= 1)
-          NUMA_CK(ctx, launch_rhs(q, ctx->Pp, ctx->R1, ctx->d_perm + p0(bu, k - 1),
-                                  p0(bu, k) - p0(bu, k - 1), G, ctx->C, ctx->R, e0, ctx->stream));
-        if (k < K && n0(bu, k + 1) > nh(k)) {
-          NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[k], 0));
-          NUMA_CK(ctx, launch_pressure_range(q, ctx->Pp, G, ctx->R, nh(k), n0(bu, k + 1),
-                                             ctx->stream, ctx->d_status));
-        }
+        NUMA_CK(ctx, cudaEventRecord(ev_pr[k], ctx->cs_p));
+      }
+      for (int k = 0; k < K; ++k) {
+        NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_pr[k], 0));
+        if (k + 1 < K) NUMA_CK(ctx, cudaStreamWaitEvent(ctx->stream, ev_ph[k + 1], 0));
+        NUMA_CK(ctx, launch_rhs(q, ctx->Pp, ctx->R1, ctx->d_perm + p0(bu, k),
+                                p0(bu, k + 1) - p0(bu, k), G, ctx->C, ctx->R, e0, ctx->stream));
       }
       prof_end(ctx, p);
     } else if ((rc = enqueue_rhs(ctx, q, ctx->R1, e0))) {

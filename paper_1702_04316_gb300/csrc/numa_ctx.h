@@ -54,7 +54,7 @@ struct numa_ctx {
   // upload and download streams and their per-slab events
   std::vector<long long> perm_row_off;
   std::vector<int> perm_row_y;
-  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  cudaStream_t cs_in = nullptr, cs_out = nullptr, cs_p = nullptr;
   std::vector<cudaEvent_t> host_ev;
   // differentiation form (allocated on first use): 59 x nnode doubles of workspace and the
   // transposed derivative tap tables of the three axes
