@@ -10,8 +10,10 @@ namespace numa_dev {
 // P' = P(rho0 + rho', theta0 + theta') - P0 without cancellation:
 //   (rho theta)/(rho0 theta0) = (1 + a)(1 + b),  a = rho'/rho0,  b = theta'/theta0,
 //   P' = P0 ((1 + x)^gamma - 1),  x = a + b + a b.
-// For |x| <= 1/64 the binomial series sum_{k=1..9} C(gamma, k) x^k is used (truncation
-// below 1e-19 relative); otherwise P0 expm1(gamma log1p(x)).
+// The binomial series sum_k C(gamma, k) x^k is used: five terms for |x| <= 2^-10 (truncation
+// below 5e-18 relative; x is about P'/(gamma P0), of order 1e-3 or less in atmospheric
+// flows), nine for |x| <= 1/64 (below 1e-19); otherwise P0 expm1(gamma log1p(x)).  The
+// choice is made per node, so a node's P' does not depend on which nodes share its warp.
 struct EosSeries {
   double c[9];   // C(gamma, k), k = 1..9
 };
@@ -22,6 +24,12 @@ __device__ __forceinline__ double eos_rel(double rp, double tp, double inv_rho0,
   const double a = rp * inv_rho0;
   const double b = tp * inv_theta0;
   const double x = fma(a, b, a + b);
+  if (fabs(x) <= 0x1p-10) {
+    double p = S.c[4];
+#pragma unroll
+    for (int k = 3; k >= 0; --k) p = fma(p, x, S.c[k]);
+    return p * x;
+  }
   if (fabs(x) <= 0.015625) {
     double p = S.c[8];
 #pragma unroll
