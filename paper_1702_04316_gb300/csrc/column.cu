@@ -196,6 +196,8 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
 // and leaves the block unwritten.  Where b or x is not 16-byte aligned, or the block's byte
 // count is not a multiple of 16 (an odd M times an odd column count in the last block),
 // plain loads and stores move the block.
+// Compile-time tuning: slots per warp ring and warps (blocks) per CTA.  Two and two were
+// fastest on GB300 (3 or 4 slots, or 4 warps per CTA, measured slower).
 #ifndef NUMA_SOLVE_STAGES
 #define NUMA_SOLVE_STAGES 2
 #endif
