@@ -35,7 +35,7 @@ def pkg():
 
 
 CASES = {
-    "cfg1": (4, 4, 4, 4, 10e3, 10e3, 10e3),
+    "tiny4": (4, 4, 4, 4, 10e3, 10e3, 10e3),
     "ragged": (3, 5, 2, 3, 7e3, 9e3, 4e3),
     "n2": (5, 2, 3, 2, 6e3, 3e3, 5e3),
     "n7": (2, 3, 2, 7, 8e3, 9e3, 6e3),
@@ -48,7 +48,7 @@ def make(name, n_bv=0.0):
     return Case(nex, ney, nez, N, Lx, Ly, Lz, n_bv)
 
 
-def config5():
+def diff_workload():
     """The differentiation workload: 16 x 16 x 8 elements of order 4 over 600 x 600 x 10
     km (horizontal Courant number 0.5 at vertical C = 15)."""
     return Case(16, 16, 8, 4, 600e3, 600e3, 10e3)
@@ -71,7 +71,7 @@ def dot(a, b):
     return float((a * b).sum())
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged", "n2", "n7", "single"])
+@pytest.mark.parametrize("name", ["tiny4", "ragged", "n2", "n7", "single"])
 def test_rhs_tlm_matches_oracle(torch, pkg, name):
     from oracle.tangent import rhs_tlm
     case = make(name, 0.01)
@@ -82,7 +82,7 @@ def test_rhs_tlm_matches_oracle(torch, pkg, name):
     assert rel_l2(out, ref).max() <= TOL
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged", "n2", "n7", "single"])
+@pytest.mark.parametrize("name", ["tiny4", "ragged", "n2", "n7", "single"])
 def test_rhs_adjoint_matches_oracle(torch, pkg, name):
     from oracle.tangent import rhs_adjoint
     case = make(name, 0.01)
@@ -94,7 +94,7 @@ def test_rhs_adjoint_matches_oracle(torch, pkg, name):
 
 
 def test_rhs_adjoint_is_bitwise_reproducible(torch, pkg):
-    case = make("cfg1")
+    case = make("tiny4")
     g = gpu_ctx(pkg, case)
     q, lam = dev(torch, case.state(5, vel=5.0)), dev(torch, case.state(6))
     a = g.rhs_adjoint(q, lam)
@@ -102,7 +102,7 @@ def test_rhs_adjoint_is_bitwise_reproducible(torch, pkg):
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged", "n2", "n7"])
+@pytest.mark.parametrize("name", ["tiny4", "ragged", "n2", "n7"])
 def test_transposed_column_solve_matches_oracle(torch, pkg, name):
     from oracle.column import lu_nopivot_banded
     from oracle.tangent import lu_solve_transposed_banded
@@ -123,7 +123,7 @@ def test_transposed_column_solve_matches_oracle(torch, pkg, name):
 
 
 @pytest.mark.parametrize("stage", [2, 3])
-@pytest.mark.parametrize("name", ["cfg1", "ragged", "n7"])
+@pytest.mark.parametrize("name", ["tiny4", "ragged", "n7"])
 def test_stage_adjoint_matches_oracle(torch, pkg, name, stage):
     from oracle.ark2 import HEVI
     from oracle.tangent import ColumnMap, stage_adjoint
@@ -164,7 +164,7 @@ def test_stage_adjoint_dot_product(torch, pkg, stage):
     assert abs(lhs - rhs) <= DOT_TOL * abs(lhs)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged"])
+@pytest.mark.parametrize("name", ["tiny4", "ragged"])
 def test_step_tlm_and_adjoint_match_oracle(torch, pkg, name):
     from oracle.ark2 import HEVI
     from oracle.tangent import step_adjoint, step_tlm
@@ -201,8 +201,8 @@ def test_gradient_matches_oracle_over_several_steps(torch, pkg):
 
 # ---- the differentiation workload ----------------------------------------------------------
 @pytest.fixture(scope="module")
-def c5(torch, pkg):
-    case = config5()
+def dw(torch, pkg):
+    case = diff_workload()
     g = gpu_ctx(pkg, case, case.dt_for(15.0))
     q0 = dev(torch, case.state(11, vel=5.0))
     target = dev(torch, case.state(12)[4])
@@ -214,9 +214,9 @@ def _misfit(torch, g, q, target, nsteps=20, every=5):
     return 0.5 * ((qT[4] - target) ** 2).sum()
 
 
-def test_c5_rhs_tlm_and_adjoint_match_oracle(torch, pkg, c5):
+def test_diff_workload_rhs_tlm_and_adjoint_match_oracle(torch, pkg, dw):
     from oracle.tangent import rhs_adjoint, rhs_tlm
-    case, g, q0, _ = c5
+    case, g, q0, _ = dw
     q = host(q0)
     dq, lam = case.state(13, vel=3.0), case.state(14, vel=2.0)
     assert rel_l2(host(g.rhs_tlm(q0, dev(torch, dq))), rhs_tlm(case.mesh, case.col, q, dq)).max() <= TOL
@@ -224,8 +224,8 @@ def test_c5_rhs_tlm_and_adjoint_match_oracle(torch, pkg, c5):
                   rhs_adjoint(case.mesh, case.col, q, lam)).max() <= TOL
 
 
-def test_c5_dot_product_of_the_run(torch, pkg, c5):
-    case, g, q0, _ = c5
+def test_diff_workload_dot_product_of_the_run(torch, pkg, dw):
+    case, g, q0, _ = dw
     dq = dev(torch, case.state(15, vel=3.0))
     lam = dev(torch, case.state(16, vel=2.0))
     _, dqT = g.step_imex1d_tlm(q0, dq, 20)
@@ -237,8 +237,8 @@ def test_c5_dot_product_of_the_run(torch, pkg, c5):
     assert g.status() == pkg.NUMA_OK
 
 
-def test_c5_gradient_matches_centred_differences(torch, pkg, c5):
-    case, g, q0, target = c5
+def test_diff_workload_gradient_matches_centred_differences(torch, pkg, dw):
+    case, g, q0, target = dw
     x = q0.clone().requires_grad_(True)
     J = _misfit(torch, g, x, target)
     J.backward()
@@ -253,8 +253,8 @@ def test_c5_gradient_matches_centred_differences(torch, pkg, c5):
             assert abs(fd - ad) <= 1e-6 * abs(ad)
 
 
-def test_c5_gradient_does_not_depend_on_the_checkpoint_interval(torch, pkg, c5):
-    case, g, q0, target = c5
+def test_diff_workload_gradient_does_not_depend_on_the_checkpoint_interval(torch, pkg, dw):
+    case, g, q0, target = dw
     grads = []
     for every in (1, 5, 7, 20):
         x = q0.clone().requires_grad_(True)
@@ -264,9 +264,9 @@ def test_c5_gradient_does_not_depend_on_the_checkpoint_interval(torch, pkg, c5):
         assert torch.equal(gr, grads[0])
 
 
-def test_forward_mode_matches_the_tlm_kernels(torch, pkg, c5):
+def test_forward_mode_matches_the_tlm_kernels(torch, pkg, dw):
     import torch.autograd.forward_ad as fwAD
-    case, g, q0, _ = c5
+    case, g, q0, _ = dw
     dq = dev(torch, case.state(19, vel=3.0))
     with fwAD.dual_level():
         out = g.rhs_autograd(fwAD.make_dual(q0, dq))
@@ -277,8 +277,8 @@ def test_forward_mode_matches_the_tlm_kernels(torch, pkg, c5):
     assert torch.equal(t_run, g.step_imex1d_tlm(q0, dq, 3)[1])
 
 
-def test_rhs_autograd_backward_is_the_adjoint(torch, pkg, c5):
-    case, g, q0, _ = c5
+def test_rhs_autograd_backward_is_the_adjoint(torch, pkg, dw):
+    case, g, q0, _ = dw
     lam = dev(torch, case.state(21, vel=2.0))
     x = q0.clone().requires_grad_(True)
     (g.rhs_autograd(x) * lam).sum().backward()
@@ -286,7 +286,7 @@ def test_rhs_autograd_backward_is_the_adjoint(torch, pkg, c5):
 
 
 def test_differentiation_needs_an_fp64_context(torch, pkg):
-    case = make("cfg1")
+    case = make("tiny4")
     nex, ney, nez, Lx, Ly, Lz, N = case.args
     g = pkg.Numa(nex, ney, nez, Lx, Ly, Lz, N, case.dt_for(15.0), precision="mixed")
     q = dev(torch, case.state(1))

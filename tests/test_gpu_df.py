@@ -24,7 +24,7 @@ def dev(a):
 
 
 CASES = {
-    "cfg1": (4, 4, 4, 4, 10e3, 10e3, 10e3),
+    "tiny4": (4, 4, 4, 4, 10e3, 10e3, 10e3),
     "ragged": (3, 5, 2, 3, 7e3, 9e3, 4e3),
     "n2": (5, 2, 3, 2, 6e3, 3e3, 5e3),
     "n7": (2, 3, 2, 7, 8e3, 9e3, 6e3),
@@ -44,7 +44,7 @@ def test_df_rhs_matches_oracle(name):
     assert np.all(e <= RHS_TOL), e
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged", "n7"])
+@pytest.mark.parametrize("name", ["tiny4", "ragged", "n7"])
 def test_df_rhs_of_a_balanced_state(name):
     """Bubble balance: P' = 0 in exact arithmetic, so the horizontal tendencies are the
     derivatives of rounding noise (no relative error is defined for them); they must be
@@ -73,7 +73,7 @@ def test_df_run_matches_oracle(C, L):
 
 def test_df_rk35_run_matches_oracle():
     from oracle import rk35
-    case = Case(*CASES["cfg1"])
+    case = Case(*CASES["tiny4"])
     dt = case.dt_for(1.0)
     q0 = case.state(5, kind="balanced")
     ref = rk35.Explicit(case.mesh, case.col).step(q0, dt, 10)

@@ -33,7 +33,7 @@ def gpu_ctx(pkg, case, dt=0.0):
 
 
 CASES = {
-    "cfg1": (4, 4, 4, 4, 10e3, 10e3, 10e3),          # the tiny configuration
+    "tiny4": (4, 4, 4, 4, 10e3, 10e3, 10e3),          # the tiny configuration
     "ragged": (3, 5, 2, 3, 7e3, 9e3, 4e3),
     "n2": (5, 2, 3, 2, 6e3, 3e3, 5e3),
     "n7": (2, 3, 2, 7, 8e3, 9e3, 6e3),
@@ -48,7 +48,7 @@ def make(name, n_bv=0.0):
     return Case(nex, ney, nez, N, Lx, Ly, Lz, n_bv)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged", "n2", "n7", "single"])
+@pytest.mark.parametrize("name", ["tiny4", "ragged", "n2", "n7", "single"])
 def test_connectivity_bit_exact(pkg, name):
     case = make(name)
     g = gpu_ctx(pkg, case)
@@ -70,7 +70,7 @@ def test_connectivity_bit_exact(pkg, name):
 
 @pytest.mark.parametrize("n_bv", [0.0, 0.015])
 def test_reference_levels(pkg, n_bv):
-    case = make("cfg1", n_bv)
+    case = make("tiny4", n_bv)
     g = gpu_ctx(pkg, case)
     lev = g.reference_levels()
     c = case.col
@@ -92,14 +92,14 @@ def test_rhs_parity(pkg, torch, name):
 
 
 def test_rhs_rest_state_is_exactly_zero(pkg, torch):
-    case = make("cfg1")
+    case = make("tiny4")
     g = gpu_ctx(pkg, case)
     r = g.rhs_explicit(torch.zeros(5, case.mesh.nnode, dtype=torch.float64, device="cuda"))
     assert torch.count_nonzero(r).item() == 0
 
 
 @pytest.mark.parametrize("C", [1, 15, 150])
-@pytest.mark.parametrize("name,n_bv", [("cfg1", 0.0), ("ragged", 0.02), ("n7", 0.0), ("n1", 0.0)])
+@pytest.mark.parametrize("name,n_bv", [("tiny4", 0.0), ("ragged", 0.02), ("n7", 0.0), ("n1", 0.0)])
 def test_factors_and_solve(pkg, torch, name, n_bv, C):
     from oracle.column import lu_nopivot_banded, lu_solve_banded
     case = make(name, n_bv)
@@ -165,7 +165,7 @@ def test_bulk_copy_solve_equals_register_solve(mesh):
 def test_bulk_copy_solve_unaligned_buffers(pkg, torch):
     """Buffers that are 8- but not 16-byte aligned take plain loads and stores for the
     right-hand side and the solution; the result bits do not change."""
-    case = make("cfg1")
+    case = make("tiny4")
     g = gpu_ctx(pkg, case, case.dt_for(15))
     nn = case.mesh.ncol * case.mesh.M
     b = torch.randn(nn, dtype=torch.float64, device="cuda",
@@ -232,8 +232,8 @@ def test_imex_stages(pkg, torch, C):
 
 
 @pytest.mark.parametrize("label,dims,C,nsteps,n_bv", [
-    ("cfg1-C15-1step", (4, 4, 4, 4, 10e3, 10e3, 10e3), 15, 1, 0.0),
-    ("cfg1-C1-10steps", (4, 4, 4, 4, 10e3, 10e3, 10e3), 1, 10, 0.0),
+    ("tiny4-C15-1step", (4, 4, 4, 4, 10e3, 10e3, 10e3), 15, 1, 0.0),
+    ("tiny4-C1-10steps", (4, 4, 4, 4, 10e3, 10e3, 10e3), 1, 10, 0.0),
     ("wide-C15-10steps", (4, 4, 4, 4, 300e3, 300e3, 10e3), 15, 10, 0.0),
     ("wide-C150-10steps", (4, 4, 4, 4, 3000e3, 3000e3, 10e3), 150, 10, 0.0),
     ("wide-stratified-C15", (3, 4, 5, 4, 300e3, 400e3, 10e3), 15, 5, 0.012),
@@ -258,7 +258,7 @@ def test_imex_run_parity(pkg, torch, label, dims, C, nsteps, n_bv):
 
 def test_rk35_run_parity(pkg, torch):
     from oracle import rk35
-    case = make("cfg1")
+    case = make("tiny4")
     dt = case.dt_for(1.0)
     q0 = case.state(5, kind="balanced")
     ref = rk35.Explicit(case.mesh, case.col).step(q0, dt, 10)
@@ -294,7 +294,7 @@ def test_zero_steps_and_errors(pkg, torch):
 
 def test_host_buffer_driver(pkg, torch):
     from oracle import ark2
-    case = make("cfg1")
+    case = make("tiny4")
     dt = case.dt_for(15)
     q0 = case.state(9, kind="balanced")
     g = gpu_ctx(pkg, case, dt)
