@@ -33,7 +33,7 @@ def gpu_ctx(pkg, case, dt=0.0):
 
 
 CASES = {
-    "tiny4": (4, 4, 4, 4, 10e3, 10e3, 10e3),          # the tiny configuration
+    "tiny4": (4, 4, 4, 4, 10e3, 10e3, 10e3),          # 4 x 4 x 4 elements, N = 4, 10 km box
     "ragged": (3, 5, 2, 3, 7e3, 9e3, 4e3),
     "n2": (5, 2, 3, 2, 6e3, 3e3, 5e3),
     "n7": (2, 3, 2, 7, 8e3, 9e3, 6e3),
