@@ -14,7 +14,11 @@ timed step advances the same resident input state to a separate output buffer, s
 
 value = simulated seconds per wall-clock second of that step (dt / step time).  Measured
 alongside, outside the headline timed region: 1D-IMEX at C = 150 and the explicit RK35
-comparator at C = 1, and their sim-s/wall-s ratios.
+comparator at C = 1, and their sim-s/wall-s ratios; the per-kernel algorithmic bytes and
+HBM fractions (`kernels`), the FP64 roofline of the dominant kernel (`roofline`), the
+stand-alone column solve against the HBM roofline (`column_solve`), the end-to-end figure
+through host buffers (`e2e`), the accuracy of the C = 15 and C = 150 runs against RK35 at
+C = 1 (`accuracy_vs_explicit_c1`), and one entry per form and variant.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
