@@ -439,7 +439,11 @@ int numa_batch_reference_levels(const numa_batch* b, int member, double* host_ou
 const char* numa_batch_last_error(const numa_batch* b);
 
 /* Size of the device scratch array used by numa_rhs_explicit_static.  Every GPU that loads
- * the library holds an array of this size until the process exits. */
+ * the library's device code holds an array of this size until the process exits.  With
+ * CUDA's default lazy module loading the array is reserved when the module is first used on
+ * a device, which can be the first call of numa_rhs_explicit_static: a process whose other
+ * allocator is about to reserve most of the device memory should make one call (a warm-up)
+ * first, or that first call can fail with NUMA_ERR_CUDA for lack of memory. */
 #define NUMA_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 
 /* numa_rhs_explicit without any allocation.  The paper has no counterpart: this entry point
@@ -447,18 +451,22 @@ const char* numa_batch_last_error(const numa_batch* b);
  * example a latency-bound loop in which cudaMalloc/cudaFree would synchronise the device,
  * or a process whose device memory is already reserved by another allocator (a caching
  * allocator holding most of the GPU).  It takes no context: the mesh, the polynomial order
- * and the stream are passed directly, the host builds the LGL and reference tables in
- * static host buffers, and the device side keeps the equation-of-state pre-pass (nnode
- * doubles) and the per-level tables in one file-scope scratch array of
- * NUMA_STATIC_SCRATCH_BYTES (64 MiB: meshes up to 8,388,608 - 10 M - (2N+1) M nodes and
- * M <= 1024 levels; larger problems return NUMA_ERR_SCRATCH before any device work).
- * q, rhs: device SoA arrays of 5*nnode doubles, as for numa_rhs_explicit, which this call
- * matches to rounding (same kernels).  The first call on each device looks up the
- * scratch array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  Every call overwrites the parts of the
- * scratch it reads, so nothing has to start at zero, but all calls share the one array:
- * calls that overlap on the GPU (different streams, or different host threads without
- * ordering) race on it.  Calls no cudaMalloc, cudaFree or other allocating routine. */
+ * and the stream are passed directly.  The host builds the LGL and reference tables with
+ * the same code as numa_init, so the result equals numa_rhs_explicit's bit for bit; the
+ * tables reach the device inside kernel launch parameters, and the device side keeps the
+ * equation-of-state pre-pass (nnode doubles) and the per-level tables in one file-scope
+ * scratch array of NUMA_STATIC_SCRATCH_BYTES (64 MiB: meshes up to
+ * 8,388,608 - 10 M - (2N+1) M nodes and M <= 1024 levels; larger problems return
+ * NUMA_ERR_SCRATCH before any device work).
+ * q, rhs: device SoA arrays of 5*nnode doubles, as for numa_rhs_explicit.  The first call
+ * on each device looks up the scratch array's device address (cudaGetSymbolAddress) with
+ * that device current and keeps it for the life of the process; make that first call before
+ * any stream capture.  A device reset (cudaDeviceReset) can move the array, so this entry
+ * point must not be called on a device after a reset in the same process.  Every call
+ * overwrites the parts of the scratch it reads, so nothing has to start at zero, but all
+ * calls share the one array: calls that overlap on the GPU (different streams, or different
+ * host threads without ordering) race on it.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine. */
 int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const double* q, double* rhs,
                              void* stream);
 

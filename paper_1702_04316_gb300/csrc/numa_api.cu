@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <initializer_list>
 #include <string>
 #include <vector>
@@ -218,7 +219,7 @@ void lgl_host(int N, double* x, double* w, double* D) {
     x[N - j] = s;
   }
   if (N % 2 == 0) x[N / 2] = 0.0;
-  std::vector<double> PNv(Nq);
+  double PNv[NUMA_MAXNQ];                // no heap: numa_rhs_explicit_static calls this too
   for (int j = 0; j < Nq; ++j) {
     double PN, PNm1;
     legendre(N, x[j], PN, PNm1);
@@ -314,61 +315,71 @@ void free_all(numa_ctx* c) {
 }
 
 // Host reference state and the column derivative (Sec. "Equation Set2NC",
-// Sec. "Direct stiffness summation").
-void build_levels(numa_ctx* c, const double* xi, const double* w, const double* D, double dz) {
-  const int N = c->G.N, M = c->G.M, nez = c->G.nez, Nq = N + 1, W = 2 * N + 1;
-  c->z.assign(M, 0.0);
-  for (int ez = 0; ez < nez; ++ez)
-    for (int k = 0; k < Nq; ++k) c->z[ez * N + k] = ez * dz + (1.0 + xi[k]) * dz / 2.0;
+// Sec. "Direct stiffness summation"), written into caller-provided arrays of M levels (the
+// band: M x (2N + 1)) without heap storage.  The one builder of these tables: contexts and
+// numa_rhs_explicit_static both call it, so their tables are the same bits.
+void ref_tables_host(int N, int nez, double dz, const double* xi, const double* w,
+                     const double* D, double theta_s, double n_bv, double* z, double* theta0,
+                     double* rho0, double* P0, double* G0, double* H0, double* dzband,
+                     double* drho0, double* dtheta0, double* F0z) {
+  const int M = nez * N + 1, Nq = N + 1, W = 2 * N + 1;
   const double g = NUMA_GRAV, cp = NUMA_CP, R = NUMA_RGAS, gam = NUMA_GAMMA;
-  c->theta0.resize(M); c->rho0.resize(M); c->P0.resize(M); c->G0.resize(M); c->H0.resize(M);
   for (int m = 0; m < M; ++m) {
-    const double zz = c->z[m];
+    // an interface node takes the upper element's coordinate expression
+    const int ez = (m == M - 1) ? nez - 1 : m / N, k = m - ez * N;
+    const double zz = ez * dz + (1.0 + xi[k]) * dz / 2.0;
     double th, pi;
-    if (c->n_bv == 0.0) {
-      th = c->theta_s;
-      pi = 1.0 - g * zz / (cp * c->theta_s);
+    if (n_bv == 0.0) {
+      th = theta_s;
+      pi = 1.0 - g * zz / (cp * theta_s);
     } else {
-      const double s = c->n_bv * c->n_bv / g;
-      th = c->theta_s * std::exp(s * zz);
-      pi = 1.0 + g * g / (cp * c->theta_s * c->n_bv * c->n_bv) * (std::exp(-s * zz) - 1.0);
+      const double s = n_bv * n_bv / g;
+      th = theta_s * std::exp(s * zz);
+      pi = 1.0 + g * g / (cp * theta_s * n_bv * n_bv) * (std::exp(-s * zz) - 1.0);
     }
-    const double P0 = NUMA_P00 * std::pow(pi, cp / R);
-    c->theta0[m] = th;
-    c->P0[m] = P0;
-    c->rho0[m] = P0 / (R * pi * th);
-    c->G0[m] = gam * P0 / c->rho0[m];
-    c->H0[m] = gam * P0 / th;
+    z[m] = zz;
+    P0[m] = NUMA_P00 * std::pow(pi, cp / R);
+    theta0[m] = th;
+    rho0[m] = P0[m] / (R * pi * th);
+    G0[m] = gam * P0[m] / rho0[m];
+    H0[m] = gam * P0[m] / th;
   }
   // DSS'd vertical derivative: element ez gives node m = ez*N + k the row (2/dz) D[k,:]
-  // weighted by w_k; rows are divided by the summed weights.
-  std::vector<double> num((size_t)M * W, 0.0), den(M, 0.0);
-  for (int ez = 0; ez < nez; ++ez)
-    for (int k = 0; k < Nq; ++k) {
-      const int m = ez * N + k;
-      for (int n = 0; n < Nq; ++n) {
-        const int j = ez * N + n;
-        num[(size_t)m * W + (j - m + N)] += w[k] * D[k * Nq + n] * (2.0 / dz);
-      }
-      den[m] += w[k];
-    }
-  c->dzband.assign((size_t)M * W, 0.0);
-  for (int m = 0; m < M; ++m)
-    for (int b = 0; b < W; ++b) c->dzband[(size_t)m * W + b] = num[(size_t)m * W + b] / den[m];
-  c->drho0.assign(M, 0.0);
-  c->dtheta0.assign(M, 0.0);
-  c->F0z.resize(M);
+  // weighted by w_k; the summed rows (lower element first) are divided by the summed weights.
   for (int m = 0; m < M; ++m) {
+    double* row = dzband + (size_t)m * W;
+    for (int b = 0; b < W; ++b) row[b] = 0.0;
+    double den = 0.0;
+    for (int ez = 0; ez < nez; ++ez) {
+      const int k = m - ez * N;
+      if (k < 0 || k > N) continue;
+      for (int n = 0; n < Nq; ++n) row[ez * N + n - m + N] += w[k] * D[k * Nq + n] * (2.0 / dz);
+      den += w[k];
+    }
+    for (int b = 0; b < W; ++b) row[b] /= den;
+  }
+  for (int m = 0; m < M; ++m) {
+    drho0[m] = dtheta0[m] = 0.0;
     for (int b = 0; b < W; ++b) {
       const int j = m - N + b;
       if (j < 0 || j >= M) continue;
       // D_z annihilates constants: taking the surface value out first is exact and gives
       // an isentropic theta0 a gradient of exactly zero.
-      c->drho0[m] += c->dzband[(size_t)m * W + b] * (c->rho0[j] - c->rho0[0]);
-      c->dtheta0[m] += c->dzband[(size_t)m * W + b] * (c->theta0[j] - c->theta0[0]);
+      drho0[m] += dzband[(size_t)m * W + b] * (rho0[j] - rho0[0]);
+      dtheta0[m] += dzband[(size_t)m * W + b] * (theta0[j] - theta0[0]);
     }
-    c->F0z[m] = c->G0[m] * c->drho0[m] + c->H0[m] * c->dtheta0[m];
+    F0z[m] = G0[m] * drho0[m] + H0[m] * dtheta0[m];
   }
+}
+
+void build_levels(numa_ctx* c, const double* xi, const double* w, const double* D, double dz) {
+  const int N = c->G.N, M = c->G.M, W = 2 * N + 1;
+  c->z.resize(M); c->theta0.resize(M); c->rho0.resize(M); c->P0.resize(M); c->G0.resize(M);
+  c->H0.resize(M); c->dzband.resize((size_t)M * W); c->drho0.resize(M); c->dtheta0.resize(M);
+  c->F0z.resize(M);
+  ref_tables_host(N, c->G.nez, dz, xi, w, D, c->theta_s, c->n_bv, c->z.data(), c->theta0.data(),
+                  c->rho0.data(), c->P0.data(), c->G0.data(), c->H0.data(), c->dzband.data(),
+                  c->drho0.data(), c->dtheta0.data(), c->F0z.data());
 }
 
 int upload_levels(numa_ctx* c) {
@@ -1348,8 +1359,10 @@ void numa_ark2_tableau(double* a, double* at, double* b) {
 // loop where cudaMalloc/cudaFree would synchronise the device, or a process whose device
 // memory is already reserved by another allocator, such as a caching allocator holding
 // most of the GPU) use numa_rhs_explicit_static.  It needs no context: the host builds the
-// LGL and reference tables into static host buffers, and the device side uses one
-// file-scope scratch array for the equation-of-state pre-pass and the per-level tables.
+// LGL and reference tables with the contexts' own builders (lgl_host, ref_tables_host)
+// into a static host buffer, and the device side uses one file-scope scratch array for
+// the equation-of-state pre-pass and the per-level tables.  The tables reach the scratch
+// as kernel parameters (k_static_tables), so no host buffer is read once the call returns.
 #include <mutex>
 
 namespace {
@@ -1362,7 +1375,20 @@ static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
 std::mutex g_static_mutex;
 double* g_static_addr[256] = {nullptr};            // device address per device ordinal
-double g_static_host[kStaticMaxLevels * (10 + 2 * NUMA_MAXN + 1)];
+double g_static_host[kStaticMaxLevels * (11 + 2 * NUMA_MAXN + 1)];
+
+// One piece of the per-level tables, carried by value in the launch parameters (16 KB, within
+// the 32 KB parameter space of sm_70 and later).
+constexpr int kTabChunk = 2000;
+struct TabChunk {
+  double* dst;
+  int n;
+  double v[kTabChunk];
+};
+
+__global__ void k_static_tables(const __grid_constant__ TabChunk c) {
+  for (int i = threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = c.v[i];
+}
 
 }  // namespace
 
@@ -1395,102 +1421,41 @@ extern "C" int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const
   }
   double* scratch = g_static_addr[dev];
 
-  // LGL nodes/weights/derivative matrix without heap storage (same Newton iteration as
-  // the context set-up).
-  const int Nq = N + 1;
-  double xi[NUMA_MAXNQ], w[NUMA_MAXNQ], D[NUMA_MAXNQ * NUMA_MAXNQ], PN[NUMA_MAXNQ];
-  xi[0] = -1.0;
-  xi[N] = 1.0;
-  for (int j = 1; j < N; ++j) {
-    double x = -std::cos(M_PI * j / N);
-    for (int it = 0; it < 100; ++it) {
-      double a, b;
-      legendre(N, x, a, b);
-      const double dx = (x * a - b) / ((N + 1.0) * a);
-      x -= dx;
-      if (std::fabs(dx) < 1e-16) break;
-    }
-    xi[j] = x;
-  }
-  for (int j = 0; j < Nq / 2; ++j) {
-    const double s = 0.5 * (xi[N - j] - xi[j]);
-    xi[j] = -s;
-    xi[N - j] = s;
-  }
-  if (N % 2 == 0) xi[N / 2] = 0.0;
-  for (int j = 0; j < Nq; ++j) {
-    double b;
-    legendre(N, xi[j], PN[j], b);
-    w[j] = 2.0 / (N * (N + 1.0) * PN[j] * PN[j]);
-  }
-  for (int i = 0; i < Nq; ++i)
-    for (int j = 0; j < Nq; ++j) D[i * Nq + j] = (i == j) ? 0.0 : PN[i] / (PN[j] * (xi[i] - xi[j]));
-  D[0] = -N * (N + 1) / 4.0;
-  D[N * Nq + N] = N * (N + 1) / 4.0;
+  double xi[NUMA_MAXNQ], w[NUMA_MAXNQ], D[NUMA_MAXNQ * NUMA_MAXNQ];
+  lgl_host(N, xi, w, D);
   Coef3 C;
   set_axis(C.x, N, w, D, mesh->Lx / mesh->nex);
   set_axis(C.y, N, w, D, mesh->Ly / mesh->ney);
   set_axis(C.z, N, w, D, mesh->Lz / mesh->nez);
 
-  // per-level tables in the static host buffer: rho0, 1/rho0, theta0, 1/theta0, P0, G0, H0,
-  // d(rho0)/dz, d(theta0)/dz, F0z (M each), then the column derivative band [M][W]
+  // the per-level tables in the order of RefLev: rho0, 1/rho0, theta0, 1/theta0, P0, G0, H0,
+  // d(rho0)/dz, d(theta0)/dz, F0z (M each), the column derivative band [M][W]; z last (host
+  // only)
   double* h = g_static_host;
-  double* rho0 = h;       double* irho0 = h + M;   double* th0 = h + 2 * M;
-  double* ith0 = h + 3 * M; double* P0 = h + 4 * M; double* G0 = h + 5 * M;
-  double* H0 = h + 6 * M;  double* drho = h + 7 * M; double* dth = h + 8 * M;
-  double* F0z = h + 9 * M; double* band = h + 10 * M;
-  const double dz = mesh->Lz / mesh->nez, g = NUMA_GRAV, cp = NUMA_CP, Rg = NUMA_RGAS;
-  const double theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
+  double *rho0 = h, *irho0 = h + M, *th0 = h + 2 * M, *ith0 = h + 3 * M, *P0 = h + 4 * M;
+  double *G0 = h + 5 * M, *H0 = h + 6 * M, *drho = h + 7 * M, *dth = h + 8 * M, *F0z = h + 9 * M;
+  double* band = h + 10 * M;
+  double* z = band + (size_t)M * W;
+  ref_tables_host(N, mesh->nez, mesh->Lz / mesh->nez, xi, w, D,
+                  mesh->theta_s > 0 ? mesh->theta_s : 300.0, mesh->n_bv, z, th0, rho0, P0, G0,
+                  H0, band, drho, dth, F0z);
   for (int m = 0; m < M; ++m) {
-    const int ez = (m == M - 1) ? mesh->nez - 1 : m / N, k = m - ez * N;
-    const double z = ez * dz + (1.0 + xi[k]) * dz / 2.0;
-    double th, pi;
-    if (mesh->n_bv == 0.0) {
-      th = theta_s;
-      pi = 1.0 - g * z / (cp * theta_s);
-    } else {
-      const double s = mesh->n_bv * mesh->n_bv / g;
-      th = theta_s * std::exp(s * z);
-      pi = 1.0 + g * g / (cp * theta_s * mesh->n_bv * mesh->n_bv) * (std::exp(-s * z) - 1.0);
-    }
-    P0[m] = NUMA_P00 * std::pow(pi, cp / Rg);
-    th0[m] = th;
-    rho0[m] = P0[m] / (Rg * pi * th);
     irho0[m] = 1.0 / rho0[m];
-    ith0[m] = 1.0 / th;
-    G0[m] = NUMA_GAMMA * P0[m] / rho0[m];
-    H0[m] = NUMA_GAMMA * P0[m] / th;
-    for (int b = 0; b < W; ++b) band[(size_t)m * W + b] = 0.0;
-  }
-  // DSS'd column derivative: weighted rows of the elements sharing each node
-  for (int m = 0; m < M; ++m) {
-    double den = 0.0;
-    for (int ez = 0; ez < mesh->nez; ++ez) {
-      const int k = m - ez * N;
-      if (k < 0 || k > N) continue;
-      for (int n = 0; n < Nq; ++n)
-        band[(size_t)m * W + (ez * N + n - m + N)] += w[k] * D[k * Nq + n] * (2.0 / dz);
-      den += w[k];
-    }
-    for (int b = 0; b < W; ++b) band[(size_t)m * W + b] /= den;
-  }
-  for (int m = 0; m < M; ++m) {
-    drho[m] = dth[m] = 0.0;
-    for (int b = 0; b < W; ++b) {
-      const int j = m - N + b;
-      if (j < 0 || j >= M) continue;
-      drho[m] += band[(size_t)m * W + b] * (rho0[j] - rho0[0]);
-      dth[m] += band[(size_t)m * W + b] * (th0[j] - th0[0]);
-    }
-    F0z[m] = G0[m] * drho[m] + H0[m] * dth[m];
+    ith0[m] = 1.0 / th0[m];
   }
 
   cudaStream_t s = (cudaStream_t)stream;
   double* dPp = scratch;                 // nnode doubles, written by the pre-pass
   double* dtab = scratch + G.nnode;      // the tables above
-  const size_t tab_bytes = ((size_t)10 * M + (size_t)M * W) * sizeof(double);
-  if (cudaMemcpyAsync(dtab, h, tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return NUMA_ERR_CUDA;
+  const long long ntab = 10LL * M + (long long)M * W;
+  for (long long o = 0; o < ntab; o += kTabChunk) {
+    TabChunk ch;
+    ch.dst = dtab + o;
+    ch.n = (int)std::min<long long>(kTabChunk, ntab - o);
+    std::memcpy(ch.v, h + o, sizeof(double) * ch.n);
+    k_static_tables<<<1, 256, 0, s>>>(ch);
+    if (cudaGetLastError() != cudaSuccess) return NUMA_ERR_CUDA;
+  }
   const RefLev R{dtab, dtab + M, dtab + 2 * M, dtab + 3 * M, dtab + 4 * M, dtab + 5 * M,
                  dtab + 6 * M, dtab + 7 * M, dtab + 8 * M, dtab + 9 * M, dtab + 10 * M};
   RhsEpilogue ep{};

@@ -1,8 +1,12 @@
 """numa_rhs_explicit_static: the right-hand side for callers that must not allocate device
 memory at the point of the call (a latency-bound loop where cudaMalloc would synchronise
 the device, or a process whose memory another allocator already holds).  It keeps its
-scratch in a static device array; checked here against numa_rhs_explicit on two calls in
-a row (the second with a different state, so stale scratch contents would show).
+scratch in a static device array.  Checked here:
+* bit for bit against numa_rhs_explicit (same kernels, same tables) on two calls in a row,
+  the second with a different state so that stale scratch contents would show, and against
+  the FP64 oracle at the right-hand-side bar;
+* on a stream other than the default one;
+* that a call after a warm-up changes the device's free memory by nothing.
 
 This file is collected last so that a run stopping at the first failure has already run
 every other test."""
@@ -13,25 +17,66 @@ from helpers import Case, rel_l2
 
 pytestmark = pytest.mark.gpu
 
+CASES = [((4, 4, 4, 4, 10e3, 10e3, 10e3), 0.0), ((3, 5, 2, 3, 7e3, 9e3, 4e3), 0.01)]
 
-@pytest.mark.parametrize("dims,n_bv", [((4, 4, 4, 4, 10e3, 10e3, 10e3), 0.0),
-                                        ((3, 5, 2, 3, 7e3, 9e3, 4e3), 0.01)])
+
+@pytest.mark.parametrize("dims,n_bv", CASES)
 def test_static_rhs_matches_context_rhs_twice(dims, n_bv):
     import torch
     import paper_1702_04316_gb300 as pkg
+    from oracle.rhs import rhs as oracle_rhs
     nex, ney, nez, N, Lx, Ly, Lz = dims
     case = Case(nex, ney, nez, N, Lx, Ly, Lz, n_bv)
     g = pkg.Numa(nex, ney, nez, Lx, Ly, Lz, N, 0.0, 300.0, n_bv)
     for seed in (11, 12):
-        q = torch.from_numpy(case.state(seed)).cuda()
+        qh = case.state(seed)
+        q = torch.from_numpy(qh).cuda()
         ref = g.rhs_explicit(q)
         out = torch.full_like(q, float("nan"))
         rc = pkg.rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out, 300.0, n_bv)
         assert rc == pkg.NUMA_OK
         torch.cuda.synchronize()
-        e = rel_l2(out.cpu().numpy(), ref.cpu().numpy())
+        assert torch.equal(out, ref), seed
+        e = rel_l2(out.cpu().numpy(), oracle_rhs(case.mesh, case.col, qh))
         assert np.all(e <= 1e-11), (seed, e)
     g.close()
+
+
+def test_static_rhs_on_a_side_stream():
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    nex, ney, nez, N, Lx, Ly, Lz = CASES[0][0]
+    case = Case(nex, ney, nez, N, Lx, Ly, Lz)
+    g = pkg.Numa(nex, ney, nez, Lx, Ly, Lz, N, 0.0)
+    side = torch.cuda.Stream()
+    for seed in (21, 22):
+        q = torch.from_numpy(case.state(seed)).cuda()
+        ref = g.rhs_explicit(q)
+        out = torch.full_like(q, float("nan"))
+        side.wait_stream(torch.cuda.current_stream())
+        rc = pkg.rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out, stream=side)
+        assert rc == pkg.NUMA_OK
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), seed
+    g.close()
+
+
+def test_static_rhs_allocates_nothing():
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    nex, ney, nez, N, Lx, Ly, Lz = CASES[1][0]
+    case = Case(nex, ney, nez, N, Lx, Ly, Lz)
+    q = torch.from_numpy(case.state(31)).cuda()
+    out = torch.empty_like(q)
+    # warm-up: loads the module (and with it the static array) on this device
+    assert pkg.rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out) == pkg.NUMA_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert pkg.rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out) == pkg.NUMA_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_static_rhs_rejects_problems_beyond_the_scratch():
