@@ -77,6 +77,44 @@ def test_full_step_sampled(setup):
         assert np.all(e <= 1e-9), (ex0, ey0, e)
 
 
+def test_full_step_c150_sampled(setup):
+    """The second Courant number the benchmark times: one ARK2 step at C = 150 (dt = 93.2 s;
+    its own factors) on the full mesh, 7 x 7 windows, margin 3."""
+    from oracle import ark2
+    from oracle.column import Column
+    s = setup
+    case = s["case"]
+    dt = case.dt_for(150.0)
+    g = s["pkg"].Numa(NEX, NEX, NEZ, L, L, LZ, N, dt)
+    out = g.step_imex1d(s["qg"], g.empty_state(), 1).cpu().numpy()
+    assert g.status() == s["pkg"].NUMA_OK
+    g.close()
+    for ex0, ey0 in WINDOWS:
+        sub, qs = window(case.mesh, s["q0"], ex0, ey0, W)
+        ref = ark2.HEVI(sub, Column(sub), dt).step(qs, 1)
+        gi, wi = window_nodes(case.mesh, ex0, ey0, W, 3)
+        e = rel_l2(out[:, gi], ref[:, wi])
+        assert np.all(e <= 1e-9), (ex0, ey0, e)
+
+
+def test_two_steps_sampled(setup):
+    """Two ARK2 steps at C = 15 in one call (the step-to-step hand-off: the final update of
+    step 1 feeds the P' pre-pass and the stages of step 2) on the full mesh: six RHS
+    evaluations, so an 11 x 11 window with margin 6, and one against the south-west
+    walls."""
+    from oracle import ark2
+    from oracle.column import Column
+    s = setup
+    case = s["case"]
+    out = s["g"].step_imex1d(s["qg"], s["g"].empty_state(), 2).cpu().numpy()
+    for ex0, ey0 in ((40, 40), (0, 0)):
+        sub, qs = window(case.mesh, s["q0"], ex0, ey0, 11)
+        ref = ark2.HEVI(sub, Column(sub), s["dt"]).step(qs, 2)
+        gi, wi = window_nodes(case.mesh, ex0, ey0, 11, 6)
+        e = rel_l2(out[:, gi], ref[:, wi])
+        assert np.all(e <= 1e-9), (ex0, ey0, e)
+
+
 def test_rk35_step_sampled(setup):
     """One RK35 step has five RHS evaluations: an 11 x 11 window, margin 5."""
     from oracle import rk35

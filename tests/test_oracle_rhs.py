@@ -149,3 +149,76 @@ def test_linearisation_matches_vertical_operator():
     Lr, Lw, Lt = col.L_V(q[0][0], q[3][0], q[4][0])
     for got, ref in ((R[0][7], Lr), (R[3][7], Lw), (R[4][7], Lt)):
         assert np.abs(got - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+def test_all_fields_nonzero_against_closed_forms():
+    """rho', u, v, w and theta' all nonzero together, each a polynomial of degree <= N = 4
+    along every axis.  Their LGL derivatives are then exact, so the continuity and theta'
+    tendencies have closed forms (u.grad rho', rho div u with rho = rho0 + rho', u.grad
+    theta').  P' is not a polynomial (equation of state over a z-dependent reference): its
+    gradient is a centred difference of the EOS, and the momentum tendencies
+    -(u.grad u + grad P' / rho + g rho' / rho z_hat) are checked to the spectral accuracy of
+    the mesh.  rho' is 1-8 % of rho0, so reading rho0 for rho anywhere (in rho div u, in
+    grad P' / rho or in the buoyancy) moves a tendency far outside these bounds; the test
+    checks that margin too."""
+    from oracle.reference import pressure, reference_profile
+    m, col = _setup(nex=8, ney=8, nez=6, L=(20e3, 20e3, 10e3))
+    X, Y, Z = _lattice(m)
+
+    def fields(X, Y, Z):
+        x, y, z = X / 1e4, Y / 1e4, Z / 1e4
+        rp = 0.02 * (1.0 + 0.3 * x - 0.2 * y + 0.1 * z + 0.05 * x * y)
+        u = 1.0 + 0.5 * x - 0.3 * y * z + 0.2 * x * x
+        v = -0.4 + 0.7 * y + 0.1 * x * z
+        w = 0.3 * z - 0.2 * x * y + 0.05 * z * z
+        tp = 0.5 * (1.0 + 0.2 * x + 0.3 * y * z - 0.1 * z * z)
+        return rp, u, v, w, tp
+
+    rp, u, v, w, tp = fields(X, Y, Z)
+    x, y, z = X / 1e4, Y / 1e4, Z / 1e4
+    s = 1e-4
+    drx, dry, drz = 0.02 * (0.3 + 0.05 * y) * s, 0.02 * (-0.2 + 0.05 * x) * s, 0.002 * s
+    dudx, dudy, dudz = (0.5 + 0.4 * x) * s, (-0.3 * z) * s, (-0.3 * y) * s
+    dvdx, dvdy, dvdz = (0.1 * z) * s, 0.7 * s, (0.1 * x) * s
+    dwdx, dwdy, dwdz = (-0.2 * y) * s, (-0.2 * x) * s, (0.3 + 0.1 * z) * s
+    dtx, dty, dtz = 0.1 * s + 0 * x, 0.15 * z * s, 0.5 * (0.3 * y - 0.2 * z) * s
+    q = np.stack([rp, u, v, w, tp])
+    R = rhs(m, col, q)
+
+    rho0 = np.tile(col.rho0, m.ncol)
+    drho0 = np.tile(col.drho0, m.ncol)
+    dth0 = np.tile(col.dtheta0, m.ncol)
+    assert 0.005 < (rp / rho0).min() and (rp / rho0).max() < 0.1
+    rho = rho0 + rp
+    div = dudx + dvdy + dwdz
+    adv = lambda fx, fy, fz: u * fx + v * fy + w * fz
+    R_rho = -(adv(drx, dry, drz) + w * drho0 + rho * div)
+    R_th = -(adv(dtx, dty, dtz) + w * dth0)
+    np.testing.assert_allclose(R[0], R_rho, rtol=1e-9, atol=1e-16)
+    np.testing.assert_allclose(R[4], R_th, rtol=1e-9, atol=1e-16)
+    # the exact tendencies tell rho from rho0 in rho div u: by far more than the bound
+    assert np.abs(rp * div).max() > 1e3 * 1e-9 * np.abs(R_rho).max()
+
+    def Pp(X, Y, Z):
+        r = reference_profile(Z, 300.0)
+        a = fields(X, Y, Z)
+        return pressure(r["rho0"] + a[0], r["theta0"] + a[4]) - r["P0"]
+
+    h = 1.0
+    dPx = (Pp(X + h, Y, Z) - Pp(X - h, Y, Z)) / (2 * h)
+    dPy = (Pp(X, Y + h, Z) - Pp(X, Y - h, Z)) / (2 * h)
+    dPz = (Pp(X, Y, Z + h) - Pp(X, Y, Z - h)) / (2 * h)
+    mx, my, mz = wall_masks(m)
+    Ru = -(adv(dudx, dudy, dudz) + dPx / rho)
+    Rv = -(adv(dvdx, dvdy, dvdz) + dPy / rho)
+    Rw = -(adv(dwdx, dwdy, dwdz) + dPz / rho + GRAV * rp / rho)
+    tol = 2e-4
+    for got, ref, mask in ((R[1], Ru, mx), (R[2], Rv, my), (R[3], Rw, mz)):
+        scale = np.abs(ref[~mask]).max()
+        assert np.abs(got[~mask] - ref[~mask]).max() < tol * scale
+        assert np.all(got[mask] == 0.0)
+    # rho0 in place of rho in grad P' / rho and in the buoyancy would miss by > 5x the bound
+    Rw_wrong = -(adv(dwdx, dwdy, dwdz) + dPz / rho0 + GRAV * rp / rho0)
+    Ru_wrong = -(adv(dudx, dudy, dudz) + dPx / rho0)
+    assert np.abs((Rw_wrong - Rw)[~mz]).max() > 5 * tol * np.abs(Rw[~mz]).max()
+    assert np.abs((Ru_wrong - Ru)[~mx]).max() > 5 * tol * np.abs(Ru[~mx]).max()
