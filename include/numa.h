@@ -219,7 +219,7 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
  * and q(1) = q^n, column solve at lam = a~_ii dt, extraction, un-shift.  R: host array of
  * i-1 device pointers R(q(1)) .. R(q(i-1)); Q: host array of i-2 device pointers q(2) ..
  * q(i-1) (may be NULL for i = 2).  Device arrays 5*nnode doubles, SoA.  q_out must not
- * overlap an input.  FP64 Schur-form 1D-IMEX contexts only (NUMA_ERR_ARG otherwise);
+ * overlap an input (NUMA_ERR_ARG).  FP64 Schur-form 1D-IMEX contexts only (NUMA_ERR_ARG otherwise);
  * NUMA_ERR_NOT_FACTORED before numa_factor_columns.  The general form of numa_imex_stage
  * (the same kernel phases; it reads only the terms with nonzero coefficients), exposed so
  * that each stage of ARK3 - ARK5 can be checked on its own. */
@@ -229,7 +229,8 @@ int numa_imex_stage_s(numa_ctx* ctx, int stage, const double* qn, const double* 
 /* One fused 1D-IMEX stage i in {2, 3} (rows 2 and 3 of Table 1): explicit predictor,
  * Schur right-hand side (Algorithm 4), column solve, extraction of (rho', w, theta')
  * and the q~ recombination, producing the stage value q(i).  qn = q^n, R1 = R(q(1)),
- * R2 = R(q(2)) (stage 3 only), q2 = q(2) (stage 3 only; pass NULL for stage 2).
+ * R2 = R(q(2)) (stage 3 only), q2 = q(2) (stage 3 only; pass NULL for stage 2).  q_out
+ * must not overlap an input (NUMA_ERR_ARG): the kernel parks intermediate values in it.
  * Exposed so that each row of the step can be checked on its own. */
 int numa_imex_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1,
                     const double* R2, const double* q2, double* q_out);

@@ -252,13 +252,17 @@ __global__ void __launch_bounds__(32 * NUMA_SOLVE_MAXW) k_solve_bulk(
   const double* bb = b + col0 * M;
   double* xb = x + col0 * M;
 
-  // chunk q < M: row q of L; chunk q >= M: row 2M - 1 - q of U
+  // chunk q < M: row q of L; chunk q >= M: row 2M - 1 - q of U.  Only the slots inside the
+  // factors' envelope are copied (a prefix of the stored row: env_l(r) slots of L, the
+  // inverted pivot and env_u(r) slots of U, r = level mod N); the rest are exact zeros.
   auto issue = [&](int q) {
     const int s = q % S;
     const bool isL = q < M;
+    const int lev = isL ? q : nch - 1 - q;
     const double* src = isL ? Lb + (long long)q * HB * kFacBlk
-                            : Ub + (long long)(nch - 1 - q) * (HB + 1) * kFacBlk;
-    const unsigned bytes = isL ? LROW : UROW;
+                            : Ub + (long long)lev * (HB + 1) * kFacBlk;
+    const unsigned bytes = (unsigned)(isL ? env_l(N, lev % N) : env_u(N, lev % N) + 1) *
+                           kFacBlk * sizeof(double);
     // plant_timeout (tests only): the first row's barrier expects 16 bytes more than arrive
     mbar_arrive_expect_tx(bar0 + 8 * s, bytes + ((plant_timeout && q == 0) ? 16u : 0u));
     bulk_g2s(slot0 + s * UROW, src, bytes, bar0 + 8 * s);
@@ -311,42 +315,65 @@ __global__ void __launch_bounds__(32 * NUMA_SOLVE_MAXW) k_solve_bulk(
     ++q;
   };
 
-  // forward: y_i = w_0; w_k <- w_{k+1} - L(i+1+k, i) y_i
+  // forward: y_i = w_0; w_k <- w_{k+1} - L(i+1+k, i) y_i for the env_l(r) slots of the
+  // envelope, a shift beyond (levels in blocks of N: r is a compile-time constant)
   double w[HB];
 #pragma unroll
   for (int k = 0; k < HB; ++k) w[k] = (k < M) ? xc[k] : 0.0;
-  for (int i = 0; i < M; ++i) {
-    const double* sl = acquire();
-    if (!sl) return;
-    double l[HB];
+  bool ok = true;
+  for (int i0 = 0; i0 < M && ok; i0 += N) {
+    static_for<N>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      constexpr int nl = env_l(N, r);
+      const int i = i0 + r;
+      if (!ok || i >= M) return;
+      const double* sl = acquire();
+      if (!sl) {
+        ok = false;
+        return;
+      }
+      double l[HB];
 #pragma unroll
-    for (int k = 0; k < HB; ++k) l[k] = sl[k * kFacBlk];
-    release();
-    const double y = w[0];
-    const double nxt = (i + HB < M) ? xc[i + HB] : 0.0;
-    xc[i] = y;
+      for (int k = 0; k < nl; ++k) l[k] = sl[k * kFacBlk];
+      release();
+      const double y = w[0];
+      const double nxt = (i + HB < M) ? xc[i + HB] : 0.0;
+      xc[i] = y;
 #pragma unroll
-    for (int k = 0; k < HB - 1; ++k) w[k] = fma(-l[k], y, w[k + 1]);
-    w[HB - 1] = fma(-l[HB - 1], y, nxt);
+      for (int k = 0; k < HB - 1; ++k) w[k] = (k < nl) ? fma(-l[k], y, w[k + 1]) : w[k + 1];
+      w[HB - 1] = (HB - 1 < nl) ? fma(-l[HB - 1], y, nxt) : nxt;
+    });
   }
-  // backward: x_i = v_0 / U(i,i); v_k <- v_{k+1} - U(i-1-k, i) x_i
+  if (!ok) return;
+  // backward: x_i = v_0 / U(i,i); v_k <- v_{k+1} - U(i-1-k, i) x_i for the env_u(r) slots;
+  // level i = M - 1 - (t0 + s) with t0 a multiple of N and M - 1 = nez N, so r = (N - s) mod N
   double v[HB];
 #pragma unroll
   for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? xc[M - 1 - k] : 0.0;
-  for (int i = M - 1; i >= 0; --i) {
-    const double* su = acquire();
-    if (!su) return;
-    double u[HB + 1];
+  for (int t0 = 0; t0 < M && ok; t0 += N) {
+    static_for<N>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      constexpr int nu = env_u(N, (N - s) % N);
+      const int i = M - 1 - (t0 + s);
+      if (!ok || i < 0) return;
+      const double* su = acquire();
+      if (!su) {
+        ok = false;
+        return;
+      }
+      double u[HB + 1];
 #pragma unroll
-    for (int k = 0; k <= HB; ++k) u[k] = su[k * kFacBlk];
-    release();
-    const double xi = v[0] * u[0];
-    xc[i] = xi;
-    const double nxt = (i - HB >= 0) ? xc[i - HB] : 0.0;
+      for (int k = 0; k <= nu; ++k) u[k] = su[k * kFacBlk];
+      release();
+      const double xi = v[0] * u[0];
+      xc[i] = xi;
+      const double nxt = (i - HB >= 0) ? xc[i - HB] : 0.0;
 #pragma unroll
-    for (int k = 0; k < HB - 1; ++k) v[k] = fma(-u[k + 1], xi, v[k + 1]);
-    v[HB - 1] = fma(-u[HB], xi, nxt);
+      for (int k = 0; k < HB - 1; ++k) v[k] = (k < nu) ? fma(-u[k + 1], xi, v[k + 1]) : v[k + 1];
+      v[HB - 1] = (HB - 1 < nu) ? fma(-u[HB], xi, nxt) : nxt;
+    });
   }
+  if (!ok) return;
   __syncwarp();
   if (bulk_io) {
     if (lane == 0) {
@@ -361,8 +388,10 @@ __global__ void __launch_bounds__(32 * NUMA_SOLVE_MAXW) k_solve_bulk(
 }
 
 // NP previous stages (see stage_body); R3 and q3 are read only when NP = 3.
+// At most 64 registers a thread: four 256-thread CTAs per SM, which the shared memory of the
+// 64-column tile also allows.
 template <int N, int NP, bool MIXED, typename RT>
-__global__ void k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
+__global__ void __maxnreg__(64) k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
                         const RT* __restrict__ R2, const double* __restrict__ q2,
                         double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
                         StageTab tb, int iters, int T, const RT* __restrict__ R3,

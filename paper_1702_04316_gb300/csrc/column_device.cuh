@@ -5,6 +5,9 @@
 #include "numa_internal.cuh"
 #include "rhs_device.cuh"
 
+#include <type_traits>
+#include <utility>
+
 namespace numa_dev {
 
 
@@ -23,6 +26,26 @@ struct Band {
                    : U[((long long)j * (hb + 1) + (j - i)) * kFacBlk];
   }
 };
+
+// ---- nonzero envelope of the Schur-form factors -------------------------------------------
+// S(lam) has the sparsity of D_z^2.  A level inside an element (i = e N + r, 0 < r < N)
+// couples to the levels (e-1) N .. (e+2) N, an element interface (r = 0) to (e-2) N ..
+// (e+2) N.  The pattern is symmetric and a no-pivot LU keeps its fill inside this envelope,
+// so column i of L has env_l(r) entries below the diagonal and column i of U env_u(r) above
+// it; every stored band entry beyond them is an exact zero, and skipping it leaves the
+// substitutions' results unchanged.
+__host__ __device__ constexpr int env_l(int N, int r) { return r == 0 ? 2 * N : 2 * N - r; }
+__host__ __device__ constexpr int env_u(int N, int r) { return r == 0 ? 2 * N : N + r; }
+
+// f(integral_constant<int, 0>) .. f(integral_constant<int, K - 1>), in order.
+template <typename F, int... Rs>
+__device__ __forceinline__ void static_for_seq(F&& f, std::integer_sequence<int, Rs...>) {
+  (f(std::integral_constant<int, Rs>{}), ...);
+}
+template <int K, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_seq(f, std::make_integer_sequence<int, K>{});
+}
 
 // (D_z f)[lev] for a column held in shared memory with stride T between levels.  lev is
 // uniform across a warp, so the tap table reads are broadcasts and the branch on the tap
@@ -72,13 +95,85 @@ __device__ __forceinline__ double col_wp(const XT* x, int T, int lev, const RefL
 // refilled, NB levels ahead, right after its last use, so no pending load is copied from
 // buffer to buffer (a copy would wait for it) and each load has NB - 1 levels of work to
 // arrive.
-template <int HB, typename VT, typename FT, int NB = 0>
+// NE = N (Schur-form factors, HB = 2N, NB = 0): the substitutions skip the exact zeros
+// outside the factors' envelope (env_l, env_u); the level loop runs in blocks of N levels so
+// that each level's entry count is a compile-time constant.  NE = 0: the full band.
+template <int HB, typename VT, typename FT, int NB = 0, int NE = 0>
 __device__ __forceinline__ void col_solve(VT* x, int T, int M, const FT* __restrict__ L,
                                           const FT* __restrict__ U, long long col) {
   const FT* Lb = L + fac_col_base(col, M, HB);
   const FT* Ub = U + fac_col_base(col, M, HB + 1);
   static_assert(NB == 0 || (NB >= 2 && NB <= 4), "NB = 0 or 2 to 4 factor buffers");
-  if constexpr (NB == 0) {
+  static_assert(NE == 0 || (NB == 0 && HB == 2 * NE), "the envelope is the Schur form's");
+  if constexpr (NE > 0) {
+    // forward: y_i = w_0; w_k <- w_{k+1} - L(i+1+k, i) y_i for k < env_l(r), shift beyond
+    VT w[HB], ln[HB];
+#pragma unroll
+    for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : (VT)0;
+#pragma unroll
+    for (int k = 0; k < env_l(NE, 0); ++k) ln[k] = (VT)__ldg(Lb + (long long)k * kFacBlk);
+#pragma unroll 1
+    for (int i0 = 0; i0 < M; i0 += NE) {
+      static_for<NE>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        constexpr int nl = env_l(NE, r);
+        constexpr int nn = env_l(NE, (r + 1) % NE);
+        const int i = i0 + r;
+        if (i < M) {
+          VT l[HB];
+#pragma unroll
+          for (int k = 0; k < nl; ++k) l[k] = ln[k];
+          if (i + 1 < M) {
+            const FT* Lc = Lb + (long long)(i + 1) * HB * kFacBlk;
+#pragma unroll
+            for (int k = 0; k < nn; ++k) ln[k] = (VT)__ldg(Lc + (long long)k * kFacBlk);
+          }
+          const VT y = w[0];
+          x[i * T] = y;
+          const VT nxt = (i + HB < M) ? x[(i + HB) * T] : (VT)0;
+#pragma unroll
+          for (int k = 0; k < HB - 1; ++k) w[k] = (k < nl) ? fma(-l[k], y, w[k + 1]) : w[k + 1];
+          w[HB - 1] = (HB - 1 < nl) ? fma(-l[HB - 1], y, nxt) : nxt;
+        }
+      });
+    }
+    // backward: x_i = v_0 / U(i,i); v_k <- v_{k+1} - U(i-1-k, i) x_i for k < env_u(r).
+    // Level i = M - 1 - t with t = t0 + s, t0 a multiple of N, and M - 1 = nez N, so
+    // r = i mod N = (N - s) mod N is a compile-time constant of s.
+    VT v[HB], un[HB + 1];
+#pragma unroll
+    for (int k = 0; k < HB; ++k) v[k] = (M - 1 - k >= 0) ? x[(M - 1 - k) * T] : (VT)0;
+    {
+      const FT* Uc = Ub + (long long)(M - 1) * (HB + 1) * kFacBlk;
+#pragma unroll
+      for (int k = 0; k <= env_u(NE, 0); ++k) un[k] = (VT)__ldg(Uc + (long long)k * kFacBlk);
+    }
+#pragma unroll 1
+    for (int t0 = 0; t0 < M; t0 += NE) {
+      static_for<NE>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        constexpr int nu = env_u(NE, (NE - s) % NE);
+        constexpr int nn = env_u(NE, (NE - (s + 1) % NE) % NE);
+        const int i = M - 1 - (t0 + s);
+        if (i >= 0) {
+          VT u[HB + 1];
+#pragma unroll
+          for (int k = 0; k <= nu; ++k) u[k] = un[k];
+          if (i > 0) {
+            const FT* Uc = Ub + (long long)(i - 1) * (HB + 1) * kFacBlk;
+#pragma unroll
+            for (int k = 0; k <= nn; ++k) un[k] = (VT)__ldg(Uc + (long long)k * kFacBlk);
+          }
+          const VT xi = v[0] * u[0];
+          x[i * T] = xi;
+          const VT nxt = (i - HB >= 0) ? x[(i - HB) * T] : (VT)0;
+#pragma unroll
+          for (int k = 0; k < HB - 1; ++k) v[k] = (k < nu) ? fma(-u[k + 1], xi, v[k + 1]) : v[k + 1];
+          v[HB - 1] = (HB - 1 < nu) ? fma(-u[HB], xi, nxt) : nxt;
+        }
+      });
+    }
+  } else if constexpr (NB == 0) {
     VT w[HB], l[HB], ln[HB];
 #pragma unroll
     for (int k = 0; k < HB; ++k) w[k] = (k < M) ? x[k * T] : (VT)0;
@@ -208,11 +303,11 @@ __device__ __forceinline__ void col_solve_refined(double* B, double* tmp, float*
                                                   long long col, const RefLev& R,
                                                   const StageTab& tb, int iters) {
   if (!MIXED) {
-    col_solve<2 * N, double, double>(B, T, M, F.L, F.U, col);
+    col_solve<2 * N, double, double, 0, N>(B, T, M, F.L, F.U, col);
     return;
   }
   for (int lev = 0; lev < M; ++lev) Tf[lev * T] = (float)B[lev * T];
-  col_solve<2 * N, float, float>(Tf, T, M, F.L32, F.U32, col);
+  col_solve<2 * N, float, float, 0, N>(Tf, T, M, F.L32, F.U32, col);
   for (int it = 0; it < iters; ++it) {
     const bool first = (it == 0), last = (it == iters - 1);
     for (int lev = 0; lev < M; ++lev)
@@ -221,7 +316,7 @@ __device__ __forceinline__ void col_solve_refined(double* B, double* tmp, float*
       const double xl = first ? (double)Tf[lev * T] : Xd[lev * T];
       Td[lev * T] = (float)col_residual<N>(B, tmp, T, lev, R, tb, xl);
     }
-    col_solve<2 * N, float, float>(Td, T, M, F.L32, F.U32, col);
+    col_solve<2 * N, float, float, 0, N>(Td, T, M, F.L32, F.U32, col);
     for (int lev = 0; lev < M; ++lev) {
       const double x = (first ? (double)Tf[lev * T] : Xd[lev * T]) + (double)Td[lev * T];
       if (last) B[lev * T] = x;
@@ -246,9 +341,11 @@ __host__ __device__ inline size_t col_smem_per_level(bool mixed, int iters) {
 // Phase 2 (one thread per column): Schur right-hand side b (Algorithm 4), the column solve,
 //   and w_p(P) (Eq. utteqn).
 // Phase 3 (coalesced): w~ = w_a - w_p(P) (formed at the end of phase 2 in the FP64 form),
-//   theta~ = theta~_e - lam w~ d(theta0)/dz, rho~ = (P - H0 theta~) / G0 (theta~_e, and in
-//   the mixed form w_a, recomputed from their sources rather than kept in shared memory,
-//   which would cut the resident columns), then q(i) = q~ - sum_j c_ij q(j).
+//   theta~ = theta~_e - lam w~ d(theta0)/dz, rho~ = (P - H0 theta~) / G0, then
+//   q(i) = q~ - sum_j c_ij q(j).  theta~_e, and in the mixed form w_a, come back from the
+//   output slots where phase 1 parked them (shared memory for them would cut the resident
+//   columns; recomputing them would repeat the predictor's FP64 work).  So out must not
+//   overlap an input.
 // RT: type of R1, R2 (double, or float in the mixed form).
 // col0: first column of this block, T columns (T <= blockDim.x: all threads share phases 1
 // and 3, the first T run phase 2); sm: dynamic shared memory of
@@ -310,8 +407,13 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     out[nn + g] = pred(1, nn + g);
     out[2 * nn + g] = pred(2, 2 * nn + g);
     const double re = pred(0, g), we = pred(3, 3 * nn + g), te = pred(4, 4 * nn + g);
-    S1[lev * T + c] = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
+    const double wa = fma(__ldg(tb.wa_th + lev), te, we) * __ldg(tb.wa_s + lev);
+    S1[lev * T + c] = wa;
     S0[lev * T + c] = fma(__ldg(tb.G0 + lev), re, __ldg(tb.H0 + lev) * te);
+    // theta~_e (and, in the mixed form, w_a) wait in the output slots for phase 3, which
+    // the same thread runs on the same node: no FP64 work is repeated there
+    out[4 * nn + g] = te;
+    if (MIXED) out[3 * nn + g] = wa;
   }
   __syncthreads();
 
@@ -335,12 +437,12 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
   });
   __syncthreads();
   if (!MIXED) {
-    if (tid < ncols) col_solve<2 * N, double, double>(S0 + tid, T, M, F.L, F.U, col0 + tid);
+    if (tid < ncols) col_solve<2 * N, double, double, 0, N>(S0 + tid, T, M, F.L, F.U, col0 + tid);
     __syncthreads();
   } else {
     // FP32 solve, then `iters` sweeps of FP64 refinement (r = b - S X with the FP64
     // matrix-free operator, correction solved in FP32); S1 is the scratch for w_p(X)
-    if (tid < ncols) col_solve<2 * N, float, float>(Tf + tid, T, M, F.L32, F.U32, col0 + tid);
+    if (tid < ncols) col_solve<2 * N, float, float, 0, N>(Tf + tid, T, M, F.L32, F.U32, col0 + tid);
     __syncthreads();
     for (int it = 0; it < iters; ++it) {
       const bool first = (it == 0), last = (it == iters - 1);
@@ -354,7 +456,7 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
         Td[lev * T + c] = (float)col_residual<N>(S0 + c, S1 + c, T, lev, R, tb, xl);
       });
       __syncthreads();
-      if (tid < ncols) col_solve<2 * N, float, float>(Td + tid, T, M, F.L32, F.U32, col0 + tid);
+      if (tid < ncols) col_solve<2 * N, float, float, 0, N>(Td + tid, T, M, F.L32, F.U32, col0 + tid);
       __syncthreads();
       level_loop([&](int lev, int c) {
         const double x = (first ? (double)Tf[lev * T + c] : SXd[lev * T + c]) + (double)Td[lev * T + c];
@@ -383,11 +485,10 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     const long long g = base + j;
     const int c = j / M, lev = j - c * M;
     const long long orr = g, ow = 3 * nn + g, oth = 4 * nn + g;
-    const double te = pred(4, oth);
+    const double te = out[oth];
     double wv;
     if (MIXED) {
-      const double wa = fma(__ldg(tb.wa_th + lev), te, pred(3, ow)) * __ldg(tb.wa_s + lev);
-      wv = wa - S1[lev * T + c];
+      wv = out[ow] - S1[lev * T + c];
     } else {
       wv = S1[lev * T + c];
     }

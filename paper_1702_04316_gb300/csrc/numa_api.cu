@@ -458,6 +458,13 @@ int check_ptr(numa_ctx* c, const void* p, const char* name) {
   return NUMA_OK;
 }
 
+// Whether two state arrays of 5 nnode doubles (a may be NULL) share any element.
+bool states_overlap(const numa_ctx* c, const double* a, const double* b) {
+  if (!a || !b) return false;
+  const long long n5 = 5 * c->G.nnode;
+  return a < b + n5 && b < a + n5;
+}
+
 // One right-hand side.  FP64 method: P' pre-pass, FP64 kernel.  Mixed form: FP64 P' and
 // FP32 field copies, FP32 kernel; in mode 0, out32 receives the FP32 tendencies.
 // pp_ready: c->Pp already holds P'(q) (written by the stage that produced q).
@@ -816,6 +823,9 @@ int numa_imex_stage(numa_ctx* ctx, int stage, const double* qn, const double* R1
       (rc = check_ptr(ctx, q_out, "q_out")))
     return rc;
   if (stage == 3 && ((rc = check_ptr(ctx, R2, "R2")) || (rc = check_ptr(ctx, q2, "q2")))) return rc;
+  if (states_overlap(ctx, q_out, qn) || states_overlap(ctx, q_out, R1) ||
+      (stage == 3 && (states_overlap(ctx, q_out, R2) || states_overlap(ctx, q_out, q2))))
+    return fail(ctx, NUMA_ERR_ARG, "q_out overlaps an input");
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
   if (ctx->imex3d) return fail(ctx, NUMA_ERR_ARG, "3D-IMEX context: use numa_imex3d_stage");
   return enqueue_stage(ctx, stage, qn, R1, R2, q2, q_out, numa_stage_coef(ctx, stage));
@@ -841,6 +851,9 @@ int numa_imex_stage_s(numa_ctx* ctx, int stage, const double* qn, const double* 
       Qv[j] = Q[j - 1];
     }
   }
+  bool ov = states_overlap(ctx, q_out, qn);
+  for (int j = 0; j < stage - 1; ++j) ov = ov || states_overlap(ctx, q_out, Rv[j]) || states_overlap(ctx, q_out, Qv[j]);
+  if (ov) return fail(ctx, NUMA_ERR_ARG, "q_out overlaps an input");
   if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
   const StagePrev P = stage_prev(t, stage - 1, ctx->dt, qn, Rv, Qv);
   long p = prof_begin(ctx, NUMA_K_STAGE);

@@ -154,3 +154,34 @@ def test_standard_form_solve_equals_schur_solve(C, n_bv):
     assert np.abs(b[3][:, [0, -1]]).max() == 0.0
     for f in range(5):
         assert np.abs(a[f] - b[f]).max() <= 1e-12 * C * np.abs(a[f]).max()
+
+
+@pytest.mark.parametrize("N,nez", [(2, 5), (3, 4), (4, 1), (4, 6), (7, 3)])
+@pytest.mark.parametrize("n_bv", [0.0, 0.02])
+@pytest.mark.parametrize("C", [1, 150])
+def test_lu_fill_stays_in_the_envelope(N, nez, n_bv, C):
+    """The column kernels skip the factor entries outside the envelope of S(lam): column j
+    of L reaches 2N - r levels below the diagonal and column j of U N + r above it, with
+    r = j mod N (2N at an element interface, r = 0).  S has the pattern of D_z^2 and a
+    no-pivot LU keeps its fill inside that envelope, so those entries of the oracle's own
+    factors are exact zeros, and the outermost entries inside it are not all zero (the
+    envelope is tight)."""
+    m, col = _col(nez=nez, N=N, n_bv=n_bv)
+    lam = _lam(col, m, C)
+    LU = lu_nopivot_banded(col.jacobian_by_probing(lam), col.half_band)
+    M = m.M
+    env_l = lambda r: 2 * N if r == 0 else 2 * N - r
+    env_u = lambda r: 2 * N if r == 0 else N + r
+    edge_l, edge_u = [], []
+    for j in range(M):
+        r = j % N
+        below = LU[j + 1 + env_l(r):, j]
+        above = LU[:max(0, j - env_u(r)), j]
+        assert np.all(below == 0.0) and np.all(above == 0.0), j
+        if j + env_l(r) < M:
+            edge_l.append(LU[j + env_l(r), j])
+        if j - env_u(r) >= 0:
+            edge_u.append(LU[j - env_u(r), j])
+    if edge_l:
+        assert np.any(np.array(edge_l) != 0.0)
+        assert np.any(np.array(edge_u) != 0.0)
