@@ -439,6 +439,78 @@ int numa_batch_member_query(const numa_batch* b, int member, int what, long long
 int numa_batch_reference_levels(const numa_batch* b, int member, double* host_out);
 const char* numa_batch_last_error(const numa_batch* b);
 
+/* ---- several GPUs: horizontal partition with a halo exchange ------------------------------
+ * In HEVI the implicit column solves cross no partition boundary (Sec. "IMEX time
+ * integration"), so a horizontal partition of the columns needs one exchange per evaluation
+ * of the explicit right-hand side: the halo node columns its stencil reads (the direct
+ * stiffness summation across the cut; Sec. "Scalability").  Rank r of a px x py process grid
+ * owns a rectangle of elements and computes on a window: the rectangle plus one element
+ * toward each neighbour, run as an ordinary context of the window's size (numa_init with
+ * info.window).  Node-column ownership: a rank owns the node columns [ex0 N, ex1 N) x
+ * [ey0 N, ey1 N), plus the last node column where its rectangle touches the east or north
+ * wall; every other node column of its window is halo, owned by one neighbour.  With the
+ * halo holding the owners' values before every right-hand side, each owned node of the
+ * window evolves exactly as on the whole mesh (the same kernels and arithmetic, so bit for
+ * bit). */
+#define NUMA_PART_MAX_NEIGH 8
+
+typedef struct numa_part_desc {
+  int px, py;   /* process grid: px ranks along x, py along y (each rectangle >= 2 elements wide) */
+  int rank;     /* this rank, 0 <= rank < px*py; its grid position (rank % px, rank / px) */
+} numa_part_desc;
+
+typedef struct numa_part_info {
+  int ex0, ex1, ey0, ey1;      /* owned elements [ex0, ex1) x [ey0, ey1) of the global mesh */
+  int wx0, wx1, wy0, wy1;      /* the window's elements (owned + one toward each neighbour) */
+  numa_mesh_desc window;       /* the window as a box of its own (same element size, bit for bit) */
+  int own_x0, own_x1, own_y0, own_y1;   /* owned node columns, window-local, [x0, x1) x [y0, y1) */
+  int nneigh;                            /* neighbours, at most NUMA_PART_MAX_NEIGH */
+  int neigh[NUMA_PART_MAX_NEIGH];        /* their ranks, ascending */
+  int nsend[NUMA_PART_MAX_NEIGH];        /* node columns sent to each */
+  int nrecv[NUMA_PART_MAX_NEIGH];        /* node columns received from each */
+} numa_part_info;
+
+/* Host only (no device work, usable without a GPU): the partition of a global mesh for one
+ * rank.  NUMA_ERR_ARG for a bad mesh or grid, or a rectangle narrower than two elements. */
+int numa_part_plan(const numa_mesh_desc* global, int N, const numa_part_desc* part,
+                   numa_part_info* info);
+
+/* Host only: the exchange lists with neighbour k (0 <= k < info.nneigh), as window-local
+ * column ids (col = iy*nxw + ix of the window), sorted by global column id.  send_cols:
+ * info.nsend[k] ints (owned columns inside the neighbour's window); recv_cols:
+ * info.nrecv[k] ints (halo columns the neighbour owns).  The send list of rank a to b and
+ * the receive list of b from a name the same global columns in the same order. */
+int numa_part_columns(const numa_mesh_desc* global, int N, const numa_part_desc* part, int k,
+                      int* send_cols, int* recv_cols);
+
+/* Halo messages: copy the listed node columns of nf <= 8 fields into (gather) or out of
+ * (scatter) one contiguous device buffer, buf[(f*ncols + c)*M + lev] = fields[f][cols[c]*M +
+ * lev].  fields: host array of nf device pointers, each a field of ncol*M doubles of the
+ * context's mesh (a state's field f is state + f*nnode); cols: device int32 array of ncols
+ * column ids; buf: device, nf*ncols*M doubles.  Enqueued on the context's stream.  A listed
+ * column outside the context is skipped and numa_status then reports NUMA_ERR_ARG. */
+int numa_gather_columns(numa_ctx* ctx, const double* const* fields, int nf, const int* cols,
+                        long long ncols, double* buf);
+int numa_scatter_columns(numa_ctx* ctx, double* const* fields, int nf, const int* cols,
+                         long long ncols, const double* buf);
+
+/* One ARK2 step of numa_step_imex1d in three phases, for a caller that refreshes a
+ * partition's halo between them (ARK2 1D-IMEX contexts; NUMA_ERR_ARG otherwise):
+ *   phase 0: R1 = R(q_n), stage 2 -> q(2);
+ *   phase 1: R2 = R(q(2)), stage 3 -> q(3);
+ *   phase 2: q_out = q_n + dt sum_i b_i R(q(i)) (R(q(3)) in the update's epilogue).
+ * q_n: the step's input (all phases; not modified), q_out: phase 2's output (may equal q_n).
+ * Run in order, with nothing in between, the phases are numa_step_imex1d's kernels in its
+ * order.  Before phases 1 and 2 the halo of q(2), resp. q(3), must hold the owners' values,
+ * and so must P' of it when numa_step_buffers reports it fused (the stage writes P' of its
+ * output for the next right-hand side); before phase 0 the halo of q_n. */
+int numa_step_phase(numa_ctx* ctx, int phase, const double* q_n, double* q_out);
+
+/* The context's stage values q(2), q(3) (5*nnode doubles each) and P' (nnode doubles, or NULL
+ * where the context has none), and whether the stages write P' of their output (1) or the
+ * next right-hand side recomputes it (0).  Device pointers owned by the context. */
+int numa_step_buffers(numa_ctx* ctx, double** q2, double** q3, double** pp, int* pp_fused);
+
 /* Size of the device scratch array used by numa_rhs_explicit_static.  Every GPU that loads
  * the library's device code holds an array of this size until the process exits.  With
  * CUDA's default lazy module loading the array is reserved when the module is first used on

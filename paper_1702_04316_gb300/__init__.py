@@ -44,6 +44,8 @@ EXPORTS = (
     "numa_imex1d_adjoint_checkpointed", "numa_ark3_tableau", "numa_ark_tableau", "numa_imex_stage_s",
     "numa_schur3d_apply",
     "numa_solve_schur3d", "numa_imex3d_stage", "numa_step_imex3d", "numa_imex3d_info",
+    "numa_part_plan", "numa_part_columns", "numa_gather_columns", "numa_scatter_columns",
+    "numa_step_phase", "numa_step_buffers",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ, K_SCHUR3D = range(9)
 
@@ -59,6 +61,23 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("nex", ctypes.c_int), ("ney", ctypes.c_int), ("nez", ctypes.c_int),
                 ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
                 ("theta_s", ctypes.c_double), ("n_bv", ctypes.c_double)]
+
+
+PART_MAX_NEIGH = 8
+
+
+class PartDesc(ctypes.Structure):
+    _fields_ = [("px", ctypes.c_int), ("py", ctypes.c_int), ("rank", ctypes.c_int)]
+
+
+class PartInfo(ctypes.Structure):
+    _fields_ = [("ex0", ctypes.c_int), ("ex1", ctypes.c_int), ("ey0", ctypes.c_int), ("ey1", ctypes.c_int),
+                ("wx0", ctypes.c_int), ("wx1", ctypes.c_int), ("wy0", ctypes.c_int), ("wy1", ctypes.c_int),
+                ("window", MeshDesc),
+                ("own_x0", ctypes.c_int), ("own_x1", ctypes.c_int), ("own_y0", ctypes.c_int),
+                ("own_y1", ctypes.c_int), ("nneigh", ctypes.c_int),
+                ("neigh", ctypes.c_int * PART_MAX_NEIGH), ("nsend", ctypes.c_int * PART_MAX_NEIGH),
+                ("nrecv", ctypes.c_int * PART_MAX_NEIGH)]
 
 
 _lib = None
@@ -122,6 +141,14 @@ def lib():
             "numa_step_imex1d_adjoint": (I, [P, P, P, P]),
             "numa_imex1d_forward_checkpointed": (I, [P, P, P, I, I, P]),
             "numa_imex1d_adjoint_checkpointed": (I, [P, P, I, I, P, P, P]),
+            "numa_part_plan": (I, [ctypes.POINTER(MeshDesc), I, ctypes.POINTER(PartDesc),
+                                   ctypes.POINTER(PartInfo)]),
+            "numa_part_columns": (I, [ctypes.POINTER(MeshDesc), I, ctypes.POINTER(PartDesc), I, P, P]),
+            "numa_gather_columns": (I, [P, P, I, P, LL, P]),
+            "numa_scatter_columns": (I, [P, P, I, P, LL, P]),
+            "numa_step_phase": (I, [P, I, P, P]),
+            "numa_step_buffers": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                      ctypes.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -211,6 +238,42 @@ class Numa:
         out = self._torch.empty_like(q) if out is None else self._state(out)
         self._check(lib().numa_rhs_explicit(self._h, _ptr(q), _ptr(out)), "numa_rhs_explicit")
         return out
+
+    # -- phased step and halo messages (horizontal partition over several GPUs) --------
+    def step_phase(self, phase, q_n, q_out=None):
+        """numa_step_phase: phase 0 (R1, stage 2), 1 (R2, stage 3) or 2 (final update into
+        q_out) of one ARK2 step."""
+        self._state(q_n)
+        if q_out is not None:
+            self._state(q_out)
+        self._check(lib().numa_step_phase(self._h, int(phase), _ptr(q_n), _ptr(q_out)),
+                    "numa_step_phase")
+        return q_out
+
+    def step_buffers(self):
+        """numa_step_buffers: (q2, q3, P', P' fused) as tensors viewing the context's
+        workspace (q2, q3 of shape (5, nnode); P' of shape (nnode,) or None)."""
+        q2, q3, pp = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        fused = ctypes.c_int()
+        self._check(lib().numa_step_buffers(self._h, ctypes.byref(q2), ctypes.byref(q3),
+                                            ctypes.byref(pp), ctypes.byref(fused)), "numa_step_buffers")
+        view = lambda p, n: _device_view(self._torch, p.value, n) if p.value else None
+        q2t, q3t = view(q2, 5 * self.nnode), view(q3, 5 * self.nnode)
+        return (q2t.view(5, self.nnode), q3t.view(5, self.nnode), view(pp, self.nnode),
+                bool(fused.value))
+
+    def gather_columns(self, fields, cols, buf):
+        """numa_gather_columns: the listed columns of `fields` (tensors of ncol*M doubles)
+        into buf (len(fields) * len(cols) * M doubles); cols: CUDA int32 tensor."""
+        arr = (ctypes.c_void_p * len(fields))(*[f.data_ptr() for f in fields])
+        self._check(lib().numa_gather_columns(self._h, arr, len(fields), _ptr(cols), cols.numel(),
+                                              _ptr(buf)), "numa_gather_columns")
+
+    def scatter_columns(self, fields, cols, buf):
+        """numa_scatter_columns: buf into the listed columns of `fields`."""
+        arr = (ctypes.c_void_p * len(fields))(*[f.data_ptr() for f in fields])
+        self._check(lib().numa_scatter_columns(self._h, arr, len(fields), _ptr(cols), cols.numel(),
+                                               _ptr(buf)), "numa_scatter_columns")
 
     def factor_columns(self, dt):
         self._check(lib().numa_factor_columns(self._h, float(dt)), "numa_factor_columns")
@@ -574,6 +637,44 @@ class Batch:
         self._check(lib().numa_batch_reference_levels(self._h, int(m), out.ctypes.data_as(ctypes.c_void_p)),
                     "reference_levels")
         return dict(zip(("z", "rho0", "theta0", "P0", "G0", "H0", "drho0", "dtheta0"), out))
+
+
+def _device_view(torch, ptr, n):
+    """A float64 CUDA tensor of n values over device memory owned by a context (no copy;
+    valid while the context lives)."""
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_Arr(), device="cuda")
+
+
+def part_plan(nex, ney, nez, Lx, Ly, Lz, N, px, py, rank, theta_s=300.0, n_bv=0.0):
+    """numa_part_plan + numa_part_columns (host only, no GPU needed): the rank's rectangle,
+    window (a MeshDesc-like dict) and, per neighbour, its rank and the send / receive column
+    lists (numpy int32, window-local column ids)."""
+    g = MeshDesc(nex, ney, nez, Lx, Ly, Lz, theta_s, n_bv)
+    d = PartDesc(px, py, rank)
+    info = PartInfo()
+    rc = lib().numa_part_plan(ctypes.byref(g), int(N), ctypes.byref(d), ctypes.byref(info))
+    if rc != NUMA_OK:
+        raise NumaError("numa_part_plan: %s" % ERRORS.get(rc, rc))
+    w = info.window
+    out = {"own_elems": (info.ex0, info.ex1, info.ey0, info.ey1),
+           "window_elems": (info.wx0, info.wx1, info.wy0, info.wy1),
+           "window": dict(nex=w.nex, ney=w.ney, nez=w.nez, Lx=w.Lx, Ly=w.Ly, Lz=w.Lz,
+                          theta_s=w.theta_s, n_bv=w.n_bv),
+           "own_cols": (info.own_x0, info.own_x1, info.own_y0, info.own_y1),
+           "neighbours": []}
+    for k in range(info.nneigh):
+        send = np.empty(info.nsend[k], dtype=np.int32)
+        recv = np.empty(info.nrecv[k], dtype=np.int32)
+        rc = lib().numa_part_columns(ctypes.byref(g), int(N), ctypes.byref(d), k,
+                                     send.ctypes.data_as(ctypes.c_void_p),
+                                     recv.ctypes.data_as(ctypes.c_void_p))
+        if rc != NUMA_OK:
+            raise NumaError("numa_part_columns: %s" % ERRORS.get(rc, rc))
+        out["neighbours"].append({"rank": info.neigh[k], "send": send, "recv": recv})
+    return out
 
 
 def rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out, theta_s=300.0, n_bv=0.0,

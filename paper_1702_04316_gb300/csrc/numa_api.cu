@@ -960,6 +960,58 @@ int numa_step_imex1d(numa_ctx* ctx, const double* q_in, double* q_out, int nstep
   return NUMA_OK;
 }
 
+int numa_step_phase(numa_ctx* ctx, int phase, const double* q_n, double* q_out) {
+  if (!ctx) return NUMA_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(ctx, q_n, "q_n"))) return rc;
+  if (phase == 2 && (rc = check_ptr(ctx, q_out, "q_out"))) return rc;
+  if (phase < 0 || phase > 2) return fail(ctx, NUMA_ERR_ARG, "phase must be 0, 1 or 2");
+  if (!ctx->factored) return fail(ctx, NUMA_ERR_NOT_FACTORED, "numa_factor_columns not called");
+  if (ctx->imex3d || ctx->scheme != NUMA_SCHEME_ARK2)
+    return fail(ctx, NUMA_ERR_ARG, "the phased step needs an ARK2 1D-IMEX context");
+  if (states_overlap(ctx, q_n, ctx->q2) || states_overlap(ctx, q_n, ctx->q3) ||
+      (phase == 2 && (states_overlap(ctx, q_out, ctx->q2) || states_overlap(ctx, q_out, ctx->q3))))
+    return fail(ctx, NUMA_ERR_ARG, "q_n or q_out overlaps the context's stage values");
+  // the phases of the ARK2 branch of numa_step_imex1d, in its order
+  const ArkTab t = ark_tab(ctx->scheme);
+  const bool mixed = ctx->precision == NUMA_PREC_MIXED || ctx->precision == NUMA_PREC_RHS32;
+  void* R1 = mixed ? (void*)ctx->R1f : (void*)ctx->R1;
+  void* R2 = mixed ? (void*)ctx->R2f : (void*)ctx->R2;
+  const bool fuse = fuse_pressure(ctx);
+  double* Pp_next = fuse ? ctx->Pp : nullptr;
+  RhsEpilogue e0{};
+  if (phase == 0) {
+    if ((rc = enqueue_rhs(ctx, q_n, ctx->R1, e0, ctx->R1f))) return rc;
+    return enqueue_stage(ctx, 2, q_n, R1, nullptr, nullptr, ctx->q2, numa_stage_coef(ctx, 2), mixed,
+                         Pp_next);
+  }
+  if (phase == 1) {
+    if ((rc = enqueue_rhs(ctx, ctx->q2, ctx->R2, e0, ctx->R2f, fuse))) return rc;
+    return enqueue_stage(ctx, 3, q_n, R1, R2, ctx->q2, ctx->q3, numa_stage_coef(ctx, 3), mixed,
+                         Pp_next);
+  }
+  RhsEpilogue ef{};
+  ef.mode = 2;
+  ef.b1dt = t.b[0] * ctx->dt;
+  ef.b2dt = t.b[1] * ctx->dt;
+  ef.b3dt = t.b[2] * ctx->dt;
+  ef.u0 = q_n;
+  ef.R1 = R1;
+  ef.R2 = R2;
+  return enqueue_rhs(ctx, ctx->q3, q_out, ef, nullptr, fuse);
+}
+
+int numa_step_buffers(numa_ctx* ctx, double** q2, double** q3, double** pp, int* pp_fused) {
+  if (!ctx) return NUMA_ERR_ARG;
+  if (ctx->imex3d || ctx->scheme != NUMA_SCHEME_ARK2)
+    return fail(ctx, NUMA_ERR_ARG, "the phased step needs an ARK2 1D-IMEX context");
+  if (q2) *q2 = ctx->q2;
+  if (q3) *q3 = ctx->q3;
+  if (pp) *pp = ctx->Pp;
+  if (pp_fused) *pp_fused = fuse_pressure(ctx) ? 1 : 0;
+  return NUMA_OK;
+}
+
 int numa_step_explicit_rk(numa_ctx* ctx, const double* q_in, double* q_out, double dt,
                           int nsteps) {
   if (!ctx) return NUMA_ERR_ARG;
@@ -1294,6 +1346,7 @@ int numa_status(numa_ctx* ctx, int* status) {
   *status = (h & NUMA_ST_PIVOT)       ? NUMA_ERR_PIVOT
             : (h & NUMA_ST_NONFINITE) ? NUMA_ERR_NONFINITE
             : (h & NUMA_ST_TIMEOUT)   ? NUMA_ERR_TIMEOUT
+            : (h & NUMA_ST_RANGE)     ? NUMA_ERR_ARG
                                       : NUMA_OK;
   return NUMA_OK;
 }

@@ -25,6 +25,7 @@
 #define NUMA_ST_PIVOT 1u
 #define NUMA_ST_NONFINITE 2u
 #define NUMA_ST_TIMEOUT 4u
+#define NUMA_ST_RANGE 8u      // an index list named a column outside the context
 
 // Mesh sizes (see the conventions in include/numa.h).
 struct Geom {

@@ -1,9 +1,8 @@
 """The multi-process (N > 1) host logic of bench.py, on CPU with the gloo backend.
 
-bench.py runs independent replicas under torchrun (the method's column solves need no
-communication and the benchmark has no data-path collective): every timing is the maximum
-over ranks, the whole-job value counts every replica's simulated time, and only rank 0
-prints.  These tests run world size 2 on 127.0.0.1 without a GPU."""
+Under torchrun every timing is the maximum over ranks and only rank 0 prints (the
+partitioned step's exchange itself is covered by tests/test_partition_gloo.py).  These
+tests run world size 2 on 127.0.0.1 without a GPU."""
 import json
 import os
 import socket
