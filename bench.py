@@ -22,8 +22,10 @@ C = 1 (`accuracy_vs_explicit_c1`), and one entry per form and variant.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference times the FP64 NumPy oracle on the host cores (one ARK2 step of the same
-workload restricted to a window of columns, scaled to the full mesh).
+--impl reference times the FP64 NumPy oracle on the host cores over the whole workload: one
+single-threaded process per core, each advancing its block of columns (with a halo that
+makes its owned nodes exact) by the same ARK2 steps; the time per step is the slowest
+process's (oracle_partitioned).
 """
 import argparse
 import hashlib
@@ -92,12 +94,31 @@ def rhs_flops_per_node():
     return 18 * 2 * (N + 1) + 46
 
 
+def envelope_entries(n=N, nez=NEZ):
+    """Nonzero factor entries of one column's Schur-form LU (the envelope of S, pattern of
+    D_z^2): column j of L holds 2N - r entries below the diagonal, column j of U N + r
+    above it (r = j mod N; 2N at interfaces), cut at the column ends.  Returns (L, U with
+    its diagonal)."""
+    M = nez * n + 1
+    nl = sum(min(2 * n if j % n == 0 else 2 * n - j % n, M - 1 - j) for j in range(M))
+    nu = sum(min(2 * n if j % n == 0 else n + j % n, j) + 1 for j in range(M))
+    return nl, nu
+
+
+def solve_fma_per_unknown(n=N, nez=NEZ):
+    """FP64 multiply-adds per unknown of the two substitutions over the envelope (the
+    off-diagonal entries, plus one multiply by the inverted pivot)."""
+    nl, nu = envelope_entries(n, nez)
+    return (nl + nu) / (nez * n + 1)
+
+
 def stage_flops_per_node(stage):
     """Algorithmic flops of one fused implicit stage per node (predictor, Schur RHS with a
-    length-(2N+1) vertical derivative, banded solve 2(4N+1), extraction)."""
+    length-(2N+1) vertical derivative, banded solve over the factors' envelope,
+    extraction)."""
     pred = (3 * 4 + 2 * 2) if stage == 3 else (3 * 2 + 2 * 1)
     schur = 4 + 2 * (N + 1) + 4
-    solve = 2 * (4 * N + 1)
+    solve = 2 * solve_fma_per_unknown()
     extract = 2 * (N + 1) + 8
     recomb = 2 * 3 if stage == 3 else 3
     return 2 * pred + schur + solve + extract + recomb
@@ -107,13 +128,13 @@ def alg_bytes_per_node(kernel, hb=2 * N):
     """Algorithmic HBM bytes per global node and launch, averaged over one ARK2 step.
     k_rhs: the five state fields and P' read, five tendencies (or the updated state)
     written.  k_pressure: rho' and theta' read, P' written.  k_stage (mean of stages 2 and
-    3): q^n and R1 (stage 3 also R2 and q(2)) read, 2 hb + 1 factor doubles per unknown read,
-    the stage value and its P' written."""
+    3): q^n and R1 (stage 3 also R2 and q(2)) read, the envelope's factor entries read
+    (envelope_entries per column over M unknowns), the stage value and its P' written."""
     if kernel == "k_rhs":
         return 8 * (6 + 5)
     if kernel == "k_pressure":
         return 8 * (2 + 1)
-    fac = 2 * hb + 1
+    fac = solve_fma_per_unknown()
     return 8 * (0.5 * ((5 + 5) + (5 + 5 + 5 + 5)) + fac + 6)
 
 
@@ -222,6 +243,95 @@ def replica_value(dt, ms_step, world):
     return dt / (ms_step / 1e3) * world
 
 
+def run_gpu_partitioned(args, world, rank, local, dist):
+    """N > 1 GPUs: the workload split over a px x py process grid (strong scaling), each rank
+    stepping its window with the phased step and a halo exchange over NCCL before every
+    right-hand side (paper_1702_04316_gb300.partition).  value: the whole mesh's simulated
+    seconds per wall second, timed as the slowest rank's."""
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    from paper_1702_04316_gb300.partition import PartitionedHEVI, process_grid
+    dev = torch.device("cuda", local)
+    px, py = process_grid(world)
+    dt15 = dt_for(C_MAIN)
+    part = PartitionedHEVI(NEX, NEY, NEZ, LX, LY, LZ, N, dt15, px, py, rank, dist=dist, device=dev)
+    lev = part.ctx.reference_levels()
+    xi = lgl_nodes()
+    # this window's part of the global state (the halo already holds the owners' values)
+    qg = make_state(lev, axis_coords(NEX, LX / NEX, xi), axis_coords(NEY, LY / NEY, xi), lev["z"])
+    q0h = part.restrict(qg)
+    del qg
+    q0 = torch.from_numpy(q0h).to(dev)
+    q1 = torch.empty_like(q0)
+    stream = torch.cuda.current_stream()
+
+    def time_steps(fn, k):
+        dist.barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        torch.cuda.synchronize()
+        dist.barrier()
+        return max_over_ranks(a.elapsed_time(b), dist, dev)
+
+    step = lambda: part.step(q0, q1, 1)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ms = time_steps(step, args.steps)
+    clk = clocks.stop()
+    ms_step = ms / args.steps
+    assert part.ctx.count_nonfinite(q1) == 0, "non-finite output"
+    assert part.ctx.status() == pkg.NUMA_OK
+    # end to end: this rank's window from pinned host memory, the step, its window back
+    qin = torch.from_numpy(q0h).pin_memory()
+    qout = torch.empty_like(qin).pin_memory()
+
+    def e2e_step():
+        q0.copy_(qin, non_blocking=True)
+        part.step(q0, q1, 1)
+        qout.copy_(q1, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    for _ in range(max(3, args.warmup)):
+        e2e_step()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    nbytes = q0.numel() * 8
+    out = {
+        "metric": METRIC, "value": round(dt15 / (ms_step / 1e3), 3), "unit": "sim-s/wall-s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "C_V": C_MAIN, "dt_s": round(dt15, 5),
+                   "columns": (NEX * N + 1) * (NEY * N + 1), "levels": NEZ * N + 1,
+                   "l2": "inputs larger than L2; no flush",
+                   "parallelism": "%d x %d horizontal partition, halo exchange over NCCL before "
+                                  "every right-hand side" % (px, py)},
+        "e2e": {"value": round(dt15 * args.steps / e2e_s, 3), "unit": "sim-s/wall-s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "api": "PartitionedHEVI.step (each rank's window from pinned host buffers)"},
+        # per step: pre-pass, 3 right-hand sides, 2 stages, and a gather and a scatter per
+        # neighbour at each of the 3 exchanges (rank 0's count)
+        "gpu_launches": (6 + 6 * len(part.halo.peers)) * args.steps,
+        "clocks": clk,
+    }
+    part.close()
+    if rank == 0:
+        print(json.dumps(out))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def run_gpu(args):
     import torch
     import paper_1702_04316_gb300 as pkg
@@ -234,6 +344,8 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    if world > 1:
+        return run_gpu_partitioned(args, world, rank, local, dist)
     dev = torch.device("cuda", local)
 
     dt15, dt150, dt1 = dt_for(C_MAIN), dt_for(150.0), dt_for(1.0)
@@ -374,13 +486,19 @@ def run_gpu(args):
     for _ in range(args.warmup):
         g.solve_columns(bcol, xcol)
     ms_solve = time_steps(lambda: g.solve_columns(bcol, xcol), args.steps) / args.steps
-    solve_bytes = fb + 2 * 8 * nn
+    # algorithmic bytes: the factors' envelope (the stored band beyond it is exact zeros and
+    # is not read), the right-hand side and the solution
+    nl, nu = envelope_entries()
+    solve_bytes = 8 * (nl + nu) * g.ncol + 2 * 8 * nn
+    fma = solve_fma_per_unknown()
     out["column_solve"] = {"ms_per_launch": round(ms_solve, 4), "bytes_per_launch": int(solve_bytes),
+                           "stored_factor_bytes": int(fb),
                            "achieved_gbs": round(solve_bytes / (ms_solve * 1e-3) / 1e9, 1),
                            "hbm_peak_gbs": hbm, "peak_source": hbm_src,
                            "frac_of_hbm_peak": round(solve_bytes / (ms_solve * 1e-3) / 1e9 / hbm, 4),
-                           "fp64_floor_ms": round(17 * nn / (FP64_PEAK_TFLOPS * 1e12 / 2) * 1e3, 4),
-                           "note": "17 FP64 multiply-adds per unknown (L and U substitutions, half-band 2N)"}
+                           "fp64_floor_ms": round(fma * nn / (FP64_PEAK_TFLOPS * 1e12 / 2) * 1e3, 4),
+                           "note": "%.2f FP64 multiply-adds per unknown (L and U substitutions over "
+                                   "the factors' envelope)" % fma}
     del bcol, xcol
     # the mixed-precision form on the same workload
     gm = pkg.Numa(NEX, NEY, NEZ, LX, LY, LZ, N, dt15, precision="mixed", refine_iters=1)
@@ -443,6 +561,8 @@ def run_gpu(args):
         out["imex3d"] = imex3d_form(pkg, torch, q0, ms_rk, args.warmup)
     if not args.no_forms:
         out["accuracy_vs_explicit_c1"] = accuracy_vs_explicit(pkg, torch)
+        out["matched_accuracy"] = matched_accuracy(pkg, torch, ms_rk,
+                                                   {"fp64": ms_step, "rhs32": ms_32})
         out["precision_form"] = precision_form(pkg, torch, min(args.steps, 20), args.warmup)
         out["batching_form"] = batching_form(pkg, torch, min(args.steps, 10), args.warmup)
         out["batching_form_small_members"] = batching_form(pkg, torch, min(args.steps, 20), args.warmup,
@@ -507,6 +627,63 @@ def accuracy_vs_explicit(pkg, torch, L=40000e3):
         gp.close()
     res["batched"] = ("ensemble members are bitwise equal to single FP64 contexts, so their "
                       "accuracy is the FP64 form's")
+    return res
+
+
+MATCHED_C = (1, 2, 3, 5, 10, 15, 25, 30, 50, 75, 150)     # divisors of 150
+MATCHED_BARS = {"theta": (1e-4, 1e-3), "w": (1e-2, 1e-1)}
+
+
+def matched_accuracy(pkg, torch, ms_rk, ms_forms, L=40000e3):
+    """Speed-up over explicit RK35 at C = 1 at a stated accuracy (the paper's 100X at
+    C_V = 150 is a time to solution at matched results, Sec. "Acoustic wave problem").
+
+    On the stretched box of accuracy_vs_explicit (same array shapes, so the same cost per
+    step), 1D-IMEX ARK2 runs to t = dt(C = 150) at every C_V in MATCHED_C (150 / C steps);
+    its relative L2 errors in theta' and w against RK35 at C = 1 (150 steps) are recorded.
+    For each bar of MATCHED_BARS the largest C_V whose error stays under it is found, and
+    the speed-up there is C_V x (RK35 ms per step) / (1D-IMEX ms per step), the step costs
+    being those measured on the benchmark workload (ms_forms: form -> ms per step).  The
+    ensemble form's members are bitwise the FP64 form's, so they share its accuracy."""
+    dt1, dt150 = dt_for(1.0), dt_for(150.0)
+    g1 = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt150)
+    lev = g1.reference_levels()
+    xi = lgl_nodes()
+    import synthetic
+    q0h = synthetic.balanced_state(axis_coords(NEX, L / NEX, xi), axis_coords(NEY, L / NEY, xi),
+                                   lev["z"], L, L, LZ, lev["rho0"], lev["theta0"], SEED, 0.5)
+    q0 = torch.from_numpy(q0h).cuda()
+    ref = g1.step_explicit_rk(q0, dt1, torch.empty_like(q0), 150)
+    ref_half = g1.step_explicit_rk(q0, 0.5 * dt1, torch.empty_like(q0), 300)
+    g1.close()
+
+    def rel(a, f):
+        return float(torch.linalg.norm(a[f] - ref[f]) / torch.linalg.norm(ref[f]))
+    res = {"box": "96x96x12 elements over %gx%g km x 15 km, N=4" % (L / 1e3, L / 1e3),
+           "t_s": round(dt150, 4), "reference": "RK35 at C=1 (150 steps)",
+           "reference_own_error_vs_rk35_c0.5": {"theta": float("%.3g" % rel(ref_half, 4)),
+                                                "w": float("%.3g" % rel(ref_half, 3))},
+           "rk35_ms_per_step": round(ms_rk, 4)}
+    for form, ms_imex in ms_forms.items():
+        errs = {}
+        for C in MATCHED_C:
+            gc = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt_for(float(C)),
+                          precision="fp64" if form == "fp64" else form)
+            out = gc.step_imex1d(q0, torch.empty_like(q0), 150 // C)
+            errs[C] = (rel(out, 4), rel(out, 3))
+            gc.close()
+        entry = {"imex_ms_per_step": round(ms_imex, 4),
+                 "errors": {"C%d" % C: {"theta": float("%.3g" % e[0]), "w": float("%.3g" % e[1])}
+                            for C, e in errs.items()}}
+        for fi, (nm, bars) in enumerate(MATCHED_BARS.items()):
+            for bar in bars:
+                ok = [C for C in MATCHED_C if errs[C][fi] <= bar]
+                Cm = max(ok) if ok else None
+                entry["%s<=%g" % (nm, bar)] = {
+                    "largest_C_V": Cm,
+                    "speedup_vs_explicit_c1": round(Cm * ms_rk / ms_imex, 2) if Cm else None}
+        res[form] = entry
+    res["batched"] = "ensemble members are bitwise the FP64 form's: its entry applies"
     return res
 
 
@@ -852,32 +1029,7 @@ def differentiation_form(pkg, torch, warmup, reps=5, nsteps=20, every=5):
             "finite": bool(torch.isfinite(grad).all().item())}
 
 
-def oracle_sample_step(window_elems, nsteps_min, seconds):
-    """Time the oracle's ARK2 step on a window of W x W elements x all levels of the
-    workload (its own lateral walls) and scale to the full column count."""
-    from oracle import ark2
-    from oracle.column import Column
-    from oracle.mesh import BoxMesh
-    import synthetic
-    W = window_elems
-    m = BoxMesh(W, W, NEZ, N, W * LX / NEX, W * LY / NEY, LZ)
-    col = Column(m)
-    xg, yg, zg = m.coords()
-    q = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Ly, m.Lz, col.rho0, col.theta0, SEED)
-    dt = dt_for(C_MAIN)
-    H = ark2.HEVI(m, col, dt)
-    times = []
-    t_start = time.perf_counter()
-    while len(times) < nsteps_min or (time.perf_counter() - t_start) < seconds:
-        t0 = time.perf_counter()
-        H.step(q, 1)
-        times.append(time.perf_counter() - t0)
-        if len(times) >= 200:
-            break
-    t_sample = float(np.median(times))
-    full_cols = (NEX * N + 1) * (NEY * N + 1)
-    scale = full_cols / m.ncol
-    return dt / (t_sample * scale), t_sample, m.ncol, len(times)
+ORACLE_HALO = 3        # elements of halo per block: one ARK2 step evaluates R three times
 
 
 def oracle_procs():
@@ -887,74 +1039,145 @@ def oracle_procs():
     return max(1, int(v)) if v else (os.cpu_count() or 1)
 
 
-def oracle_parallel(call, nproc, timeout):
-    """Runs bench.<call> in nproc fresh single-threaded interpreters at once (each on its
-    own window of the workload) and returns their JSON results."""
-    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.%s))" % (ROOT, call))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
-                              stderr=subprocess.PIPE, text=True, env=env) for _ in range(nproc)]
-    outs, errs = [], []
-    for p in procs:
-        try:
-            o, e = p.communicate(timeout=timeout)
-        except subprocess.TimeoutExpired:
-            p.kill()
-            o, e = p.communicate()
-            errs.append("timed out")
-            continue
-        if p.returncode != 0:
-            errs.append((e.strip().splitlines() or ["exit %d" % p.returncode])[-1][:200])
-        else:
-            outs.append(json.loads(o.strip().splitlines()[-1]))
-    if errs:
-        raise RuntimeError("; ".join(errs))
-    return outs
+def oracle_blocks(nex, ney, nproc):
+    """Split an nex x ney element grid into nproc rectangular blocks, px x py = nproc with
+    px, py as close as possible: list of (ex0, ex1, ey0, ey1)."""
+    px = max(d for d in range(1, int(nproc ** 0.5) + 1) if nproc % d == 0)
+    py = nproc // px
+    if px > nex or py > ney:
+        raise ValueError("more blocks than elements")
+    cx = [nex * i // px for i in range(px + 1)]
+    cy = [ney * j // py for j in range(py + 1)]
+    return [(cx[i], cx[i + 1], cy[j], cy[j + 1]) for j in range(py) for i in range(px)]
 
 
-def cpu_baseline(seconds):
-    """The oracle, as it stands, on every host core: one single-threaded process per core,
-    each timing the bounded sample (oracle_sample_step) on its own window; the whole-job
-    rate is the sum of the per-core rates."""
-    nproc = oracle_procs()
-    try:
-        outs = oracle_parallel("oracle_sample_step(8, 3, %f)" % seconds, nproc,
-                               timeout=max(120, 10 * seconds))
-    except RuntimeError as e:
-        return {"value": None, "unit": "sim-s/wall-s", "cores": nproc, "kind": "oracle",
-                "sample": "failed: " + str(e)[:200]}
-    v = float(sum(o[0] for o in outs))
-    t = float(np.median([o[1] for o in outs]))
-    nc, n = outs[0][2], int(np.median([o[3] for o in outs]))
-    return {"value": v, "unit": "sim-s/wall-s", "cores": nproc, "kind": "oracle",
-            "per_core_value": float(np.median([o[0] for o in outs])),
-            "sample": ("one ARK2 step at C=15 on an 8x8x12-element window (%d of 148225 columns) "
-                       "per core, %d single-threaded processes at once, median of %d steps "
-                       "(%.2f s each) per process, scaled by the column count and summed over "
-                       "the processes" % (nc, nproc, n, t))}
-
-
-def reference_worker(warmup, steps):
-    """One core's share of the reference arm: warmup + timed oracle ARK2 steps on an
-    8 x 8-element window of the workload.  Returns (seconds, timed steps, window columns)."""
-    W = 8
-    dt = dt_for(C_MAIN)
+def _oracle_block_worker(mesh, dt, block, qpath, opath, warmup, steps, barrier, results):
+    """One process of the partitioned oracle run: its block of elements plus a halo of
+    ORACLE_HALO elements (clipped at the real walls) as a box of its own, ARK2 steps of
+    that window from the same input, the owned nodes of the last result written out.
+    The halo makes the owned nodes exact: a window's artificial walls corrupt one more
+    element ring per evaluation of R, three per step."""
+    import numpy as np
     from oracle import ark2
     from oracle.column import Column
     from oracle.mesh import BoxMesh
-    import synthetic
-    m = BoxMesh(W, W, NEZ, N, W * LX / NEX, W * LY / NEY, LZ)
-    col = Column(m)
-    xg, yg, zg = m.coords()
-    q = synthetic.balanced_state(xg, yg, zg, m.Lx, m.Ly, m.Lz, col.rho0, col.theta0, SEED)
-    H = ark2.HEVI(m, col, dt)
+    nex, ney, nez, Nn, Lx, Ly, Lz = mesh
+    ex0, ex1, ey0, ey1 = block
+    wx0, wx1 = max(0, ex0 - ORACLE_HALO), min(nex, ex1 + ORACLE_HALO)
+    wy0, wy1 = max(0, ey0 - ORACLE_HALO), min(ney, ey1 + ORACLE_HALO)
+    dx, dy = Lx / nex, Ly / ney
+    m = BoxMesh(wx1 - wx0, wy1 - wy0, nez, Nn, (wx1 - wx0) * dx, (wy1 - wy0) * dy, Lz)
+    H = ark2.HEVI(m, Column(m), dt)
+    nxg, nyg, M = nex * Nn + 1, ney * Nn + 1, nez * Nn + 1
+    q0 = np.load(qpath, mmap_mode="r").reshape(5, nyg, nxg, M)
+    q = np.ascontiguousarray(q0[:, wy0 * Nn:wy1 * Nn + 1, wx0 * Nn:wx1 * Nn + 1, :]).reshape(5, -1)
+    del q0
     for _ in range(warmup):
         H.step(q, 1)
-    t0 = time.perf_counter()
+    barrier.wait()
     for _ in range(steps):
-        H.step(q, 1)
-    return time.perf_counter() - t0, steps, m.ncol
+        out = H.step(q, 1)
+    barrier.wait()
+    # owned node columns: [e0 N, e1 N), plus the last node at the east / north wall
+    ox1 = ex1 * Nn + (1 if ex1 == nex else 0)
+    oy1 = ey1 * Nn + (1 if ey1 == ney else 0)
+    o = np.load(opath, mmap_mode="r+").reshape(5, nyg, nxg, M)
+    w = out.reshape(5, m.nyg, m.nxg, M)
+    o[:, ey0 * Nn:oy1, ex0 * Nn:ox1, :] = w[:, (ey0 - wy0) * Nn:oy1 - wy0 * Nn,
+                                             (ex0 - wx0) * Nn:ox1 - wx0 * Nn, :]
+    o.flush()
+    results.put(m.ncol)
+
+
+def oracle_partitioned(mesh, dt, q0, nproc, warmup, steps, timeout=3600):
+    """The oracle, as it stands, over a whole mesh on nproc single-threaded processes (spawned
+    fresh, so no GPU state is inherited).  Each process advances its block of columns (plus
+    a halo) by `steps` ARK2 steps from the same input q0 after `warmup` untimed ones; the
+    parent times from the barrier that starts the timed steps to the one that ends them, so
+    the figure is the slowest process's.  Returns (seconds per step, the assembled result
+    of one step, columns computed per step including the halos)."""
+    import multiprocessing as mp
+    import tempfile
+    nex, ney = mesh[0], mesh[1]
+    blocks = oracle_blocks(nex, ney, nproc)
+    tmp = "/dev/shm" if os.path.isdir("/dev/shm") and os.access("/dev/shm", os.W_OK) else None
+    with tempfile.TemporaryDirectory(dir=tmp) as d:
+        qpath, opath = os.path.join(d, "q0.npy"), os.path.join(d, "out.npy")
+        np.save(qpath, np.ascontiguousarray(q0, dtype=np.float64))
+        np.lib.format.open_memmap(opath, mode="w+", dtype=np.float64, shape=q0.shape).flush()
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                  "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(len(blocks) + 1, timeout=timeout)
+        results = ctx.Queue()
+        procs = [ctx.Process(target=_oracle_block_worker,
+                             args=(mesh, dt, b, qpath, opath, warmup, steps, barrier, results))
+                 for b in blocks]
+        try:
+            for pr in procs:
+                pr.start()
+            barrier.wait()
+            t0 = time.perf_counter()
+            barrier.wait()
+            t1 = time.perf_counter()
+            cols = sum(results.get(timeout=timeout) for _ in procs)
+            for pr in procs:
+                pr.join(timeout)
+        finally:
+            for pr in procs:
+                if pr.is_alive():
+                    pr.kill()
+            for v, x in saved.items():
+                if x is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = x
+        if any(pr.exitcode != 0 for pr in procs):
+            raise RuntimeError("an oracle worker failed")
+        out = np.array(np.load(opath))
+    return (t1 - t0) / max(steps, 1), out, cols
+
+
+def workload_state():
+    """The benchmark's input on the host: the seeded balanced state of the workload."""
+    import synthetic
+    from oracle.column import Column
+    from oracle.mesh import BoxMesh
+    m = BoxMesh(NEX, NEY, NEZ, N, LX, LY, LZ)
+    col = Column(m)
+    xg, yg, zg = m.coords()
+    return synthetic.balanced_state(xg, yg, zg, LX, LY, LZ, col.rho0, col.theta0, SEED)
+
+
+def oracle_workload(warmup, steps, nproc):
+    """The partitioned oracle on the whole benchmark workload: (s per step, procs, sample)."""
+    sec, _, cols = oracle_partitioned((NEX, NEY, NEZ, N, LX, LY, LZ), dt_for(C_MAIN),
+                                      workload_state(), nproc, warmup, steps)
+    full_cols = (NEX * N + 1) * (NEY * N + 1)
+    bl = oracle_blocks(NEX, NEY, nproc)
+    sample = ("the whole %dx%dx%d-element mesh (%d columns) every step: %d single-threaded "
+              "processes, each on a block of about %dx%d elements with a %d-element halo "
+              "(%.2fx the columns), %d timed ARK2 steps at C=15 from the same input after %d "
+              "untimed; time from the barrier that starts them to the one that ends them"
+              % (NEX, NEY, NEZ, full_cols, nproc, bl[0][1] - bl[0][0], bl[0][3] - bl[0][2],
+                 ORACLE_HALO, cols / full_cols, steps, warmup))
+    return sec, nproc, sample
+
+
+def cpu_baseline(seconds):
+    """The oracle, as it stands, on every host core over the whole workload: one timed ARK2
+    step of the full mesh after one untimed step (oracle_partitioned).  `seconds` is
+    unused: the sample is the whole mesh once."""
+    nproc = oracle_procs()
+    try:
+        sec, nproc, sample = oracle_workload(1, 1, nproc)
+    except Exception as e:
+        return {"value": None, "unit": "sim-s/wall-s", "cores": nproc, "kind": "oracle",
+                "sample": "failed: " + str(e)[:200]}
+    return {"value": dt_for(C_MAIN) / sec, "unit": "sim-s/wall-s", "cores": nproc,
+            "kind": "oracle", "ms_per_step": round(sec * 1e3, 1), "sample": sample}
 
 
 def run_reference(args):
@@ -963,16 +1186,10 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     nproc = oracle_procs()
-    outs = oracle_parallel("reference_worker(%d, %d)" % (args.warmup, args.steps), nproc,
-                           timeout=3600)
+    sec, nproc, sample = oracle_workload(args.warmup, args.steps, nproc)
     dt = dt_for(C_MAIN)
-    cols_per_s = sum(k * nc / el for el, k, nc in outs)
-    full_cols = (NEX * N + 1) * (NEY * N + 1)
-    ms_step = full_cols / cols_per_s * 1e3
-    value = dt / (ms_step / 1e3)
-    sample = ("one ARK2 step at C=15 per timed step on an 8x8x12-element window (%d of 148225 "
-              "columns) of the workload in each of %d single-threaded processes at once, "
-              "scaled by the column count" % (outs[0][2], nproc))
+    ms_step = sec * 1e3
+    value = dt / sec
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "sim-s/wall-s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
