@@ -1,4 +1,5 @@
-"""Small-case driver for Nsight Compute captures of the library's kernels.
+"""Small-case driver for Nsight Compute captures of the library's kernels (measurement
+support beside bench.py, not part of the package).
 
 Runs ``--steps`` HEVI 1D-IMEX ARK2 steps (and optionally RK35 steps) of the benchmark's
 workload shape on a smaller box: ``--nex`` x ``--nex`` x 12 elements of order 4 over
@@ -6,9 +7,8 @@ workload shape on a smaller box: ``--nex`` x ``--nex`` x 12 elements of order 4 
 gives a 164 MB state (larger than the 129 MB L2) and about 1.7 GB of device memory.
 Every step reads the same input and writes a separate output.
 
-  python -m paper_1702_04316_gb300.profile_case [--nex 72] [--steps 3] [--rk 0] [--adj 0]
-                                                [--precision mixed] [--scheme ark5]
-                                                [--solve 0] [--imex3d 0]
+  python profile_case.py [--nex 72] [--steps 3] [--rk 0] [--adj 0] [--precision mixed]
+                         [--scheme ark5] [--solve 0] [--imex3d 0]
 
 --adj K also runs K adjoint steps (numa_step_imex1d_adjoint) and K tangent-linear steps from
 the same input, for captures of the differentiation form's kernels.  --scheme selects the
@@ -22,7 +22,7 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
