@@ -830,6 +830,30 @@ def batching_form(pkg, torch, steps, warmup, nmembers=64, h_range=(8, 48), v_ran
     same = all(torch.equal(o, b.member(q1, m)) for m, (a, o) in enumerate(views))
     for g in ctxs:
         g.close()
+    # the bound of the work itself: per order, the time per node-step of one large member
+    # (48 x 48 x 12 elements, the biggest member shape, which fills the GPU), summed over the
+    # ensemble's nodes of that order
+    ns_node = {}
+    for n in sorted(set(Ns)):
+        nh, nz = h_range[1], 12
+        dtn = 15.0 * lgl_min_fraction(n) * (10e3 / nz) / C_S
+        gb = pkg.Numa(nh, nh, nz, 50e3 * nh, 50e3 * nh, 10e3, n, dtn)
+        qa = gb.empty_state().zero_()
+        qb = gb.empty_state()
+        for _ in range(warmup):
+            gb.step_imex1d(qa, qb, 1)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            gb.step_imex1d(qa, qb, 1)
+        e1.record()
+        e1.synchronize()
+        ns_node[n] = e0.elapsed_time(e1) / steps * 1e6 / gb.nnode
+        gb.close()
+    node_counts = {}
+    for m, n in enumerate(Ns):
+        node_counts[n] = node_counts.get(n, 0) + b.member_query(m, pkg.Q_NNODE)
+    ms_bound = sum(node_counts[n] * ns_node[n] for n in node_counts) / 1e6
     b.close()
     sim = float(np.sum(dts))
     norders = len(set(Ns))
@@ -844,6 +868,12 @@ def batching_form(pkg, torch, steps, warmup, nmembers=64, h_range=(8, 48), v_ran
             "one_context_at_a_time": {"ms_per_step": round(ms_seq, 3),
                                       "launches_per_step": 8 * nmembers},
             "speedup": round(ms_seq / ms_batch, 3), "identical_to_single_contexts": same,
+            "work_bound": {"ns_per_node_step_by_order": {str(k): round(v, 4) for k, v in ns_node.items()},
+                           "nodes_by_order": {str(k): int(v) for k, v in node_counts.items()},
+                           "ms_per_step": round(ms_bound, 3),
+                           "ensemble_over_bound": round(ms_batch / ms_bound, 3),
+                           "note": "each order's time per node-step in one 48x48x12-element "
+                                   "context, summed over the ensemble's nodes of that order"},
             "finite": finite}
 
 
