@@ -149,6 +149,11 @@ __device__ __forceinline__ void rhs_point(long long g, int ix, int iy, int iz, c
                                           const RT* dz, OT* out0, double* out, const Geom& G,
                                           const RefLev& R, const RhsEpilogue& ep);
 
+template <typename RT, typename OT>
+__device__ __forceinline__ void rhs_store(long long g, const RT* t, const double* __restrict__ q,
+                                          OT* out0, double* out, const Geom& G,
+                                          const RhsEpilogue& ep);
+
 // The same with rho', u, v, w at g given as values.
 template <typename RT, typename OT>
 __device__ __forceinline__ void rhs_point_v(long long g, int ix, int iy, int iz,
@@ -156,7 +161,6 @@ __device__ __forceinline__ void rhs_point_v(long long g, int ix, int iy, int iz,
                                             RT w_, const RT* dx, const RT* dy, const RT* dz,
                                             OT* out0, double* out, const Geom& G, const RefLev& R,
                                             const RhsEpilogue& ep) {
-  const long long nn = G.nnode;
   const RT rho = (RT)R.rho0[iz] + r_;
   const RT irho = (RT)1 / rho;
   const RT grav = (RT)NUMA_GRAV;
@@ -171,6 +175,16 @@ __device__ __forceinline__ void rhs_point_v(long long g, int ix, int iy, int iz,
   if (iz == 0 || iz == G.M - 1) t_w = (RT)0;
 
   const RT t[5] = {t_r, t_u, t_v, t_w, t_t};
+  rhs_store<RT, OT>(g, t, q, out0, out, G, ep);
+}
+
+// The epilogue of a right-hand side at node g: mode 0 writes the tendencies t (to out0);
+// modes 1-3 combine them with states and earlier tendencies into out (RhsEpilogue).
+template <typename RT, typename OT>
+__device__ __forceinline__ void rhs_store(long long g, const RT* t, const double* __restrict__ q,
+                                          OT* out0, double* out, const Geom& G,
+                                          const RhsEpilogue& ep) {
+  const long long nn = G.nnode;
   if (ep.mode == 0) {
 #pragma unroll
     for (int f = 0; f < 5; ++f) out0[f * nn + g] = (OT)t[f];

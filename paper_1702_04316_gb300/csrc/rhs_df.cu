@@ -1,13 +1,14 @@
 // Double-float ("DF") variant of the explicit right-hand side (precision NUMA_PREC_DF).
 //
 // GB300 issues FP64 at 2 FMA per clock per SM and FP32 at 128, and the FP64 right-hand side
-// is bound by the FP64 pipe (93 % busy).  Its bulk is the DSS'd derivative sums (about 90
-// multiply-adds per node at N = 4).  Here those sums run in double-float arithmetic: every
-// value is an unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits), the
-// products by Dekker's method (the exact residual of a product from one fused
-// multiply-add) and the sums by Knuth's TwoSum, with the low-order parts accumulated
-// without renormalisation and the pair rounded to FP64 once per derivative.  The pointwise
-// Set2NC terms, the equation of state and the state stay FP64 (rhs_point).
+// is bound by the FP64 pipe (93 % busy).  Here the derivative sums (about 90 multiply-adds
+// per node at N = 4) and the pointwise products of the Set2NC tendencies (u.grad f,
+// rho div u, grad P' / rho) run in double-float arithmetic: every value is an unevaluated
+// sum hi + lo of two FP32 numbers (about 48 significant bits), products by Dekker's method
+// (the exact residual of a product from one fused multiply-add), sums by Knuth's TwoSum,
+// the low-order parts accumulated without renormalisation.  FP64 is left with rho, 1 / rho,
+// g rho', the five tendencies formed from their pairs, and the epilogue; the equation of
+// state, the column solves and the state stay FP64.
 //
 // A pre-pass writes every stencil field -- rho', u, v, w, theta' and P' from the FP64
 // equation of state -- as a (hi, lo) pair of FP32 numbers (see split): 8 bytes per value, as
@@ -80,10 +81,20 @@ __device__ __forceinline__ double widen(float f) {
   return __longlong_as_double((long long)b);
 }
 
-// The six fields' derivatives along one axis with K taps (the class's exact count).
+// (ah, al) += (bh + bl) for a pair whose parts need not be normalised: TwoSum of the high
+// parts, the low parts added to the low accumulator.
+__device__ __forceinline__ void df_add(float bh, float bl, float& ah, float& al) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(e, bl));
+}
+
+// The six fields' derivatives along one axis with K taps (the class's exact count), as
+// unnormalised (hi, lo) pairs.
 template <int K, int N>
 __device__ __forceinline__ void derivs_df(const float2* const* F, long long g, long long stride,
-                                          const Taps<N, float2>& T, double* d) {
+                                          const Taps<N, float2>& T, float2* d) {
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const float2* p = F[f] + g;
@@ -93,16 +104,27 @@ __device__ __forceinline__ void derivs_df(const float2* const* F, long long g, l
       const float2 v = __ldg(p + T.o[t] * stride);
       df_mac(T.c[t].x, T.c[t].y, v.x, v.y, ah, al);
     }
-    d[f] = widen(ah) + widen(al);
+    d[f] = make_float2(ah, al);
   }
 }
 
 template <int N>
 __device__ __forceinline__ void axis_derivs_df(const float2* const* F, long long g, long long stride,
-                                               int cls, const Taps<N, float2>& T, double* d) {
+                                               int cls, const Taps<N, float2>& T, float2* d) {
   if (cls == CLS_IFACE) derivs_df<2 * N, N>(F, g, stride, T, d);
   else if (cls == CLS_WALL) derivs_df<N + 1, N>(F, g, stride, T, d);
   else derivs_df<N, N>(F, g, stride, T, d);
+}
+
+// The pointwise products of one axis a (velocity component X = u, v or w) folded into the
+// tendency accumulators A (rho', u, v, w, theta') and the divergence DV:
+//   A_f += X d_f (f = 0..4),  DV += d_{1+a},  A_{1+a} += (1 / rho) d_5.
+__device__ __forceinline__ void fold_axis(int a, float2 X, float2 IR, const float2* d, float2* A,
+                                          float2& DV) {
+#pragma unroll
+  for (int f = 0; f < 5; ++f) df_mac(X.x, X.y, d[f].x, d[f].y, A[f].x, A[f].y);
+  df_add(d[1 + a].x, d[1 + a].y, DV.x, DV.y);
+  df_mac(IR.x, IR.y, d[5].x, d[5].y, A[1 + a].x, A[1 + a].y);
 }
 
 // P' from the FP64 equation of state, and the (hi, lo) pairs of the six stencil fields.
@@ -116,8 +138,11 @@ __global__ void k_prep_df(const double* __restrict__ q, float2* __restrict__ F2,
   F2[5 * nn + g] = split(eos_node(q, g, G, R, S));
 }
 
+// Five 128-thread CTAs per SM (at most 102 registers): measured fastest against three, four,
+// six and eight (1.12 against 1.39, 1.20, 1.17 and 1.17 ms per launch on the 96 x 96 x 12
+// workload); the spill this costs is eight bytes.
 template <int N>
-__global__ void k_rhs_df(const double* __restrict__ q, const float2* __restrict__ F2, double* out0,
+__global__ void __launch_bounds__(128, 5) k_rhs_df(const double* __restrict__ q, const float2* __restrict__ F2, double* out0,
                          double* out, const int* __restrict__ perm, long long nthreads, Geom G,
                          Coef3 C, RefLev R, RhsEpilogue ep) {
   constexpr int Nq = N + 1;
@@ -144,17 +169,43 @@ __global__ void k_rhs_df(const double* __restrict__ q, const float2* __restrict_
   const int iy = (int)(col / G.nxg);
   const int ix = (int)(col - (long long)iy * G.nxg);
   const float2* Fld[6] = {F2, F2 + nn, F2 + 2 * nn, F2 + 3 * nn, F2 + 4 * nn, F2 + 5 * nn};
-  double dx[6], dy[6], dz[6];
+  // FP64: rho = rho0 + rho', 1 / rho and g rho'; everything else in pairs
+  const double r_ = q[g];
+  const double rho = R.rho0[iz] + r_;
+  const double irho = 1.0 / rho;
+  const float2 U = split(q[nn + g]), V = split(q[2 * nn + g]), W = split(q[3 * nn + g]);
+  const float2 IR = split(irho);
+  float2 A[5], DV = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) A[f] = make_float2(0.0f, 0.0f);
   {
     Taps<N, float2> T;
+    float2 d[6];
     int cls = axis_taps<N, float2>(ix, G.nex, sD, sDl, sDr, T);
-    axis_derivs_df<N>(Fld, g, G.M, cls, T, dx);
+    axis_derivs_df<N>(Fld, g, G.M, cls, T, d);
+    fold_axis(0, U, IR, d, A, DV);
     cls = axis_taps<N, float2>(iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
-    axis_derivs_df<N>(Fld, g, (long long)G.nxg * G.M, cls, T, dy);
+    axis_derivs_df<N>(Fld, g, (long long)G.nxg * G.M, cls, T, d);
+    fold_axis(1, V, IR, d, A, DV);
     cls = axis_taps<N, float2>(iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
-    axis_derivs_df<N>(Fld, g, 1, cls, T, dz);
+    axis_derivs_df<N>(Fld, g, 1, cls, T, d);
+    // the reference gradients and the buoyancy join the vertical derivatives
+    const float2 dr0 = split(R.drho0[iz]), dt0 = split(R.dtheta0[iz]), gr = split(NUMA_GRAV * r_);
+    df_add(dr0.x, dr0.y, d[0].x, d[0].y);
+    df_add(dt0.x, dt0.y, d[4].x, d[4].y);
+    df_add(gr.x, gr.y, d[5].x, d[5].y);
+    fold_axis(2, W, IR, d, A, DV);
   }
-  rhs_point<double, double, double>(g, ix, iy, iz, q, q, dx, dy, dz, out0, out, G, R, ep);
+  const float2 RH = split(rho);
+  df_mac(RH.x, RH.y, DV.x, DV.y, A[0].x, A[0].y);
+  double t[5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) t[f] = -(widen(A[f].x) + widen(A[f].y));
+  // walls: no normal flow
+  if (ix == 0 || ix == G.nxg - 1) t[1] = 0.0;
+  if (iy == 0 || iy == G.nyg - 1) t[2] = 0.0;
+  if (iz == 0 || iz == G.M - 1) t[3] = 0.0;
+  rhs_store<double, double>(g, t, q, out0, out, G, ep);
 }
 
 }  // namespace
