@@ -473,8 +473,13 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
   // FP64: S1 still holds w_a, so it becomes w = w_a - w_p(P) here; the mixed form used S1 as
   // scratch and keeps w_p(P) (phase 3 recomputes w_a)
   level_loop([&](int lev, int c) {
-    const double wp = col_wp<N, double>(S0 + c, T, lev, R, tb);
-    S1[lev * T + c] = MIXED ? wp : S1[lev * T + c] - wp;
+    if (MIXED) {
+      S1[lev * T + c] = col_wp<N, double>(S0 + c, T, lev, R, tb);
+    } else {   // w_a - (kp1 D_z P + kp2 P), the subtraction folded into the multiply-adds
+      const double dzp = col_dz<N, double>(S0 + c, T, lev, R);
+      S1[lev * T + c] = fma(-__ldg(tb.kp1 + lev), dzp,
+                            fma(-__ldg(tb.kp2 + lev), S0[lev * T + c], S1[lev * T + c]));
+    }
   });
   __syncthreads();
 

@@ -14,6 +14,8 @@
 // equation of state -- as a (hi, lo) pair of FP32 numbers (see split): 8 bytes per value, as
 // a double, so the stencil reads the same bytes as the FP64 kernel.  The derivative rows are
 // split the same way, once per CTA, into shared memory.
+#include <algorithm>
+
 #include "numa_internal.cuh"
 #include "rhs_device.cuh"
 
@@ -116,17 +118,6 @@ __device__ __forceinline__ void axis_derivs_df(const float2* const* F, long long
   else derivs_df<N, N>(F, g, stride, T, d);
 }
 
-// The pointwise products of one axis a (velocity component X = u, v or w) folded into the
-// tendency accumulators A (rho', u, v, w, theta') and the divergence DV:
-//   A_f += X d_f (f = 0..4),  DV += d_{1+a},  A_{1+a} += (1 / rho) d_5.
-__device__ __forceinline__ void fold_axis(int a, float2 X, float2 IR, const float2* d, float2* A,
-                                          float2& DV) {
-#pragma unroll
-  for (int f = 0; f < 5; ++f) df_mac(X.x, X.y, d[f].x, d[f].y, A[f].x, A[f].y);
-  df_add(d[1 + a].x, d[1 + a].y, DV.x, DV.y);
-  df_mac(IR.x, IR.y, d[5].x, d[5].y, A[1 + a].x, A[1 + a].y);
-}
-
 // P' from the FP64 equation of state, and the (hi, lo) pairs of the six stencil fields.
 __global__ void k_prep_df(const double* __restrict__ q, float2* __restrict__ F2, Geom G, RefLev R,
                           EosSeries S) {
@@ -138,31 +129,16 @@ __global__ void k_prep_df(const double* __restrict__ q, float2* __restrict__ F2,
   F2[5 * nn + g] = split(eos_node(q, g, G, R, S));
 }
 
-// Five 128-thread CTAs per SM (at most 102 registers): measured fastest against three, four,
-// six and eight (1.12 against 1.39, 1.20, 1.17 and 1.17 ms per launch on the 96 x 96 x 12
-// workload); the spill this costs is eight bytes.
+// One node of the right-hand side (g, at ix, iy, iz).  The three axes run through one copy of
+// the derivative code (a loop that is not unrolled): three unrolled copies, each with its three
+// tap-count variants, overflowed the instruction cache (ncu: "no instruction" stalls).
 template <int N>
-__global__ void __launch_bounds__(128, 5) k_rhs_df(const double* __restrict__ q, const float2* __restrict__ F2, double* out0,
-                         double* out, const int* __restrict__ perm, long long nthreads, Geom G,
-                         Coef3 C, RefLev R, RhsEpilogue ep) {
+__device__ __forceinline__ void rhs_df_node(long long g, const double* __restrict__ q,
+                                            const float2* __restrict__ F2, double* out0,
+                                            double* out, const Geom& G, const RefLev& R,
+                                            const RhsEpilogue& ep, const float2* sD,
+                                            const float2* sDl, const float2* sDr) {
   constexpr int Nq = N + 1;
-  __shared__ float2 sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
-  for (int t = threadIdx.x; t < Nq * Nq; t += blockDim.x) {
-    sD[t] = split(C.x.D[t]);
-    sD[Nq * Nq + t] = split(C.y.D[t]);
-    sD[2 * Nq * Nq + t] = split(C.z.D[t]);
-  }
-  for (int t = threadIdx.x; t < Nq; t += blockDim.x) {
-    sDl[t] = split(C.x.Dl[t]); sDr[t] = split(C.x.Dr[t]);
-    sDl[Nq + t] = split(C.y.Dl[t]); sDr[Nq + t] = split(C.y.Dr[t]);
-    sDl[2 * Nq + t] = split(C.z.Dl[t]); sDr[2 * Nq + t] = split(C.z.Dr[t]);
-  }
-  __syncthreads();
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (tid >= nthreads) return;
-  const int gi = perm[tid];
-  if (gi < 0) return;
-  const long long g = gi;
   const long long nn = G.nnode;
   const long long col = g / G.M;
   const int iz = (int)(g - col * G.M);
@@ -178,23 +154,32 @@ __global__ void __launch_bounds__(128, 5) k_rhs_df(const double* __restrict__ q,
   float2 A[5], DV = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int f = 0; f < 5; ++f) A[f] = make_float2(0.0f, 0.0f);
-  {
+  // axis a: the six derivatives d, then  A_f += X d_f (X = u, v, w),  DV += d_{1+a},
+  // A_{1+a} += (1 / rho) d_5
+#pragma unroll 1
+  for (int a = 0; a < 3; ++a) {
+    const int ia = a == 0 ? ix : (a == 1 ? iy : iz);
+    const int nel = a == 0 ? G.nex : (a == 1 ? G.ney : G.nez);
+    const long long stride = a == 0 ? (long long)G.M : (a == 1 ? (long long)G.nxg * G.M : 1LL);
     Taps<N, float2> T;
+    const int cls = axis_taps<N, float2>(ia, nel, sD + a * Nq * Nq, sDl + a * Nq, sDr + a * Nq, T);
     float2 d[6];
-    int cls = axis_taps<N, float2>(ix, G.nex, sD, sDl, sDr, T);
-    axis_derivs_df<N>(Fld, g, G.M, cls, T, d);
-    fold_axis(0, U, IR, d, A, DV);
-    cls = axis_taps<N, float2>(iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
-    axis_derivs_df<N>(Fld, g, (long long)G.nxg * G.M, cls, T, d);
-    fold_axis(1, V, IR, d, A, DV);
-    cls = axis_taps<N, float2>(iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
-    axis_derivs_df<N>(Fld, g, 1, cls, T, d);
-    // the reference gradients and the buoyancy join the vertical derivatives
-    const float2 dr0 = split(R.drho0[iz]), dt0 = split(R.dtheta0[iz]), gr = split(NUMA_GRAV * r_);
-    df_add(dr0.x, dr0.y, d[0].x, d[0].y);
-    df_add(dt0.x, dt0.y, d[4].x, d[4].y);
-    df_add(gr.x, gr.y, d[5].x, d[5].y);
-    fold_axis(2, W, IR, d, A, DV);
+    axis_derivs_df<N>(Fld, g, stride, cls, T, d);
+    if (a == 2) {   // the reference gradients and the buoyancy join the vertical derivatives
+      const float2 dr0 = split(R.drho0[iz]), dt0 = split(R.dtheta0[iz]);
+      const float2 gr = split(NUMA_GRAV * r_);
+      df_add(dr0.x, dr0.y, d[0].x, d[0].y);
+      df_add(dt0.x, dt0.y, d[4].x, d[4].y);
+      df_add(gr.x, gr.y, d[5].x, d[5].y);
+    }
+    const float2 X = a == 0 ? U : (a == 1 ? V : W);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) df_mac(X.x, X.y, d[f].x, d[f].y, A[f].x, A[f].y);
+    const float2 dv = a == 0 ? d[1] : (a == 1 ? d[2] : d[3]);
+    df_add(dv.x, dv.y, DV.x, DV.y);
+#pragma unroll
+    for (int f = 1; f <= 3; ++f)
+      if (f == 1 + a) df_mac(IR.x, IR.y, d[5].x, d[5].y, A[f].x, A[f].y);
   }
   const float2 RH = split(rho);
   df_mac(RH.x, RH.y, DV.x, DV.y, A[0].x, A[0].y);
@@ -208,6 +193,39 @@ __global__ void __launch_bounds__(128, 5) k_rhs_df(const double* __restrict__ q,
   rhs_store<double, double>(g, t, q, out0, out, G, ep);
 }
 
+// Five 128-thread CTAs per SM (at most 102 registers): measured fastest against three, four,
+// six and eight.  Each CTA splits the derivative rows into shared memory once and then walks
+// 128-node chunks of the thread order with a grid stride (a grid of five CTAs per SM), so the
+// split and its barrier are not repeated for every 128 nodes.
+template <int N>
+__global__ void __launch_bounds__(128, 5) k_rhs_df(const double* __restrict__ q,
+                                                   const float2* __restrict__ F2, double* out0,
+                                                   double* out, const int* __restrict__ perm,
+                                                   long long nthreads, Geom G, Coef3 C, RefLev R,
+                                                   RhsEpilogue ep) {
+  constexpr int Nq = N + 1;
+  __shared__ float2 sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
+  for (int t = threadIdx.x; t < Nq * Nq; t += blockDim.x) {
+    sD[t] = split(C.x.D[t]);
+    sD[Nq * Nq + t] = split(C.y.D[t]);
+    sD[2 * Nq * Nq + t] = split(C.z.D[t]);
+  }
+  for (int t = threadIdx.x; t < Nq; t += blockDim.x) {
+    sDl[t] = split(C.x.Dl[t]); sDr[t] = split(C.x.Dr[t]);
+    sDl[Nq + t] = split(C.y.Dl[t]); sDr[Nq + t] = split(C.y.Dr[t]);
+    sDl[2 * Nq + t] = split(C.z.Dl[t]); sDr[2 * Nq + t] = split(C.z.Dr[t]);
+  }
+  __syncthreads();
+  const long long nchunk = (nthreads + blockDim.x - 1) / blockDim.x;
+  for (long long c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const long long tid = c * blockDim.x + threadIdx.x;
+    if (tid >= nthreads) continue;
+    const int gi = perm[tid];
+    if (gi < 0) continue;                 // padding of a class group
+    rhs_df_node<N>(gi, q, F2, out0, out, G, R, ep, sD, sDl, sDr);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_prep_df(const double* q, float2* F2, const Geom& G, const RefLev& R,
@@ -219,7 +237,14 @@ cudaError_t launch_prep_df(const double* q, float2* F2, const Geom& G, const Ref
 cudaError_t launch_rhs_df(const double* q, const float2* F2, double* out, const int* perm,
                           long long nthreads, const Geom& G, const Coef3& C, const RefLev& R,
                           const RhsEpilogue& ep, cudaStream_t s) {
-  const unsigned nb = (unsigned)((nthreads + 127) / 128);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 152;
+  }
+  const unsigned nb = (unsigned)std::min<long long>((nthreads + 127) / 128, 5LL * nsm);
 #define NUMA_DF_CASE(n) \
   case n: k_rhs_df<n><<<nb, 128, 0, s>>>(q, F2, out, out, perm, nthreads, G, C, R, ep); break;
   switch (G.N) {
