@@ -122,14 +122,14 @@ class PartitionedHEVI:
                 (slice(wy0 * N + y0, wy0 * N + y1), slice(wx0 * N + x0, wx0 * N + x1)))
 
     def restrict(self, q_global):
-        """The window's part of a global state (5, nyg, nxg, M) or (5, nnode) array/tensor,
-        as a (5, nnode_window) contiguous copy."""
+        """The window's part of a global state ((5, nyg, nxg, M) or (5, nnode); a numpy
+        array or a torch tensor), as a (5, nnode_window) contiguous copy."""
         nex, ney, nez, _, _, _, N = self.global_dims
-        M = nez * N + 1
-        q = q_global.reshape(5, ney * N + 1, nex * N + 1, M)
         sy, sx = self.window_slices()
-        return q[:, sy, sx, :].reshape(5, -1).clone() if hasattr(q, "clone") else \
-            np.ascontiguousarray(q[:, sy, sx, :]).reshape(5, -1)
+        q = q_global.reshape(5, ney * N + 1, nex * N + 1, nez * N + 1)[:, sy, sx, :]
+        if isinstance(q, np.ndarray):
+            return np.array(q, copy=True).reshape(5, -1)
+        return q.clone(memory_format=self.ctx._torch.contiguous_format).reshape(5, -1)
 
     def owned(self, q_window):
         """The owned node columns of a window state, as (5, ny_own, nx_own, M)."""
