@@ -237,60 +237,78 @@ __device__ __forceinline__ double col_dzT(const double* v, int T, int j, int M, 
 
 // Solve S^T x = b in place for one column (stride T), S = L U in the stored layout:
 // U^T y = b by forward substitution (row i of U^T is stored column i of U: the entries
-// U(i-k, i), k = 1..HB, and 1/U(i,i)), then L^T x = y by back substitution (row i of L^T is
-// stored column i of L).  The last HB values of the recurrence stay in registers, and the
-// factor row of the next step is loaded while the current one is used.
-template <int HB>
+// U(i-k, i), k = 1..2N, and 1/U(i,i)), then L^T x = y by back substitution (row i of L^T is
+// stored column i of L).  The last 2N values of the recurrence stay in registers, and the
+// factor row of the next step is loaded while the current one is used.  Only the entries
+// inside the factors' envelope are read and used (env_u, env_l: the stored entries beyond
+// are exact zeros); the level loops run in blocks of N so that each level's count is a
+// compile-time constant (r = i mod N, and M - 1 = nez N).
+template <int N>
 __device__ __forceinline__ void col_solve_T(double* x, int T, int M, const double* __restrict__ L,
                                             const double* __restrict__ U, long long col) {
+  constexpr int HB = 2 * N;
   const double* Lb = L + fac_col_base(col, M, HB);
   const double* Ub = U + fac_col_base(col, M, HB + 1);
-  double z[HB], f[HB + 1], fn[HB + 1];
+  double z[HB], fn[HB + 1];
 #pragma unroll
   for (int k = 0; k < HB; ++k) z[k] = 0.0;          // z[k] = y_{i-1-k}
 #pragma unroll
-  for (int k = 0; k <= HB; ++k) fn[k] = __ldg(Ub + (long long)k * kFacBlk);
+  for (int k = 0; k <= env_u(N, 0); ++k) fn[k] = __ldg(Ub + (long long)k * kFacBlk);
 #pragma unroll 1
-  for (int i = 0; i < M; ++i) {
+  for (int i0 = 0; i0 < M; i0 += N) {
+    static_for<N>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      constexpr int nu = env_u(N, r), nn = env_u(N, (r + 1) % N);
+      const int i = i0 + r;
+      if (i >= M) return;
+      double f[HB + 1];
 #pragma unroll
-    for (int k = 0; k <= HB; ++k) f[k] = fn[k];
-    if (i + 1 < M) {
-      const double* Uc = Ub + (long long)(i + 1) * (HB + 1) * kFacBlk;
+      for (int k = 0; k <= nu; ++k) f[k] = fn[k];
+      if (i + 1 < M) {
+        const double* Uc = Ub + (long long)(i + 1) * (HB + 1) * kFacBlk;
 #pragma unroll
-      for (int k = 0; k <= HB; ++k) fn[k] = __ldg(Uc + (long long)k * kFacBlk);
-    }
-    double acc = x[i * T];
+        for (int k = 0; k <= nn; ++k) fn[k] = __ldg(Uc + (long long)k * kFacBlk);
+      }
+      double acc = x[i * T];
 #pragma unroll
-    for (int k = 1; k <= HB; ++k) acc = fma(-f[k], z[k - 1], acc);
-    const double y = acc * f[0];
-    x[i * T] = y;
+      for (int k = 1; k <= nu; ++k) acc = fma(-f[k], z[k - 1], acc);
+      const double y = acc * f[0];
+      x[i * T] = y;
 #pragma unroll
-    for (int k = HB - 1; k > 0; --k) z[k] = z[k - 1];
-    z[0] = y;
+      for (int k = HB - 1; k > 0; --k) z[k] = z[k - 1];
+      z[0] = y;
+    });
   }
 #pragma unroll
   for (int k = 0; k < HB; ++k) z[k] = 0.0;          // z[k] = x_{i+1+k}
   {
     const double* Lc = Lb + (long long)(M - 1) * HB * kFacBlk;
 #pragma unroll
-    for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * kFacBlk);
+    for (int k = 0; k < env_l(N, 0); ++k) fn[k] = __ldg(Lc + (long long)k * kFacBlk);
   }
 #pragma unroll 1
-  for (int i = M - 1; i >= 0; --i) {
+  for (int t0 = 0; t0 < M; t0 += N) {
+    static_for<N>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      constexpr int nl = env_l(N, (N - s) % N), nn = env_l(N, (N - (s + 1) % N) % N);
+      const int i = M - 1 - (t0 + s);
+      if (i < 0) return;
+      double f[HB];
 #pragma unroll
-    for (int k = 0; k < HB; ++k) f[k] = fn[k];
-    if (i > 0) {
-      const double* Lc = Lb + (long long)(i - 1) * HB * kFacBlk;
+      for (int k = 0; k < nl; ++k) f[k] = fn[k];
+      if (i > 0) {
+        const double* Lc = Lb + (long long)(i - 1) * HB * kFacBlk;
 #pragma unroll
-      for (int k = 0; k < HB; ++k) fn[k] = __ldg(Lc + (long long)k * kFacBlk);
-    }
-    double acc = x[i * T];
+        for (int k = 0; k < nn; ++k) fn[k] = __ldg(Lc + (long long)k * kFacBlk);
+      }
+      double acc = x[i * T];
 #pragma unroll
-    for (int k = 1; k <= HB; ++k) acc = fma(-f[k - 1], z[k - 1], acc);
-    x[i * T] = acc;
+      for (int k = 1; k <= nl; ++k) acc = fma(-f[k - 1], z[k - 1], acc);
+      x[i * T] = acc;
 #pragma unroll
-    for (int k = HB - 1; k > 0; --k) z[k] = z[k - 1];
-    z[0] = acc;
+      for (int k = HB - 1; k > 0; --k) z[k] = z[k - 1];
+      z[0] = acc;
+    });
   }
 }
 
@@ -310,7 +328,7 @@ __global__ void k_solve_T(const double* __restrict__ b, double* __restrict__ x, 
   }
   __syncthreads();
   if ((int)threadIdx.x < ncols)
-    col_solve_T<2 * N>(sm + threadIdx.x, T, M, F.L, F.U, col0 + threadIdx.x);
+    col_solve_T<N>(sm + threadIdx.x, T, M, F.L, F.U, col0 + threadIdx.x);
   __syncthreads();
   for (int j = threadIdx.x; j < cnt; j += NT) {
     const int c = j / M, lev = j - c * M;
@@ -378,7 +396,7 @@ __global__ void k_stage_adj(const double* __restrict__ lam, double* __restrict__
     double* p = P + t;
     for (int lev = 0; lev < M; ++lev)   // P* += kp2 w_p* + D_z^T (kp1 w_p*)
       p[lev * T] += fma(-__ldg(tb.kp2 + lev), wt[lev * T], col_dzT<N>(a, T, lev, M, R));
-    col_solve_T<2 * N>(p, T, M, F.L, F.U, col0 + t);      // b* = S^-T P*
+    col_solve_T<N>(p, T, M, F.L, F.U, col0 + t);          // b* = S^-T P*
     for (int lev = 0; lev < M; ++lev) a[lev * T] = __ldg(tb.kD + lev) * p[lev * T];
     for (int lev = 0; lev < M; ++lev)   // w_a* = w* - kF b* - D_z^T (kD b*)
       wt[lev * T] -= fma(__ldg(tb.kF + lev), p[lev * T], col_dzT<N>(a, T, lev, M, R));

@@ -87,3 +87,24 @@ def test_ark_tableaux_match_the_oracle_bitwise(scheme):
     assert np.array_equal(a, A) and np.array_equal(at, AT) and np.array_equal(b, B)
     a2, at2, b2 = pkg.ark_tableau("ark2")
     np.testing.assert_allclose(at2, ark2.tableau()[1], rtol=0, atol=1e-15)
+
+
+def test_partition_plan_rejects_bad_grids_without_a_gpu(pkg):
+    """numa_part_plan is host only: bad grids are rejected, good ones planned, no device."""
+    L = pkg.lib()
+    g = pkg.MeshDesc(8, 6, 2, 8e3, 6e3, 4e3, 300.0, 0.0)
+    info = pkg.PartInfo()
+    for px, py, rank in [(0, 1, 0), (2, 2, 4), (2, 2, -1), (5, 1, 0), (1, 4, 0)]:
+        d = pkg.PartDesc(px, py, rank)       # (5, 1) and (1, 4): rectangles narrower than 2
+        assert L.numa_part_plan(ctypes.byref(g), 3, ctypes.byref(d), ctypes.byref(info)) == 1
+    d = pkg.PartDesc(2, 3, 5)
+    assert L.numa_part_plan(ctypes.byref(g), 3, ctypes.byref(d), ctypes.byref(info)) == 0
+    assert (info.ex0, info.ex1, info.ey0, info.ey1) == (4, 8, 4, 6)
+    assert (info.wx0, info.wx1, info.wy0, info.wy1) == (3, 8, 3, 6)
+    assert info.window.nex == 5 and info.window.ney == 3 and info.window.nez == 2
+    assert info.window.Lx / info.window.nex == 8e3 / 8      # the element size, bit for bit
+    assert info.nneigh == 3 and list(info.neigh[:3]) == [2, 3, 4]
+    one = pkg.PartDesc(1, 1, 0)
+    assert L.numa_part_plan(ctypes.byref(g), 3, ctypes.byref(one), ctypes.byref(info)) == 0
+    assert info.nneigh == 0 and (info.own_x1, info.own_y1) == (25, 19)
+    assert L.numa_part_columns(ctypes.byref(g), 3, ctypes.byref(d), 3, None, None) == 1

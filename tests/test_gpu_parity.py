@@ -302,3 +302,18 @@ def test_host_buffer_driver(pkg, torch):
     g.run_host(0, qh, 1)
     ref = ark2.HEVI(case.mesh, case.col, dt).step(q0, 1)
     assert np.all(rel_l2(qh.numpy(), ref) <= RUN_TOL)
+
+
+def test_stage_rejects_an_output_overlapping_an_input():
+    """The fused stage parks intermediate values in its output, so numa_imex_stage and
+    numa_imex_stage_s refuse an output that overlaps an input."""
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    g = pkg.Numa(3, 3, 2, 30e3, 30e3, 8e3, 3, 1.0)
+    q = torch.zeros(5, g.nnode, dtype=torch.float64, device="cuda")
+    R1 = torch.zeros_like(q)
+    with pytest.raises(pkg.NumaError):
+        g.imex_stage(2, q, R1, out=q)
+    with pytest.raises(pkg.NumaError):
+        g.imex_stage(2, q, R1, out=R1)
+    g.close()

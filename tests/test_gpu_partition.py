@@ -112,3 +112,20 @@ def test_gather_scatter_columns():
     assert g.status() == pkg.NUMA_ERR_ARG
     assert torch.equal(buf[:M], fields[0].view(ncol, M)[1])
     g.close()
+
+
+def test_phased_step_rejects_what_it_cannot_run():
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    g = pkg.Numa(3, 3, 2, 30e3, 30e3, 8e3, 3, 1.0, scheme="ark3")
+    q = torch.zeros(5, g.nnode, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.NumaError):
+        g.step_phase(0, q)
+    g.close()
+    g = pkg.Numa(3, 3, 2, 30e3, 30e3, 8e3, 3, 1.0)
+    q2, _, _, _ = g.step_buffers()
+    with pytest.raises(pkg.NumaError):      # the input may not be a stage buffer
+        g.step_phase(0, q2)
+    with pytest.raises(pkg.NumaError):
+        g.step_phase(3, q)
+    g.close()
