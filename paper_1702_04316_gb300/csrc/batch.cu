@@ -112,9 +112,11 @@ __global__ void k_batch_rhs(const MemberDev* __restrict__ md, WorkList W, int sr
 }
 
 // T columns per work item; blockDim.x >= T threads share the stage's coalesced phases.
+// The stage writes P' of its output for the next right-hand side (as the single-mesh step
+// does), so the ensemble's step needs the equation-of-state pass only at its start.
 template <int N, bool S3>
 __global__ void k_batch_stage(const MemberDev* __restrict__ md, WorkList W, const double* qin,
-                              int T) {
+                              int T, EosSeries eos) {
   extern __shared__ double sm[];
   for (long long item = blockIdx.x; item < W.nitems; item += gridDim.x) {
     const int k = find_slot(W, item);
@@ -122,7 +124,7 @@ __global__ void k_batch_stage(const MemberDev* __restrict__ md, WorkList W, cons
     const long long col0 = (item - W.start[k]) * T;
     stage_body<N, S3 ? 2 : 1, false, double>(col0, T, sm, qin + d.soff, d.R1, d.R2, d.q2,
                                               S3 ? d.q3 : d.q2, d.G, d.R, d.F, S3 ? d.s3 : d.s2,
-                                              d.tb, 0);
+                                              d.tb, 0, nullptr, nullptr, d.Pp, &eos);
     __syncthreads();
   }
 }
@@ -280,8 +282,9 @@ void launch_group_rhs(numa_batch* b, const OrderGroup& g, int src, int mode, con
 template <int N>
 void launch_group_stage(numa_batch* b, const OrderGroup& g, bool s3, const double* qin,
                         cudaStream_t s) {
-  if (s3) k_batch_stage<N, true><<<g.grid_col, g.stage_threads(), g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin, g.col_tile);
-  else k_batch_stage<N, false><<<g.grid_col, g.stage_threads(), g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin, g.col_tile);
+  const EosSeries S = eos_series();
+  if (s3) k_batch_stage<N, true><<<g.grid_col, g.stage_threads(), g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin, g.col_tile, S);
+  else k_batch_stage<N, false><<<g.grid_col, g.stage_threads(), g.stage_smem, s>>>(b->d_md, g.col_list.dev(), qin, g.col_tile, S);
 }
 
 void enqueue_rhs_all(numa_batch* b, int src, int mode, const double* qin, double* qout, cudaStream_t s) {
@@ -307,11 +310,9 @@ int enqueue_step(numa_batch* b, const double* qin, double* qout, cudaStream_t s)
   const WorkList Wn = b->node_list.dev();
   k_batch_pressure<<<b->grid_node, 256, 0, s>>>(b->d_md, Wn, 0, qin, S);
   enqueue_rhs_all(b, 0, 0, qin, qout, s);
-  enqueue_stage_all(b, false, qin, s);
-  k_batch_pressure<<<b->grid_node, 256, 0, s>>>(b->d_md, Wn, 1, qin, S);
+  enqueue_stage_all(b, false, qin, s);          // also P' of q(2)
   enqueue_rhs_all(b, 1, 0, qin, qout, s);
-  enqueue_stage_all(b, true, qin, s);
-  k_batch_pressure<<<b->grid_node, 256, 0, s>>>(b->d_md, Wn, 2, qin, S);
+  enqueue_stage_all(b, true, qin, s);           // also P' of q(3)
   enqueue_rhs_all(b, 2, 2, qin, qout, s);
   NUMA_BCK(b, cudaGetLastError());
   return NUMA_OK;
