@@ -559,8 +559,8 @@ def run_gpu(args):
                           "rhs_ms_per_launch": round(t_df / max(n_df, 1), 4),
                           "prepass_ms_per_launch": round(t_pd / max(n_pd, 1), 4),
                           "rhs_rel_l2_vs_fp64_kernel": [float("%.3g" % x) for x in rel],
-                          "form": "double-float (FP32-pair) derivative sums, FP64 pointwise terms, "
-                                  "EOS, column LU and state"}
+                          "form": "double-float (FP32-pair) derivative sums and pointwise products "
+                                  "in the RHS; FP64 EOS, column LU and state"}
     # the higher-order schemes on the same workload: ARK3(2)4L[2]SA (4 RHS + 3 column stages
     # per step), ARK4(3)6L[2]SA (6 + 5, general fused stage), ARK5(4)8L[2]SA (8 + 7)
     for scheme, name in (("ark3", "ARK3(2)4L[2]SA"), ("ark4", "ARK4(3)6L[2]SA"),

@@ -388,19 +388,28 @@ __global__ void k_stage_adj(const double* __restrict__ lam, double* __restrict__
   }
   __syncthreads();
 
-  // phase 2 backwards (one thread per column)
-  if ((int)threadIdx.x < ncols) {
-    const int t = threadIdx.x;
-    double* wt = Wt + t;
-    double* a = A + t;
-    double* p = P + t;
-    for (int lev = 0; lev < M; ++lev)   // P* += kp2 w_p* + D_z^T (kp1 w_p*)
-      p[lev * T] += fma(-__ldg(tb.kp2 + lev), wt[lev * T], col_dzT<N>(a, T, lev, M, R));
-    col_solve_T<N>(p, T, M, F.L, F.U, col0 + t);          // b* = S^-T P*
-    for (int lev = 0; lev < M; ++lev) a[lev * T] = __ldg(tb.kD + lev) * p[lev * T];
-    for (int lev = 0; lev < M; ++lev)   // w_a* = w* - kF b* - D_z^T (kD b*)
-      wt[lev * T] -= fma(__ldg(tb.kF + lev), p[lev * T], col_dzT<N>(a, T, lev, M, R));
-  }
+  // phase 2 backwards.  The level-parallel steps run on all threads (level lev of column c,
+  // consecutive threads on consecutive columns), the transposed substitutions one thread per
+  // column; every (level, column) value is the same arithmetic as in a thread-per-column
+  // sweep.
+  const int tid = threadIdx.x;
+  auto level_loop = [&](auto&& body) {
+    for (int j = tid; j < cnt; j += NT) {
+      const int lev = j / ncols;
+      body(lev, j - lev * ncols);
+    }
+  };
+  level_loop([&](int lev, int c) {      // P* += kp2 w_p* + D_z^T (kp1 w_p*)
+    P[lev * T + c] += fma(-__ldg(tb.kp2 + lev), Wt[lev * T + c], col_dzT<N>(A + c, T, lev, M, R));
+  });
+  __syncthreads();
+  if (tid < ncols) col_solve_T<N>(P + tid, T, M, F.L, F.U, col0 + tid);   // b* = S^-T P*
+  __syncthreads();
+  level_loop([&](int lev, int c) { A[lev * T + c] = __ldg(tb.kD + lev) * P[lev * T + c]; });
+  __syncthreads();
+  level_loop([&](int lev, int c) {      // w_a* = w* - kF b* - D_z^T (kD b*)
+    Wt[lev * T + c] -= fma(__ldg(tb.kF + lev), P[lev * T + c], col_dzT<N>(A + c, T, lev, M, R));
+  });
   __syncthreads();
 
   // phase 1 backwards (coalesced)

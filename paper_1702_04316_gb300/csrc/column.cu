@@ -388,29 +388,68 @@ __global__ void __launch_bounds__(32 * NUMA_SOLVE_MAXW) k_solve_bulk(
 }
 
 // NP previous stages (see stage_body); R3 and q3 are read only when NP = 3.
-// At most 64 registers a thread: four 256-thread CTAs per SM, which the shared memory of the
-// 64-column tile also allows.
 template <int N, int NP, bool MIXED, typename RT>
-__global__ void __maxnreg__(64) k_stage(const double* __restrict__ qn, const RT* __restrict__ R1,
-                        const RT* __restrict__ R2, const double* __restrict__ q2,
-                        double* __restrict__ out, Geom G, RefLev R, Factors F, StageCoef sc,
-                        StageTab tb, int iters, int T, const RT* __restrict__ R3,
-                        const double* __restrict__ q3, double* __restrict__ Pp_out, EosSeries eos) {
+__device__ __forceinline__ void stage_kernel(const double* __restrict__ qn, const RT* __restrict__ R1,
+                                             const RT* __restrict__ R2, const double* __restrict__ q2,
+                                             double* __restrict__ out, const Geom& G, const RefLev& R,
+                                             const Factors& F, const StageCoef& sc, const StageTab& tb,
+                                             int iters, int T, const RT* __restrict__ R3,
+                                             const double* __restrict__ q3, double* __restrict__ Pp_out,
+                                             const EosSeries& eos) {
   extern __shared__ double sm[];
   stage_body<N, NP, MIXED, RT>(blockIdx.x * (long long)T, T, sm, qn, R1, R2, q2, out, G, R, F, sc,
                                tb, iters, R3, q3, Pp_out, &eos);
 }
 
-// Any stage of an s-stage scheme: the previous stages listed in P (FP64 Schur form).
+#define NUMA_STAGE_PARAMS                                                                       \
+  const double *__restrict__ qn, const RT *__restrict__ R1, const RT *__restrict__ R2,           \
+      const double *__restrict__ q2, double *__restrict__ out, Geom G, RefLev R, Factors F,      \
+      StageCoef sc, StageTab tb, int iters, int T, const RT *__restrict__ R3,                    \
+      const double *__restrict__ q3, double *__restrict__ Pp_out, EosSeries eos
+#define NUMA_STAGE_ARGS qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3, Pp_out, eos
+
+// Register bounds of the fused stage.  N = 4: at most 64 registers a thread (written as a
+// bound of 1024 threads a CTA, so any thread count stays launchable), so four 256-thread
+// CTAs fit on an SM, as the shared memory of the 64-column tile also allows.  Other orders:
+// three 256-thread CTAs per SM (at most 85 registers; a few hundred bytes of spill at
+// N = 7, 8).  On the 64 x 64 x 10, N = 7 workload this beat both the compiler's own choice
+// (94-100 registers, two CTAs) and a 64-register cap: 18.1 against 19.3 and 18.7 ms per FP64
+// step, 8.9 against 10.1 and 9.4 ms with the FP32 right-hand side.
+template <int N, int NP, bool MIXED, typename RT>
+__global__ void __launch_bounds__(1024) k_stage4(NUMA_STAGE_PARAMS) {
+  stage_kernel<N, NP, MIXED, RT>(NUMA_STAGE_ARGS);
+}
+template <int N, int NP, bool MIXED, typename RT>
+__global__ void __launch_bounds__(256, 3) k_stage(NUMA_STAGE_PARAMS) {
+  stage_kernel<N, NP, MIXED, RT>(NUMA_STAGE_ARGS);
+}
+
+// Any stage of an s-stage scheme: the previous stages listed in P (FP64 Schur form); the
+// N = 4 variant has the 64-register bound of k_stage4.
 template <int N>
-__global__ void k_stage_general(const __grid_constant__ StagePrev P, double* __restrict__ out,
-                                Geom G, RefLev R, Factors F, StageTab tb, int T,
-                                double* __restrict__ Pp_out, EosSeries eos) {
+__device__ __forceinline__ void stage_general_kernel(const StagePrev& P, double* __restrict__ out,
+                                                     const Geom& G, const RefLev& R,
+                                                     const Factors& F, const StageTab& tb, int T,
+                                                     double* __restrict__ Pp_out,
+                                                     const EosSeries& eos) {
   extern __shared__ double sm[];
   StageCoef sc{};
   stage_body<N, 0, false, double>(blockIdx.x * (long long)T, T, sm, P.qn, nullptr, nullptr,
                                   nullptr, out, G, R, F, sc, tb, 0, nullptr, nullptr, Pp_out,
                                   &eos, &P);
+}
+template <int N>
+__global__ void __launch_bounds__(1024) k_stage_general4(const __grid_constant__ StagePrev P,
+                                                         double* __restrict__ out, Geom G, RefLev R,
+                                                         Factors F, StageTab tb, int T,
+                                                         double* __restrict__ Pp_out, EosSeries eos) {
+  stage_general_kernel<N>(P, out, G, R, F, tb, T, Pp_out, eos);
+}
+template <int N>
+__global__ void k_stage_general(const __grid_constant__ StagePrev P, double* __restrict__ out,
+                                Geom G, RefLev R, Factors F, StageTab tb, int T,
+                                double* __restrict__ Pp_out, EosSeries eos) {
+  stage_general_kernel<N>(P, out, G, R, F, tb, T, Pp_out, eos);
 }
 
 // Fused stage with the standard column system (rows 2 or 3 of Table 1).  Phase 1: the
@@ -538,12 +577,15 @@ cudaError_t launch_stage_k(const double* qn, const RT* R1, const RT* R2, const d
                            cudaStream_t s, const RT* R3 = nullptr, const double* q3 = nullptr,
                            double* Pp_out = nullptr) {
   const size_t smem = stage_smem(G.M, T, MIXED, iters);
-  cudaError_t e = cudaFuncSetAttribute(k_stage<N, NP, MIXED, RT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_stage<N, NP, MIXED, RT><<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T), smem, s>>>(
-      qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3, Pp_out, eos_series());
-  return cudaGetLastError();
+  const auto launch = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T), smem, s>>>(
+        qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3, Pp_out, eos_series());
+    return cudaGetLastError();
+  };
+  if constexpr (N == 4) return launch(k_stage4<N, NP, MIXED, RT>);
+  else return launch(k_stage<N, NP, MIXED, RT>);
 }
 
 template <int N>
@@ -652,22 +694,23 @@ cudaError_t launch_stage_general(const StagePrev& P, double* out, const Geom& G,
     return cudaErrorInvalidValue;
   const size_t smem = stage_smem(G.M, T, false, 0);
   const unsigned nb = (unsigned)((G.ncol + T - 1) / T);
-#define NUMA_GEN_CASE(n)                                                                    \
-  case n: {                                                                                 \
-    cudaError_t e = cudaFuncSetAttribute(k_stage_general<n>,                                \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (e != cudaSuccess) return e;                                                         \
-    k_stage_general<n><<<nb, stage_threads(T), smem, s>>>(P, out, G, R, F, tb, T, Pp_out,   \
-                                                          eos_series());                    \
-    break;                                                                                  \
-  }
+  const auto launch = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nb, stage_threads(T), smem, s>>>(P, out, G, R, F, tb, T, Pp_out, eos_series());
+    return cudaGetLastError();
+  };
   switch (G.N) {
-    NUMA_GEN_CASE(1) NUMA_GEN_CASE(2) NUMA_GEN_CASE(3) NUMA_GEN_CASE(4)
-    NUMA_GEN_CASE(5) NUMA_GEN_CASE(6) NUMA_GEN_CASE(7) NUMA_GEN_CASE(8)
+    case 1: return launch(k_stage_general<1>);
+    case 2: return launch(k_stage_general<2>);
+    case 3: return launch(k_stage_general<3>);
+    case 4: return launch(k_stage_general4<4>);
+    case 5: return launch(k_stage_general<5>);
+    case 6: return launch(k_stage_general<6>);
+    case 7: return launch(k_stage_general<7>);
+    case 8: return launch(k_stage_general<8>);
     default: return cudaErrorInvalidValue;
   }
-#undef NUMA_GEN_CASE
-  return cudaGetLastError();
 }
 
 size_t stage_smem_bytes(int M, int T, bool mixed, int iters) {

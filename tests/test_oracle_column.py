@@ -185,3 +185,21 @@ def test_lu_fill_stays_in_the_envelope(N, nez, n_bv, C):
     if edge_l:
         assert np.any(np.array(edge_l) != 0.0)
         assert np.any(np.array(edge_u) != 0.0)
+
+
+@pytest.mark.parametrize("N,nez", [(4, 12), (3, 5), (7, 2), (2, 1)])
+def test_envelope_counts_used_by_the_benchmark(N, nez):
+    """bench.envelope_entries (the algorithmic factor entries of the column-solve roofline)
+    counts the entries of the oracle's factors that lie inside the envelope: L's below the
+    diagonal, U's on and above it."""
+    import bench
+    m, col = _col(nez=nez, N=N)
+    LU = lu_nopivot_banded(col.jacobian_by_probing(_lam(col, m, 15)), col.half_band)
+    M = m.M
+    nl = sum(min(2 * N if j % N == 0 else 2 * N - j % N, M - 1 - j) for j in range(M))
+    nu = sum(min(2 * N if j % N == 0 else N + j % N, j) + 1 for j in range(M))
+    assert bench.envelope_entries(N, nez) == (nl, nu)
+    inside_l = sum(np.count_nonzero(LU[j + 1:, j]) for j in range(M))
+    inside_u = sum(np.count_nonzero(LU[:j + 1, j]) for j in range(M))
+    assert inside_l <= nl and inside_u <= nu          # no nonzero outside (see above)
+    assert inside_l >= 0.9 * nl and inside_u >= 0.9 * nu
