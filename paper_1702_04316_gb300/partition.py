@@ -84,6 +84,10 @@ class PartitionedHEVI:
         self.halo = HaloExchange(self.plan, self.ctx.M, dist, device)
         self.nxw = w["nex"] * N + 1
         self.nyw = w["ney"] * N + 1
+        if dist is not None:
+            # every rank constructs its share: one collective here sets up the group's
+            # communicators before the first batch of point-to-point operations
+            dist.barrier()
 
     # -- the phases and what each must refresh ------------------------------------------
     def phase(self, k, q_n, q_out=None):
