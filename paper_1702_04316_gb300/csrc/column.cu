@@ -196,13 +196,15 @@ __global__ void k_solve(const double* b, double* x, Geom G, Factors F, RefLev R,
 // and leaves the block unwritten.  Where b or x is not 16-byte aligned, or the block's byte
 // count is not a multiple of 16 (an odd M times an odd column count in the last block),
 // plain loads and stores move the block.
-// Compile-time tuning: slots per warp ring and warps (blocks) per CTA.  Two and two were
-// fastest on GB300 (3 or 4 slots, or 4 warps per CTA, measured slower).
+// Compile-time tuning: slots per warp ring and warps (blocks) per CTA.  With the envelope's
+// shorter copies, three slots and one warp per CTA are fastest on GB300 on the 96 x 96 x 12
+// workload: 0.203 ms against 0.219 (two and two), 0.216 (one warp, two slots), 0.241 (two
+// warps, three slots) and 0.240 (one warp, four slots).
 #ifndef NUMA_SOLVE_STAGES
-#define NUMA_SOLVE_STAGES 2
+#define NUMA_SOLVE_STAGES 3
 #endif
 #ifndef NUMA_SOLVE_MAXW
-#define NUMA_SOLVE_MAXW 2
+#define NUMA_SOLVE_MAXW 1
 #endif
 constexpr int kSolveStages = NUMA_SOLVE_STAGES;   // slots in a warp's ring
 constexpr size_t kSmemPerCta = 227 * 1024;           // opt-in shared memory per CTA
