@@ -19,6 +19,8 @@
 //    the shared node cancels: 2N taps instead of 2N+2;
 //  * threads run in a permuted node order in which every warp holds nodes of one class
 //    (interior / interface / wall) per axis, so no warp executes both tap counts.
+#include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "numa_internal.cuh"
@@ -67,13 +69,54 @@ __global__ void __launch_bounds__(256) k_rhs(const double* __restrict__ q,
   rhs_node<N, RT, OT>(tid, q, fld, fp, out0, out, perm, nthreads, G, R, ep, sD, sDl, sDr);
 }
 
+// The FP32 right-hand side of the precision forms (RT = float).  Its FP32 work is light, so
+// the per-CTA row load and barrier of k_rhs showed up in its time (ncu: barrier stalls 2.0 per
+// issue): here a grid of as many CTAs as fit on the GPU loads the rows once per CTA and walks
+// the thread order in CTA-sized chunks (grid stride).  The per-node arithmetic is k_rhs's.
+// Three 256-thread CTAs per SM (at most 85 registers) measured fastest: 0.36 ms per launch on
+// the 96 x 96 x 12 workload and 0.89 ms on the 64 x 64 x 10, N = 7 one, against 0.46 and
+// 1.10 ms for k_rhs, 0.37 and 1.00 ms for the compiler's own register choice, 0.37 and 0.99 ms
+// for four CTAs per SM.
+template <int N, typename RT, typename OT>
+__global__ void __launch_bounds__(256, 3) k_rhs_gs(const double* __restrict__ q,
+                                                const RT* __restrict__ fld,
+                                                const RT* __restrict__ fp, OT* out0, double* out,
+                                                const int* __restrict__ perm, long long nthreads,
+                                                Geom G, Coef3 C, RefLev R, RhsEpilogue ep) {
+  constexpr int Nq = N + 1;
+  __shared__ RT sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
+  load_rows<N, RT>(C, sD, sDl, sDr);
+  __syncthreads();
+  const long long nchunk = (nthreads + blockDim.x - 1) / blockDim.x;
+  for (long long c = blockIdx.x; c < nchunk; c += gridDim.x)
+    rhs_node<N, RT, OT>(c * blockDim.x + threadIdx.x, q, fld, fp, out0, out, perm, nthreads, G, R,
+                        ep, sD, sDl, sDr);
+}
+
 template <int N, typename RT, typename OT>
 cudaError_t launch_rhs_n(const double* q, const RT* fld, const RT* fp, OT* out0, double* out,
                          const int* perm, long long nthreads, const Geom& G, const Coef3& C,
                          const RefLev& R, const RhsEpilogue& ep, cudaStream_t s) {
   const int bs = 256;
-  k_rhs<N, RT, OT><<<(unsigned)((nthreads + bs - 1) / bs), bs, 0, s>>>(q, fld, fp, out0, out,
-                                                                        perm, nthreads, G, C, R, ep);
+  const long long nb = (nthreads + bs - 1) / bs;
+  if constexpr (std::is_same<RT, float>::value) {
+    static int resident = 0;     // CTAs of this instantiation that fit on the GPU at once
+    if (resident == 0) {
+      int dev = 0, nsm = 0, per_sm = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rhs_gs<N, RT, OT>, bs, 0) !=
+              cudaSuccess ||
+          nsm < 1 || per_sm < 1)
+        return cudaErrorUnknown;
+      resident = nsm * per_sm;
+    }
+    if (nb < 1) return cudaSuccess;
+    k_rhs_gs<N, RT, OT><<<(unsigned)std::min<long long>(nb, resident), bs, 0, s>>>(
+        q, fld, fp, out0, out, perm, nthreads, G, C, R, ep);
+  } else {
+    k_rhs<N, RT, OT><<<(unsigned)nb, bs, 0, s>>>(q, fld, fp, out0, out, perm, nthreads, G, C, R, ep);
+  }
   return cudaGetLastError();
 }
 
