@@ -88,3 +88,32 @@ def test_static_rhs_rejects_problems_beyond_the_scratch():
     rc = pkg.rhs_explicit_static(110, 110, 12, 1e5, 1e5, 1e4, 4, q, out)
     assert rc == 8          # NUMA_ERR_SCRATCH, before any device work
     assert torch.count_nonzero(out).item() == 0
+
+
+def test_static_rhs_replays_from_a_cuda_graph():
+    """A captured call carries its tables in its own launch parameters: replayed after a call
+    for another mesh (which rewrites the shared scratch), it still computes its own mesh."""
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    (da, bva), (db, bvb) = CASES[0], CASES[1]
+    ca, cb = Case(*da[:3], da[3], *da[4:], bva), Case(*db[:3], db[3], *db[4:], bvb)
+    qa = torch.from_numpy(ca.state(41)).cuda()
+    qb = torch.from_numpy(cb.state(42)).cuda()
+    ga = pkg.Numa(*da[:3], *da[4:], da[3], 0.0, 300.0, bva)
+    ref = ga.rhs_explicit(qa)
+    ga.close()
+    out_a = torch.full_like(qa, float("nan"))
+    out_b = torch.empty_like(qb)
+    # warm-up on the capturing device, outside the capture
+    assert pkg.rhs_explicit_static(*da[:3], *da[4:], da[3], qa, out_a, 300.0, bva) == pkg.NUMA_OK
+    torch.cuda.synchronize()
+    out_a.fill_(float("nan"))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rc = pkg.rhs_explicit_static(*da[:3], *da[4:], da[3], qa, out_a, 300.0, bva)
+    assert rc == pkg.NUMA_OK
+    assert pkg.rhs_explicit_static(*db[:3], *db[4:], db[3], qb, out_b, 300.0, bvb) == pkg.NUMA_OK
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, ref)
