@@ -582,6 +582,7 @@ def run_gpu(args):
         out["imex_" + scheme] = dict(res, scheme=name + ", FP64, Schur form")
     if not args.no_forms:
         out["imex3d"] = imex3d_form(pkg, torch, q0, ms_rk, args.warmup)
+        out["imex3d_large_aspect"] = imex3d_aspect_form(pkg, torch, ms_rk)
     if not args.no_forms:
         out["accuracy_vs_explicit_c1"] = accuracy_vs_explicit(pkg, torch)
         out["matched_accuracy"] = matched_accuracy(pkg, torch, ms_rk,
@@ -667,7 +668,9 @@ def matched_accuracy(pkg, torch, ms_rk, ms_forms, L=40000e3):
     For each bar of MATCHED_BARS the largest C_V whose error stays under it is found, and
     the speed-up there is C_V x (RK35 ms per step) / (1D-IMEX ms per step), the step costs
     being those measured on the benchmark workload (ms_forms: form -> ms per step).  The
-    ensemble form's members are bitwise the FP64 form's, so they share its accuracy."""
+    ensemble form's members are bitwise the FP64 form's, so they share its accuracy.
+    3D-IMEX (column-LU preconditioner) is run the same way; its cost per step depends on
+    C_V, so each of its runs is timed on this machine."""
     dt1, dt150 = dt_for(1.0), dt_for(150.0)
     g1 = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt150)
     lev = g1.reference_levels()
@@ -706,6 +709,34 @@ def matched_accuracy(pkg, torch, ms_rk, ms_forms, L=40000e3):
                     "largest_C_V": Cm,
                     "speedup_vs_explicit_c1": round(Cm * ms_rk / ms_imex, 2) if Cm else None}
         res[form] = entry
+    # 3D-IMEX with the column-LU preconditioner: its cost per step grows with C_V (BiCGstab
+    # iterations), so each C_V's run is timed (after one untimed step)
+    errs, ms3d = {}, {}
+    for C in MATCHED_C:
+        gc = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt_for(float(C)), imex="3d", precond="column",
+                      krylov_tol=1e-10, krylov_max_iters=4000)
+        out = torch.empty_like(q0)
+        gc.step_imex3d(q0, out, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        gc.step_imex3d(q0, out, 150 // C)
+        e1.record()
+        e1.synchronize()
+        ms3d[C] = e0.elapsed_time(e1) / (150 // C)
+        errs[C] = (rel(out, 4), rel(out, 3))
+        gc.close()
+    entry = {"imex_ms_per_step": {"C%d" % C: round(ms3d[C], 3) for C in MATCHED_C},
+             "errors": {"C%d" % C: {"theta": float("%.3g" % e[0]), "w": float("%.3g" % e[1])}
+                        for C, e in errs.items()}}
+    for fi, (nm, bars) in enumerate(MATCHED_BARS.items()):
+        for bar in bars:
+            ok = [C for C in MATCHED_C if errs[C][fi] <= bar]
+            Cm = max(ok) if ok else None
+            entry["%s<=%g" % (nm, bar)] = {
+                "largest_C_V": Cm,
+                "speedup_vs_explicit_c1": round(Cm * ms_rk / ms3d[Cm], 2) if Cm else None}
+    res["imex3d_column_lu"] = entry
     res["batched"] = "ensemble members are bitwise the FP64 form's: its entry applies"
     return res
 
@@ -992,6 +1023,56 @@ def imex3d_form(pkg, torch, q0, ms_rk, warmup, steps=3):
                           "speedup_vs_explicit_c1": round((dt / ms) / (dt_for(1.0) / ms_rk), 3),
                           "finite": bool(torch.isfinite(q1).all().item())}
         g.close()
+    return out
+
+
+def stretched_state(pkg, torch, L):
+    """The benchmark's balanced theta' recipe (0.5 K) on the box stretched to L x L."""
+    import synthetic
+    g = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, 0.0)
+    lev = g.reference_levels()
+    g.close()
+    xi = lgl_nodes()
+    q0h = synthetic.balanced_state(axis_coords(NEX, L / NEX, xi), axis_coords(NEY, L / NEY, xi),
+                                   lev["z"], L, L, LZ, lev["rho0"], lev["theta0"], SEED, 0.5)
+    return torch.from_numpy(q0h).cuda()
+
+
+def imex3d_aspect_form(pkg, torch, ms_rk, steps=3, L=40000e3):
+    """3D-IMEX in the paper's regime of large aspect ratio: the benchmark's array shapes on
+    the box stretched to 40,000 x 40,000 km (C_H = 0.045 at C_V = 15, 0.45 at C_V = 150), where
+    the vertical acoustics dominate the implicit operator.  Per preconditioner (Chebyshev of
+    degree 1 and 4, column LU) and C_V: ms per step, BiCGstab iterations per step (two
+    solves) and the speedup over explicit RK35 at C = 1, whose cost per step does not depend
+    on the box's size."""
+    q0 = stretched_state(pkg, torch, L)
+    q1 = torch.empty_like(q0)
+    out = {"workload": "96x96x12 hex elements over 40000x40000x15 km, N=4, FP64, ARK2, BiCGstab "
+                       "stop at 1e-10 preconditioned-residual drop"}
+    for C in (15, 150):
+        dt = dt_for(float(C))
+        res = {"C_H": round(C_S * dt / (dx_min() * L / LX), 3)}
+        for P in (1, 4, "column"):
+            kw = {"precond": "column"} if P == "column" else {"pbno_order": P}
+            g = pkg.Numa(NEX, NEY, NEZ, L, L, LZ, N, dt, imex="3d", krylov_tol=1e-10,
+                         krylov_max_iters=4000, **kw)
+            g.step_imex3d(q0, q1, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            its = 0
+            for _ in range(steps):
+                g.step_imex3d(q0, q1, 1)
+                its += g.imex3d_info()["iters_last_step"]
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res["column_lu" if P == "column" else "P%d" % P] = {
+                "ms_per_step": round(ms, 3), "bicgstab_iters_per_step": its / steps,
+                "speedup_vs_explicit_c1": round(C * ms_rk / ms, 2),
+                "finite": bool(torch.isfinite(q1).all().item())}
+            g.close()
+        out["C%d" % C] = res
     return out
 
 

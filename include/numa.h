@@ -557,6 +557,17 @@ void numa_ark3_tableau(double* a, double* at, double* b);
  * unknown scheme; any pointer may be NULL. */
 int numa_ark_tableau(int scheme, double* a, double* at, double* b, int* s);
 
+/* The FP64 <-> FP32 conversions that the FP32 forms' pre-pass and column stages do with
+ * integer instructions (the conversion instructions compete with FP64 arithmetic on GB300),
+ * exposed so that they can be checked against IEEE-754 conversion.  numa_convert_f64_f32:
+ * y[i] = x[i] rounded to the nearest float, ties to even (FP32 subnormals, overflow to
+ * infinity); numa_convert_f32_f64: y[i] = x[i] exactly.  A NaN gives a NaN.  x, y: device
+ * arrays of n elements, n >= 0, naturally aligned; enqueued on `stream` (NULL: the default
+ * stream).  Returns NUMA_ERR_ARG for a bad pointer or size, NUMA_ERR_CUDA if the launch
+ * fails. */
+int numa_convert_f64_f32(const double* x, float* y, long long n, void* stream);
+int numa_convert_f32_f64(const float* x, double* y, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

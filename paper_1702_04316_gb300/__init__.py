@@ -45,7 +45,7 @@ EXPORTS = (
     "numa_schur3d_apply",
     "numa_solve_schur3d", "numa_imex3d_stage", "numa_step_imex3d", "numa_imex3d_info",
     "numa_part_plan", "numa_part_columns", "numa_gather_columns", "numa_scatter_columns",
-    "numa_step_phase", "numa_step_buffers",
+    "numa_step_phase", "numa_step_buffers", "numa_convert_f64_f32", "numa_convert_f32_f64",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ, K_SCHUR3D = range(9)
 
@@ -149,6 +149,8 @@ def lib():
             "numa_step_phase": (I, [P, I, P, P]),
             "numa_step_buffers": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                       ctypes.POINTER(I)]),
+            "numa_convert_f64_f32": (I, [P, P, LL, P]),
+            "numa_convert_f32_f64": (I, [P, P, LL, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -686,6 +688,25 @@ def rhs_explicit_static(nex, ney, nez, Lx, Ly, Lz, N, q, out, theta_s=300.0, n_b
     d = MeshDesc(nex, ney, nez, Lx, Ly, Lz, theta_s, n_bv)
     return lib().numa_rhs_explicit_static(ctypes.byref(d), int(N), _ptr(q), _ptr(out),
                                           ctypes.c_void_p(s.cuda_stream))
+
+
+def convert(x, stream=None):
+    """numa_convert_f64_f32 (x FP64) or numa_convert_f32_f64 (x FP32) on a contiguous device
+    tensor: the library's integer-pipe conversions."""
+    import torch
+    if not (x.is_cuda and x.is_contiguous() and x.dtype in (torch.float64, torch.float32)):
+        raise ValueError("convert: x must be a contiguous FP64 or FP32 CUDA tensor")
+    s = torch.cuda.current_stream() if stream is None else stream
+    if x.dtype == torch.float64:
+        y = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+        fn = lib().numa_convert_f64_f32
+    else:
+        y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+        fn = lib().numa_convert_f32_f64
+    rc = fn(_ptr(x), _ptr(y), x.numel(), ctypes.c_void_p(s.cuda_stream))
+    if rc != NUMA_OK:
+        raise NumaError("convert: code %d" % rc)
+    return y
 
 
 def rk35_coefficients():

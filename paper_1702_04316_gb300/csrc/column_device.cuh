@@ -60,19 +60,19 @@ __device__ __forceinline__ double col_dz(const XT* f, int T, int lev, const RefL
   // one accumulator: FP64 issue, not latency, bounds the column kernels (a warp-wide FP64
   // multiply-add occupies the pipe 16 cycles), so a second chain would only add a final add
   if (n == N) {
-    double acc = __ldg(c) * (double)p[__ldg(o) * T];
+    double acc = __ldg(c) * to_f64(p[__ldg(o) * T]);
 #pragma unroll
-    for (int t = 1; t < N; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);
+    for (int t = 1; t < N; ++t) acc = fma(__ldg(c + t), to_f64(p[__ldg(o + t) * T]), acc);
     return acc;
   }
   if (n == 2 * N) {
-    double acc = __ldg(c) * (double)p[__ldg(o) * T];
+    double acc = __ldg(c) * to_f64(p[__ldg(o) * T]);
 #pragma unroll
-    for (int t = 1; t < 2 * N; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);
+    for (int t = 1; t < 2 * N; ++t) acc = fma(__ldg(c + t), to_f64(p[__ldg(o + t) * T]), acc);
     return acc;
   }
   double acc = 0.0;
-  for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), (double)p[__ldg(o + t) * T], acc);
+  for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), to_f64(p[__ldg(o + t) * T]), acc);
   return acc;
 }
 
@@ -82,7 +82,7 @@ template <int N, typename XT>
 __device__ __forceinline__ double col_wp(const XT* x, int T, int lev, const RefLev& R,
                                          const StageTab& tb) {
   return fma(__ldg(tb.kp1 + lev), col_dz<N, XT>(x, T, lev, R),
-             __ldg(tb.kp2 + lev) * (double)x[lev * T]);
+             __ldg(tb.kp2 + lev) * to_f64(x[lev * T]));
 }
 
 // Solve L U x = b in place for one column held in shared memory (stride T), VT the value
@@ -306,25 +306,25 @@ __device__ __forceinline__ void col_solve_refined(double* B, double* tmp, float*
     col_solve<2 * N, double, double, 0, N>(B, T, M, F.L, F.U, col);
     return;
   }
-  for (int lev = 0; lev < M; ++lev) Tf[lev * T] = (float)B[lev * T];
+  for (int lev = 0; lev < M; ++lev) Tf[lev * T] = f32_of(B[lev * T]);
   col_solve<2 * N, float, float, 0, N>(Tf, T, M, F.L32, F.U32, col);
   for (int it = 0; it < iters; ++it) {
     const bool first = (it == 0), last = (it == iters - 1);
     for (int lev = 0; lev < M; ++lev)
       tmp[lev * T] = first ? col_wp<N, float>(Tf, T, lev, R, tb) : col_wp<N, double>(Xd, T, lev, R, tb);
     for (int lev = 0; lev < M; ++lev) {
-      const double xl = first ? (double)Tf[lev * T] : Xd[lev * T];
-      Td[lev * T] = (float)col_residual<N>(B, tmp, T, lev, R, tb, xl);
+      const double xl = first ? f64_of(Tf[lev * T]) : Xd[lev * T];
+      Td[lev * T] = f32_of(col_residual<N>(B, tmp, T, lev, R, tb, xl));
     }
     col_solve<2 * N, float, float, 0, N>(Td, T, M, F.L32, F.U32, col);
     for (int lev = 0; lev < M; ++lev) {
-      const double x = (first ? (double)Tf[lev * T] : Xd[lev * T]) + (double)Td[lev * T];
+      const double x = (first ? f64_of(Tf[lev * T]) : Xd[lev * T]) + f64_of(Td[lev * T]);
       if (last) B[lev * T] = x;
       else Xd[lev * T] = x;
     }
   }
   if (iters == 0)
-    for (int lev = 0; lev < M; ++lev) B[lev * T] = (double)Tf[lev * T];
+    for (int lev = 0; lev < M; ++lev) B[lev * T] = f64_of(Tf[lev * T]);
 }
 
 // Shared memory of the column kernels, per column and level: the FP64 method keeps two
@@ -389,9 +389,9 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
       for (int k = 0; k < P->nq; ++k) v = fma(P->c[k], __ldg(P->q[k] + o), v);
       return v;
     }
-    double v = fma(a1dt, (double)R1[o], qv);
-    if (NP >= 2) v = fma(a2dt, (double)R2[o], v);
-    if (NP >= 3) v = fma(a3dt, (double)R3[o], v);
+    double v = fma(a1dt, to_f64(R1[o]), qv);
+    if (NP >= 2) v = fma(a2dt, to_f64(R2[o]), v);
+    if (NP >= 3) v = fma(a3dt, to_f64(R3[o]), v);
     if (f == 1 || f == 2) return v;
     v = fma(c1, qv, v);
     if (NP >= 2) v = fma(c2, q2[o], v);
@@ -433,7 +433,7 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     const double b = fma(-__ldg(tb.kF + lev), S1[lev * T + c],
                          fma(-__ldg(tb.kD + lev), dzw, S0[lev * T + c]));
     S0[lev * T + c] = b;
-    if (MIXED) Tf[lev * T + c] = (float)b;
+    if (MIXED) Tf[lev * T + c] = f32_of(b);
   });
   __syncthreads();
   if (!MIXED) {
@@ -452,21 +452,21 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
       });
       __syncthreads();
       level_loop([&](int lev, int c) {
-        const double xl = first ? (double)Tf[lev * T + c] : SXd[lev * T + c];
-        Td[lev * T + c] = (float)col_residual<N>(S0 + c, S1 + c, T, lev, R, tb, xl);
+        const double xl = first ? f64_of(Tf[lev * T + c]) : SXd[lev * T + c];
+        Td[lev * T + c] = f32_of(col_residual<N>(S0 + c, S1 + c, T, lev, R, tb, xl));
       });
       __syncthreads();
       if (tid < ncols) col_solve<2 * N, float, float, 0, N>(Td + tid, T, M, F.L32, F.U32, col0 + tid);
       __syncthreads();
       level_loop([&](int lev, int c) {
-        const double x = (first ? (double)Tf[lev * T + c] : SXd[lev * T + c]) + (double)Td[lev * T + c];
+        const double x = (first ? f64_of(Tf[lev * T + c]) : SXd[lev * T + c]) + f64_of(Td[lev * T + c]);
         if (last) S0[lev * T + c] = x;
         else SXd[lev * T + c] = x;
       });
       __syncthreads();
     }
     if (iters == 0) {
-      level_loop([&](int lev, int c) { S0[lev * T + c] = (double)Tf[lev * T + c]; });
+      level_loop([&](int lev, int c) { S0[lev * T + c] = f64_of(Tf[lev * T + c]); });
       __syncthreads();
     }
   }

@@ -47,12 +47,12 @@ __global__ void k_prep32(const double* __restrict__ q, float* __restrict__ F32, 
   if (g >= G.nnode) return;
   const long long nn = G.nnode;
   const double Pp = eos_node(q, g, G, R, S);
-  F32[g] = (float)q[g];
-  F32[nn + g] = (float)q[nn + g];
-  F32[2 * nn + g] = (float)q[2 * nn + g];
-  F32[3 * nn + g] = (float)q[3 * nn + g];
-  F32[4 * nn + g] = (float)q[4 * nn + g];
-  F32[5 * nn + g] = (float)Pp;
+  F32[g] = f32_of(q[g]);
+  F32[nn + g] = f32_of(q[nn + g]);
+  F32[2 * nn + g] = f32_of(q[2 * nn + g]);
+  F32[3 * nn + g] = f32_of(q[3 * nn + g]);
+  F32[4 * nn + g] = f32_of(q[4 * nn + g]);
+  F32[5 * nn + g] = f32_of(Pp);
 }
 
 template <int N, typename RT, typename OT>
@@ -253,4 +253,35 @@ void rhs_perm_rows(const Geom& G, std::vector<long long>& off, std::vector<int>&
   });
   off.push_back(n);
   y0.push_back(G.nyg);
+}
+
+// ---- the integer-pipe conversions, exposed for testing ----------------------------------------
+namespace {
+__global__ void k_convert_f64_f32(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = numa_dev::f32_of(x[i]);
+}
+__global__ void k_convert_f32_f64(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = numa_dev::f64_of(x[i]);
+}
+unsigned convert_grid(long long n) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 8));
+}
+}  // namespace
+
+extern "C" int numa_convert_f64_f32(const double* x, float* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y)) || ((uintptr_t)x % 8) || ((uintptr_t)y % 4)) return NUMA_ERR_ARG;
+  if (n == 0) return NUMA_OK;
+  k_convert_f64_f32<<<convert_grid(n), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? NUMA_OK : NUMA_ERR_CUDA;
+}
+
+extern "C" int numa_convert_f32_f64(const float* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y)) || ((uintptr_t)x % 4) || ((uintptr_t)y % 8)) return NUMA_ERR_ARG;
+  if (n == 0) return NUMA_OK;
+  k_convert_f32_f64<<<convert_grid(n), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? NUMA_OK : NUMA_ERR_CUDA;
 }

@@ -5,6 +5,70 @@
 
 namespace numa_dev {
 
+// ---- FP64 <-> FP32 conversions on the integer pipe ---------------------------------------------
+// On GB300 the conversion instructions between FP64 and FP32 issue at about the FP64 pipe's
+// rate (two a clock per SM, like a multiply-add) and compete with the FP64 arithmetic of the
+// kernels around them.  These two do the same conversions on the IEEE-754 bit patterns with
+// integer instructions and return the same bits (NaN payloads aside: a NaN stays a NaN).
+// They pay where the FP64 pipe is the bound (the FP32 forms' pre-pass and column stages:
+// 0.232 -> 0.158 ms and 0.852 -> 0.809 ms per launch on 96 x 96 x 12 elements, N = 4), not
+// in the FP32 right-hand side, whose FP64 pipe is mostly idle and whose issue slots are
+// not (0.36 -> 0.43 ms there with them).
+//
+// f32_of: round to nearest, ties to even.  The 52-bit fraction keeps its top 23 bits; the
+// 29 bits below decide the rounding, whose carry may run into the exponent (up to infinity).
+// Results below 2^-126 are FP32 subnormals: the 53-bit significand is shifted right with the
+// same rounding.
+__device__ __forceinline__ float f32_of(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned s = hi & 0x80000000u;
+  const int ed = (int)((hi >> 20) & 0x7ffu);
+  const int e = ed - 896;                         // FP32 biased exponent (1023 - 127 = 896)
+  if (e >= 1) {
+    if (e >= 255)                                 // beyond FP32's range, infinity or NaN
+      return __uint_as_float(s | ((ed == 0x7ff && (b << 12)) ? 0x7fffffffu : 0x7f800000u));
+    unsigned r = ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    r += (rem > 0x10000000u) | ((rem == 0x10000000u) & (r & 1u));
+    return __uint_as_float(s | r);
+  }
+  const int sh = 30 - e;                          // value = significand * 2^-149 >> sh
+  if (sh >= 54) return __uint_as_float(s);
+  const unsigned long long m = (1ull << 52) | (b & 0xfffffffffffffull);
+  unsigned long long k = m >> sh;
+  const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  k += (rem > half) | ((rem == half) & (k & 1ull));
+  return __uint_as_float(s | (unsigned)k);
+}
+
+// f64_of: exact.  A subnormal float is normalised with its leading one.
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned s = u & 0x80000000u, ef = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi, lo;
+  if (ef - 1u < 254u) {                           // normal
+    hi = s | ((ef + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (ef == 255u) {                        // infinity, NaN
+    hi = s | 0x7ff00000u | (m ? 0x80000u : 0u);
+    lo = 0u;
+  } else if (m == 0u) {                           // zero
+    hi = s;
+    lo = 0u;
+  } else {                                        // subnormal: m 2^-149
+    const int p = 31 - __clz(m);
+    const unsigned long long fr = (unsigned long long)(m ^ (1u << p)) << (52 - p);
+    hi = s | ((unsigned)(p + 874) << 20) | (unsigned)(fr >> 32);
+    lo = (unsigned)fr;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// x as a double (exact); the identity for a double.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f64_of(x); }
+
 
 // ---- equation of state ---------------------------------------------------------------------
 // P' = P(rho0 + rho', theta0 + theta') - P0 without cancellation:
