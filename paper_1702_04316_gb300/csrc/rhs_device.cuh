@@ -88,13 +88,16 @@ __device__ __forceinline__ double eos_rel(double rp, double tp, double inv_rho0,
   const double a = rp * inv_rho0;
   const double b = tp * inv_theta0;
   const double x = fma(a, b, a + b);
-  if (fabs(x) <= 0x1p-10) {
+  // |x| against 2^-10 and 2^-6 on the bit pattern without its sign, which orders like |x|
+  // for every x that is not a NaN: integer instructions instead of an FP64 comparison
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  if (ax <= 0x3F50000000000000ull) {            // 2^-10
     double p = S.c[4];
 #pragma unroll
     for (int k = 3; k >= 0; --k) p = fma(p, x, S.c[k]);
     return p * x;
   }
-  if (fabs(x) <= 0.015625) {
+  if (ax <= 0x3F90000000000000ull) {            // 2^-6
     double p = S.c[8];
 #pragma unroll
     for (int k = 7; k >= 0; --k) p = fma(p, x, S.c[k]);
