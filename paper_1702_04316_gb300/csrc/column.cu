@@ -515,23 +515,34 @@ size_t stage_smem(int M, int T, bool mixed, int iters) {
   return col_smem_per_level(mixed, iters) * M * T;
 }
 
-// Threads per CTA of the fused stage for T columns: at least kStageMinThreads (the coalesced
-// phases and the level-parallel steps of the column phase share them; only the substitutions
-// run one thread per column); NUMA_STAGE_THREADS (a multiple of 32, at least T) overrides,
-// for tuning.
-const int kStageMinThreads = 256;
-
-int stage_threads(int T) {
+// Threads per CTA of the fused stage for T columns.  The coalesced phases and the
+// level-parallel steps of the column phase share them; only the substitutions run one thread
+// per column.  Per column: four for the FP64 stage, six for the mixed form's (its refinement
+// adds level-parallel FP64 residual steps), eight when the grid has fewer than two CTAs per
+// SM (small meshes); at least T, at most `limit` (the kernel's bound).  On the 96 x 96 x 12,
+// N = 4 workload, T = 32 columns with 128 threads took the FP64 stage from 0.908 ms (64
+// columns, 256 threads) to 0.892 ms and the rhs32 stage from 0.808 to 0.788 ms; the mixed
+// stage went from 1.43 to 1.27 ms with 192 threads (1.37 with 128).  Fewer, larger CTAs
+// (64 or 128 columns) and fewer threads per column (2 or 3) were slower.
+// NUMA_STAGE_THREADS (a multiple of 32, at least T) overrides, for tuning.
+int stage_threads(int T, long long ncol, bool mixed, int limit = 1024) {
   static int env = -1;
+  static int nsm = 0;
   if (env < 0) {
     env = 0;
     if (const char* t = std::getenv("NUMA_STAGE_THREADS")) {
       const int v = std::atoi(t);
       if (v >= 32 && v <= 1024 && v % 32 == 0) env = v;
     }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 152;
   }
   if (env >= T) return env;
-  return std::min(1024, std::max(T, kStageMinThreads));
+  const long long nblocks = (ncol + T - 1) / T;
+  const int per_col = nblocks < 2LL * nsm ? 8 : (mixed ? 6 : 4);
+  return std::max(T, std::min(limit, per_col * T));
 }
 
 // Warps (32-column blocks) per CTA of k_solve_bulk for M levels at order N; 0 when one
@@ -582,8 +593,8 @@ cudaError_t launch_stage_k(const double* qn, const RT* R1, const RT* R2, const d
   const auto launch = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T), smem, s>>>(
-        qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3, Pp_out, eos_series());
+    kern<<<(unsigned)((G.ncol + T - 1) / T), stage_threads(T, G.ncol, MIXED, N == 4 ? 1024 : 256),
+           smem, s>>>(qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3, Pp_out, eos_series());
     return cudaGetLastError();
   };
   if constexpr (N == 4) return launch(k_stage4<N, NP, MIXED, RT>);
@@ -612,11 +623,11 @@ cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const vo
     if (stage == 3) {
       e = cudaFuncSetAttribute(k_stage_standard<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_stage_standard<N, true><<<nb, stage_threads(T), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
+      k_stage_standard<N, true><<<nb, stage_threads(T, G.ncol, false), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
     } else {
       e = cudaFuncSetAttribute(k_stage_standard<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_stage_standard<N, false><<<nb, stage_threads(T), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
+      k_stage_standard<N, false><<<nb, stage_threads(T, G.ncol, false), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
     }
     return cudaGetLastError();
   }
@@ -699,7 +710,7 @@ cudaError_t launch_stage_general(const StagePrev& P, double* out, const Geom& G,
   const auto launch = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<nb, stage_threads(T), smem, s>>>(P, out, G, R, F, tb, T, Pp_out, eos_series());
+    kern<<<nb, stage_threads(T, G.ncol, false), smem, s>>>(P, out, G, R, F, tb, T, Pp_out, eos_series());
     return cudaGetLastError();
   };
   switch (G.N) {

@@ -635,10 +635,9 @@ int numa_init_ex(const numa_mesh_desc* mesh, int N, double dt, const numa_option
   c->precond = precond;
   c->theta_s = mesh->theta_s > 0 ? mesh->theta_s : 300.0;
   {
-    // columns per CTA of the column kernels: 64, or 32 when 64 would leave SMs without a
-    // CTA (small meshes); NUMA_COL_TILE overrides (a multiple of 32 in [32, 256])
-    const long long ncol = (long long)(mesh->nex * N + 1) * (mesh->ney * N + 1);
-    if ((ncol + 63) / 64 < 152) c->col_tile = 32;
+    // columns per CTA of the column kernels: 32 (one warp's worth; see stage_threads for the
+    // threads per column); NUMA_COL_TILE overrides (a multiple of 32 in [32, 256])
+    c->col_tile = 32;
     if (const char* t = std::getenv("NUMA_COL_TILE")) {
       const int v = std::atoi(t);
       if (v >= 32 && v <= 256 && v % 32 == 0) c->col_tile = v;

@@ -20,7 +20,7 @@ struct numa_ctx {
   // device memory
   double* d_lev = nullptr;      // reference tables + dz band + dz taps
   int* d_levi = nullptr;        // dz tap offsets and counts
-  int col_tile = 64;            // columns per CTA of the column kernels
+  int col_tile = 32;            // columns per CTA of the column kernels
   RefLev R{};
   StageTab T{};
   double* d_stage_tab = nullptr;
