@@ -430,9 +430,11 @@ int numa_batch_step_imex1d(numa_batch* b, const double* q_in, double* q_out, int
 /* 1 (default): replay each step as a CUDA graph; 0: launch the kernels directly. */
 int numa_batch_set_graph(numa_batch* b, int enable);
 
-/* The autotuned threads per CTA of the right-hand side and columns per CTA of the stage for
- * the members of order N (0 and 0 if the ensemble has none). */
-int numa_batch_tuning(const numa_batch* b, int N, int* rhs_threads, int* col_tile);
+/* The autotuned threads per CTA of the right-hand side, and columns and threads per CTA of
+ * the stage, for the members of order N (all 0 if the ensemble has none); any output pointer
+ * may be NULL. */
+int numa_batch_tuning(const numa_batch* b, int N, int* rhs_threads, int* col_tile,
+                      int* stage_threads);
 
 /* numa_query / numa_reference_levels of one member. */
 int numa_batch_member_query(const numa_batch* b, int member, int what, long long* out);

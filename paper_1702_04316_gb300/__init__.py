@@ -129,7 +129,7 @@ def lib():
             "numa_batch_layout": (I, [P, P]),
             "numa_batch_step_imex1d": (I, [P, P, P, I]),
             "numa_batch_set_graph": (I, [P, I]),
-            "numa_batch_tuning": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "numa_batch_tuning": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "numa_batch_member_query": (I, [P, I, I, ctypes.POINTER(LL)]),
             "numa_batch_reference_levels": (I, [P, I, P]),
             "numa_batch_last_error": (ctypes.c_char_p, [P]),
@@ -619,13 +619,16 @@ class Batch:
         self._check(lib().numa_batch_set_graph(self._h, 1 if enable else 0), "set_graph")
 
     def tuning(self):
-        """{N: {"rhs_threads_per_cta", "stage_columns_per_cta"}} for the orders present."""
+        """{N: {"rhs_threads_per_cta", "stage_columns_per_cta", "stage_threads_per_cta"}} for
+        the orders present."""
         out = {}
         for n in (4, 5, 6):
-            a, b = ctypes.c_int(), ctypes.c_int()
-            self._check(lib().numa_batch_tuning(self._h, n, ctypes.byref(a), ctypes.byref(b)), "tuning")
+            a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            self._check(lib().numa_batch_tuning(self._h, n, ctypes.byref(a), ctypes.byref(b),
+                                                ctypes.byref(c)), "tuning")
             if a.value:
-                out[n] = {"rhs_threads_per_cta": a.value, "stage_columns_per_cta": b.value}
+                out[n] = {"rhs_threads_per_cta": a.value, "stage_columns_per_cta": b.value,
+                          "stage_threads_per_cta": c.value}
         return out
 
     def member_query(self, m, what):

@@ -145,11 +145,12 @@ struct OrderGroup {
   int N = 0;
   std::vector<int> members;
   HostList rhs_list, col_list;
-  int rhs_threads = 256, col_tile = 64;
+  int rhs_threads = 256, col_tile = 64, col_threads = 4;
   int grid_rhs = 0, grid_col = 0;
   size_t stage_smem = 0;
-  // threads per CTA of the stage: the column tile, at least 256 (the level-parallel steps)
-  int stage_threads() const { return std::max(col_tile, 256); }
+  // threads per CTA of the stage: col_threads per column of the tile (the coalesced phases
+  // and the level-parallel steps; the substitutions run one thread per column)
+  int stage_threads() const { return std::min(1024, col_threads * col_tile); }
 };
 
 struct numa_batch {
@@ -391,18 +392,21 @@ int autotune(numa_batch* b) {
     if (rc) break;
     g.rhs_threads = best_rt;
     best = 1e30f;
-    int best_ct = 32;
-    for (int ct : {32, 64, 96}) {
-      g.col_tile = ct;
-      if (build_group(b, g)) { b->err.clear(); continue; }     // does not fit: skip
-      float ms = 0;
-      rc = time_it([&] { enqueue_stage_all(b, false, b->d_state, b->stream); }, &ms);
-      if (rc) break;
-      b->tune_ms.push_back(ms);
-      if (ms < best) { best = ms; best_ct = ct; }
-    }
+    int best_ct = 32, best_tc = 8;
+    for (int ct : {32, 64, 96})
+      for (int tc : {4, 8}) {
+        g.col_tile = ct;
+        g.col_threads = tc;
+        if (build_group(b, g)) { b->err.clear(); continue; }     // does not fit: skip
+        float ms = 0;
+        rc = time_it([&] { enqueue_stage_all(b, false, b->d_state, b->stream); }, &ms);
+        if (rc) break;
+        b->tune_ms.push_back(ms);
+        if (ms < best) { best = ms; best_ct = ct; best_tc = tc; }
+      }
     if (rc) break;
     g.col_tile = best_ct;
+    g.col_threads = best_tc;
     if ((rc = build_group(b, g))) break;
   }
   cudaEventDestroy(e0);
@@ -546,11 +550,13 @@ int numa_batch_step_imex1d(numa_batch* b, const double* q_in, double* q_out, int
   return NUMA_OK;
 }
 
-int numa_batch_tuning(const numa_batch* b, int N, int* rhs_threads, int* col_tile) {
+int numa_batch_tuning(const numa_batch* b, int N, int* rhs_threads, int* col_tile,
+                      int* stage_threads) {
   if (!b || N < 4 || N > 6) return NUMA_ERR_ARG;
   const OrderGroup& g = b->groups[N - 4];
   if (rhs_threads) *rhs_threads = g.members.empty() ? 0 : g.rhs_threads;
   if (col_tile) *col_tile = g.members.empty() ? 0 : g.col_tile;
+  if (stage_threads) *stage_threads = g.members.empty() ? 0 : g.stage_threads();
   return NUMA_OK;
 }
 

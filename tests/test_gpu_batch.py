@@ -41,6 +41,7 @@ def test_batch_matches_single_contexts_exactly():
     assert sorted(t) == [4, 5, 6]
     for v in t.values():
         assert v["rhs_threads_per_cta"] in (128, 256) and v["stage_columns_per_cta"] in (32, 64, 96)
+        assert v["stage_threads_per_cta"] in (4 * v["stage_columns_per_cta"], 8 * v["stage_columns_per_cta"])
 
 
 def test_graph_replay_equals_direct_launches_and_in_place():
