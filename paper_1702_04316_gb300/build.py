@@ -51,7 +51,7 @@ def build(verbose=False, extra_flags=()):
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
         return obj, r.stderr
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(srcs), max(8, os.cpu_count() or 8))) as ex:
         results = list(ex.map(compile_one, srcs))
     objs = [o for o, _ in results]
     if verbose:

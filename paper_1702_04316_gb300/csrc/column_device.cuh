@@ -1,5 +1,5 @@
 // Device code of the column kernels (factor, solve, fused stage), shared by the
-// single-mesh kernels (column.cu) and the persistent ensemble kernels (batch.cu).
+// single-mesh kernels (column.cu, column_stage.cuh) and the persistent ensemble kernels (batch.cu).
 // See column.cu for the method.
 #pragma once
 #include "numa_internal.cuh"

@@ -1,6 +1,6 @@
 // C ABI of libnuma (declared in include/numa.h): the context, the host-side set-up
 // (LGL tables, reference state, column derivative and stage tables) and the entry points
-// that enqueue the kernels of rhs.cu, column.cu and misc.cu.
+// that enqueue the kernels of rhs.cu, column.cu (with column_stage_n*.cu) and misc.cu.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>

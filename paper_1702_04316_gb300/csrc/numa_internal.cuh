@@ -206,7 +206,6 @@ cudaError_t launch_stage(int stage, const double* qn, const void* R1, const void
                          bool r_float, cudaStream_t s, const double* R3 = nullptr,
                          const double* q3 = nullptr, double* Pp_out = nullptr);
 size_t stage_smem_bytes(int M, int T, bool mixed, int iters);
-
 // The previous stages of stage i of an s-stage scheme (s <= NUMA_MAX_STAGES), read by the
 // general form of the fused stage: q(i)_e = qn + sum_k adt[k] R[k] and the shift
 // sum_k c[k] q[k], over the terms with nonzero coefficients only (q(1) = qn may appear in
@@ -225,6 +224,24 @@ struct StagePrev {
 cudaError_t launch_stage_general(const StagePrev& P, double* out, const Geom& G, const RefLev& R,
                                  const Factors& F, const StageTab& tb, int T, cudaStream_t s,
                                  double* Pp_out);
+// Per-order entry points of launch_stage and launch_stage_general (column_stage_nN.cu).
+#define NUMA_STAGE_ORDER_SIG(n)                                                                  \
+  cudaError_t launch_stage_order##n(int stage, const double* qn, const void* R1, const void* R2, \
+                                    const double* q2, double* out, const Geom& G,                \
+                                    const RefLev& R, const Factors& F, const StageCoef& sc,      \
+                                    const StageTab& tb, int T, bool r_float, cudaStream_t s,     \
+                                    const double* R3, const double* q3, double* Pp_out)
+#define NUMA_STAGE_GENERAL_ORDER_SIG(n)                                                          \
+  cudaError_t launch_stage_general_order##n(const StagePrev& P, double* out, const Geom& G,      \
+                                            const RefLev& R, const Factors& F,                   \
+                                            const StageTab& tb, int T, cudaStream_t s,           \
+                                            double* Pp_out)
+
+NUMA_STAGE_ORDER_SIG(1); NUMA_STAGE_ORDER_SIG(2); NUMA_STAGE_ORDER_SIG(3); NUMA_STAGE_ORDER_SIG(4);
+NUMA_STAGE_ORDER_SIG(5); NUMA_STAGE_ORDER_SIG(6); NUMA_STAGE_ORDER_SIG(7); NUMA_STAGE_ORDER_SIG(8);
+NUMA_STAGE_GENERAL_ORDER_SIG(1); NUMA_STAGE_GENERAL_ORDER_SIG(2); NUMA_STAGE_GENERAL_ORDER_SIG(3);
+NUMA_STAGE_GENERAL_ORDER_SIG(4); NUMA_STAGE_GENERAL_ORDER_SIG(5); NUMA_STAGE_GENERAL_ORDER_SIG(6);
+NUMA_STAGE_GENERAL_ORDER_SIG(7); NUMA_STAGE_GENERAL_ORDER_SIG(8);
 // out = qn + sum_k bdt[k] R[k] (k < n; in place on qn allowed); a value that is not finite
 // latches NUMA_ST_NONFINITE into status (NULL: no check).
 struct StageSum {
