@@ -35,8 +35,8 @@ __device__ __forceinline__ void stage_kernel(const double* __restrict__ qn, cons
 #define NUMA_STAGE_ARGS qn, R1, R2, q2, out, G, R, F, sc, tb, iters, T, R3, q3, Pp_out, eos
 
 // Register bounds of the fused stage.  N = 4: at most 64 registers a thread (written as a
-// bound of 1024 threads a CTA, so any thread count stays launchable), so four 256-thread
-// CTAs fit on an SM, as the shared memory of the 64-column tile also allows.  Other orders:
+// bound of 1024 threads a CTA, so any thread count stays launchable), so 32 warps fit on an
+// SM (eight 128-thread CTAs of 32 columns), as their shared memory also allows.  Other orders:
 // three 256-thread CTAs per SM (at most 85 registers; a few hundred bytes of spill at
 // N = 7, 8).  On the 64 x 64 x 10, N = 7 workload this beat both the compiler's own choice
 // (94-100 registers, two CTAs) and a 64-register cap: 18.1 against 19.3 and 18.7 ms per FP64
@@ -209,11 +209,11 @@ cudaError_t launch_stage_n(int stage, const double* qn, const void* R1, const vo
     if (stage == 3) {
       e = cudaFuncSetAttribute(k_stage_standard<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_stage_standard<N, true><<<nb, stage_threads(T, G.ncol, false), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
+      k_stage_standard<N, true><<<nb, stage_threads(T, G.ncol, false, 512), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
     } else {
       e = cudaFuncSetAttribute(k_stage_standard<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_stage_standard<N, false><<<nb, stage_threads(T, G.ncol, false), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
+      k_stage_standard<N, false><<<nb, stage_threads(T, G.ncol, false, 512), smem, s>>>(qn, a, b, q2, out, G, F, sc, T);
     }
     return cudaGetLastError();
   }
@@ -254,7 +254,8 @@ cudaError_t launch_stage_general_n(const StagePrev& P, double* out, const Geom& 
   const auto launch = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<nb, stage_threads(T, G.ncol, false), smem, s>>>(P, out, G, R, F, tb, T, Pp_out, eos_series());
+    kern<<<nb, stage_threads(T, G.ncol, false, N == 4 ? 1024 : 256), smem, s>>>(P, out, G, R, F, tb, T,
+                                                                            Pp_out, eos_series());
     return cudaGetLastError();
   };
   if constexpr (N == 4) return launch(k_stage_general4<N>);
