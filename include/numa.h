@@ -570,6 +570,15 @@ int numa_ark_tableau(int scheme, double* a, double* at, double* b, int* s);
 int numa_convert_f64_f32(const double* x, float* y, long long n, void* stream);
 int numa_convert_f32_f64(const float* x, double* y, long long n, void* stream);
 
+/* y[i] = 1 / x[i] as the FP64 right-hand side computes 1 / rho: Newton's method for the
+ * reciprocal from an FP32 seed with one third-order step, within one unit in the last place
+ * of the correctly rounded quotient; where x or 1 / x lies outside the normal FP32 range
+ * (zeros, infinities and NaN included) it is the IEEE quotient.  Exposed so that it can be
+ * checked against division.  x, y: device arrays of n doubles (8-byte aligned); enqueued on
+ * `stream` (NULL: the default stream).  Returns NUMA_ERR_ARG for a bad pointer or size,
+ * NUMA_ERR_CUDA if the launch fails. */
+int numa_reciprocal(const double* x, double* y, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,7 @@ EXPORTS = (
     "numa_solve_schur3d", "numa_imex3d_stage", "numa_step_imex3d", "numa_imex3d_info",
     "numa_part_plan", "numa_part_columns", "numa_gather_columns", "numa_scatter_columns",
     "numa_step_phase", "numa_step_buffers", "numa_convert_f64_f32", "numa_convert_f32_f64",
+    "numa_reciprocal",
 )
 K_PRESSURE, K_RHS, K_STAGE, K_SOLVE, K_FACTOR, K_RHS_TLM, K_RHS_ADJ, K_STAGE_ADJ, K_SCHUR3D = range(9)
 
@@ -151,6 +152,7 @@ def lib():
                                       ctypes.POINTER(I)]),
             "numa_convert_f64_f32": (I, [P, P, LL, P]),
             "numa_convert_f32_f64": (I, [P, P, LL, P]),
+            "numa_reciprocal": (I, [P, P, LL, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -709,6 +711,20 @@ def convert(x, stream=None):
     rc = fn(_ptr(x), _ptr(y), x.numel(), ctypes.c_void_p(s.cuda_stream))
     if rc != NUMA_OK:
         raise NumaError("convert: code %d" % rc)
+    return y
+
+
+def reciprocal(x, stream=None):
+    """numa_reciprocal on a contiguous FP64 device tensor: 1 / x as the right-hand side
+    computes it."""
+    import torch
+    if not (x.is_cuda and x.is_contiguous() and x.dtype == torch.float64):
+        raise ValueError("reciprocal: x must be a contiguous FP64 CUDA tensor")
+    s = torch.cuda.current_stream() if stream is None else stream
+    y = torch.empty_like(x)
+    rc = lib().numa_reciprocal(_ptr(x), _ptr(y), x.numel(), ctypes.c_void_p(s.cuda_stream))
+    if rc != NUMA_OK:
+        raise NumaError("reciprocal: code %d" % rc)
     return y
 
 

@@ -255,7 +255,7 @@ void rhs_perm_rows(const Geom& G, std::vector<long long>& off, std::vector<int>&
   y0.push_back(G.nyg);
 }
 
-// ---- the integer-pipe conversions, exposed for testing ----------------------------------------
+// ---- the integer-pipe conversions and the reciprocal, exposed for testing ---------------------
 namespace {
 __global__ void k_convert_f64_f32(const double* __restrict__ x, float* __restrict__ y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -266,6 +266,11 @@ __global__ void k_convert_f32_f64(const float* __restrict__ x, double* __restric
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = numa_dev::f64_of(x[i]);
+}
+__global__ void k_reciprocal(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = numa_dev::recip(x[i]);
 }
 unsigned convert_grid(long long n) {
   return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 8));
@@ -283,5 +288,12 @@ extern "C" int numa_convert_f32_f64(const float* x, double* y, long long n, void
   if (n < 0 || (n > 0 && (!x || !y)) || ((uintptr_t)x % 4) || ((uintptr_t)y % 8)) return NUMA_ERR_ARG;
   if (n == 0) return NUMA_OK;
   k_convert_f32_f64<<<convert_grid(n), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? NUMA_OK : NUMA_ERR_CUDA;
+}
+
+extern "C" int numa_reciprocal(const double* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y)) || ((uintptr_t)x % 8) || ((uintptr_t)y % 8)) return NUMA_ERR_ARG;
+  if (n == 0) return NUMA_OK;
+  k_reciprocal<<<convert_grid(n), 256, 0, (cudaStream_t)stream>>>(x, y, n);
   return cudaGetLastError() == cudaSuccess ? NUMA_OK : NUMA_ERR_CUDA;
 }

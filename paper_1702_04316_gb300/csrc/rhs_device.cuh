@@ -69,6 +69,27 @@ __device__ __forceinline__ double f64_of(float f) {
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f64_of(x); }
 
+// 1 / x in FP64 by Newton's method for the reciprocal from an FP32 seed, with the
+// third-order step: y0 = rcp.approx of x narrowed by truncation (relative error below
+// 2^-21), e = 1 - x y0, y = y0 (1 + e + e^2), whose error is about e^3 < 2^-63.  The result
+// lies within one unit in the last place of the correctly rounded 1 / x, for three FP64
+// multiply-adds (the seed runs on the integer pipe and the special-function unit).  Where x
+// or 1 / x leaves the normal FP32 range (zeros, infinities and NaN included) it divides.
+__device__ __forceinline__ double recip(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ed = (hi >> 20) & 0x7ffu;
+  if (ed - 897u >= 252u) return 1.0 / x;            // x outside [2^-126, 2^126): x or 1 / x
+                                                    // not a normal float
+  const float xf = __uint_as_float((hi & 0x80000000u) | ((ed - 896u) << 23) |
+                                   ((hi & 0xfffffu) << 3) | (lo >> 29));
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+  const double y0 = f64_of(yf);
+  const double e = fma(-x, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+
 
 // ---- equation of state ---------------------------------------------------------------------
 // P' = P(rho0 + rho', theta0 + theta') - P0 without cancellation:
@@ -229,7 +250,7 @@ __device__ __forceinline__ void rhs_point_v(long long g, int ix, int iy, int iz,
                                             OT* out0, double* out, const Geom& G, const RefLev& R,
                                             const RhsEpilogue& ep) {
   const RT rho = (RT)R.rho0[iz] + r_;
-  const RT irho = (RT)1 / rho;
+  const RT irho = recip(rho);
   const RT grav = (RT)NUMA_GRAV;
   RT t_r = -fma(u_, dx[0], fma(v_, dy[0], fma(w_, dz[0] + (RT)R.drho0[iz], rho * (dx[1] + dy[2] + dz[3]))));
   RT t_u = -fma(u_, dx[1], fma(v_, dy[1], fma(w_, dz[1], dx[5] * irho)));

@@ -71,3 +71,32 @@ def test_convert_rejects_bad_arguments():
     with pytest.raises(ValueError):
         pkg.convert(torch.zeros(4, dtype=torch.float16, device="cuda"))
     assert pkg.convert(torch.zeros(0, dtype=torch.float64, device="cuda")).numel() == 0
+
+
+def test_reciprocal_within_one_ulp_of_division():
+    """The right-hand side's 1 / rho (Newton's method from an FP32 seed with a third-order
+    step) against the IEEE quotient (numpy on the host, and the GPU's own division): at most
+    one unit in the last place apart over densities and over every FP32-normal exponent, and
+    the quotient itself outside that range."""
+    import torch
+    import paper_1702_04316_gb300 as pkg
+    rng = np.random.Generator(np.random.PCG64(79))
+    dens = rng.uniform(0.01, 2.0, 1 << 20)                 # densities, kg / m^3
+    b = rng.integers(0, 2 ** 64, 1 << 20, dtype=np.uint64)
+    e = rng.integers(1023 - 126, 1023 + 127, b.size, dtype=np.uint64)
+    wide = ((b & np.uint64(0x800FFFFFFFFFFFFF)) | (e << np.uint64(52))).view(np.float64)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 2.0 ** -126, 2.0 ** -127,
+                        2.0 ** 126, 2.0 ** 127, 2.0 ** 128, 1e-300, 1e300, 5e-324, 3.0, 0.1])
+    x = np.concatenate([special, dens, wide])
+    xd = torch.from_numpy(x).cuda()
+    got = pkg.reciprocal(xd).cpu().numpy()
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        ref = 1.0 / x
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    fin = np.isfinite(ref) & (ref != 0)
+    ulp = np.abs(got[fin].view(np.int64) - ref[fin].view(np.int64))
+    assert ulp.max() <= 1
+    assert np.array_equal(got[~fin & ~np.isnan(ref)], ref[~fin & ~np.isnan(ref)])
+    hw = (1.0 / xd).cpu().numpy()
+    assert np.abs(got[fin].view(np.int64) - hw[fin].view(np.int64)).max() <= 1
+    assert (ulp == 0).mean() > 0.5                          # mostly the correctly rounded value
