@@ -56,7 +56,7 @@ __global__ void k_dpressure(const double* __restrict__ q, const double* __restri
   const int iz = (int)(g % G.M);
   const double P = R.P0[iz] + Pp[g];
   const double rho = R.rho0[iz] + q[g], th = R.theta0[iz] + q[4 * nn + g];
-  dPp[g] = NUMA_GAMMA * P * (dq[g] / rho + dq[4 * nn + g] / th);
+  dPp[g] = NUMA_GAMMA * P * fma(dq[g], recip(rho), dq[4 * nn + g] * recip(th));
 }
 
 // dR = R'(q) dq at every node (natural node order).
@@ -93,7 +93,7 @@ __global__ void k_rhs_tlm(const double* __restrict__ q, const double* __restrict
   }
   const double r = q[g], u = q[nn + g], v = q[2 * nn + g], w = q[3 * nn + g];
   const double dr = dq[g], du = dq[nn + g], dv = dq[2 * nn + g], dw = dq[3 * nn + g];
-  const double rho = R.rho0[iz] + r, ir = 1.0 / rho, ir2 = ir * ir;
+  const double rho = R.rho0[iz] + r, ir = recip(rho), ir2 = ir * ir;
   auto dadv = [&](int f) {   // d(u.grad f) = du f_x + u df_x + ...
     return du * dx[f] + u * ex[f] + dv * dy[f] + v * ey[f] + dw * dz[f] + w * ez[f];
   };
@@ -134,7 +134,7 @@ __global__ void k_adj_weights(const double* __restrict__ q, const double* __rest
   const int ix = (int)(col - (long long)iy * G.nxg);
   double l[5];
   masked_lam(lam, h, nn, ix, iy, iz, G, l);
-  const double rho = R.rho0[iz] + q[h], ir = 1.0 / rho;
+  const double rho = R.rho0[iz] + q[h], ir = recip(rho);
   const double vel[3] = {q[nn + h], q[2 * nn + h], q[3 * nn + h]};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -206,7 +206,7 @@ __global__ void k_rhs_adj(const double* __restrict__ q, const double* __restrict
   double l[5];
   masked_lam(lam, g, nn, ix, iy, iz, G, l);
   const double r = q[g];
-  const double rho = R.rho0[iz] + r, ir = 1.0 / rho, ir2 = ir * ir;
+  const double rho = R.rho0[iz] + r, ir = recip(rho), ir2 = ir * ir;
   acc[0] += -(dx[1] + dy[2] + dz[3]) * l[0] + dx[5] * ir2 * l[1] + dy[5] * ir2 * l[2] +
             ((dz[5] + NUMA_GRAV * r) * ir2 - NUMA_GRAV * ir) * l[3];
   acc[1] -= dx[0] * l[0] + dx[1] * l[1] + dx[2] * l[2] + dx[3] * l[3] + dx[4] * l[4];
