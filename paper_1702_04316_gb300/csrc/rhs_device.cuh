@@ -252,11 +252,15 @@ __device__ __forceinline__ void rhs_point_v(long long g, int ix, int iy, int iz,
   const RT rho = (RT)R.rho0[iz] + r_;
   const RT irho = recip(rho);
   const RT grav = (RT)NUMA_GRAV;
-  RT t_r = -fma(u_, dx[0], fma(v_, dy[0], fma(w_, dz[0] + (RT)R.drho0[iz], rho * (dx[1] + dy[2] + dz[3]))));
-  RT t_u = -fma(u_, dx[1], fma(v_, dy[1], fma(w_, dz[1], dx[5] * irho)));
-  RT t_v = -fma(u_, dx[2], fma(v_, dy[2], fma(w_, dz[2], dy[5] * irho)));
-  RT t_w = -fma(u_, dx[3], fma(v_, dy[3], fma(w_, dz[3], fma(grav, r_, dz[5]) * irho)));
-  RT t_t = -fma(u_, dx[4], fma(v_, dy[4], w_ * (dz[4] + (RT)R.dtheta0[iz])));
+  // the tendencies are minus sums of products; the minus sign sits on the operands (-x y =
+  // (-x) y and -fma(a, b, c) = fma(-a, b, -c) exactly, rounding being symmetric), so no
+  // instruction negates a result
+  const RT nu = -u_, nv = -v_, nw = -w_;
+  RT t_r = fma(nu, dx[0], fma(nv, dy[0], fma(nw, dz[0] + (RT)R.drho0[iz], -rho * (dx[1] + dy[2] + dz[3]))));
+  RT t_u = fma(nu, dx[1], fma(nv, dy[1], fma(nw, dz[1], -dx[5] * irho)));
+  RT t_v = fma(nu, dx[2], fma(nv, dy[2], fma(nw, dz[2], -dy[5] * irho)));
+  RT t_w = fma(nu, dx[3], fma(nv, dy[3], fma(nw, dz[3], fma(-grav, r_, -dz[5]) * irho)));
+  RT t_t = fma(nu, dx[4], fma(nv, dy[4], nw * (dz[4] + (RT)R.dtheta0[iz])));
   // walls: no normal flow
   if (ix == 0 || ix == G.nxg - 1) t_u = (RT)0;
   if (iy == 0 || iy == G.nyg - 1) t_v = (RT)0;
