@@ -94,15 +94,18 @@ __global__ void k_rhs_tlm(const double* __restrict__ q, const double* __restrict
   const double r = q[g], u = q[nn + g], v = q[2 * nn + g], w = q[3 * nn + g];
   const double dr = dq[g], du = dq[nn + g], dv = dq[2 * nn + g], dw = dq[3 * nn + g];
   const double rho = R.rho0[iz] + r, ir = recip(rho), ir2 = ir * ir;
-  auto dadv = [&](int f) {   // d(u.grad f) = du f_x + u df_x + ...
-    return du * dx[f] + u * ex[f] + dv * dy[f] + v * ey[f] + dw * dz[f] + w * ez[f];
+  // minus d(u.grad f) = -(du f_x + u df_x + ...), the minus signs on the operands so that no
+  // instruction negates a result (as in the forward right-hand side)
+  const double ndu = -du, nu = -u, ndv = -dv, nv = -v, ndw = -dw, nw = -w;
+  auto ndadv = [&](int f) {
+    return ndu * dx[f] + nu * ex[f] + ndv * dy[f] + nv * ey[f] + ndw * dz[f] + nw * ez[f];
   };
   double t[5];
-  t[0] = -(dadv(0) + dw * R.drho0[iz] + dr * (dx[1] + dy[2] + dz[3]) + rho * (ex[1] + ey[2] + ez[3]));
-  t[1] = -(dadv(1) + ex[5] * ir - dx[5] * dr * ir2);
-  t[2] = -(dadv(2) + ey[5] * ir - dy[5] * dr * ir2);
-  t[3] = -(dadv(3) + (ez[5] + NUMA_GRAV * dr) * ir - (dz[5] + NUMA_GRAV * r) * dr * ir2);
-  t[4] = -(dadv(4) + dw * R.dtheta0[iz]);
+  t[0] = ndadv(0) + ndw * R.drho0[iz] - dr * (dx[1] + dy[2] + dz[3]) - rho * (ex[1] + ey[2] + ez[3]);
+  t[1] = ndadv(1) - ex[5] * ir + dx[5] * dr * ir2;
+  t[2] = ndadv(2) - ey[5] * ir + dy[5] * dr * ir2;
+  t[3] = ndadv(3) - (ez[5] + NUMA_GRAV * dr) * ir + (dz[5] + NUMA_GRAV * r) * dr * ir2;
+  t[4] = ndadv(4) + ndw * R.dtheta0[iz];
   if (ix == 0 || ix == G.nxg - 1) t[1] = 0.0;
   if (iy == 0 || iy == G.nyg - 1) t[2] = 0.0;
   if (iz == 0 || iz == G.M - 1) t[3] = 0.0;

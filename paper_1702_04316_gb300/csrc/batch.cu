@@ -97,9 +97,11 @@ __device__ __forceinline__ void batch_rhs_item(const MemberDev& d, long long tid
                               sDr);
 }
 
+// At most 85 registers a thread (three 256-thread or six 128-thread CTAs per SM), as k_rhs.
 template <int N>
-__global__ void k_batch_rhs(const MemberDev* __restrict__ md, WorkList W, int src, int mode,
-                            const double* qin, double* qout) {
+__global__ void __launch_bounds__(256, 3) k_batch_rhs(const MemberDev* __restrict__ md, WorkList W,
+                                                      int src, int mode, const double* qin,
+                                                      double* qout) {
   constexpr int Nq = N + 1;
   __shared__ double sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
   for (long long item = blockIdx.x; item < W.nitems; item += gridDim.x) {

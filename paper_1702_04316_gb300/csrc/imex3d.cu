@@ -38,10 +38,12 @@ const int kRedThreads = 256;
 // exact tap count of the node's class (uniform across a warp in the class-sorted order).
 template <int N>
 __device__ __forceinline__ double deriv1(const double* __restrict__ f, long long g, long long stride,
-                                         int cls, const Taps<N, double>& T) {
-  // one accumulator: the operator is bound by FP64 issue, not by the chain's latency
+                                         int cls, const Taps<N, double>& T, const double* acc0 = nullptr) {
+  // one accumulator: the operator is bound by FP64 issue, not by the chain's latency; acc0
+  // (optional) is added by the first multiply-add (the divergence's sum of three derivatives)
   const double* p = f + g;
-  double acc = T.c[0] * __ldg(p + T.o[0] * stride);
+  double acc = acc0 ? fma(T.c[0], __ldg(p + T.o[0] * stride), *acc0)
+                    : T.c[0] * __ldg(p + T.o[0] * stride);
   if (cls == CLS_IFACE) {
 #pragma unroll
     for (int t = 1; t < 2 * N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
@@ -122,10 +124,10 @@ __global__ void k_s3_div(const double* __restrict__ U3, const double* __restrict
   int cls = axis_taps<N, double>(n.ix, G.nex, sD, sDl, sDr, T);
   const double du = deriv1<N>(U3, g, sx, cls, T);
   cls = axis_taps<N, double>(n.iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
-  const double dv = deriv1<N>(U3 + nn, g, sy, cls, T);
+  const double duv = deriv1<N>(U3 + nn, g, sy, cls, T, &du);
   cls = axis_taps<N, double>(n.iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
-  const double dw = deriv1<N>(U3 + 2 * nn, g, 1, cls, T);
-  double v = fma(-__ldg(tb.kD + n.iz), du + dv + dw, fma(-__ldg(tb.kF + n.iz), U3[2 * nn + g], base[g]));
+  const double div = deriv1<N>(U3 + 2 * nn, g, 1, cls, T, &duv);   // D_x u + D_y v + D_z w
+  double v = fma(-__ldg(tb.kD + n.iz), div, fma(-__ldg(tb.kF + n.iz), U3[2 * nn + g], base[g]));
   if (alpha != 1.0) v *= alpha;                       // uniform: S itself has alpha = 1
   if (y) v = fma(beta, y[g], v);
   out[g] = v;

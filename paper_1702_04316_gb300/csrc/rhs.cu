@@ -55,12 +55,16 @@ __global__ void k_prep32(const double* __restrict__ q, float* __restrict__ F32, 
   F32[5 * nn + g] = f32_of(Pp);
 }
 
+// Three 256-thread CTAs per SM (at most 85 registers a thread; a few dozen bytes of spill at
+// N = 4): with the reference gradients folded into the z derivatives the compiler's own
+// choice rose to 104 registers and two CTAs per SM.  1.537 -> 1.505 ms per launch on the
+// 96 x 96 x 12 workload, 4.28 -> 4.19 ms at N = 7 (64 x 64 x 10).
 template <int N, typename RT, typename OT>
-__global__ void __launch_bounds__(256) k_rhs(const double* __restrict__ q,
-                                             const RT* __restrict__ fld,
-                                             const RT* __restrict__ fp, OT* out0, double* out,
-                                             const int* __restrict__ perm, long long nthreads,
-                                             Geom G, Coef3 C, RefLev R, RhsEpilogue ep) {
+__global__ void __launch_bounds__(256, 3) k_rhs(const double* __restrict__ q,
+                                                const RT* __restrict__ fld,
+                                                const RT* __restrict__ fp, OT* out0, double* out,
+                                                const int* __restrict__ perm, long long nthreads,
+                                                Geom G, Coef3 C, RefLev R, RhsEpilogue ep) {
   constexpr int Nq = N + 1;
   __shared__ RT sD[3 * Nq * Nq], sDl[3 * Nq], sDr[3 * Nq];
   load_rows<N, RT>(C, sD, sDl, sDr);

@@ -193,15 +193,23 @@ __device__ __forceinline__ int axis_taps(int idx, int nel, const RT* sD, const R
   return CLS_INTERIOR;
 }
 
-// d/d(axis) of the six fields at node g.
-template <int N, typename RT>
+// d/d(axis) of the six fields at node g.  ZINIT: d[0] and d[4] start from i0 and i4, the
+// addition taken by the first multiply-add (along z the tendencies add the reference
+// gradients d(rho0)/dz and d(theta0)/dz to them).
+template <int N, typename RT, bool ZINIT = false>
 __device__ __forceinline__ void axis_derivs(const RT* const* F, long long g, long long stride,
-                                            int cls, const Taps<N, RT>& T, RT* d) {
+                                            int cls, const Taps<N, RT>& T, RT* d,
+                                            const double* i0 = nullptr, const double* i4 = nullptr) {
+  auto first = [&](int f, const RT* p) {
+    const RT a = __ldg(p + T.o[0] * stride);
+    if (ZINIT && (f == 0 || f == 4)) return fma(T.c[0], a, (RT)__ldg(f == 0 ? i0 : i4));
+    return T.c[0] * a;
+  };
   if (cls == CLS_IFACE) {
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const RT* p = F[f] + g;
-      RT acc = T.c[0] * __ldg(p + T.o[0] * stride);
+      RT acc = first(f, p);
 #pragma unroll
       for (int t = 1; t < 2 * N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
       d[f] = acc;
@@ -210,7 +218,7 @@ __device__ __forceinline__ void axis_derivs(const RT* const* F, long long g, lon
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const RT* p = F[f] + g;
-      RT acc = T.c[0] * __ldg(p + T.o[0] * stride);
+      RT acc = first(f, p);
 #pragma unroll
       for (int t = 1; t <= N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
       d[f] = acc;
@@ -219,7 +227,7 @@ __device__ __forceinline__ void axis_derivs(const RT* const* F, long long g, lon
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const RT* p = F[f] + g;
-      RT acc = T.c[0] * __ldg(p + T.o[0] * stride);
+      RT acc = first(f, p);
 #pragma unroll
       for (int t = 1; t < N; ++t) acc = fma(T.c[t], __ldg(p + T.o[t] * stride), acc);
       d[f] = acc;
@@ -228,7 +236,8 @@ __device__ __forceinline__ void axis_derivs(const RT* const* F, long long g, lon
 }
 
 // The Set2NC tendencies at node g from the DSS'd derivatives of the six fields (dx, dy, dz:
-// rho', u, v, w, theta', P'), and the epilogue.  RT: arithmetic type; fld: the fields read at
+// rho', u, v, w, theta', P'; dz[0] and dz[4] with d(rho0)/dz and d(theta0)/dz added), and
+// the epilogue.  RT: arithmetic type; fld: the fields read at
 // g (rho', u, v, w; stride nnode); OT: type written in mode 0.  Modes 1 and 2 read and
 // write the FP64 state; R1, R2 are OT arrays.
 template <typename RT, typename OT, typename FT>
@@ -256,11 +265,12 @@ __device__ __forceinline__ void rhs_point_v(long long g, int ix, int iy, int iz,
   // (-x) y and -fma(a, b, c) = fma(-a, b, -c) exactly, rounding being symmetric), so no
   // instruction negates a result
   const RT nu = -u_, nv = -v_, nw = -w_;
-  RT t_r = fma(nu, dx[0], fma(nv, dy[0], fma(nw, dz[0] + (RT)R.drho0[iz], -rho * (dx[1] + dy[2] + dz[3]))));
+  // dz[0] and dz[4] arrive with d(rho0)/dz and d(theta0)/dz added (rhs_node)
+  RT t_r = fma(nu, dx[0], fma(nv, dy[0], fma(nw, dz[0], -rho * (dx[1] + dy[2] + dz[3]))));
   RT t_u = fma(nu, dx[1], fma(nv, dy[1], fma(nw, dz[1], -dx[5] * irho)));
   RT t_v = fma(nu, dx[2], fma(nv, dy[2], fma(nw, dz[2], -dy[5] * irho)));
   RT t_w = fma(nu, dx[3], fma(nv, dy[3], fma(nw, dz[3], fma(-grav, r_, -dz[5]) * irho)));
-  RT t_t = fma(nu, dx[4], fma(nv, dy[4], nw * (dz[4] + (RT)R.dtheta0[iz])));
+  RT t_t = fma(nu, dx[4], fma(nv, dy[4], nw * dz[4]));
   // walls: no normal flow
   if (ix == 0 || ix == G.nxg - 1) t_u = (RT)0;
   if (iy == 0 || iy == G.nyg - 1) t_v = (RT)0;
@@ -354,7 +364,9 @@ __device__ __forceinline__ void rhs_node(long long tid, const double* __restrict
     cls = axis_taps<N, RT>(iy, G.ney, sD + Nq * Nq, sDl + Nq, sDr + Nq, T);
     axis_derivs<N, RT>(Fld, g, sys, cls, T, dy);
     cls = axis_taps<N, RT>(iz, G.nez, sD + 2 * Nq * Nq, sDl + 2 * Nq, sDr + 2 * Nq, T);
-    axis_derivs<N, RT>(Fld, g, 1, cls, T, dz);
+    // the z derivatives of rho' and theta' start from d(rho0)/dz and d(theta0)/dz, the
+    // reference gradients the tendencies add to them (one multiply-add instead of an add)
+    axis_derivs<N, RT, true>(Fld, g, 1, cls, T, dz, R.drho0 + iz, R.dtheta0 + iz);
   }
   rhs_point<RT, OT, RT>(g, ix, iy, iz, q, fld, dx, dy, dz, out0, out, G, R, ep);
 }
