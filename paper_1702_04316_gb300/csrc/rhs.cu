@@ -18,7 +18,10 @@
 //  * at an interface the two elements' weights are equal (w_0 = w_N) and D_00 = -D_NN, so
 //    the shared node cancels: 2N taps instead of 2N+2;
 //  * threads run in a permuted node order in which every warp holds nodes of one class
-//    (interior / interface / wall) per axis, so no warp executes both tap counts.
+//    (interior / interface / wall) per axis, so no warp executes both tap counts;
+//  * no instruction that the method does not need: 1 / rho by a Newton reciprocal (three
+//    multiply-adds), the tendencies' minus signs on the operands, the reference gradients
+//    d(rho0)/dz and d(theta0)/dz as the start of two z derivatives (rhs_device.cuh).
 #include <algorithm>
 #include <type_traits>
 #include <vector>
