@@ -47,32 +47,33 @@ __device__ __forceinline__ void static_for(F&& f) {
   static_for_seq(f, std::make_integer_sequence<int, K>{});
 }
 
-// (D_z f)[lev] for a column held in shared memory with stride T between levels.  lev is
-// uniform across a warp, so the tap table reads are broadcasts and the branch on the tap
-// count (N interior, 2N interface, N+1 wall) does not diverge.
-template <int N, typename XT>
-__device__ __forceinline__ double col_dz(const XT* f, int T, int lev, const RefLev& R) {
+// acc + s (k D_z f)[lev] for a column held in shared memory with stride T between levels,
+// with the scaled taps kc = k dz_c of a StageTab (dzD or dzP) and s = +1 or -1 (NEG): one
+// multiply-add per tap, the scale and the sign riding on the taps, into one accumulator
+// (FP64 issue, not latency, bounds the column kernels: a warp-wide FP64 multiply-add
+// occupies the pipe 16 cycles).  lev is uniform across a warp, so the tap table reads are
+// broadcasts and the branch on the tap count (N interior, 2N interface, N+1 wall) does not
+// diverge.
+template <int N, bool NEG, typename XT>
+__device__ __forceinline__ double col_kdz(const XT* f, int T, int lev, const RefLev& R,
+                                          const double* kc, double acc) {
   constexpr int W = 2 * N + 1;
-  const double* c = R.dz_c + (long long)lev * W;
+  const double* c = kc + (long long)lev * W;
   const int* o = R.dz_o + (long long)lev * W;
   const int n = __ldg(R.dz_n + lev);
   const XT* p = f + lev * T;
-  // one accumulator: FP64 issue, not latency, bounds the column kernels (a warp-wide FP64
-  // multiply-add occupies the pipe 16 cycles), so a second chain would only add a final add
+  auto tap = [&](int t) { return NEG ? -__ldg(c + t) : __ldg(c + t); };
   if (n == N) {
-    double acc = __ldg(c) * to_f64(p[__ldg(o) * T]);
 #pragma unroll
-    for (int t = 1; t < N; ++t) acc = fma(__ldg(c + t), to_f64(p[__ldg(o + t) * T]), acc);
+    for (int t = 0; t < N; ++t) acc = fma(tap(t), to_f64(p[__ldg(o + t) * T]), acc);
     return acc;
   }
   if (n == 2 * N) {
-    double acc = __ldg(c) * to_f64(p[__ldg(o) * T]);
 #pragma unroll
-    for (int t = 1; t < 2 * N; ++t) acc = fma(__ldg(c + t), to_f64(p[__ldg(o + t) * T]), acc);
+    for (int t = 0; t < 2 * N; ++t) acc = fma(tap(t), to_f64(p[__ldg(o + t) * T]), acc);
     return acc;
   }
-  double acc = 0.0;
-  for (int t = 0; t < n; ++t) acc = fma(__ldg(c + t), to_f64(p[__ldg(o + t) * T]), acc);
+  for (int t = 0; t < n; ++t) acc = fma(tap(t), to_f64(p[__ldg(o + t) * T]), acc);
   return acc;
 }
 
@@ -81,8 +82,7 @@ __device__ __forceinline__ double col_dz(const XT* f, int T, int lev, const RefL
 template <int N, typename XT>
 __device__ __forceinline__ double col_wp(const XT* x, int T, int lev, const RefLev& R,
                                          const StageTab& tb) {
-  return fma(__ldg(tb.kp1 + lev), col_dz<N, XT>(x, T, lev, R),
-             __ldg(tb.kp2 + lev) * to_f64(x[lev * T]));
+  return col_kdz<N, false, XT>(x, T, lev, R, tb.dzP, __ldg(tb.kp2 + lev) * to_f64(x[lev * T]));
 }
 
 // Solve L U x = b in place for one column held in shared memory (stride T), VT the value
@@ -292,9 +292,9 @@ __device__ __forceinline__ void col_solve(VT* x, int T, int M, const FT* __restr
 template <int N>
 __device__ __forceinline__ double col_residual(const double* B, const double* tmp, int T, int lev,
                                                const RefLev& R, const StageTab& tb, double xl) {
-  const double Sx = xl - fma(__ldg(tb.kF + lev), tmp[lev * T],
-                             __ldg(tb.kD + lev) * col_dz<N, double>(tmp, T, lev, R));
-  return B[lev * T] - Sx;
+  // b - (x - kF w_p - kD D_z w_p)
+  return col_kdz<N, false, double>(tmp, T, lev, R, tb.dzD,
+                                   fma(__ldg(tb.kF + lev), tmp[lev * T], B[lev * T] - xl));
 }
 
 template <int N, bool MIXED>
@@ -429,9 +429,8 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     }
   };
   level_loop([&](int lev, int c) {     // b = P_e - lam F0z w_a - lam rho0 G0 D_z w_a
-    const double dzw = col_dz<N, double>(S1 + c, T, lev, R);
-    const double b = fma(-__ldg(tb.kF + lev), S1[lev * T + c],
-                         fma(-__ldg(tb.kD + lev), dzw, S0[lev * T + c]));
+    const double b = col_kdz<N, true, double>(
+        S1 + c, T, lev, R, tb.dzD, fma(-__ldg(tb.kF + lev), S1[lev * T + c], S0[lev * T + c]));
     S0[lev * T + c] = b;
     if (MIXED) Tf[lev * T + c] = f32_of(b);
   });
@@ -476,9 +475,8 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     if (MIXED) {
       S1[lev * T + c] = col_wp<N, double>(S0 + c, T, lev, R, tb);
     } else {   // w_a - (kp1 D_z P + kp2 P), the subtraction folded into the multiply-adds
-      const double dzp = col_dz<N, double>(S0 + c, T, lev, R);
-      S1[lev * T + c] = fma(-__ldg(tb.kp1 + lev), dzp,
-                            fma(-__ldg(tb.kp2 + lev), S0[lev * T + c], S1[lev * T + c]));
+      S1[lev * T + c] = col_kdz<N, true, double>(
+          S0 + c, T, lev, R, tb.dzP, fma(-__ldg(tb.kp2 + lev), S0[lev * T + c], S1[lev * T + c]));
     }
   });
   __syncthreads();

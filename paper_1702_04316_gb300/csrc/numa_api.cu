@@ -382,6 +382,23 @@ void build_levels(numa_ctx* c, const double* xi, const double* w, const double* 
                   c->drho0.data(), c->dtheta0.data(), c->F0z.data());
 }
 
+// The non-zero entries of each row of the column derivative band: coef[m W + t] at level
+// m + off[m W + t] for t < off[M W + m] (off holds M W offsets, then M counts).
+void dz_taps(const numa_ctx* c, double* coef, int* off) {
+  const int M = c->G.M, N = c->G.N, W = 2 * N + 1;
+  for (int m = 0; m < M; ++m) {
+    int n = 0;
+    for (int b = 0; b < W; ++b) {
+      const double v = c->dzband[(size_t)m * W + b];
+      if (v == 0.0) continue;
+      coef[(size_t)m * W + n] = v;
+      off[(size_t)m * W + n] = b - N;
+      ++n;
+    }
+    off[(size_t)M * W + m] = n;
+  }
+}
+
 int upload_levels(numa_ctx* c) {
   const int M = c->G.M, N = c->G.N, W = 2 * N + 1;
   const int nt = 10;
@@ -400,17 +417,7 @@ int upload_levels(numa_ctx* c) {
   // tap lists: the non-zero entries of each band row
   double* dzc = &h[(size_t)nt * M + (size_t)M * W];
   std::vector<int> hi((size_t)M * W + M, 0);
-  for (int m = 0; m < M; ++m) {
-    int n = 0;
-    for (int b = 0; b < W; ++b) {
-      const double v = c->dzband[(size_t)m * W + b];
-      if (v == 0.0) continue;
-      dzc[(size_t)m * W + n] = v;
-      hi[(size_t)m * W + n] = b - N;
-      ++n;
-    }
-    hi[(size_t)M * W + m] = n;
-  }
+  dz_taps(c, dzc, hi.data());
   NUMA_CK(c, cudaMalloc(&c->d_lev, h.size() * sizeof(double)));
   NUMA_CK(c, cudaMemcpy(c->d_lev, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
   NUMA_CK(c, cudaMalloc(&c->d_levi, hi.size() * sizeof(int)));
@@ -424,9 +431,9 @@ int upload_levels(numa_ctx* c) {
 
 // Stage tables for one lam (the coefficient tables listed with StageTab).
 int upload_stage_tables(numa_ctx* c, double lam) {
-  const int M = c->G.M;
+  const int M = c->G.M, W = 2 * c->G.N + 1;
   const double g = NUMA_GRAV;
-  std::vector<double> h((size_t)11 * M);
+  std::vector<double> h((size_t)11 * M + 2 * (size_t)M * W, 0.0);
   for (int m = 0; m < M; ++m) {
     const bool wall = (m == 0 || m == M - 1);
     const double A = 1.0 + lam * lam * g * c->dtheta0[m] / c->theta0[m];
@@ -442,13 +449,24 @@ int upload_stage_tables(numa_ctx* c, double lam) {
     h[9 * M + m] = c->G0[m];
     h[10 * M + m] = c->H0[m];
   }
+  std::vector<double> coef((size_t)M * W, 0.0);
+  std::vector<int> off((size_t)M * W + M, 0);
+  dz_taps(c, coef.data(), off.data());
+  double* dzD = &h[(size_t)11 * M];
+  double* dzP = dzD + (size_t)M * W;
+  for (int m = 0; m < M; ++m)
+    for (int t = 0; t < W; ++t) {
+      dzD[(size_t)m * W + t] = h[3 * M + m] * coef[(size_t)m * W + t];
+      dzP[(size_t)m * W + t] = h[4 * M + m] * coef[(size_t)m * W + t];
+    }
   if (!c->d_stage_tab) NUMA_CK(c, cudaMalloc(&c->d_stage_tab, h.size() * sizeof(double)));
   NUMA_CK(c, cudaMemcpyAsync(c->d_stage_tab, h.data(), h.size() * sizeof(double),
                              cudaMemcpyHostToDevice, c->stream));
   NUMA_CK(c, cudaStreamSynchronize(c->stream));
   const double* d = c->d_stage_tab;
   c->T = StageTab{d, d + M, d + 2 * M, d + 3 * M, d + 4 * M, d + 5 * M,
-                  d + 6 * M, d + 7 * M, d + 8 * M, d + 9 * M, d + 10 * M, c->d_status};
+                  d + 6 * M, d + 7 * M, d + 8 * M, d + 9 * M, d + 10 * M, c->d_status,
+                  d + 11 * M, d + 11 * M + (size_t)M * W};
   return NUMA_OK;
 }
 

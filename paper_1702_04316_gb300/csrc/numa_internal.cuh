@@ -121,11 +121,14 @@ struct StageCoef {
 //   kF = lam F0z;  kD = lam rho0 G0
 //   kp1 = lam / (A rho0), kp2 = lam g / (A G0 rho0)  (0 at the two walls: w_p = 0 there)
 //   kth = lam d(theta0)/dz;  invG0 = 1/G0;  H0G0 = H0/G0;  G0, H0
-// with A = 1 + lam^2 (g/theta0) d(theta0)/dz.
+// with A = 1 + lam^2 (g/theta0) d(theta0)/dz; and, in the layout of RefLev::dz_c (M x (2N+1)),
+// the column derivative's taps scaled per level: dzD = kD dz_c, dzP = kp1 dz_c, so that
+// kD D_z f and kp1 D_z f cost one multiply-add per tap.
 struct StageTab {
   const double *wa_th, *wa_s, *kF, *kD, *kp1, *kp2, *kth, *invG0, *H0G0, *G0, *H0;
   unsigned* status;   // the fused stage latches NUMA_ST_NONFINITE here when P' of its output
                       // is not finite (NULL: no check)
+  const double *dzD, *dzP;
 };
 
 // True when x is an infinity or a NaN, from the exponent bits of its high word: integer
