@@ -148,7 +148,7 @@ size_t stage_smem(int M, int T, bool mixed, int iters) {
 // columns, 256 threads) to 0.892 ms and the rhs32 stage from 0.808 to 0.788 ms; the mixed
 // stage went from 1.43 to 1.27 ms with 192 threads (1.37 with 128).  Fewer, larger CTAs
 // (64 or 128 columns) and fewer threads per column (2 or 3) were slower.
-// NUMA_STAGE_THREADS (a multiple of 32, at least T) overrides, for tuning.
+// NUMA_STAGE_THREADS (a multiple of 32, at least T; clamped to `limit`) overrides, for tuning.
 int stage_threads(int T, long long ncol, bool mixed, int limit = 1024) {
   static int env = -1;
   static int nsm = 0;
@@ -163,7 +163,7 @@ int stage_threads(int T, long long ncol, bool mixed, int limit = 1024) {
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       nsm = 152;
   }
-  if (env >= T) return env;
+  if (env >= T) return std::max(T, std::min(limit, env));
   const long long nblocks = (ncol + T - 1) / T;
   const int per_col = nblocks < 2LL * nsm ? 8 : (mixed ? 6 : 4);
   return std::max(T, std::min(limit, per_col * T));
