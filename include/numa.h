@@ -531,7 +531,7 @@ int numa_step_buffers(numa_ctx* ctx, double** q2, double** q3, double** pp, int*
  * tables reach the device inside kernel launch parameters, and the device side keeps the
  * equation-of-state pre-pass (nnode doubles) and the per-level tables in one file-scope
  * scratch array of NUMA_STATIC_SCRATCH_BYTES (64 MiB: meshes up to
- * 8,388,608 - 10 M - (2N+1) M nodes and M <= 1024 levels; larger problems return
+ * 8,388,608 - 15 M - (2N+1) M nodes and M <= 1024 levels; larger problems return
  * NUMA_ERR_SCRATCH before any device work).
  * q, rhs: device SoA arrays of 5*nnode doubles, as for numa_rhs_explicit.  The first call
  * on each device looks up the scratch array's device address (cudaGetSymbolAddress) with

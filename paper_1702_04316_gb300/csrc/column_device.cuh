@@ -528,7 +528,7 @@ __device__ __forceinline__ void stage_body(long long col0, int T, double* sm,
     out[oth] = o_t;
     // P'(q(i)) for the next right-hand side, by the arithmetic of its pre-pass (eos_node)
     if (Pp_out) {
-      const double pv = R.P0[lev] * eos_rel(o_r, o_t, R.inv_rho0[lev], R.inv_theta0[lev], NUMA_GAMMA, *eos);
+      const double pv = eos_pp(o_r, o_t, lev, R, *eos);
       Pp_out[g] = pv;
       bad |= not_finite(pv);
     }

@@ -402,7 +402,7 @@ void dz_taps(const numa_ctx* c, double* coef, int* off) {
 int upload_levels(numa_ctx* c) {
   const int M = c->G.M, N = c->G.N, W = 2 * N + 1;
   const int nt = 10;
-  std::vector<double> h((size_t)nt * M + 2 * (size_t)M * W, 0.0);
+  std::vector<double> h((size_t)nt * M + 2 * (size_t)M * W + 5 * (size_t)M, 0.0);
   auto put = [&](int slot, const std::vector<double>& v) {
     std::memcpy(&h[(size_t)slot * M], v.data(), sizeof(double) * M);
   };
@@ -418,6 +418,7 @@ int upload_levels(numa_ctx* c) {
   double* dzc = &h[(size_t)nt * M + (size_t)M * W];
   std::vector<int> hi((size_t)M * W + M, 0);
   dz_taps(c, dzc, hi.data());
+  eos_level_coefs(c->P0.data(), M, dzc + (size_t)M * W);
   NUMA_CK(c, cudaMalloc(&c->d_lev, h.size() * sizeof(double)));
   NUMA_CK(c, cudaMemcpy(c->d_lev, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
   NUMA_CK(c, cudaMalloc(&c->d_levi, hi.size() * sizeof(int)));
@@ -425,7 +426,8 @@ int upload_levels(numa_ctx* c) {
   const double* d = c->d_lev;
   c->R = RefLev{d, d + M, d + 2 * M, d + 3 * M, d + 4 * M, d + 5 * M, d + 6 * M,
                 d + 7 * M, d + 8 * M, d + 9 * M, d + (size_t)nt * M,
-                d + (size_t)nt * M + (size_t)M * W, c->d_levi, c->d_levi + (size_t)M * W};
+                d + (size_t)nt * M + (size_t)M * W, c->d_levi, c->d_levi + (size_t)M * W,
+                d + (size_t)nt * M + 2 * (size_t)M * W};
   return NUMA_OK;
 }
 
@@ -1458,7 +1460,7 @@ static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
 std::mutex g_static_mutex;
 double* g_static_addr[256] = {nullptr};            // device address per device ordinal
-double g_static_host[kStaticMaxLevels * (11 + 2 * NUMA_MAXN + 1)];
+double g_static_host[kStaticMaxLevels * (16 + 2 * NUMA_MAXN + 1)];
 
 // One piece of the per-level tables, carried by value in the launch parameters (16 KB, within
 // the 32 KB parameter space of sm_70 and later).
@@ -1488,7 +1490,7 @@ extern "C" int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const
   G.ncol = (long long)G.nxg * G.nyg;
   G.nnode = G.ncol * G.M;
   const int M = G.M, W = 2 * N + 1;
-  const long long need = G.nnode + 10LL * M + (long long)M * W;
+  const long long need = G.nnode + 15LL * M + (long long)M * W;
   if (M > kStaticMaxLevels || need > (long long)kStaticScratchDoubles) return NUMA_ERR_SCRATCH;
 
   std::lock_guard<std::mutex> lock(g_static_mutex);
@@ -1512,13 +1514,14 @@ extern "C" int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const
   set_axis(C.z, N, w, D, mesh->Lz / mesh->nez);
 
   // the per-level tables in the order of RefLev: rho0, 1/rho0, theta0, 1/theta0, P0, G0, H0,
-  // d(rho0)/dz, d(theta0)/dz, F0z (M each), the column derivative band [M][W]; z last (host
-  // only)
+  // d(rho0)/dz, d(theta0)/dz, F0z (M each), the column derivative band [M][W], the
+  // equation of state's coefficients P0c [M][5]; z last (host only)
   double* h = g_static_host;
   double *rho0 = h, *irho0 = h + M, *th0 = h + 2 * M, *ith0 = h + 3 * M, *P0 = h + 4 * M;
   double *G0 = h + 5 * M, *H0 = h + 6 * M, *drho = h + 7 * M, *dth = h + 8 * M, *F0z = h + 9 * M;
   double* band = h + 10 * M;
-  double* z = band + (size_t)M * W;
+  double* P0c = band + (size_t)M * W;
+  double* z = P0c + 5 * (size_t)M;
   ref_tables_host(N, mesh->nez, mesh->Lz / mesh->nez, xi, w, D,
                   mesh->theta_s > 0 ? mesh->theta_s : 300.0, mesh->n_bv, z, th0, rho0, P0, G0,
                   H0, band, drho, dth, F0z);
@@ -1526,11 +1529,12 @@ extern "C" int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const
     irho0[m] = 1.0 / rho0[m];
     ith0[m] = 1.0 / th0[m];
   }
+  eos_level_coefs(P0, M, P0c);
 
   cudaStream_t s = (cudaStream_t)stream;
   double* dPp = scratch;                 // nnode doubles, written by the pre-pass
   double* dtab = scratch + G.nnode;      // the tables above
-  const long long ntab = 10LL * M + (long long)M * W;
+  const long long ntab = 15LL * M + (long long)M * W;
   for (long long o = 0; o < ntab; o += kTabChunk) {
     TabChunk ch;
     ch.dst = dtab + o;
@@ -1540,7 +1544,8 @@ extern "C" int numa_rhs_explicit_static(const numa_mesh_desc* mesh, int N, const
     if (cudaGetLastError() != cudaSuccess) return NUMA_ERR_CUDA;
   }
   const RefLev R{dtab, dtab + M, dtab + 2 * M, dtab + 3 * M, dtab + 4 * M, dtab + 5 * M,
-                 dtab + 6 * M, dtab + 7 * M, dtab + 8 * M, dtab + 9 * M, dtab + 10 * M};
+                 dtab + 6 * M, dtab + 7 * M, dtab + 8 * M, dtab + 9 * M, dtab + 10 * M,
+                 nullptr, nullptr, nullptr, dtab + 10 * M + (size_t)M * W};
   RhsEpilogue ep{};
   ep.mode = 0;
   if (launch_pressure(q, dPp, G, R, s) != cudaSuccess) return NUMA_ERR_CUDA;

@@ -69,6 +69,9 @@ struct RefLev {
   const double* dz_c;
   const int* dz_o;
   const int* dz_n;
+  // P0 C(gamma, k), k = 1..5, per level ([M][5]): the equation of state's five-term series
+  // with P0 folded into its coefficients
+  const double* P0c;
 };
 
 // Stored column factors, by matrix column j, transposed so that consecutive columns of the
@@ -139,6 +142,8 @@ __device__ __forceinline__ unsigned not_finite(double x) {
 
 // ---- launchers (return the launch error) ----------------------------------------------
 // rhs.cu
+// RefLev::P0c on the host: P0c[m * 5 + k] = P0[m] C(gamma, k + 1), k < 5.
+void eos_level_coefs(const double* P0, int M, double* P0c);
 cudaError_t launch_pressure(const double* q, double* Pp, const Geom& G, const RefLev& R,
                             cudaStream_t s, unsigned* status = nullptr);
 // P' for the nodes g0 <= g < g1 only.  Both pre-passes latch NUMA_ST_NONFINITE into status

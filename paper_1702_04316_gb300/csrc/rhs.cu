@@ -172,6 +172,12 @@ cudaError_t launch_pressure_range(const double* q, double* Pp, const Geom& G, co
   return cudaGetLastError();
 }
 
+void eos_level_coefs(const double* P0, int M, double* P0c) {
+  const EosSeries S = eos_series();
+  for (int m = 0; m < M; ++m)
+    for (int k = 0; k < 5; ++k) P0c[(size_t)m * 5 + k] = P0[m] * S.c[k];
+}
+
 cudaError_t launch_prep32(const double* q, float* F32, const Geom& G, const RefLev& R,
                           cudaStream_t s) {
   const int bs = 256;

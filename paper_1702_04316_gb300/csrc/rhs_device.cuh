@@ -103,36 +103,40 @@ struct EosSeries {
   double c[9];   // C(gamma, k), k = 1..9
 };
 
-// (1 + x)^gamma - 1 for x = a + b + a b at one node.
-__device__ __forceinline__ double eos_rel(double rp, double tp, double inv_rho0, double inv_theta0,
-                                          double gamma, const EosSeries& S) {
-  const double a = rp * inv_rho0;
-  const double b = tp * inv_theta0;
+// P' at level lev from rho' and theta' (x = a + b + a b as above).  Where |x| <= 2^-10 the
+// five-term series runs with P0 folded into its coefficients (R.P0c: one multiplication
+// fewer); otherwise P0 times the nine-term series or expm1(gamma log1p(x)).  |x| is compared
+// on the bit pattern without its sign, which orders like |x| for every x that is not a NaN:
+// integer instructions instead of FP64 comparisons.
+__device__ __forceinline__ double eos_pp(double rp, double tp, int lev, const RefLev& R,
+                                         const EosSeries& S) {
+  const double a = rp * R.inv_rho0[lev];
+  const double b = tp * R.inv_theta0[lev];
   const double x = fma(a, b, a + b);
-  // |x| against 2^-10 and 2^-6 on the bit pattern without its sign, which orders like |x|
-  // for every x that is not a NaN: integer instructions instead of an FP64 comparison
   const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
   if (ax <= 0x3F50000000000000ull) {            // 2^-10
-    double p = S.c[4];
+    const double* k = R.P0c + (long long)lev * 5;
+    double p = __ldg(k + 4);
 #pragma unroll
-    for (int k = 3; k >= 0; --k) p = fma(p, x, S.c[k]);
+    for (int j = 3; j >= 0; --j) p = fma(p, x, __ldg(k + j));
     return p * x;
   }
+  double r;
   if (ax <= 0x3F90000000000000ull) {            // 2^-6
     double p = S.c[8];
 #pragma unroll
     for (int k = 7; k >= 0; --k) p = fma(p, x, S.c[k]);
-    return p * x;
+    r = p * x;
+  } else {
+    r = expm1(NUMA_GAMMA * log1p(x));
   }
-  return expm1(gamma * log1p(x));
+  return R.P0[lev] * r;
 }
 
 // P' of node g of state q (FP64).
 __device__ __forceinline__ double eos_node(const double* __restrict__ q, long long g, const Geom& G,
                                            const RefLev& R, const EosSeries& S) {
-  const int iz = (int)(g % G.M);
-  return R.P0[iz] * eos_rel(q[g], q[4 * G.nnode + g], R.inv_rho0[iz], R.inv_theta0[iz],
-                            NUMA_GAMMA, S);
+  return eos_pp(q[g], q[4 * G.nnode + g], (int)(g % G.M), R, S);
 }
 
 // The series coefficients C(gamma, k), k = 1..9.
