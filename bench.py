@@ -18,7 +18,9 @@ comparator at C = 1, and their sim-s/wall-s ratios; the per-kernel algorithmic b
 HBM fractions (`kernels`), the FP64 roofline of the dominant kernel (`roofline`), the
 stand-alone column solve against the HBM roofline (`column_solve`), the end-to-end figure
 through host buffers (`e2e`), the accuracy of the C = 15 and C = 150 runs against RK35 at
-C = 1 (`accuracy_vs_explicit_c1`), and one entry per form and variant.
+C = 1 (`accuracy_vs_explicit_c1`), the speed-up at a stated accuracy for 1D- and 3D-IMEX
+(`matched_accuracy`), 3D-IMEX on the headline box and at large aspect ratio (`imex3d`,
+`imex3d_large_aspect`), and one entry per form and variant.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
